@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the CGD-EnKF analysis step on GB300.
+
+One step = one full analysis (observation gather + anomalies + perturbed innovations, the
+persistent CG solve of S Z = D, and the ensemble update X_a = X_f + A W) through the C ABI
+on the synthetic 512x512 Gaussian-random-field workload: n = 262,144 state variables,
+N = 64 members, m = 65,536 randomly placed observations, r ~ U[0.5, 1.5], CG tolerance
+1e-8 (true FP64 relative residual).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). `value` is analyses/s summed over ranks (each rank runs its
+own independent analyses: weak scaling, no collective on the data path). The headline path
+is the FP32 CG with FP64 residual refresh (meets 1e-6 relative Frobenius error); the plain
+FP64 GPU CG is timed beside it. `--impl reference` times the CPU oracle instead (host cores).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "grf512_N64_m65536"
+METRIC = "analysis steps/s and HBM-roofline fraction vs plain FP64 GPU CG at stated error"
+UNIT = "analyses/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes (read + write) of one solve_kernel launch on this workload, from the ncu capture
+# summarised in profiles/solve_kernel_grf512_N64_m65536.md, and the hash of the kernel source
+# that capture measured; reported as null once the source has changed.
+NCU_TRAFFIC = {"fp32": {"bytes": 4.126482e9, "src_sha": None}}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_fp.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_19224_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    except OSError:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 0) for i in threadpool_info()), default=0)
+        if n:
+            return n
+    except Exception:
+        pass
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(problem, E, budget_s=20.0):
+    """The CPU oracle as it stands on the host cores: exact analysis through Algorithm 2
+    (N x N Cholesky), repeated on the benchmark's full-size problem within the budget."""
+    import oracle
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.enkf_exact(problem.Xf.astype("float64"), problem.rowptr, problem.col, problem.w,
+                          problem.r, problem.y, E)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or reps >= 8:
+            break
+    return {"value": reps / el, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"{reps} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, FP64 numpy) "
+                      f"in {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    p = synth.workload(WORKLOAD, args.seed, dtype=np.float32)
+    E = oracle.obs_perturbations(args.seed, 0, p.r, p.N)
+    for _ in range(args.warmup):
+        oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        E = oracle.obs_perturbations(args.seed, k, p.r, p.N)
+        oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": p.n, "m": p.m, "N": p.N, "tol": 1e-8,
+                       "route": "CPU oracle, exact FP64 analysis (Algorithm 2, N x N Cholesky)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                             "sample": f"{args.steps} full-size exact analyses, perturbations "
+                                       f"from the oracle's Philox stream"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2606_19224_gb300 as enkf
+    import synth
+
+    seed = args.seed + 1000 * rank
+    p = synth.workload(WORKLOAD, seed, dtype=np.float32)
+    n, m, N = p.n, p.m, p.N
+    an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8)
+    an.set_phase_timing(True)
+    Xf = torch.from_numpy(p.Xf).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    out = torch.empty_like(Xf)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        an.analyze(Xf, y, seed, k, out=out)
+    st = an.stats()
+    if st["status"] != "ok":
+        raise SystemExit(f"warm-up analysis failed: {st}")
+
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    solve_ms, iters, refines = [], [], []
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # L2 flush, outside the timed window
+        ev[k][0].record(stream)
+        an.analyze(Xf, y, seed, args.warmup + k, out=out)
+        ev[k][1].record(stream)
+        ph = an.phase_times()                      # syncs on the last kernel's event
+        solve_ms.append(ph[1])
+        s = an.stats()
+        iters.append(s["iters_max"])
+        refines.append(s["refinements"])
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1e3)
+    last_status = an.stats()
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside)
+    Xh = torch.from_numpy(p.Xf).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    Xo = torch.empty_like(Xh).pin_memory()
+    for k in range(2):
+        an.analyze_host(Xh, yh, seed, k, out=Xo)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 4)
+    for k in range(e2e_steps):
+        an.analyze_host(Xh, yh, seed, k, out=Xo)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
+           "d2h_bytes_per_step": int(Xo.numel() * 4)}
+
+    # plain FP64 GPU CG on the same problem (the comparison point)
+    p64 = synth.workload(WORKLOAD, seed, dtype=np.float64)
+    an64 = enkf.Analysis(n, m, N, p64.rowptr, p64.col, p64.w, p64.r, precision="fp64", tol=1e-8)
+    X64 = torch.from_numpy(p64.Xf).to(dev)
+    o64 = torch.empty_like(X64)
+    an64.analyze(X64, y, seed, 0, out=o64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.fp64_steps):
+        an64.analyze(X64, y, seed, k, out=o64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
+    s64 = an64.stats()
+
+    if rank != 0:
+        return
+    # accuracy of one timed configuration against the FP64 oracle (exact analysis)
+    import oracle
+    E = oracle.obs_perturbations(seed, 0, p.r, N)
+    an.analyze(Xf, y, seed, 0, out=out)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    err = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
+    an64.analyze(X64, y, seed, 0, out=o64)
+    err64 = oracle.rel_frobenius(o64.cpu().numpy(), ref)
+
+    # roofline of the dominant kernel (the persistent CG solve)
+    mN = m * N
+    it_avg = float(np.mean(iters))
+    ref_avg = float(np.mean(refines))
+    b_iter = 2 * mN * 4 + 8 * mN * 4 + 2 * m * 8          # FP32 HA twice, r/p/x vectors, r twice
+    b_ref = 56 * mN                                       # FP64 refresh: HA64 x2, Z, D, X, B
+    alg_bytes = it_avg * b_iter + ref_avg * b_ref
+    solve_avg_ms = float(np.mean(solve_ms))
+    peak, peak_src = _peaks()
+    achieved = alg_bytes / (solve_avg_ms / 1e3) / 1e9
+    tr = NCU_TRAFFIC.get("fp32", {})
+    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash() else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64>",
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
+                "launch_ms": solve_avg_ms, "cg_iterations": it_avg, "fp64_refreshes": ref_avg}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
+                       "precision": "fp32 CG + fp64 residual refresh", "l2": "flushed between steps",
+                       "status": last_status["status"]},
+            "error": {"rel_frobenius_vs_fp64_oracle": err, "fp64_cg_rel_frobenius": err64,
+                      "true_relres_max": last_status["true_relres_max"]},
+            "fp64_cg": {"ms_per_step": fp64_ms, "value": 1e3 / fp64_ms, "unit": UNIT,
+                        "iters": s64["iters_max"], "speedup_of_value": value / (ws * 1e3 / fp64_ms)},
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, E)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * enkf.h -- C ABI of the GB300 CGD-EnKF analysis-step library (libenkf.so).
+ *
+ * The library computes one EnKF analysis step (Lee, Liu, Valyou, Zikatanov, "A Conjugate
+ * Gradient Formulation of the EnKF Algorithm"):
+ *
+ *   Z_obs = H X_f,  zbar = Z_obs 1/N,  HA = Z_obs - zbar 1^T            (Sec. 2.3, Eq. Zhat_def)
+ *   D     = y 1^T + E - Z_obs                                          (Sec. 2.3; E = 0 is the
+ *                                                                       paper's unperturbed form)
+ *   S Z   = D,  S = HA HA^T/(N-1) + R  by conjugate gradients, never
+ *           forming S: S V = HA (HA^T V)/(N-1) + R V                   (Sec. 3.1-3.3,
+ *                                                                       Eq. matvec_decomp)
+ *   X_a   = X_f + A (HA^T Z)/(N-1),  A = X_f - xbar 1^T                (Fig. 2, Algorithm 1)
+ *
+ * and, as the variant ENKF_CGD_REDUCED, Algorithm 2 with the N x N inverse applied by CG
+ * (Sec. 5.2): X_a = X_f (I + P^T P)^{-1} [I + P^T L^{-1}((y - zbar) 1^T + E)],
+ * P = L^{-1} HA, L L^T = (N-1) R.
+ *
+ * Letters: n = state dimension, m = observation count, N = ensemble size (the paper writes
+ * m, p, N).
+ *
+ * Layouts. Every ensemble-shaped array is row-major with the member index fastest:
+ * X_f, X_a are [n][N]; E is [m][N]. H is a CSR index-and-weight operator: observation i is
+ * sum_{k = rowptr[i]}^{rowptr[i+1]-1} w[k] * x[col[k]]. R is diagonal, given as r[m] > 0.
+ * y, r and E are FP64 in every precision mode; X_f / X_a are FP64 in ENKF_FP64 mode and
+ * FP32 in every other mode.
+ *
+ * Ownership and execution. The caller owns X_f, y, E and X_a (device pointers unless the
+ * function says "host"). The handle owns H, R and all workspace, allocated once in
+ * enkf_create; enkf_analyze* never allocate. Calls are asynchronous and ordered on the
+ * stream given at creation; results of an analysis (status, iteration counts, residuals)
+ * are read with enkf_get_stats, which synchronises that stream.
+ *
+ * Errors. No exception crosses this boundary. Argument errors are returned synchronously
+ * and nothing is enqueued. Numerical outcomes (not converged, non-finite values, CG
+ * breakdown, a device wait that timed out) are recorded on the device and returned by
+ * enkf_get_stats; X_a is written in every case. enkf_last_error gives a message for the
+ * last failing call on a handle.
+ */
+#ifndef ENKF_H
+#define ENKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct enkf_handle_s* enkf_handle;
+
+typedef enum {
+  ENKF_OK = 0,
+  ENKF_ERR_INVALID_ARG = 1,   /* bad argument; nothing was enqueued                     */
+  ENKF_ERR_CUDA = 2,          /* a CUDA runtime call failed                             */
+  ENKF_ERR_OOM = 3,           /* device memory allocation failed in enkf_create         */
+  ENKF_ERR_NOT_CONVERGED = 4, /* some column missed the tolerance within max_iter       */
+  ENKF_ERR_NONFINITE = 5,     /* a NaN/Inf appeared in the inputs or the recurrences    */
+  ENKF_ERR_BREAKDOWN = 6,     /* p^T S p <= 0 in a CG step (S not positive definite)    */
+  ENKF_ERR_TIMEOUT = 7,       /* a bounded device-side grid barrier gave up             */
+  ENKF_ERR_UNSUPPORTED = 8    /* configuration outside what this build implements       */
+} enkf_status;
+
+typedef enum {
+  ENKF_FP64 = 0,        /* FP64 storage and arithmetic throughout (the plain FP64 CG)    */
+  ENKF_FP32 = 1,        /* FP32 CG inner solves + FP64 residual refresh (iterative
+                           refinement) with FP64 scalar recurrences                      */
+  ENKF_BF16_REFINE = 2, /* BF16 HA contractions on tensor cores, FP32 accumulation,
+                           FP32 vectors, FP32 residual refresh every refresh_every steps */
+  ENKF_FP16_REFINE = 3  /* as ENKF_BF16_REFINE with FP16 HA                              */
+} enkf_precision;
+
+typedef enum {
+  ENKF_CGD = 0,         /* CGD-EnKF: CG on S Z = D (m x m operator, N columns)           */
+  ENKF_CGD_REDUCED = 1  /* CGD-EnKF-Reduced: CG on I + P^T P (N x N, N columns)          */
+} enkf_variant;
+
+typedef struct enkf_config {
+  int64_t n;              /* state dimension, >= 1                                       */
+  int64_t m;              /* observation count, >= 1                                     */
+  int32_t N;              /* ensemble size, 2 <= N <= 128                                */
+  int32_t precision;      /* enkf_precision                                              */
+  int32_t variant;        /* enkf_variant                                                */
+  int32_t max_iter;       /* cap on CG iterations per column (inner iterations summed)   */
+  double tol;             /* stop column j when ||r_j||_2 <= tol * ||d_j||_2             */
+  int32_t fixed_iters;    /* > 0: run exactly this many CG steps (the paper's Tables 4-5
+                             mode); tol is then ignored                                  */
+  int32_t max_refine;     /* ENKF_FP32: maximum FP64 residual refreshes (default 4)      */
+  double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
+  int32_t refresh_every;  /* BF16/FP16 modes: FP32 residual refresh period (default 8)   */
+  int32_t perturb_obs;    /* 1: E ~ N(0, R) drawn from (seed, counter); 0: E = 0         */
+  int32_t warm_start;     /* 0: start CG from Z = 0; 1: learned warm start (model set)   */
+  int32_t true_residual;  /* 1: FP64 true residual check (and W = HA^T Z/(N-1) from the
+                             final Z) after an FP64 solve; always on in ENKF_FP32        */
+  int32_t grid_blocks;    /* 0: automatic persistent-grid size; > 0: use this many CTAs  */
+  int32_t reserved[7];    /* must be zero                                                */
+} enkf_config;
+
+typedef struct enkf_stats {
+  int32_t status;            /* enkf_status of the last analysis                         */
+  int32_t iters_max;         /* max over columns of CG iterations                        */
+  int32_t iters_min;         /* min over columns of CG iterations                        */
+  int32_t refinements;       /* FP64 residual refreshes performed                        */
+  double relres_max;         /* max over columns of the recursive ||r_j|| / ||d_j||      */
+  double true_relres_max;    /* max over columns of the FP64 true residual
+                                ||d_j - S z_j|| / ||d_j||; -1 when not computed          */
+  int32_t columns_converged; /* columns that met tol                                     */
+  int32_t grid_blocks;       /* persistent-grid size used                                */
+  double reserved[4];
+} enkf_stats;
+
+/* Fill *cfg with defaults for an (n, m, N) problem: ENKF_FP64, ENKF_CGD, tol 1e-8,
+   max_iter 1000, max_refine 4, inner_tol 1e-5, refresh_every 8, perturb_obs 1,
+   true_residual 1. Returns ENKF_ERR_INVALID_ARG when cfg is NULL. */
+enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t N);
+
+/* Create a handle for one problem shape. h_rowptr[m+1], h_col[nnz], h_w[nnz] (the CSR
+   observation operator, nnz = h_rowptr[m]) and r_diag[m] (> 0, finite) are HOST arrays
+   and are copied to the device. cuda_stream is a cudaStream_t (NULL: the legacy default
+   stream); every later call on the handle is ordered on it. Allocates all workspace
+   (about 44 m N bytes in ENKF_FP32 mode at N <= 128, 40 m N in ENKF_FP64 mode, plus
+   O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad shape, column index outside [0, n),
+   decreasing rowptr, r <= 0), ENKF_ERR_UNSUPPORTED (N > 128, unknown precision or
+   variant), ENKF_ERR_OOM, ENKF_ERR_CUDA. *out is NULL on error. */
+enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                        const double* h_w, const double* r_diag, void* cuda_stream,
+                        enkf_handle* out);
+
+/* One analysis on the handle's stream. d_Xf: device [n][N] (FP64 in ENKF_FP64 mode, FP32
+   otherwise); d_y: device [m] FP64; (seed, counter) select the Philox4x32-10 stream of the
+   perturbations E when cfg.perturb_obs = 1 (element (i, j) uses counter
+   (i, j >> 1, counter_lo, counter_hi) and key (seed_lo, seed_hi); two 53-bit uniforms and
+   Box-Muller give the normal, E_ij = sqrt(r_i) * normal). d_Xa: device [n][N], same dtype
+   as d_Xf; d_Xa == d_Xf (in-place) is allowed, partial overlap is not. Never allocates. */
+enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uint64_t seed,
+                         uint64_t counter, void* d_Xa);
+
+/* As enkf_analyze with the perturbations given explicitly: d_E device [m][N] FP64
+   (NULL means E = 0, the paper's unperturbed EnKF). */
+enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d_y,
+                                const double* d_E, void* d_Xa);
+
+/* End-to-end form with HOST buffers: copies h_Xf [n][N] and h_y [m] to device staging
+   buffers owned by the handle, runs enkf_analyze, copies X_a back into h_Xa [n][N] and
+   synchronises the stream before returning. Pinned host memory gives asynchronous
+   copies; pageable memory works but is slower. */
+enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y,
+                              uint64_t seed, uint64_t counter, void* h_Xa);
+
+/* Synchronise the handle's stream and return the last analysis's outcome in *out. The
+   return value is out->status. */
+enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out);
+
+/* Synchronise and copy per-column results to HOST arrays of length N (any may be NULL):
+   CG iterations, recursive relative residual, FP64 true relative residual (-1 if not
+   computed). */
+enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
+                                  double* true_relres);
+
+/* Copy the last analysis's intermediate results to DEVICE buffers (any may be NULL):
+   d_HA [m][N] and d_D [m][N] (FP64), d_Z [m][N] (FP64 solution of S Z = D; for
+   ENKF_CGD_REDUCED the N x N solution V), d_W [N][N] (FP64, W = HA^T Z/(N-1)). Enqueued
+   on the handle's stream. */
+enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z,
+                                    double* d_W);
+
+/* Draw the observation perturbations exactly as enkf_analyze does: d_r device [m] FP64,
+   d_E device [m][N] FP64 output, on cuda_stream. */
+enkf_status enkf_draw_perturbations(uint64_t seed, uint64_t counter, const double* d_r,
+                                    int64_t m, int32_t N, double* d_E, void* cuda_stream);
+
+/* Per-kernel timing of later analyses (enable != 0) with CUDA events recorded on the
+   handle's stream around the three kernels of an analysis; off by default. Creating the
+   events happens here, not in the analysis calls. */
+enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable);
+
+/* Synchronise and return the last timed analysis's kernel durations in milliseconds:
+   ms[0] innovations (gather, anomalies, perturbations), ms[1] the persistent CG solve,
+   ms[2] the ensemble update. ENKF_ERR_INVALID_ARG if timing is off or nothing was timed. */
+enkf_status enkf_get_phase_times(enkf_handle h, float* ms);
+
+/* Release the handle and all device memory it owns (synchronises its stream first).
+   NULL is accepted. */
+enkf_status enkf_destroy(enkf_handle h);
+
+/* Static description of a status code. */
+const char* enkf_status_str(enkf_status s);
+
+/* Message for the last failing call on h (h == NULL: the last failing enkf_create on the
+   calling thread). Valid until the next call on h. */
+const char* enkf_last_error(enkf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENKF_H */

@@ -1,0 +1,360 @@
+// C ABI of libenkf.so (declared in include/enkf.h): argument checking, workspace
+// ownership, and the enqueue order of one analysis step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using enkf::Workspace;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enkf_status fail(enkf_handle_s* h, enkf_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? ENKF_ERR_OOM : ENKF_ERR_CUDA, msg);
+}
+
+void free_workspace(Workspace& ws) {
+  void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.D, ws.Z, ws.B, ws.X,
+                  ws.Res, ws.P, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
+                  ws.col_relres, ws.col_true, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  ws = Workspace{};
+}
+
+size_t elem_size(const enkf_config& c) { return c.precision == ENKF_FP64 ? 8 : 4; }
+
+}  // namespace
+
+extern "C" {
+
+enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t N) {
+  if (!cfg) return ENKF_ERR_INVALID_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n = n;
+  cfg->m = m;
+  cfg->N = N;
+  cfg->precision = ENKF_FP64;
+  cfg->variant = ENKF_CGD;
+  cfg->max_iter = 1000;
+  cfg->tol = 1e-8;
+  cfg->fixed_iters = 0;
+  cfg->max_refine = 4;
+  cfg->inner_tol = 1e-5;
+  cfg->refresh_every = 8;
+  cfg->perturb_obs = 1;
+  cfg->warm_start = 0;
+  cfg->true_residual = 1;
+  cfg->grid_blocks = 0;
+  return ENKF_OK;
+}
+
+const char* enkf_status_str(enkf_status s) {
+  switch (s) {
+    case ENKF_OK: return "ok";
+    case ENKF_ERR_INVALID_ARG: return "invalid argument";
+    case ENKF_ERR_CUDA: return "CUDA error";
+    case ENKF_ERR_OOM: return "out of device memory";
+    case ENKF_ERR_NOT_CONVERGED: return "CG did not converge within max_iter";
+    case ENKF_ERR_NONFINITE: return "non-finite value in the inputs or the CG recurrences";
+    case ENKF_ERR_BREAKDOWN: return "CG breakdown (p^T S p <= 0)";
+    case ENKF_ERR_TIMEOUT: return "device grid barrier timed out";
+    case ENKF_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* enkf_last_error(enkf_handle h) {
+  return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                        const double* h_w, const double* r_diag, void* cuda_stream,
+                        enkf_handle* out) {
+  if (out) *out = nullptr;
+  if (!cfg || !out || !h_rowptr || !r_diag)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: NULL argument");
+  const enkf_config c = *cfg;
+  if (c.n < 1 || c.m < 1 || c.N < 2)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: need n >= 1, m >= 1, N >= 2");
+  if (c.m >= (int64_t(1) << 32) || c.n >= (int64_t(1) << 31))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: m must be < 2^32 and n < 2^31");
+  if (c.N > 128) return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: N > 128");
+  if (c.precision != ENKF_FP64 && c.precision != ENKF_FP32)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: precision mode not built in this library");
+  if (c.variant != ENKF_CGD)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: variant not built in this library");
+  if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: bad iteration limits");
+  if (c.fixed_iters == 0 && !(c.tol > 0.0 && std::isfinite(c.tol)))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: tol must be positive and finite");
+  if (c.precision == ENKF_FP32 && !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: inner_tol must be in (0, 1)");
+  if (c.grid_blocks < 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: grid_blocks < 0");
+  for (int q = 0; q < 7; ++q)
+    if (c.reserved[q]) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: reserved fields must be 0");
+  // observation operator and R
+  if (h_rowptr[0] != 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr[0] != 0");
+  for (int64_t i = 0; i < c.m; ++i)
+    if (h_rowptr[i + 1] < h_rowptr[i])
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr decreases");
+  const int64_t nnz = h_rowptr[c.m];
+  if (nnz > 0 && (!h_col || !h_w))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: NULL col/w with nnz > 0");
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (h_col[k] < 0 || h_col[k] >= c.n)
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: column index outside [0, n)");
+    if (!std::isfinite(h_w[k])) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: non-finite weight");
+  }
+  for (int64_t i = 0; i < c.m; ++i)
+    if (!(r_diag[i] > 0.0) || !std::isfinite(r_diag[i]))
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: r must be positive and finite");
+
+  auto* h = new enkf_handle_s();
+  h->cfg = c;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->nnz = nnz;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = enkf::plan_solve(h);
+  if (e != cudaSuccess) {
+    enkf_status s = cuda_fail(nullptr, e, "enkf_create: device query / planning");
+    delete h;
+    return s;
+  }
+  const int64_t mN = c.m * c.N;
+  const int G = h->launch.G, NT = h->launch.NT;
+  const int64_t NE = (int64_t)c.N * c.N + c.N;
+  const size_t vs = elem_size(c);
+  Workspace& ws = h->ws;
+  struct Alloc { void** p; size_t bytes; };
+  std::vector<Alloc> allocs = {
+      {(void**)&ws.rowptr, sizeof(int32_t) * (c.m + 1)},
+      {(void**)&ws.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)},
+      {(void**)&ws.w, sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)},
+      {(void**)&ws.r, sizeof(double) * c.m},
+      {(void**)&ws.HA64, sizeof(double) * mN},
+      {(void**)&ws.D, sizeof(double) * mN},
+      {(void**)&ws.Z, sizeof(double) * mN},
+      {(void**)&ws.Res, vs * mN},
+      {(void**)&ws.P, vs * mN},
+      {(void**)&ws.Tpart, sizeof(double) * G * NE},
+      {(void**)&ws.Tred, sizeof(double) * NE},
+      {(void**)&ws.rrpart, sizeof(double) * 2 * G * NT},
+      {(void**)&ws.Wacc, sizeof(double) * c.N * c.N},
+      {(void**)&ws.W, sizeof(double) * c.N * c.N},
+      {(void**)&ws.col_iters, sizeof(int32_t) * c.N},
+      {(void**)&ws.col_relres, sizeof(double) * c.N},
+      {(void**)&ws.col_true, sizeof(double) * c.N},
+      {(void**)&ws.status, sizeof(int32_t) * 4},
+      {(void**)&ws.bar, sizeof(unsigned) * 4},
+      {(void**)&ws.stage_Xf, vs * c.n * c.N},
+      {(void**)&ws.stage_y, sizeof(double) * c.m},
+  };
+  if (c.precision != ENKF_FP64) {
+    allocs.push_back({(void**)&ws.HA32, sizeof(float) * mN});
+    allocs.push_back({(void**)&ws.r32, sizeof(float) * c.m});
+    allocs.push_back({(void**)&ws.B, vs * mN});
+    allocs.push_back({(void**)&ws.X, vs * mN});
+  }
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      free_workspace(ws);
+      delete h;
+      return cuda_fail(nullptr, e, "enkf_create: cudaMalloc");
+    }
+  }
+  e = cudaMemcpy(ws.rowptr, h_rowptr, sizeof(int32_t) * (c.m + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.col, h_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.w, h_w, sizeof(double) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ws.r, r_diag, sizeof(double) * c.m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ws.status, 0, sizeof(int32_t) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ws.bar, 0, sizeof(unsigned) * 4);
+  if (e == cudaSuccess) e = enkf::launch_convert_r(h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    free_workspace(ws);
+    delete h;
+    return cuda_fail(nullptr, e, "enkf_create: upload");
+  }
+  *out = h;
+  return ENKF_OK;
+}
+
+static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d_y,
+                                const double* d_E, int emode, uint64_t seed, uint64_t counter,
+                                void* d_Xa) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze: NULL handle");
+  if (!d_Xf || !d_y || !d_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze: NULL X_f, y or X_a");
+  const auto& c = h->cfg;
+  const size_t xb = elem_size(c) * c.n * c.N;
+  const char* a = static_cast<const char*>(d_Xf);
+  const char* b = static_cast<const char*>(d_Xa);
+  if (a != b && a < b + xb && b < a + xb)
+    return fail(h, ENKF_ERR_INVALID_ARG, "analyze: X_a partially overlaps X_f");
+  cudaError_t e = cudaSuccess;
+  if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
+  if (e == cudaSuccess) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
+  if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
+  if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
+  if (e == cudaSuccess) e = enkf::launch_solve(h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
+  if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
+  if (e == cudaSuccess) e = enkf::launch_update(h, d_Xf, d_Xa);
+  if (e != cudaSuccess) return cuda_fail(h, e, "analyze: update launch");
+  if (h->timing) {
+    e = cudaEventRecord(h->ev[3], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze: timing event");
+    h->timed = true;
+  }
+  h->has_result = true;
+  return ENKF_OK;
+}
+
+enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uint64_t seed,
+                         uint64_t counter, void* d_Xa) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze: NULL handle");
+  return analyze_impl(h, d_Xf, d_y, nullptr, h->cfg.perturb_obs ? 2 : 0, seed, counter, d_Xa);
+}
+
+enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d_y,
+                                const double* d_E, void* d_Xa) {
+  return analyze_impl(h, d_Xf, d_y, d_E, d_E ? 1 : 0, 0, 0, d_Xa);
+}
+
+enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y, uint64_t seed,
+                              uint64_t counter, void* h_Xa) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze_host: NULL handle");
+  if (!h_Xf || !h_y || !h_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze_host: NULL buffer");
+  const auto& c = h->cfg;
+  const size_t xb = elem_size(c) * c.n * c.N;
+  cudaError_t e = cudaMemcpyAsync(h->ws.stage_Xf, h_Xf, xb, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws.stage_y, h_y, sizeof(double) * c.m, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: upload");
+  enkf_status s = enkf_analyze(h, h->ws.stage_Xf, h->ws.stage_y, seed, counter, h->ws.stage_Xf);
+  if (s != ENKF_OK) return s;
+  e = cudaMemcpyAsync(h_Xa, h->ws.stage_Xf, xb, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: download");
+  return ENKF_OK;
+}
+
+enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres, double* true_relres) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "get_column_stats: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  const int N = h->cfg.N;
+  if (e == cudaSuccess && iters) e = cudaMemcpy(iters, h->ws.col_iters, sizeof(int32_t) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && relres) e = cudaMemcpy(relres, h->ws.col_relres, sizeof(double) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && true_relres) e = cudaMemcpy(true_relres, h->ws.col_true, sizeof(double) * N, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_column_stats");
+  return ENKF_OK;
+}
+
+enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out) {
+  if (!h || !out) return fail(h, ENKF_ERR_INVALID_ARG, "get_stats: NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  const int N = h->cfg.N;
+  std::vector<int32_t> it(N);
+  std::vector<double> rel(N), tr(N);
+  enkf_status s = enkf_get_column_stats(h, it.data(), rel.data(), tr.data());
+  if (s != ENKF_OK) return s;
+  int32_t st[4];
+  cudaError_t e = cudaMemcpy(st, h->ws.status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_stats");
+  out->iters_max = 0;
+  out->iters_min = 1 << 30;
+  out->relres_max = 0.0;
+  out->true_relres_max = -1.0;
+  for (int j = 0; j < N; ++j) {
+    out->iters_max = std::max(out->iters_max, it[j]);
+    out->iters_min = std::min(out->iters_min, it[j]);
+    out->relres_max = std::max(out->relres_max, rel[j]);
+    if (tr[j] >= 0.0) out->true_relres_max = std::max(out->true_relres_max, tr[j]);
+  }
+  const int bits = st[0];
+  out->refinements = st[1];
+  out->grid_blocks = h->launch.G;
+  enkf_status status = ENKF_OK;
+  if (bits & enkf::DS_TIMEOUT) status = ENKF_ERR_TIMEOUT;
+  else if (bits & enkf::DS_NONFINITE) status = ENKF_ERR_NONFINITE;
+  else if (bits & enkf::DS_BREAKDOWN) status = ENKF_ERR_BREAKDOWN;
+  else if (bits & enkf::DS_NOT_CONVERGED) status = ENKF_ERR_NOT_CONVERGED;
+  int conv = 0;
+  const double tol = h->cfg.tol;
+  for (int j = 0; j < N; ++j) conv += (h->cfg.fixed_iters > 0 || rel[j] <= tol) ? 1 : 0;
+  out->columns_converged = conv;
+  out->status = status;
+  return status;
+}
+
+enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z, double* d_W) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "copy_intermediates: NULL handle");
+  const auto& c = h->cfg;
+  const size_t mN = sizeof(double) * c.m * c.N;
+  cudaError_t e = cudaSuccess;
+  if (d_HA) e = cudaMemcpyAsync(d_HA, h->ws.HA64, mN, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && d_D) e = cudaMemcpyAsync(d_D, h->ws.D, mN, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && d_Z) e = cudaMemcpyAsync(d_Z, h->ws.Z, mN, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && d_W)
+    e = cudaMemcpyAsync(d_W, h->ws.W, sizeof(double) * c.N * c.N, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy_intermediates");
+  return ENKF_OK;
+}
+
+enkf_status enkf_draw_perturbations(uint64_t seed, uint64_t counter, const double* d_r, int64_t m,
+                                    int32_t N, double* d_E, void* cuda_stream) {
+  if (!d_r || !d_E || m < 1 || N < 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "draw_perturbations: bad argument");
+  cudaError_t e = enkf::launch_draw_perturbations(seed, counter, d_r, m, N, d_E,
+                                                  static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "draw_perturbations");
+  return ENKF_OK;
+}
+
+enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "set_phase_timing: NULL handle");
+  if (enable && !h->ev[0]) {
+    for (auto& ev : h->ev) {
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(h, e, "set_phase_timing: cudaEventCreate");
+    }
+  }
+  h->timing = enable != 0;
+  h->timed = false;
+  return ENKF_OK;
+}
+
+enkf_status enkf_get_phase_times(enkf_handle h, float* ms) {
+  if (!h || !ms) return fail(h, ENKF_ERR_INVALID_ARG, "get_phase_times: NULL argument");
+  if (!h->timing || !h->timed) return fail(h, ENKF_ERR_INVALID_ARG, "get_phase_times: no timed analysis");
+  cudaError_t e = cudaEventSynchronize(h->ev[3]);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventElapsedTime(&ms[q], h->ev[q], h->ev[q + 1]);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_phase_times");
+  return ENKF_OK;
+}
+
+enkf_status enkf_destroy(enkf_handle h) {
+  if (!h) return ENKF_OK;
+  cudaStreamSynchronize(h->stream);
+  for (auto& ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+  free_workspace(h->ws);
+  delete h;
+  return ENKF_OK;
+}
+
+}  // extern "C"

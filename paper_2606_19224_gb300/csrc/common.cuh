@@ -1,0 +1,172 @@
+// Internal declarations shared by the CUDA translation units of libenkf.so.
+// Not part of the public ABI (that is include/enkf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "enkf.h"
+
+namespace enkf {
+
+constexpr int kThreads = 256;                          // every kernel here uses 256-thread CTAs
+constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s per grid-barrier wait
+
+// Device status bits (folded into enkf_status by enkf_get_stats).
+enum : int { DS_NOT_CONVERGED = 1, DS_NONFINITE = 2, DS_BREAKDOWN = 4, DS_TIMEOUT = 8 };
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch. `count` is a monotonic arrival
+// counter zeroed before the launch; `epoch` is the block's local barrier number. Each wait
+// is bounded: after kBarrierTimeoutNs the waiting block raises `abort_flag` and the
+// DS_TIMEOUT status bit, and every block that sees the flag leaves the barrier with false.
+// Returns the same value to all threads of the block.
+struct GridBarrier {
+  unsigned* count;
+  int* abort_flag;
+  int* status;
+  unsigned nblocks;
+  unsigned epoch;
+
+  __device__ bool sync() {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      epoch += 1;
+      if (nblocks > 1) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned target = epoch * nblocks;
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u32(count) < target) {
+          if (*(volatile int*)abort_flag) { ok = 0; break; }
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(abort_flag, 1);
+            atomicOr(status, DS_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+        __threadfence();
+      } else if (*(volatile int*)abort_flag) {
+        ok = 0;
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64-bit
+// multiplies by 0xD2511F53 / 0xCD9E8D57 with a Weyl key schedule (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                              uint32_t& c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int rnd = 0; rnd < 10; ++rnd) {
+    if (rnd) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+}
+
+// Standard normal for element (i, j) of the perturbation matrix: counter
+// (i, j >> 1, ctr_lo, ctr_hi), key (seed_lo, seed_hi); 53-bit uniforms
+// u1 = ((w0 << 21 | w1 >> 11) + 0.5) 2^-53, u2 = (w2 << 21 | w3 >> 11) 2^-53; Box-Muller
+// radius sqrt(-2 ln u1) times cos(2 pi u2) for even j, sin(2 pi u2) for odd j.
+__device__ __forceinline__ double perturbation_normal(int64_t i, int j, uint64_t seed,
+                                                      uint64_t counter) {
+  uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(j >> 1), c2 = (uint32_t)counter,
+           c3 = (uint32_t)(counter >> 32);
+  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint64_t x1 = ((uint64_t)c0 << 21) | (c1 >> 11);
+  const uint64_t x2 = ((uint64_t)c2 << 21) | (c3 >> 11);
+  const double u1 = ((double)x1 + 0.5) * 0x1p-53;
+  const double u2 = (double)x2 * 0x1p-53;
+  const double rho = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincos(6.283185307179586 * u2, &s, &c);
+  return rho * ((j & 1) ? s : c);
+}
+
+// ------------------------------------------------------------------ host-side state
+// Device workspace of one handle. Sizes in elements; all pointers are device pointers.
+struct Workspace {
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* w = nullptr;
+  double* r = nullptr;          // [m]
+  float* r32 = nullptr;         // [m]     (FP32 mode)
+  double* HA64 = nullptr;       // [m][N]
+  float* HA32 = nullptr;        // [m][N]   (FP32 mode)
+  double* D = nullptr;          // [m][N]
+  double* Z = nullptr;          // [m][N]   FP64 solution (FP64 mode: the CG iterate itself)
+  void* B = nullptr;            // [m][N]   inner right-hand side (FP32 mode)
+  void* X = nullptr;            // [m][N]   inner iterate (FP32 mode)
+  void* Res = nullptr;          // [m][N]
+  void* P = nullptr;            // [m][N]
+  double* Tpart = nullptr;      // [G][N*N+N]
+  double* Tred = nullptr;       // [N*N+N]
+  double* rrpart = nullptr;     // [2][G][NT]
+  double* Wacc = nullptr;       // [N][N]
+  double* W = nullptr;          // [N][N]
+  int32_t* col_iters = nullptr; // [N]
+  double* col_relres = nullptr; // [N]
+  double* col_true = nullptr;   // [N]
+  int32_t* status = nullptr;    // [4]: status bits, refinements, grid, spare
+  unsigned* bar = nullptr;      // [4]: barrier counter, abort flag, spare
+  void* stage_Xf = nullptr;     // host-API staging [n][N]
+  double* stage_y = nullptr;    // [m]
+};
+
+struct SolveLaunch {
+  int G = 0;          // persistent grid size
+  int NT = 0;         // padded column tile: 32, 64 or 128
+  size_t smem = 0;    // dynamic shared memory per CTA
+};
+
+}  // namespace enkf
+
+struct enkf_handle_s {
+  enkf_config cfg;
+  cudaStream_t stream = nullptr;
+  int64_t nnz = 0;
+  int device = 0;
+  int sms = 0;
+  enkf::Workspace ws;
+  enkf::SolveLaunch launch;
+  std::string last_error;
+  bool has_result = false;
+  bool timing = false;
+  bool timed = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace enkf {
+// Launchers (kernels_fp.cu). Each enqueues on h->stream and returns a cudaError_t.
+cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y,
+                               const double* E, int emode, uint64_t seed, uint64_t counter);
+cudaError_t plan_solve(enkf_handle_s* h);
+cudaError_t launch_solve(enkf_handle_s* h);
+cudaError_t launch_convert_r(enkf_handle_s* h);
+cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa);
+cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r,
+                                      int64_t m, int N, double* E, cudaStream_t s);
+}  // namespace enkf

@@ -1,0 +1,1017 @@
+// CUDA kernels of the CGD-EnKF analysis step on CUDA cores (FP64 and FP32 paths).
+//
+//   innov_kernel   Z_obs = H X_f (CSR gather), zbar, HA = Z_obs - zbar 1^T, E (Philox or given),
+//                  D = y 1^T - Z_obs + E                         (Sec. 2.3, Eq. Zhat_def)
+//   solve_kernel   persistent cooperative CG on S Z = D with S V = HA (HA^T V)/(N-1) + R V
+//                  (Sec. 3.3, Eq. matvec_decomp); N independent recurrences share each
+//                  matvec; FP64 scalars; FP32 mode = FP32 inner solves + FP64 residual
+//                  refresh (iterative refinement), all on the device in one launch
+//   update_kernel  X_a = X_f + A W, W = HA^T Z/(N-1), A = X_f - xbar 1^T  (Fig. 2, Alg. 1)
+//
+// Data layout: every [rows][N] array is row-major with the member index fastest. The
+// persistent grid splits the m observation rows into contiguous blocks, one per CTA (the
+// paper's row-block distribution, Sec. 3.3, with CTAs in place of MPI ranks); the only
+// cross-CTA traffic per CG step is the N x N partial Gram T = HA^T P (+ N values of
+// sum r p^2) and N residual norms, reduced in a fixed order so results are bitwise
+// reproducible run to run.
+//
+// Element work is done on 4-column fragments (one 128-bit access for FP32, two for FP64
+// when N % 4 == 0), and the operands of each pass-B epilogue are loaded before the
+// contraction so their latency overlaps it. In the FP32 mode the inner loops contain no
+// FP64 arithmetic (FP64 runs at 1/64 of the FP32 rate on this part): per-thread partial
+// sums are FP32 and only the cross-thread / cross-CTA reductions and the CG scalars are FP64.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace enkf {
+
+// ------------------------------------------------------------------ tiling
+// NT = padded column count (N <= NT). Pass A (T = HA^T V): MA x MA register tile per
+// thread over (k, j), TRA rows of HA and V staged in shared memory per step, RG row groups.
+// Pass B (Q = HA T): 4 x 4 register tile per thread over (i, j), TRB rows per tile.
+template <int NT> struct Tile;
+template <> struct Tile<32> { static constexpr int MA = 4, TRA = 32, TRB = 128; };
+template <> struct Tile<64> { static constexpr int MA = 4, TRA = 32, TRB = 64; };
+template <> struct Tile<128> { static constexpr int MA = 8, TRA = 16, TRB = 32; };
+
+// shared scalars: 8 FP64 arrays, 4 int arrays, 2 VT-sized (<= 8 B) arrays, each of length NT
+template <int NT> __host__ __device__ constexpr int scalar_bytes() { return NT * 8 * 8 + NT * 4 * 4 + NT * 8 * 2; }
+template <int NT> __host__ __device__ constexpr int union_bytes() {
+  constexpr int MA = Tile<NT>::MA, TRA = Tile<NT>::TRA, TRB = Tile<NT>::TRB;
+  constexpr int NG = NT / MA, RG = kThreads / (NG * NG);
+  constexpr int a = 2 * TRA * NT * 8 + TRA * 8;
+  constexpr int a2 = RG * NT * NT * 8;
+  constexpr int a3 = RG * NG * NT * 8;
+  constexpr int b = NT * (NT + 2) * 8 + TRB * (NT + 2) * 8;
+  constexpr int m1 = a > a2 ? a : a2;
+  constexpr int m2 = m1 > a3 ? m1 : a3;
+  return m2 > b ? m2 : b;
+}
+template <int NT> __host__ __device__ constexpr int solve_smem_bytes() {
+  return scalar_bytes<NT>() + kThreads * 8 + union_bytes<NT>();
+}
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ------------------------------------------------------------------ 4-wide fragments
+template <typename CT> __device__ __forceinline__ void load_vec(CT* d, const CT* s, int n);
+template <> __device__ __forceinline__ void load_vec<float>(float* d, const float* s, int n) {
+  for (int q = 0; q < n; q += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(s + q);
+    d[q] = v.x; d[q + 1] = v.y; d[q + 2] = v.z; d[q + 3] = v.w;
+  }
+}
+template <> __device__ __forceinline__ void load_vec<double>(double* d, const double* s, int n) {
+  for (int q = 0; q < n; q += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(s + q);
+    d[q] = v.x; d[q + 1] = v.y;
+  }
+}
+template <typename CT> __device__ __forceinline__ void store_vec4(CT* d, const CT* s);
+template <> __device__ __forceinline__ void store_vec4<float>(float* d, const float* s) {
+  *reinterpret_cast<float4*>(d) = make_float4(s[0], s[1], s[2], s[3]);
+}
+template <> __device__ __forceinline__ void store_vec4<double>(double* d, const double* s) {
+  *reinterpret_cast<double2*>(d) = make_double2(s[0], s[1]);
+  *reinterpret_cast<double2*>(d + 2) = make_double2(s[2], s[3]);
+}
+// row pointer p, columns j0..j0+3 (vec: N % 4 == 0, so the 4 columns exist and are aligned)
+template <typename CT>
+__device__ __forceinline__ void ld4(CT (&d)[4], const CT* p, int j0, int N, bool vec) {
+  if (vec) { load_vec<CT>(d, p + j0, 4); return; }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) d[y] = (j0 + y < N) ? p[j0 + y] : CT(0);
+}
+template <typename CT>
+__device__ __forceinline__ void st4(CT* p, int j0, int N, bool vec, const CT (&s)[4]) {
+  if (vec) { store_vec4<CT>(p + j0, s); return; }
+#pragma unroll
+  for (int y = 0; y < 4; ++y)
+    if (j0 + y < N) p[j0 + y] = s[y];
+}
+
+// ------------------------------------------------------------------ reductions
+// Block partial of a per-column sum over the CTA's rows: f(i, j, acc) is called once per
+// element (i in [row0,row1), j < N); the per-column totals land in out[0..NT).
+template <int NT, class F>
+__device__ __forceinline__ void rows_reduce(int64_t row0, int64_t row1, int N, F f, double* out,
+                                            double* scratch) {
+  constexpr int L = kThreads / NT;
+  const int t = threadIdx.x, j = t % NT, lane = t / NT;
+  double acc = 0.0;
+  if (j < N)
+    for (int64_t i = row0 + lane; i < row1; i += L) f(i, j, acc);
+  scratch[t] = acc;
+  __syncthreads();
+  if (t < NT) {
+    double s = 0.0;
+    for (int q = 0; q < L; ++q) s += scratch[q * NT + t];
+    out[t] = s;
+  }
+  __syncthreads();
+}
+
+// Every CTA sums the G block partials part[b*NT + j] (b < G, j < N) in the same fixed order,
+// so all CTAs obtain bitwise identical totals (and take identical decisions).
+template <int NT>
+__device__ __forceinline__ void reduce_all(const double* __restrict__ part, int G, int N,
+                                           double* out, double* scratch) {
+  constexpr int Q = kThreads / NT;
+  const int t = threadIdx.x, j = t % NT, q = t / NT;
+  double s = 0.0;
+  if (j < N) {
+    const int b0 = (int)((int64_t)q * G / Q), b1 = (int)((int64_t)(q + 1) * G / Q);
+#pragma unroll 8
+    for (int b = b0; b < b1; ++b) s += __ldcg(part + (int64_t)b * NT + j);
+  }
+  scratch[t] = s;
+  __syncthreads();
+  if (t < NT) {
+    double v = 0.0;
+    for (int qq = 0; qq < Q; ++qq) v += scratch[qq * NT + t];
+    out[t] = v;
+  }
+  __syncthreads();
+}
+
+// CTA b sums its slice of the NE-long partial vectors part[g*NE + e] over g < G (fixed order)
+// and writes red[e].
+__device__ __forceinline__ void reduce_slice(const double* __restrict__ part, int G, int NE,
+                                             double* __restrict__ red, double* scratch) {
+  const int t = threadIdx.x;
+  const int chunk = (NE + G - 1) / G;
+  const int e0 = blockIdx.x * chunk;
+  const int cnt = min(NE, e0 + chunk) - e0;
+  if (cnt <= 0) return;
+  if (cnt >= kThreads) {
+    for (int e = e0 + t; e < e0 + cnt; e += kThreads) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int g = 0; g < G; ++g) s += __ldcg(part + (int64_t)g * NE + e);
+      red[e] = s;
+    }
+    return;
+  }
+  const int parts = kThreads / cnt;
+  const int q = t / cnt, el = t % cnt;
+  double s = 0.0;
+  if (q < parts) {
+    const int g0 = (int)((int64_t)q * G / parts), g1 = (int)((int64_t)(q + 1) * G / parts);
+#pragma unroll 8
+    for (int g = g0; g < g1; ++g) s += __ldcg(part + (int64_t)g * NE + e0 + el);
+  }
+  scratch[t] = s;
+  __syncthreads();
+  if (t < cnt) {
+    double v = 0.0;
+    for (int qq = 0; qq < parts; ++qq) v += scratch[qq * cnt + t];
+    red[e0 + t] = v;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ pass A
+// out[k*N + j] = sum_i HA[i][k] V[i][j] over the CTA's rows and (want_s)
+// out[N*N + j] = sum_i r_i V[i][j]^2, where pro(i, j0, v) produces (and may store) the four
+// values V[i][j0..j0+3]. Per-thread partial sums are kept in CT.
+template <typename CT, int NT, class Pro>
+__device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, int64_t row1,
+                                      int N, const CT* __restrict__ rv, bool want_s, Pro& pro,
+                                      unsigned char* uni, double* __restrict__ out) {
+  constexpr int MA = Tile<NT>::MA, TRA = Tile<NT>::TRA;
+  constexpr int NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG, C4 = NT / 4;
+  CT* sA = reinterpret_cast<CT*>(uni);
+  CT* sV = sA + TRA * NT;
+  CT* sR = sV + TRA * NT;
+  const int t = threadIdx.x, g = t / TPG, u = t % TPG, tj = u % NG, tk = u / NG;
+  const int k0 = tk * MA, j0 = tj * MA;
+  const bool vec = (N & 3) == 0;
+  CT acc[MA][MA];
+#pragma unroll
+  for (int x = 0; x < MA; ++x)
+#pragma unroll
+    for (int y = 0; y < MA; ++y) acc[x][y] = CT(0);
+  CT sacc[MA];
+#pragma unroll
+  for (int y = 0; y < MA; ++y) sacc[y] = CT(0);
+
+  for (int64_t i0 = row0; i0 < row1; i0 += TRA) {
+    __syncthreads();
+#pragma unroll
+    for (int c = t; c < TRA * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      CT a[4] = {CT(0), CT(0), CT(0), CT(0)}, v[4] = {CT(0), CT(0), CT(0), CT(0)};
+      if (i < row1 && c0 < N) {
+        ld4<CT>(a, HA + i * N, c0, N, vec);
+        pro(i, c0, v, vec);
+      }
+      store_vec4<CT>(sA + ii * NT + c0, a);
+      store_vec4<CT>(sV + ii * NT + c0, v);
+    }
+    if (t < TRA) {
+      const int64_t i = i0 + t;
+      sR[t] = (want_s && i < row1) ? rv[i] : CT(0);
+    }
+    __syncthreads();
+    const int nrows = (int)imin64(TRA, row1 - i0);
+    for (int ii = g; ii < nrows; ii += RG) {
+      CT a[MA], v[MA];
+      load_vec<CT>(a, sA + ii * NT + k0, MA);
+      load_vec<CT>(v, sV + ii * NT + j0, MA);
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) acc[x][y] = fma(a[x], v[y], acc[x][y]);
+      if (want_s && ((ii / RG) % NG) == tk) {
+        const CT ri = sR[ii];
+#pragma unroll
+        for (int y = 0; y < MA; ++y) sacc[y] = fma(ri * v[y], v[y], sacc[y]);
+      }
+    }
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(uni);
+  if (RG > 1) {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + j0 + y] = (double)acc[x][y];
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) {
+          const int k = k0 + x, j = j0 + y;
+          double s = 0.0;
+          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
+          if (k < N && j < N) out[k * N + j] = s;
+        }
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) {
+        const int k = k0 + x, j = j0 + y;
+        if (k < N && j < N) out[k * N + j] = (double)acc[x][y];
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int y = 0; y < MA; ++y) red[(g * NG + tk) * NT + j0 + y] = (double)sacc[y];
+  __syncthreads();
+  if (t < N) {
+    double s = 0.0;
+    for (int q = 0; q < RG * NG; ++q) s += red[q * NT + t];
+    out[N * N + t] = want_s ? s : 0.0;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ pass B
+// For each of the CTA's rows i and 4-column fragment j0: acc[y] = sum_k HA[i][k] T[k][j0+y];
+// epi.prefetch loads the fragment's operands before the contraction, epi.apply updates the
+// fragment and accumulates squared residuals into rr[y] (CT). rr_out[j] = block sum (FP64).
+template <typename CT, int NT, class Epi>
+__device__ __forceinline__ void passB(const CT* __restrict__ HA, int64_t row0, int64_t row1,
+                                      int N, const CT* sT, unsigned char* sHbytes, Epi& epi,
+                                      double* rr_out) {
+  constexpr int PB = 16 / (int)sizeof(CT), LD = NT + PB, TRB = Tile<NT>::TRB, C4 = NT / 4;
+  constexpr int NJ = NT / 4, NI = kThreads / NJ;
+  static_assert(NI * 4 == TRB, "tile");
+  CT* sH = reinterpret_cast<CT*>(sHbytes);
+  const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * 4;
+  const bool vec = (N & 3) == 0;
+  CT rr[4] = {CT(0), CT(0), CT(0), CT(0)};
+  for (int64_t i0 = row0; i0 < row1; i0 += TRB) {
+    __syncthreads();
+#pragma unroll
+    for (int c = t; c < TRB * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      CT a[4] = {CT(0), CT(0), CT(0), CT(0)};
+      if (i < row1 && c0 < N) ld4<CT>(a, HA + i * N, c0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) sH[ii * LD + c0 + y] = a[y];
+    }
+    // FP32 fragments are loaded before the contraction (latency overlap); FP64 passes are
+    // DFMA-bound, so their fragments are loaded just before use to save registers
+    constexpr int NF = Epi::kPrefetch ? 4 : 1;
+    typename Epi::Frag frag[NF];
+    if constexpr (Epi::kPrefetch) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int64_t i = i0 + r0 + x;
+        if (i < row1 && j0 < N) epi.prefetch(i, j0, frag[x], vec);
+      }
+    }
+    __syncthreads();
+    CT acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = CT(0);
+    if (N == NT) {
+#pragma unroll 8
+      for (int k = 0; k < NT; ++k) {
+        CT a[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) a[x] = sH[(r0 + x) * LD + k];
+        load_vec<CT>(bv, sT + k * LD + j0, 4);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < N; ++k) {
+        CT a[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) a[x] = sH[(r0 + x) * LD + k];
+        load_vec<CT>(bv, sT + k * LD + j0, 4);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t i = i0 + r0 + x;
+      if (i < row1 && j0 < N) {
+        if constexpr (Epi::kPrefetch) {
+          epi.apply(i, j0, acc[x], frag[x], rr, vec);
+        } else {
+          epi.prefetch(i, j0, frag[0], vec);
+          epi.apply(i, j0, acc[x], frag[0], rr, vec);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(sHbytes);
+#pragma unroll
+  for (int y = 0; y < 4; ++y) red[ti * NT + j0 + y] = (double)rr[y];
+  __syncthreads();
+  if (t < NT) {
+    double s = 0.0;
+    for (int q = 0; q < NI; ++q) s += red[q * NT + t];
+    rr_out[t] = s;
+  }
+  __syncthreads();
+}
+
+// Stage the reduced N x N matrix (FP64 in global) into shared memory as CT with stride
+// NT + 16/sizeof(CT), zero-padded to NT x NT.
+template <typename CT, int NT>
+__device__ __forceinline__ void stage_T(const double* __restrict__ Tred, int N, CT* sT) {
+  constexpr int LD = NT + 16 / (int)sizeof(CT);
+  for (int e = threadIdx.x; e < NT * LD; e += kThreads) {
+    const int k = e / LD, j = e % LD;
+    sT[e] = (k < N && j < N) ? (CT)__ldcg(Tred + k * N + j) : CT(0);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ element operators
+// CG pass A: P = Res + beta P (P = Res on the first step of an inner solve; frozen columns
+// keep P).
+template <typename VT>
+struct ProCG {
+  VT* P;
+  const VT* Res;
+  const VT* beta;   // shared, VT copy of beta_j (0 beyond N)
+  const int* active;
+  int N;
+  bool first;
+  __device__ __forceinline__ void operator()(int64_t i, int j0, VT (&v)[4], bool vec) {
+    VT res[4];
+    ld4<VT>(res, Res + i * N, j0, N, vec);
+    if (first) {
+#pragma unroll
+      for (int y = 0; y < 4; ++y) v[y] = res[y];
+    } else {
+      VT p[4];
+      ld4<VT>(p, P + i * N, j0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) v[y] = active[j0 + y] ? fma(beta[j0 + y], p[y], res[y]) : p[y];
+    }
+    st4<VT>(P + i * N, j0, N, vec, v);
+  }
+};
+
+// CG pass B: q = HA T/(N-1) + r p; x += alpha p; res -= alpha q; rr += res^2.
+template <typename VT>
+struct EpiCG {
+  VT* X;
+  VT* Res;
+  const VT* P;
+  const VT* rv;
+  const VT* alpha;  // shared, VT copy of alpha_j (0 for frozen columns and beyond N)
+  VT vinv;
+  int N;
+  static constexpr bool kPrefetch = sizeof(VT) == 4;
+  struct Frag { VT p[4], x[4], res[4]; VT ri; };
+  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
+    ld4<VT>(f.p, P + i * N, j0, N, vec);
+    ld4<VT>(f.x, X + i * N, j0, N, vec);
+    ld4<VT>(f.res, Res + i * N, j0, N, vec);
+    f.ri = rv[i];
+  }
+  __device__ __forceinline__ void apply(int64_t i, int j0, const VT (&acc)[4], Frag& f,
+                                        VT (&rr)[4], bool vec) {
+    VT xn[4], rn[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const VT al = alpha[j0 + y];
+      const VT q = fma(acc[y], vinv, f.ri * f.p[y]);
+      xn[y] = fma(al, f.p[y], f.x[y]);
+      rn[y] = fma(-al, q, f.res[y]);
+      rr[y] = fma(rn[y], rn[y], rr[y]);
+    }
+    st4<VT>(X + i * N, j0, N, vec, xn);
+    st4<VT>(Res + i * N, j0, N, vec, rn);
+  }
+};
+
+// Refresh pass A (FP64): Z += X (refinement) and V = Z.
+template <typename VT>
+struct ProRefresh {
+  double* Z;
+  const VT* X;
+  int N;
+  bool accumulate;
+  __device__ __forceinline__ void operator()(int64_t i, int j0, double (&v)[4], bool vec) {
+    ld4<double>(v, Z + i * N, j0, N, vec);
+    if (accumulate) {
+      VT x[4];
+      ld4<VT>(x, X + i * N, j0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) v[y] += (double)x[y];
+      st4<double>(Z + i * N, j0, N, vec, v);
+    }
+  }
+};
+
+// Refresh pass B (FP64): true residual D - (HA T/(N-1) + r Z); optionally the next
+// right-hand side B = (VT) residual.
+template <typename VT>
+struct EpiRefresh {
+  const double* Z;
+  const double* D;
+  const double* r;
+  VT* B;
+  double inv;
+  int N;
+  static constexpr bool kPrefetch = false;
+  struct Frag { double z[4], d[4]; double ri; };
+  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
+    ld4<double>(f.z, Z + i * N, j0, N, vec);
+    ld4<double>(f.d, D + i * N, j0, N, vec);
+    f.ri = r[i];
+  }
+  __device__ __forceinline__ void apply(int64_t i, int j0, const double (&acc)[4], Frag& f,
+                                        double (&rr)[4], bool vec) {
+    double rt[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const double q = fma(acc[y], inv, f.ri * f.z[y]);
+      rt[y] = f.d[y] - q;
+      rr[y] = fma(rt[y], rt[y], rr[y]);
+    }
+    if (B) {
+      VT b[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = (VT)rt[y];
+      st4<VT>(B + i * N, j0, N, vec, b);
+    }
+  }
+};
+
+struct SolveParams {
+  int64_t m;
+  int N;
+  int mode;  // 0: FP64 CG (X is the FP64 solution Z); 1: FP32 inner CG + FP64 refresh
+  const void* HA;
+  const double* HA64;
+  const double* D;
+  const double* r;
+  const void* rv;   // r in the inner-solve type
+  void* B;
+  void* X;
+  void* Res;
+  void* P;
+  double* Z;
+  double* Tpart;
+  double* Tred;
+  double* rrpart;
+  double* Wacc;
+  double* W;
+  double tol, inner_tol;
+  int max_iter, fixed_iters, max_refine, true_residual;
+  int* col_iters;
+  double* col_relres;
+  double* col_true;
+  int* status;
+  unsigned* bar;
+};
+
+template <typename VT, int NT>
+__global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* s_rr = reinterpret_cast<double*>(smem);
+  double* s_bn2 = s_rr + NT;
+  double* s_dn2 = s_bn2 + NT;
+  double* s_alpha = s_dn2 + NT;
+  double* s_beta = s_alpha + NT;
+  double* s_itol = s_beta + NT;
+  double* s_tmp = s_itol + NT;
+  double* s_true = s_tmp + NT;
+  int* s_active = reinterpret_cast<int*>(s_true + NT);
+  int* s_done = s_active + NT;
+  int* s_iters = s_done + NT;
+  int* s_flag = s_iters + NT;
+  VT* s_alpha_v = reinterpret_cast<VT*>(s_flag + NT);
+  VT* s_beta_v = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(s_flag + NT) + NT * 8);
+  double* scratch = reinterpret_cast<double*>(smem + scalar_bytes<NT>());
+  unsigned char* uni = smem + scalar_bytes<NT>() + kThreads * 8;
+
+  const int N = p.N, G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int64_t rows_per = (p.m + G - 1) / G;
+  const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
+  const int64_t row1 = imin64(p.m, row0 + rows_per);
+  const int NE = N * N + N;
+  GridBarrier bar{p.bar, reinterpret_cast<int*>(p.bar + 1), p.status, (unsigned)G, 0u};
+  const double inv_nm1 = 1.0 / (double)(N - 1);
+  const bool refine = (p.mode == 1);
+  const bool fixed = p.fixed_iters > 0;
+  VT* X = refine ? static_cast<VT*>(p.X) : reinterpret_cast<VT*>(p.Z);
+  VT* Res = static_cast<VT*>(p.Res);
+  VT* P = static_cast<VT*>(p.P);
+  const VT* B = refine ? static_cast<const VT*>(p.B) : reinterpret_cast<const VT*>(p.D);
+  const VT* HA = static_cast<const VT*>(p.HA);
+  const VT* rv = static_cast<const VT*>(p.rv);
+  double* Tp = p.Tpart + (int64_t)b * NE;
+  int par = 0;
+  bool ok = true;
+
+  // ---- ||d_j||^2 (and Z = 0 for the refinement accumulator)
+  rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
+    const double d = p.D[i * N + j];
+    acc = fma(d, d, acc);
+    if (refine) p.Z[i * N + j] = 0.0;
+  }, s_tmp, scratch);
+  if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+  ok = bar.sync();
+  if (ok) {
+    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_dn2, scratch);
+    par ^= 1;
+    if (t < NT) {
+      const bool zero = (t >= N) || (s_dn2[t] == 0.0);
+      s_done[t] = zero ? 1 : 0;
+      s_iters[t] = 0;
+      s_true[t] = (t < N && s_dn2[t] == 0.0) ? 0.0 : -1.0;
+      s_rr[t] = 0.0;
+      s_bn2[t] = 0.0;
+      s_itol[t] = refine ? p.inner_tol : p.tol;
+      s_alpha_v[t] = VT(0);
+      s_beta_v[t] = VT(0);
+    }
+    if (b == 0)
+      for (int e = t; e < N * N; e += kThreads) p.Wacc[e] = 0.0;
+    __syncthreads();
+  }
+
+  int outer = 0, total_iter = 0, refinements = 0;
+  while (ok) {
+    // ---- inner solve of S X = B from X = 0
+    rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
+      const VT bv = B[i * N + j];
+      X[i * N + j] = VT(0);
+      Res[i * N + j] = bv;
+      acc = fma((double)bv, (double)bv, acc);
+    }, s_tmp, scratch);
+    if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+    if (!(ok = bar.sync())) break;
+    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_rr, scratch);
+    par ^= 1;
+    if (t < NT) {
+      s_bn2[t] = s_rr[t];
+      s_active[t] = (t < N && !s_done[t] && s_rr[t] > 0.0) ? 1 : 0;
+      s_beta[t] = 0.0;
+      s_alpha[t] = 0.0;
+    }
+    __syncthreads();
+    const int limit = fixed ? p.fixed_iters : (p.max_iter - total_iter);
+    bool first = true;
+    int it = 0;
+    for (; it < limit; ++it) {
+      if (t == 0) {
+        int any = 0;
+        for (int j = 0; j < N; ++j) any |= s_active[j];
+        s_flag[0] = any;
+      }
+      __syncthreads();
+      if (!s_flag[0]) break;
+      // pass A: P = R + beta P (P = R on the first step); T = HA^T P; s_j = sum r_i p_ij^2
+      ProCG<VT> pro{P, Res, s_beta_v, s_active, N, first};
+      passA<VT, NT>(HA, row0, row1, N, rv, true, pro, uni, Tp);
+      if (!(ok = bar.sync())) break;
+      reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
+      if (!(ok = bar.sync())) break;
+      // alpha_j = rr_j / (||T_:j||^2/(N-1) + s_j)   (p^T S p, Eq. matvec_decomp)
+      if (t < N) {
+        double t2 = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < N; ++k) {
+          const double v = __ldcg(p.Tred + k * N + t);
+          t2 = fma(v, v, t2);
+        }
+        const double pSp = t2 * inv_nm1 + __ldcg(p.Tred + N * N + t);
+        double al = 0.0;
+        if (s_active[t]) {
+          if (!isfinite(pSp)) { atomicOr(p.status, DS_NONFINITE); s_active[t] = 0; }
+          else if (pSp <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); s_active[t] = 0; }
+          else al = s_rr[t] / pSp;
+        }
+        s_alpha[t] = al;
+        s_alpha_v[t] = (VT)al;
+      }
+      VT* sT = reinterpret_cast<VT*>(uni);
+      stage_T<VT, NT>(p.Tred, N, sT);
+      if (b == 0)
+        for (int e = t; e < N * N; e += kThreads) p.Wacc[e] += __ldcg(p.Tred + e) * s_alpha[e % N];
+      // pass B: q = HA T/(N-1) + r p; x += alpha p; res -= alpha q; rr = ||res||^2
+      constexpr int LDT = NT + 16 / (int)sizeof(VT);
+      EpiCG<VT> epi{X, Res, P, rv, s_alpha_v, (VT)inv_nm1, N};
+      passB<VT, NT>(HA, row0, row1, N, sT, uni + NT * LDT * sizeof(VT), epi, s_tmp);
+      if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+      if (!(ok = bar.sync())) break;
+      reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
+      par ^= 1;
+      if (t < N && s_active[t]) {
+        const double rn = s_tmp[t];
+        s_iters[t] += 1;
+        if (!isfinite(rn)) { atomicOr(p.status, DS_NONFINITE); s_active[t] = 0; s_alpha_v[t] = VT(0); }
+        else {
+          const double be = rn / s_rr[t];
+          s_beta[t] = be;
+          s_beta_v[t] = (VT)be;
+          s_rr[t] = rn;
+          if (fixed) { if (rn == 0.0) s_active[t] = 0; }
+          else if (sqrt(rn) <= s_itol[t] * sqrt(s_bn2[t])) s_active[t] = 0;
+        }
+      }
+      if (t < N && !s_active[t]) s_alpha_v[t] = VT(0);
+      __syncthreads();
+      first = false;
+    }
+    if (!ok) break;
+    total_iter += it;
+
+    if (!refine && !p.true_residual) {
+      if (b == 0)
+        for (int e = t; e < N * N; e += kThreads) p.W[e] = p.Wacc[e] * inv_nm1;
+      break;
+    }
+    // ---- FP64 refresh: Z (+)= X; T = HA^T Z; true residual D - S Z; next right-hand side
+    ProRefresh<VT> pro{p.Z, X, N, refine};
+    passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
+    if (!(ok = bar.sync())) break;
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
+    if (!(ok = bar.sync())) break;
+    double* sT64 = reinterpret_cast<double*>(uni);
+    stage_T<double, NT>(p.Tred, N, sT64);
+    if (b == 0)
+      for (int e = t; e < N * N; e += kThreads) p.W[e] = __ldcg(p.Tred + e) * inv_nm1;
+    constexpr int LD64 = NT + 2;
+    EpiRefresh<VT> epi{p.Z, p.D, p.r, refine ? static_cast<VT*>(p.B) : nullptr, inv_nm1, N};
+    passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
+    if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+    if (!(ok = bar.sync())) break;
+    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
+    par ^= 1;
+    ++refinements;
+    if (t < N) {
+      const double tr = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+      s_true[t] = tr;
+      if (refine) {
+        if (tr <= p.tol) s_done[t] = 1;
+        // next inner solve only has to gain the remaining factor tol/tr (with margin 0.1)
+        s_itol[t] = fmax(p.inner_tol, tr > 0.0 ? 0.1 * p.tol / tr : p.inner_tol);
+        if (s_itol[t] > 0.5) s_itol[t] = 0.5;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      int all = 1;
+      for (int j = 0; j < N; ++j) all &= s_done[j];
+      s_flag[1] = all;
+    }
+    __syncthreads();
+    if (!refine || fixed || s_flag[1] || outer >= p.max_refine || total_iter >= p.max_iter) break;
+    ++outer;
+  }
+
+  if (b == 0) {
+    if (t < N) {
+      p.col_iters[t] = s_iters[t];
+      const double rec = s_dn2[t] > 0.0 ? sqrt(s_rr[t] / s_dn2[t]) : 0.0;
+      p.col_relres[t] = refine ? s_true[t] : rec;
+      p.col_true[t] = s_true[t];
+      bool conv;
+      if (fixed) conv = true;
+      else if (refine) conv = s_true[t] >= 0.0 && s_true[t] <= p.tol;
+      else conv = s_dn2[t] == 0.0 || sqrt(s_rr[t]) <= p.tol * sqrt(s_dn2[t]);
+      if (!conv && ok) atomicOr(p.status, DS_NOT_CONVERGED);
+    }
+    if (t == 0) p.status[1] = refinements;
+  }
+}
+
+// ------------------------------------------------------------------ K1: innovations
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) innov_kernel(
+    const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
+    const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
+    double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
+    float* __restrict__ B32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t i = warp; i < m; i += nwarps) {
+    double z[4] = {0.0, 0.0, 0.0, 0.0};
+    const int k0 = rowptr[i], k1 = rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const double wk = w[k];
+      const VT* xr = Xf + (int64_t)col[k] * N;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        if (j < N) z[q] = fma(wk, (double)xr[j], z[q]);
+      }
+    }
+    double s = z[0] + z[1] + z[2] + z[3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double zbar = s / (double)N;
+    const double yi = y[i], sr = sqrt(r[i]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = lane + 32 * q;
+      if (j < N) {
+        const int64_t e = i * N + j;
+        double pert = 0.0;
+        if (emode == 1) pert = E[e];
+        else if (emode == 2) pert = sr * perturbation_normal(i, j, seed, counter);
+        const double ha = z[q] - zbar;
+        const double d = (yi - z[q]) + pert;
+        HA64[e] = ha;
+        D[e] = d;
+        if (HA32) HA32[e] = (float)ha;
+        if (B32) B32[e] = (float)d;
+      }
+    }
+  }
+}
+
+__global__ void draw_perturbations_kernel(uint64_t seed, uint64_t counter,
+                                          const double* __restrict__ r, int64_t m, int N,
+                                          double* __restrict__ E) {
+  const int64_t total = m * N;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = e / N;
+    const int j = (int)(e % N);
+    E[e] = sqrt(r[i]) * perturbation_normal(i, j, seed, counter);
+  }
+}
+
+__global__ void convert_r_kernel(const double* __restrict__ r, float* __restrict__ r32, int64_t m) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < m; i += (int64_t)gridDim.x * kThreads)
+    r32[i] = (float)r[i];
+}
+
+// ------------------------------------------------------------------ K4: final update
+// X_a = X_f + (X_f - xbar 1^T) W, row tiles of TRB rows staged in shared memory.
+template <typename VT, int NT>
+__global__ void __launch_bounds__(kThreads) update_kernel(const VT* Xf, VT* Xa,
+                                                          const double* __restrict__ W,
+                                                          int64_t n, int N) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int LD = NT + 16 / (int)sizeof(VT), TRB = Tile<NT>::TRB, C4 = NT / 4;
+  constexpr int NJ = NT / 4;
+  VT* sW = reinterpret_cast<VT*>(smem);
+  VT* sX = sW + NT * LD;
+  VT* smean = sX + TRB * LD;
+  const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * 4;
+  const bool vec = (N & 3) == 0;
+  for (int e = t; e < NT * LD; e += kThreads) {
+    const int k = e / LD, j = e % LD;
+    sW[e] = (k < N && j < N) ? (VT)W[k * N + j] : VT(0);
+  }
+  for (int64_t i0 = (int64_t)blockIdx.x * TRB; i0 < n; i0 += (int64_t)gridDim.x * TRB) {
+    __syncthreads();
+#pragma unroll
+    for (int c = t; c < TRB * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      VT a[4] = {VT(0), VT(0), VT(0), VT(0)};
+      if (i < n && c0 < N) ld4<VT>(a, Xf + i * N, c0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) sX[ii * LD + c0 + y] = a[y];
+    }
+    __syncthreads();
+    if (t < TRB) {
+      VT s = VT(0);
+      for (int k = 0; k < N; ++k) s += sX[t * LD + k];
+      smean[t] = s / (VT)N;
+    }
+    __syncthreads();
+    // original X_f fragments for the output (same threads write X_a, so X_a may alias X_f)
+    VT xf[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) xf[x][y] = sX[(r0 + x) * LD + j0 + y];
+    __syncthreads();
+    for (int e = t; e < TRB * NT; e += kThreads) {
+      const int ii = e / NT, k = e % NT;
+      if (k < N) sX[ii * LD + k] -= smean[ii];
+    }
+    __syncthreads();
+    VT acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = VT(0);
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      VT a[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = sX[(r0 + x) * LD + k];
+      load_vec<VT>(bv, sW + k * LD + j0, 4);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t i = i0 + r0 + x;
+      if (i < n && j0 < N) {
+        VT o[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[y] = xf[x][y] + acc[x][y];
+        st4<VT>(Xa + i * N, j0, N, vec, o);
+      }
+    }
+  }
+}
+
+template <typename VT, int NT> constexpr int update_smem_bytes() {
+  constexpr int LD = NT + 16 / (int)sizeof(VT);
+  return (NT * LD + Tile<NT>::TRB * LD + Tile<NT>::TRB) * (int)sizeof(VT);
+}
+
+// ------------------------------------------------------------------ host launchers
+static int pick_nt(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
+
+template <typename VT>
+static void* solve_fn(int NT) {
+  if (NT == 32) return (void*)solve_kernel<VT, 32>;
+  if (NT == 64) return (void*)solve_kernel<VT, 64>;
+  return (void*)solve_kernel<VT, 128>;
+}
+static size_t solve_smem(int NT) {
+  return NT == 32 ? solve_smem_bytes<32>() : (NT == 64 ? solve_smem_bytes<64>() : solve_smem_bytes<128>());
+}
+
+cudaError_t plan_solve(enkf_handle_s* h) {
+  const int N = h->cfg.N;
+  const int NT = pick_nt(N);
+  const bool fp64 = h->cfg.precision == ENKF_FP64;
+  void* fn = fp64 ? solve_fn<double>(NT) : solve_fn<float>(NT);
+  const size_t smem = solve_smem(NT);
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+  if (err != cudaSuccess) return err;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int max_coresident = occ * h->sms;
+  const int64_t min_rows = 32;
+  int G = (int)std::min<int64_t>(max_coresident, std::max<int64_t>(1, (h->cfg.m + min_rows - 1) / min_rows));
+  if (h->cfg.grid_blocks > 0) G = std::min(h->cfg.grid_blocks, max_coresident);
+  h->launch.G = G;
+  h->launch.NT = NT;
+  h->launch.smem = smem;
+  return cudaSuccess;
+}
+
+cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y, const double* E,
+                               int emode, uint64_t seed, uint64_t counter) {
+  const auto& c = h->cfg;
+  auto& ws = h->ws;
+  const int blocks = (int)std::min<int64_t>((c.m + 7) / 8, (int64_t)h->sms * 16);
+  const bool fp64 = c.precision == ENKF_FP64;
+  if (fp64)
+    innov_kernel<double><<<blocks, kThreads, 0, h->stream>>>(
+        static_cast<const double*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
+        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr);
+  else
+    innov_kernel<float><<<blocks, kThreads, 0, h->stream>>>(
+        static_cast<const float*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
+        c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_r(enkf_handle_s* h) {
+  if (!h->ws.r32) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((h->cfg.m + kThreads - 1) / kThreads, 4096);
+  convert_r_kernel<<<blocks, kThreads, 0, h->stream>>>(h->ws.r, h->ws.r32, h->cfg.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve(enkf_handle_s* h) {
+  const auto& c = h->cfg;
+  auto& ws = h->ws;
+  const bool fp64 = c.precision == ENKF_FP64;
+  SolveParams p{};
+  p.m = c.m;
+  p.N = c.N;
+  p.mode = fp64 ? 0 : 1;
+  p.HA = fp64 ? (const void*)ws.HA64 : (const void*)ws.HA32;
+  p.HA64 = ws.HA64;
+  p.D = ws.D;
+  p.r = ws.r;
+  p.rv = fp64 ? (const void*)ws.r : (const void*)ws.r32;
+  p.B = ws.B;
+  p.X = ws.X;
+  p.Res = ws.Res;
+  p.P = ws.P;
+  p.Z = ws.Z;
+  p.Tpart = ws.Tpart;
+  p.Tred = ws.Tred;
+  p.rrpart = ws.rrpart;
+  p.Wacc = ws.Wacc;
+  p.W = ws.W;
+  p.tol = c.tol;
+  p.inner_tol = c.inner_tol;
+  p.max_iter = c.max_iter;
+  p.fixed_iters = c.fixed_iters;
+  p.max_refine = c.max_refine;
+  p.true_residual = c.true_residual;
+  p.col_iters = ws.col_iters;
+  p.col_relres = ws.col_relres;
+  p.col_true = ws.col_true;
+  p.status = ws.status;
+  p.bar = ws.bar;
+  cudaError_t err = cudaMemsetAsync(ws.bar, 0, 4 * sizeof(unsigned), h->stream);
+  if (err != cudaSuccess) return err;
+  err = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);
+  if (err != cudaSuccess) return err;
+  void* fn = fp64 ? solve_fn<double>(h->launch.NT) : solve_fn<float>(h->launch.NT);
+  void* args[] = {&p};
+  return cudaLaunchCooperativeKernel(fn, dim3(h->launch.G), dim3(kThreads), args,
+                                     h->launch.smem, h->stream);
+}
+
+cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
+  const auto& c = h->cfg;
+  const int NT = h->launch.NT;
+  const bool fp64 = c.precision == ENKF_FP64;
+  const int TRB = NT == 32 ? Tile<32>::TRB : (NT == 64 ? Tile<64>::TRB : Tile<128>::TRB);
+  const int tiles = (int)std::min<int64_t>((c.n + TRB - 1) / TRB, (int64_t)h->sms * 8);
+  void* fn;
+  int smem;
+  if (fp64) {
+    fn = NT == 32 ? (void*)update_kernel<double, 32> : NT == 64 ? (void*)update_kernel<double, 64> : (void*)update_kernel<double, 128>;
+    smem = NT == 32 ? update_smem_bytes<double, 32>() : NT == 64 ? update_smem_bytes<double, 64>() : update_smem_bytes<double, 128>();
+  } else {
+    fn = NT == 32 ? (void*)update_kernel<float, 32> : NT == 64 ? (void*)update_kernel<float, 64> : (void*)update_kernel<float, 128>;
+    smem = NT == 32 ? update_smem_bytes<float, 32>() : NT == 64 ? update_smem_bytes<float, 64>() : update_smem_bytes<float, 128>();
+  }
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (err != cudaSuccess) return err;
+  const double* W = h->ws.W;
+  int64_t n = c.n;
+  int N = c.N;
+  void* args[] = {const_cast<void**>(&Xf), &Xa, const_cast<double**>(&W), &n, &N};
+  return cudaLaunchKernel(fn, dim3(tiles), dim3(kThreads), args, smem, h->stream);
+}
+
+cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r, int64_t m,
+                                      int N, double* E, cudaStream_t s) {
+  const int64_t total = m * N;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + kThreads - 1) / kThreads, 4096));
+  draw_perturbations_kernel<<<blocks, kThreads, 0, s>>>(seed, counter, r, m, N, E);
+  return cudaGetLastError();
+}
+
+}  // namespace enkf

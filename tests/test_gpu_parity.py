@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element,
+on seeded inputs. Bars: rel. Frobenius error (Eq. rel_frob) against the exact analysis
+<= 1e-6 for the FP64 and FP32 paths; fixed-iteration FP64 CG iterates equal to the oracle's
+up to round-off (1e-11); perturbations within 1e-14 relative (the integer Philox stream is
+identical; log/sincos may differ in the last bits)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _csr_problem(n, N, m, seed, dtype=np.float64):
+    """Random general CSR operator (1..3 weighted entries per row), non-uniform R."""
+    rng = np.random.default_rng(seed)
+    Xf = (rng.standard_normal((n, N)) + 2.0 * rng.standard_normal(n)[:, None]).astype(dtype)
+    rowptr, col, w = [0], [], []
+    for _ in range(m):
+        k = int(rng.integers(1, 4))
+        col += list(rng.choice(n, size=k, replace=False))
+        w += list(rng.uniform(-1.5, 1.5, size=k))
+        rowptr.append(len(col))
+    r = rng.uniform(0.3, 2.0, size=m)
+    y = rng.standard_normal(m) * 2.0
+    return synth.Problem(np.ascontiguousarray(Xf), np.array(rowptr, np.int32),
+                         np.array(col, np.int32), np.array(w), r, y)
+
+
+def _run(lib, p, prec="fp64", seed=7, counter=3, E=None, **cfg):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec, **cfg)
+    Xf = torch.from_numpy(np.ascontiguousarray(p.Xf)).to("cuda", dt)
+    y = torch.from_numpy(p.y).to("cuda", torch.float64)
+    if E is None:
+        Xa = an.analyze(Xf, y, seed=seed, counter=counter)
+    else:
+        Xa = an.analyze_with_E(Xf, y, None if E is False else torch.from_numpy(E).cuda())
+    st = an.stats()
+    return an, Xa.double().cpu().numpy(), st
+
+
+def _oracle_exact(p, E):
+    return oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+
+
+def test_perturbations_match_oracle_generator(lib):
+    r = np.random.default_rng(0).uniform(0.2, 3.0, size=3001)
+    for N, seed, counter in ((64, 7, 3), (37, 2 ** 40 + 5, 2 ** 33 + 1), (2, 0, 0)):
+        E = lib.draw_perturbations(seed, counter, torch.from_numpy(r).cuda(), N).cpu().numpy()
+        ref = oracle.obs_perturbations(seed, counter, r, N)
+        assert np.max(np.abs(E - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(4096, 64, 1024), (2500, 37, 999), (1600, 20, 400),
+                                   (3000, 100, 700), (2048, 128, 1536), (500, 2, 130)])
+def test_analysis_matches_exact_oracle(lib, prec, shape):
+    n, N, m = shape
+    side = int(round(n ** 0.5))
+    p = synth.grf_problem(side, 6.0, N, m, 0.5, 1.5, seed=n + N + m,
+                          dtype=np.float64 if prec == "fp64" else np.float32)
+    an, Xa, st = _run(lib, p, prec, tol=1e-10)
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = _oracle_exact(p, E)
+    err = oracle.rel_frobenius(Xa, ref)
+    assert st["status"] == "ok", st
+    assert err <= 1e-6, (err, st)
+    if prec == "fp64":
+        assert err <= 1e-8, (err, st)
+        assert st["true_relres_max"] <= 1e-9
+
+
+def test_general_csr_operator_and_explicit_E(lib):
+    p = _csr_problem(900, 24, 333, 5)
+    E = np.random.default_rng(9).standard_normal((p.m, p.N)) * np.sqrt(p.r)[:, None]
+    an, Xa, st = _run(lib, p, "fp64", E=E, tol=1e-12)
+    ref = oracle.enkf_alg1(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert oracle.rel_frobenius(Xa, ref) <= 1e-9
+    # E = NULL is the paper's unperturbed EnKF
+    an, Xa0, st = _run(lib, p, "fp64", E=False, tol=1e-12)
+    ref0 = oracle.enkf_alg1(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, None)
+    assert oracle.rel_frobenius(Xa0, ref0) <= 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 12])
+def test_fixed_iteration_cg_iterates_match_oracle(lib, k):
+    p = synth.workload("grf512_N64_m65536", 11, scale=8)
+    an, Xa, st = _run(lib, p, "fp64", fixed_iters=k)
+    HA, D, Z, W = (t.cpu().numpy() for t in an.intermediates())
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    Xa_ref, info = oracle.cgd_enkf(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E, fixed_iters=k)
+    assert np.linalg.norm(HA - info["Zhat"]) <= 1e-13 * np.linalg.norm(info["Zhat"])
+    assert np.linalg.norm(D - info["D"]) <= 1e-13 * np.linalg.norm(info["D"])
+    assert np.linalg.norm(Z - info["Z"]) <= 1e-11 * np.linalg.norm(info["Z"])
+    assert np.linalg.norm(W - info["W"]) <= 1e-11 * np.linalg.norm(info["W"])
+    assert oracle.rel_frobenius(Xa, Xa_ref) <= 1e-11
+    it, _, _ = an.column_stats()
+    assert np.all(it == k)
+
+
+def test_iteration_counts_match_oracle_stopping_rule(lib):
+    p = synth.workload("grf512_N64_m65536", 12, scale=8)
+    an, Xa, st = _run(lib, p, "fp64", tol=1e-8)
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    _, info = oracle.cgd_enkf(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E, tol=1e-8)
+    it, rel, _ = an.column_stats()
+    # FP64 rounding differs between the two implementations; near the tolerance a column
+    # can need a few more or fewer steps, so most columns must agree exactly and all closely
+    diff = np.abs(it - info["iters"])
+    assert np.mean(diff == 0) >= 0.75 and diff.max() <= max(3, int(0.06 * info["iters"].max()))
+    assert np.all(rel <= 1e-8)
+
+
+def test_lemma1_equal_variances_converge_within_N_plus_1(lib):
+    p = synth.workload("grf512_N64_m65536", 13, scale=8)
+    p.r[:] = 0.8
+    an, Xa, st = _run(lib, p, "fp64", tol=1e-12, max_iter=p.N + 1)
+    assert st["status"] == "ok" and st["iters_max"] <= p.N + 1
+
+
+def test_in_place_and_host_api_and_determinism(lib):
+    p = synth.workload("grf512_N64_m65536", 14, scale=8, dtype=np.float32)
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32")
+    Xf = torch.from_numpy(p.Xf).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    a = an.analyze(Xf, y, seed=1, counter=2)
+    b = an.analyze(Xf, y, seed=1, counter=2)
+    assert torch.equal(a, b)                       # fixed-order reductions: bitwise repeatable
+    Xh = torch.from_numpy(p.Xf).pin_memory()
+    c = an.analyze_host(Xh, torch.from_numpy(p.y).pin_memory(), seed=1, counter=2)
+    assert torch.equal(a.cpu(), c)
+    X2 = Xf.clone()
+    an.analyze(X2, y, seed=1, counter=2, out=X2)   # in place
+    assert torch.equal(a, X2)
+
+
+def test_zero_innovation_column_and_tiny_problem(lib):
+    p = _csr_problem(40, 20, 20, 21)
+    Z = oracle.apply_H(p.rowptr, p.col, p.w, p.Xf)
+    E = np.random.default_rng(3).standard_normal((p.m, p.N))
+    E[:, 5] = Z[:, 5] - p.y                        # d_5 = 0 exactly
+    an, Xa, st = _run(lib, p, "fp64", E=E, tol=1e-12)
+    ref = oracle.enkf_alg1(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert oracle.rel_frobenius(Xa, ref) <= 1e-10
+    it, rel, _ = an.column_stats()
+    assert it[5] == 0
+
+
+def test_not_converged_and_nonfinite_statuses(lib):
+    p = synth.workload("grf512_N64_m65536", 15, scale=8)
+    an, Xa, st = _run(lib, p, "fp64", tol=1e-12, max_iter=3)
+    assert st["status"] == "not_converged" and np.all(np.isfinite(Xa))
+    q = synth.workload("grf512_N64_m65536", 15, scale=8)
+    q.Xf[q.col[3], 4] = np.nan
+    an, Xa, st = _run(lib, q, "fp64", tol=1e-8)
+    assert st["status"] == "nonfinite"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_grf512_N64_m65536(lib, prec):
+    """The benchmark workload at full size (n=262,144, m=65,536, N=64, tol 1e-8), in the
+    launch configuration bench.py times, against the exact oracle (N x N route)."""
+    dtype = np.float64 if prec == "fp64" else np.float32
+    p = synth.workload("grf512_N64_m65536", 1, dtype=dtype)
+    an, Xa, st = _run(lib, p, prec, seed=1, counter=0, tol=1e-8)
+    E = oracle.obs_perturbations(1, 0, p.r, p.N)
+    ref = _oracle_exact(p, E)
+    err = oracle.rel_frobenius(Xa, ref)
+    assert st["status"] == "ok", st
+    assert err <= 1e-6, (err, st)
+    assert st["true_relres_max"] <= 1e-8
+
+
+def test_l96_cycling_lockstep(lib):
+    """Lorenz-96 (n=40, N=20, m=20, R=I, tol 1e-10): 200 cycles in lockstep. Every cycle the
+    GPU and the oracle analyse the same forecast ensemble with the same perturbations, and
+    the oracle's analysis is propagated (the chaotic model amplifies last-bit differences,
+    so a GPU-driven trajectory would separate from the oracle's after a few dozen cycles)."""
+    cyc = synth.L96Cycle(seed=4)
+    an = lib.Analysis(40, cyc.col.size, 20, cyc.rowptr, cyc.col, cyc.w, cyc.r, precision="fp64",
+                      tol=1e-10)
+    for k in range(200):
+        cyc.forecast()
+        y = cyc.observe()
+        Xa = an.analyze(torch.from_numpy(cyc.ensemble).cuda(), torch.from_numpy(y).cuda(),
+                        seed=99, counter=k).cpu().numpy()
+        assert an.stats()["status"] == "ok"
+        E = oracle.obs_perturbations(99, k, cyc.r, 20)
+        ref = oracle.enkf_alg1(cyc.ensemble, cyc.rowptr, cyc.col, cyc.w, cyc.r, y, E)
+        err = oracle.rel_frobenius(Xa, ref)
+        assert err <= 1e-8, (k, err)
+        cyc.ensemble = ref
