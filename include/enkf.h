@@ -179,6 +179,29 @@ enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable);
    ms[2] the ensemble update. ENKF_ERR_INVALID_ARG if timing is off or nothing was timed. */
 enkf_status enkf_get_phase_times(enkf_handle h, float* ms);
 
+/* One analysis step that allocates no device memory, for callers that cannot call
+   cudaMalloc when they need it: code running while a stream is captured into a CUDA graph,
+   applications whose own pool allocator owns all device memory, real-time assimilation
+   loops that forbid allocation after start-up. The paper has no counterpart; this is a
+   deployment form of enkf_create + enkf_analyze + enkf_get_stats without a handle.
+   Inputs and outputs are as for enkf_create / enkf_analyze, except that the observation
+   operator and R are DEVICE arrays here (d_rowptr[m+1], d_col[nnz], d_w[nnz], d_r[m] > 0;
+   they are not validated, so the caller guarantees 0 <= col < n and r > 0), and cfg must
+   use ENKF_CGD with ENKF_FP64 or ENKF_FP32. All working memory lives in one fixed 16 MiB
+   array in the library's device memory (held by every GPU that loads the library until the
+   process exits); problems whose working memory (about 40 m N bytes in FP64 mode, 44 m N in
+   FP32 mode, plus the CG partials) exceeds it are rejected with ENKF_ERR_UNSUPPORTED and a
+   one-line message on stderr. The first call on each device looks up the array's device
+   address; make that first call before any stream capture. Every call shares the array, so
+   calls that may overlap on the GPU (different streams, or different host threads without
+   ordering) race and must be serialised by the caller. If out_stats (HOST) is non-NULL the
+   call synchronises the stream, fills it, and returns out_stats->status. */
+enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr,
+                                 const int32_t* d_col, const double* d_w, const double* d_r,
+                                 const void* d_Xf, const double* d_y, uint64_t seed,
+                                 uint64_t counter, void* d_Xa, void* cuda_stream,
+                                 enkf_stats* out_stats);
+
 /* Release the handle and all device memory it owns (synchronises its stream first).
    NULL is accepted. */
 enkf_status enkf_destroy(enkf_handle h);

@@ -23,7 +23,7 @@ EXPORTS = (
     "enkf_config_default", "enkf_create", "enkf_analyze", "enkf_analyze_with_E",
     "enkf_analyze_host", "enkf_get_stats", "enkf_get_column_stats", "enkf_copy_intermediates",
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
-    "enkf_set_phase_timing", "enkf_get_phase_times",
+    "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
 )
 
 
@@ -84,6 +84,8 @@ def load(path: str = None):
         "enkf_last_error": (ctypes.c_char_p, [vp]),
         "enkf_set_phase_timing": (i32, [vp, i32]),
         "enkf_get_phase_times": (i32, [vp, vp]),
+        "enkf_analyze_noalloc": (i32, [ctypes.POINTER(Config), vp, vp, vp, vp, vp, dp, u64, u64,
+                                       vp, vp, ctypes.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,3 +228,18 @@ def draw_perturbations(seed, counter, r, N, stream=None):
     _check(load().enkf_draw_perturbations(seed, counter, _ptr(r), r.shape[0], N, _ptr(E),
                                           _stream_handle(stream)))
     return E
+
+
+def analyze_noalloc(cfg, rowptr, col, w, r, Xf, y, seed=0, counter=0, out=None, stream=None):
+    """One analysis through enkf_analyze_noalloc, which allocates no device memory (for
+    callers that must not allocate, e.g. inside stream capture). rowptr, col, w, r are
+    DEVICE tensors (int32, int32, float64, float64); returns (X_a, stats dict)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(Xf)
+    s = Stats()
+    st = load().enkf_analyze_noalloc(ctypes.byref(cfg), _ptr(rowptr), _ptr(col), _ptr(w), _ptr(r),
+                                     _ptr(Xf), _ptr(y), seed, counter, _ptr(out),
+                                     _stream_handle(stream), ctypes.byref(s))
+    return out, dict(status=STATUS.get(st, st), iters_max=s.iters_max, refinements=s.refinements,
+                     true_relres_max=s.true_relres_max, grid_blocks=s.grid_blocks)
