@@ -158,9 +158,10 @@ enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
                                   double* true_relres);
 
 /* Copy the last analysis's intermediate results to DEVICE buffers (any may be NULL):
-   d_HA [m][N] and d_D [m][N] (FP64), d_Z [m][N] (FP64 solution of S Z = D; for
-   ENKF_CGD_REDUCED the N x N solution V), d_W [N][N] (FP64, W = HA^T Z/(N-1)). Enqueued
-   on the handle's stream. */
+   d_HA [m][N] and d_D [m][N] (FP64), d_Z [m][N] (FP64 solution of S Z = D), d_W [N][N]
+   (FP64, W = HA^T Z/(N-1)). For ENKF_CGD_REDUCED, d_HA and d_D must be NULL (that variant
+   never stores them), d_Z receives the N x N CG solution V and d_W the N x N matrix
+   G = I + P^T P. Enqueued on the handle's stream. */
 enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z,
                                     double* d_W);
 

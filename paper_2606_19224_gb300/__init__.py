@@ -200,6 +200,16 @@ class Analysis:
         self.stream.synchronize()
         return HA, D, Z, W
 
+    def intermediates_reduced(self):
+        """(V, G) of the last CGD-EnKF-Reduced analysis as FP64 device tensors (N x N)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        V = torch.empty((self.N, self.N), dtype=torch.float64, device=dev)
+        G = torch.empty_like(V)
+        _check(load().enkf_copy_intermediates(self.h, None, None, _ptr(V), _ptr(G)), self.h)
+        self.stream.synchronize()
+        return V, G
+
     def set_phase_timing(self, enable=True):
         _check(load().enkf_set_phase_timing(self.h, 1 if enable else 0), self.h)
 

@@ -94,8 +94,8 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (c.N > 128) return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: N > 128");
   if (c.precision != ENKF_FP64 && c.precision != ENKF_FP32)
     return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: precision mode not built in this library");
-  if (c.variant != ENKF_CGD)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: variant not built in this library");
+  if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: unknown variant");
   if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: bad iteration limits");
   if (c.fixed_iters == 0 && !(c.tol > 0.0 && std::isfinite(c.tol)))
@@ -140,17 +140,14 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   const size_t vs = elem_size(c);
   Workspace& ws = h->ws;
   struct Alloc { void** p; size_t bytes; };
+  const bool reduced = c.variant == ENKF_CGD_REDUCED;
+  const int64_t tpart = reduced ? (int64_t)enkf::reduced_grid(h) * 2 * c.N * c.N : (int64_t)G * NE;
   std::vector<Alloc> allocs = {
       {(void**)&ws.rowptr, sizeof(int32_t) * (c.m + 1)},
       {(void**)&ws.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)},
       {(void**)&ws.w, sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)},
       {(void**)&ws.r, sizeof(double) * c.m},
-      {(void**)&ws.HA64, sizeof(double) * mN},
-      {(void**)&ws.D, sizeof(double) * mN},
-      {(void**)&ws.Z, sizeof(double) * mN},
-      {(void**)&ws.Res, vs * mN},
-      {(void**)&ws.P, vs * mN},
-      {(void**)&ws.Tpart, sizeof(double) * G * NE},
+      {(void**)&ws.Tpart, sizeof(double) * tpart},
       {(void**)&ws.Tred, sizeof(double) * NE},
       {(void**)&ws.rrpart, sizeof(double) * 2 * G * NT},
       {(void**)&ws.Wacc, sizeof(double) * c.N * c.N},
@@ -163,7 +160,14 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       {(void**)&ws.stage_Xf, vs * c.n * c.N},
       {(void**)&ws.stage_y, sizeof(double) * c.m},
   };
-  if (c.precision != ENKF_FP64) {
+  if (!reduced) {
+    allocs.push_back({(void**)&ws.HA64, sizeof(double) * mN});
+    allocs.push_back({(void**)&ws.D, sizeof(double) * mN});
+    allocs.push_back({(void**)&ws.Z, sizeof(double) * mN});
+    allocs.push_back({(void**)&ws.Res, vs * mN});
+    allocs.push_back({(void**)&ws.P, vs * mN});
+  }
+  if (!reduced && c.precision != ENKF_FP64) {
     allocs.push_back({(void**)&ws.HA32, sizeof(float) * mN});
     allocs.push_back({(void**)&ws.r32, sizeof(float) * c.m});
     allocs.push_back({(void**)&ws.B, vs * mN});
@@ -206,14 +210,17 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   if (a != b && a < b + xb && b < a + xb)
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: X_a partially overlaps X_f");
   cudaError_t e = cudaSuccess;
+  const bool reduced = c.variant == ENKF_CGD_REDUCED;
   if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
-  if (e == cudaSuccess) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
+  if (e == cudaSuccess && !reduced) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
   if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
-  if (e == cudaSuccess) e = enkf::launch_solve(h);
+  if (e == cudaSuccess)
+    e = reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter) : enkf::launch_solve(h);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
   if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
-  if (e == cudaSuccess) e = enkf::launch_update(h, d_Xf, d_Xa);
+  if (e == cudaSuccess)
+    e = reduced ? enkf::launch_update_product(h, d_Xf, d_Xa) : enkf::launch_update(h, d_Xf, d_Xa);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: update launch");
   if (h->timing) {
     e = cudaEventRecord(h->ev[3], h->stream);
@@ -306,6 +313,14 @@ enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, do
   const auto& c = h->cfg;
   const size_t mN = sizeof(double) * c.m * c.N;
   cudaError_t e = cudaSuccess;
+  if (c.variant == ENKF_CGD_REDUCED) {
+    if (d_HA || d_D) return fail(h, ENKF_ERR_INVALID_ARG, "copy_intermediates: the reduced variant keeps no HA or D");
+    const size_t nn = sizeof(double) * c.N * c.N;
+    if (d_Z) e = cudaMemcpyAsync(d_Z, h->ws.W, nn, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && d_W) e = cudaMemcpyAsync(d_W, h->ws.Tred, nn, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy_intermediates");
+    return ENKF_OK;
+  }
   if (d_HA) e = cudaMemcpyAsync(d_HA, h->ws.HA64, mN, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess && d_D) e = cudaMemcpyAsync(d_D, h->ws.D, mN, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess && d_Z) e = cudaMemcpyAsync(d_Z, h->ws.Z, mN, cudaMemcpyDeviceToDevice, h->stream);

@@ -167,6 +167,12 @@ cudaError_t plan_solve(enkf_handle_s* h);
 cudaError_t launch_solve(enkf_handle_s* h);
 cudaError_t launch_convert_r(enkf_handle_s* h);
 cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa);
+cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa);
+// kernels_reduced.cu: Gram pass + N x N CG of CGD-EnKF-Reduced; V lands in ws.W,
+// G in ws.Tred, M in ws.Wacc; the CTA partials use ws.Tpart ([reduced_grid][2 N N]).
+int reduced_grid(const enkf_handle_s* h);
+cudaError_t launch_reduced(enkf_handle_s* h, const void* Xf, const double* y, const double* E,
+                           int emode, uint64_t seed, uint64_t counter);
 cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r,
                                       int64_t m, int N, double* E, cudaStream_t s);
 }  // namespace enkf

@@ -798,8 +798,10 @@ __global__ void convert_r_kernel(const double* __restrict__ r, float* __restrict
 }
 
 // ------------------------------------------------------------------ K4: final update
-// X_a = X_f + (X_f - xbar 1^T) W, row tiles of TRB rows staged in shared memory.
-template <typename VT, int NT>
+// MODE 0: X_a = X_f + (X_f - xbar 1^T) W (CGD-EnKF, Fig. 2 / Algorithm 1);
+// MODE 1: X_a = X_f W (CGD-EnKF-Reduced, Algorithm 2 with W = V).
+// Row tiles of TRB rows staged in shared memory.
+template <typename VT, int NT, int MODE = 0>
 __global__ void __launch_bounds__(kThreads) update_kernel(const VT* Xf, VT* Xa,
                                                           const double* __restrict__ W,
                                                           int64_t n, int N) {
@@ -840,9 +842,11 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const VT* Xf, VT* Xa,
 #pragma unroll
       for (int y = 0; y < 4; ++y) xf[x][y] = sX[(r0 + x) * LD + j0 + y];
     __syncthreads();
-    for (int e = t; e < TRB * NT; e += kThreads) {
-      const int ii = e / NT, k = e % NT;
-      if (k < N) sX[ii * LD + k] -= smean[ii];
+    if (MODE == 0) {
+      for (int e = t; e < TRB * NT; e += kThreads) {
+        const int ii = e / NT, k = e % NT;
+        if (k < N) sX[ii * LD + k] -= smean[ii];
+      }
     }
     __syncthreads();
     VT acc[4][4];
@@ -867,7 +871,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const VT* Xf, VT* Xa,
       if (i < n && j0 < N) {
         VT o[4];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) o[y] = xf[x][y] + acc[x][y];
+        for (int y = 0; y < 4; ++y) o[y] = MODE == 0 ? xf[x][y] + acc[x][y] : acc[x][y];
         st4<VT>(Xa + i * N, j0, N, vec, o);
       }
     }
@@ -982,7 +986,8 @@ cudaError_t launch_solve(enkf_handle_s* h) {
                                      h->launch.smem, h->stream);
 }
 
-cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
+template <int MODE>
+static cudaError_t launch_update_mode(enkf_handle_s* h, const void* Xf, void* Xa) {
   const auto& c = h->cfg;
   const int NT = h->launch.NT;
   const bool fp64 = c.precision == ENKF_FP64;
@@ -991,10 +996,10 @@ cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
   void* fn;
   int smem;
   if (fp64) {
-    fn = NT == 32 ? (void*)update_kernel<double, 32> : NT == 64 ? (void*)update_kernel<double, 64> : (void*)update_kernel<double, 128>;
+    fn = NT == 32 ? (void*)update_kernel<double, 32, MODE> : NT == 64 ? (void*)update_kernel<double, 64, MODE> : (void*)update_kernel<double, 128, MODE>;
     smem = NT == 32 ? update_smem_bytes<double, 32>() : NT == 64 ? update_smem_bytes<double, 64>() : update_smem_bytes<double, 128>();
   } else {
-    fn = NT == 32 ? (void*)update_kernel<float, 32> : NT == 64 ? (void*)update_kernel<float, 64> : (void*)update_kernel<float, 128>;
+    fn = NT == 32 ? (void*)update_kernel<float, 32, MODE> : NT == 64 ? (void*)update_kernel<float, 64, MODE> : (void*)update_kernel<float, 128, MODE>;
     smem = NT == 32 ? update_smem_bytes<float, 32>() : NT == 64 ? update_smem_bytes<float, 64>() : update_smem_bytes<float, 128>();
   }
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1004,6 +1009,14 @@ cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
   int N = c.N;
   void* args[] = {const_cast<void**>(&Xf), &Xa, const_cast<double**>(&W), &n, &N};
   return cudaLaunchKernel(fn, dim3(tiles), dim3(kThreads), args, smem, h->stream);
+}
+
+cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
+  return launch_update_mode<0>(h, Xf, Xa);
+}
+
+cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa) {
+  return launch_update_mode<1>(h, Xf, Xa);
 }
 
 cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r, int64_t m,
