@@ -190,7 +190,8 @@ def run_ours(args):
     seed = args.seed + 1000 * rank
     p = synth.workload(WORKLOAD, seed, dtype=np.float32)
     n, m, N = p.n, p.m, p.N
-    an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8)
+    an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8,
+                       precondition=args.precondition)
     an.set_phase_timing(True)
     Xf = torch.from_numpy(p.Xf).to(dev)
     y = torch.from_numpy(p.y).to(dev)
@@ -256,6 +257,21 @@ def run_ours(args):
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
            "d2h_bytes_per_step": int(Xo.numel() * 4)}
 
+    # the same FP32 path with plain (unpreconditioned) CG, for reference
+    an_plain = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8,
+                             precondition=0)
+    an_plain.analyze(Xf, y, seed, 0, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.fp64_steps):
+        an_plain.analyze(Xf, y, seed, k, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain32_ms = e0.elapsed_time(e1) / args.fp64_steps
+    s_plain = an_plain.stats()
+    an_plain.close()
+
     # plain FP64 GPU CG on the same problem (the comparison point)
     p64 = synth.workload(WORKLOAD, seed, dtype=np.float64)
     an64 = enkf.Analysis(n, m, N, p64.rowptr, p64.col, p64.w, p64.r, precision="fp64", tol=1e-8)
@@ -287,7 +303,7 @@ def run_ours(args):
     mN = m * N
     it_avg = float(np.mean(iters))
     ref_avg = float(np.mean(refines))
-    b_iter = 2 * mN * 4 + 8 * mN * 4 + 2 * m * 8          # FP32 HA twice, r/p/x vectors, r twice
+    b_iter = 2 * mN * 4 + 8 * mN * 4 + 2 * m * 8          # per CG step (the plain CG count)
     b_ref = 56 * mN                                       # FP64 refresh: HA64 x2, Z, D, X, B
     alg_bytes = it_avg * b_iter + ref_avg * b_ref
     solve_avg_ms = float(np.mean(solve_ms))
@@ -305,12 +321,16 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
-                       "precision": "fp32 CG + fp64 residual refresh", "l2": "flushed between steps",
-                       "status": last_status["status"]},
+                       "precision": "fp32 CG + fp64 residual refresh",
+                       "solver": "CG preconditioned by R" if args.precondition else "plain CG",
+                       "l2": "flushed between steps", "status": last_status["status"]},
             "error": {"rel_frobenius_vs_fp64_oracle": err, "fp64_cg_rel_frobenius": err64,
                       "true_relres_max": last_status["true_relres_max"]},
             "fp64_cg": {"ms_per_step": fp64_ms, "value": 1e3 / fp64_ms, "unit": UNIT,
-                        "iters": s64["iters_max"], "speedup_of_value": value / (ws * 1e3 / fp64_ms)},
+                        "iters": s64["iters_max"], "speedup_of_value": value / (ws * 1e3 / fp64_ms),
+                        "solver": "plain CG, FP64 throughout"},
+            "fp32_plain_cg": {"ms_per_step": plain32_ms, "value": 1e3 / plain32_ms, "unit": UNIT,
+                              "iters": s_plain["iters_max"], "refinements": s_plain["refinements"]},
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
@@ -329,6 +349,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precondition", type=int, default=1,
+                    help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

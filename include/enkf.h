@@ -93,7 +93,10 @@ typedef struct enkf_config {
   int32_t true_residual;  /* 1: FP64 true residual check (and W = HA^T Z/(N-1) from the
                              final Z) after an FP64 solve; always on in ENKF_FP32        */
   int32_t grid_blocks;    /* 0: automatic persistent-grid size; > 0: use this many CTAs  */
-  int32_t reserved[7];    /* must be zero                                                */
+  int32_t precondition;   /* ENKF_CGD: 0 plain CG (the paper's method); 1 CG preconditioned
+                             by R (Jacobi), which ends within about N steps because
+                             R^-1/2 S R^-1/2 is the identity plus a rank < N term        */
+  int32_t reserved[6];    /* must be zero                                                */
 } enkf_config;
 
 typedef struct enkf_stats {
@@ -118,7 +121,7 @@ enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t 
    observation operator, nnz = h_rowptr[m]) and r_diag[m] (> 0, finite) are HOST arrays
    and are copied to the device. cuda_stream is a cudaStream_t (NULL: the legacy default
    stream); every later call on the handle is ordered on it. Allocates all workspace
-   (about 44 m N bytes in ENKF_FP32 mode at N <= 128, 40 m N in ENKF_FP64 mode, plus
+   (about 48 m N bytes in ENKF_FP32 mode at N <= 128, 48 m N in ENKF_FP64 mode, plus
    O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad shape, column index outside [0, n),
    decreasing rowptr, r <= 0), ENKF_ERR_UNSUPPORTED (N > 128, unknown precision or
    variant), ENKF_ERR_OOM, ENKF_ERR_CUDA. *out is NULL on error. */
@@ -172,13 +175,21 @@ enkf_status enkf_draw_perturbations(uint64_t seed, uint64_t counter, const doubl
 
 /* Per-kernel timing of later analyses (enable != 0) with CUDA events recorded on the
    handle's stream around the three kernels of an analysis; off by default. Creating the
-   events happens here, not in the analysis calls. */
+   events happens here, not in the analysis calls. enable >= 2 also turns on in-kernel phase
+   timers of the persistent solve (read with enkf_get_solve_phases). */
 enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable);
 
 /* Synchronise and return the last timed analysis's kernel durations in milliseconds:
    ms[0] innovations (gather, anomalies, perturbations), ms[1] the persistent CG solve,
    ms[2] the ensemble update. ENKF_ERR_INVALID_ARG if timing is off or nothing was timed. */
 enkf_status enkf_get_phase_times(enkf_handle h, float* ms);
+
+/* Synchronise and return the in-kernel phase timers of the last timed solve, measured by
+   CTA 0 with the global nanosecond timer, in microseconds: us[0] set-up reductions,
+   us[1] fused CG passes, us[2] first grid barrier, us[3] cross-CTA reduction, us[4] second
+   grid barrier, us[5] scalar recurrences and staging, us[6] FP64 refreshes, us[7] unused.
+   ENKF_ERR_INVALID_ARG unless enkf_set_phase_timing(h, 2) preceded a timed analysis. */
+enkf_status enkf_get_solve_phases(enkf_handle h, double* us);
 
 /* One analysis step that allocates no device memory, for callers that cannot call
    cudaMalloc when they need it: code running while a stream is captured into a CUDA graph,
@@ -190,7 +201,7 @@ enkf_status enkf_get_phase_times(enkf_handle h, float* ms);
    they are not validated, so the caller guarantees 0 <= col < n and r > 0), and cfg must
    use ENKF_CGD with ENKF_FP64 or ENKF_FP32. All working memory lives in one fixed 16 MiB
    array in the library's device memory (held by every GPU that loads the library until the
-   process exits); problems whose working memory (about 40 m N bytes in FP64 mode, 44 m N in
+   process exits); problems whose working memory (about 48 m N bytes in FP64 mode, 48 m N in
    FP32 mode, plus the CG partials) exceeds it are rejected with ENKF_ERR_UNSUPPORTED and a
    one-line message on stderr. The first call on each device looks up the array's device
    address; make that first call before any stream capture. Every call shares the array, so

@@ -24,6 +24,7 @@ EXPORTS = (
     "enkf_analyze_host", "enkf_get_stats", "enkf_get_column_stats", "enkf_copy_intermediates",
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
     "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
+    "enkf_get_solve_phases",
 )
 
 
@@ -35,7 +36,7 @@ class Config(ctypes.Structure):
         ("inner_tol", ctypes.c_double), ("refresh_every", ctypes.c_int32),
         ("perturb_obs", ctypes.c_int32), ("warm_start", ctypes.c_int32),
         ("true_residual", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("precondition", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -84,6 +85,7 @@ def load(path: str = None):
         "enkf_last_error": (ctypes.c_char_p, [vp]),
         "enkf_set_phase_timing": (i32, [vp, i32]),
         "enkf_get_phase_times": (i32, [vp, vp]),
+        "enkf_get_solve_phases": (i32, [vp, vp]),
         "enkf_analyze_noalloc": (i32, [ctypes.POINTER(Config), vp, vp, vp, vp, vp, dp, u64, u64,
                                        vp, vp, ctypes.POINTER(Stats)]),
     }
@@ -210,8 +212,15 @@ class Analysis:
         self.stream.synchronize()
         return V, G
 
-    def set_phase_timing(self, enable=True):
-        _check(load().enkf_set_phase_timing(self.h, 1 if enable else 0), self.h)
+    def set_phase_timing(self, enable=True, phases=False):
+        _check(load().enkf_set_phase_timing(self.h, (2 if phases else 1) if enable else 0), self.h)
+
+    def solve_phases(self):
+        """In-kernel phase timers (us) of the last timed solve: set-up, fused passes, barrier 1,
+        reduction, barrier 2, scalars, FP64 refreshes."""
+        us = (ctypes.c_double * 8)()
+        _check(load().enkf_get_solve_phases(self.h, us), self.h)
+        return dict(zip(("setup", "pass", "barrier1", "reduce", "barrier2", "scalars", "refresh"), us[:7]))
 
     def phase_times(self):
         """(innovations, solve, update) kernel milliseconds of the last timed analysis."""

@@ -27,7 +27,7 @@ enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
 
 void free_workspace(Workspace& ws) {
   void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.D, ws.Z, ws.B, ws.X,
-                  ws.Res, ws.P, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
+                  ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -103,7 +103,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (c.precision == ENKF_FP32 && !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: inner_tol must be in (0, 1)");
   if (c.grid_blocks < 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: grid_blocks < 0");
-  for (int q = 0; q < 7; ++q)
+  if (c.precondition != 0 && c.precondition != 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: precondition must be 0 or 1");
+  for (int q = 0; q < 6; ++q)
     if (c.reserved[q]) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: reserved fields must be 0");
   // observation operator and R
   if (h_rowptr[0] != 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr[0] != 0");
@@ -136,7 +138,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   }
   const int64_t mN = c.m * c.N;
   const int G = h->launch.G, NT = h->launch.NT;
-  const int64_t NE = (int64_t)c.N * c.N + c.N;
+  const int64_t NE = (int64_t)c.N * c.N + 2 * c.N;
   const size_t vs = elem_size(c);
   Workspace& ws = h->ws;
   struct Alloc { void** p; size_t bytes; };
@@ -159,8 +161,10 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       {(void**)&ws.bar, sizeof(unsigned) * 4},
       {(void**)&ws.stage_Xf, vs * c.n * c.N},
       {(void**)&ws.stage_y, sizeof(double) * c.m},
+      {(void**)&ws.prof, sizeof(unsigned long long) * 8},
   };
   if (!reduced) {
+    allocs.push_back({(void**)&ws.Sv, vs * mN});
     allocs.push_back({(void**)&ws.HA64, sizeof(double) * mN});
     allocs.push_back({(void**)&ws.D, sizeof(double) * mN});
     allocs.push_back({(void**)&ws.Z, sizeof(double) * mN});
@@ -349,7 +353,19 @@ enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable) {
     }
   }
   h->timing = enable != 0;
+  h->prof_enabled = enable >= 2;
   h->timed = false;
+  return ENKF_OK;
+}
+
+enkf_status enkf_get_solve_phases(enkf_handle h, double* us) {
+  if (!h || !us) return fail(h, ENKF_ERR_INVALID_ARG, "get_solve_phases: NULL argument");
+  if (!h->prof_enabled || !h->timed) return fail(h, ENKF_ERR_INVALID_ARG, "get_solve_phases: phase timers off");
+  unsigned long long ns[8];
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(ns, h->ws.prof, sizeof(ns), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_solve_phases");
+  for (int q = 0; q < 8; ++q) us[q] = 1e-3 * (double)ns[q];
   return ENKF_OK;
 }
 

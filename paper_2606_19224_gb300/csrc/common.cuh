@@ -122,8 +122,9 @@ struct Workspace {
   void* X = nullptr;            // [m][N]   inner iterate (FP32 mode)
   void* Res = nullptr;          // [m][N]
   void* P = nullptr;            // [m][N]
-  double* Tpart = nullptr;      // [G][N*N+N]
-  double* Tred = nullptr;       // [N*N+N]
+  void* Sv = nullptr;           // [m][N]   S p, carried by the CG recurrences
+  double* Tpart = nullptr;      // [G][N*N+2N]
+  double* Tred = nullptr;       // [N*N+2N]
   double* rrpart = nullptr;     // [2][G][NT]
   double* Wacc = nullptr;       // [N][N]
   double* W = nullptr;          // [N][N]
@@ -134,6 +135,7 @@ struct Workspace {
   unsigned* bar = nullptr;      // [4]: barrier counter, abort flag, spare
   void* stage_Xf = nullptr;     // host-API staging [n][N]
   double* stage_y = nullptr;    // [m]
+  unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
 };
 
 struct SolveLaunch {
@@ -156,6 +158,7 @@ struct enkf_handle_s {
   bool has_result = false;
   bool timing = false;
   bool timed = false;
+  bool prof_enabled = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 

@@ -35,21 +35,36 @@ template <> struct Tile<32> { static constexpr int MA = 4, TRA = 32, TRB = 128; 
 template <> struct Tile<64> { static constexpr int MA = 4, TRA = 32, TRB = 64; };
 template <> struct Tile<128> { static constexpr int MA = 8, TRA = 16, TRB = 32; };
 
-// shared scalars: 8 FP64 arrays, 4 int arrays, 2 VT-sized (<= 8 B) arrays, each of length NT
-template <int NT> __host__ __device__ constexpr int scalar_bytes() { return NT * 8 * 8 + NT * 4 * 4 + NT * 8 * 2; }
-template <int NT> __host__ __device__ constexpr int union_bytes() {
+// Fused CG pass tile: TR rows of HA, r, p, s, x staged per step; MR rows per thread in the
+// update (pass-B mapping, NT/4 column groups of 4).
+template <typename CT, int NT> struct FTile;
+template <int NT> struct FTile<float, NT> { static constexpr int MR = 4, TR = (1024 / NT) * 4; };
+template <> struct FTile<double, 32> { static constexpr int MR = 2, TR = 64; };
+template <> struct FTile<double, 64> { static constexpr int MR = 2, TR = 32; };
+template <> struct FTile<double, 128> { static constexpr int MR = 1, TR = 8; };
+
+// shared scalars: 12 FP64 arrays, 4 int arrays, 2 VT-sized (<= 8 B) arrays, each of length NT
+template <int NT> __host__ __device__ constexpr int scalar_bytes() { return NT * 8 * 12 + NT * 4 * 4 + NT * 8 * 2; }
+template <int NT> __host__ __device__ constexpr int refresh_union_bytes() {
   constexpr int MA = Tile<NT>::MA, TRA = Tile<NT>::TRA, TRB = Tile<NT>::TRB;
   constexpr int NG = NT / MA, RG = kThreads / (NG * NG);
   constexpr int a = 2 * TRA * NT * 8 + TRA * 8;
   constexpr int a2 = RG * NT * NT * 8;
-  constexpr int a3 = RG * NG * NT * 8;
+  constexpr int a3 = 2 * RG * NG * NT * 8;
   constexpr int b = NT * (NT + 2) * 8 + TRB * (NT + 2) * 8;
   constexpr int m1 = a > a2 ? a : a2;
   constexpr int m2 = m1 > a3 ? m1 : a3;
   return m2 > b ? m2 : b;
 }
-template <int NT> __host__ __device__ constexpr int solve_smem_bytes() {
-  return scalar_bytes<NT>() + kThreads * 8 + union_bytes<NT>();
+template <typename CT, int NT> __host__ __device__ constexpr int passF_bytes() {
+  constexpr int LD = NT + 16 / (int)sizeof(CT), TR = FTile<CT, NT>::TR;
+  return NT * LD * (int)sizeof(CT) + 5 * TR * LD * (int)sizeof(CT) + TR * (int)sizeof(CT);
+}
+template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
+  return refresh_union_bytes<NT>() > passF_bytes<VT, NT>() ? refresh_union_bytes<NT>() : passF_bytes<VT, NT>();
+}
+template <typename VT, int NT> __host__ __device__ constexpr int solve_smem_bytes() {
+  return scalar_bytes<NT>() + kThreads * 8 + union_bytes<VT, NT>();
 }
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -173,9 +188,10 @@ __device__ __forceinline__ void reduce_slice(const double* __restrict__ part, in
 
 // ------------------------------------------------------------------ pass A
 // out[k*N + j] = sum_i HA[i][k] V[i][j] over the CTA's rows and (want_s)
-// out[N*N + j] = sum_i r_i V[i][j]^2, where pro(i, j0, v) produces (and may store) the four
-// values V[i][j0..j0+3]. Per-thread partial sums are kept in CT.
-template <typename CT, int NT, class Pro>
+// out[N*N + j] = sum_i r_i V[i][j]^2 and out[N*N + N + j] = sum_i V[i][j]^2, where
+// pro(i, j0, v) produces (and may store) the four values V[i][j0..j0+3]. Per-thread partial
+// sums are kept in CT.
+template <typename CT, int NT, class Pro, bool PC = false>
 __device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, int64_t row1,
                                       int N, const CT* __restrict__ rv, bool want_s, Pro& pro,
                                       unsigned char* uni, double* __restrict__ out) {
@@ -192,9 +208,9 @@ __device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, i
   for (int x = 0; x < MA; ++x)
 #pragma unroll
     for (int y = 0; y < MA; ++y) acc[x][y] = CT(0);
-  CT sacc[MA];
+  CT sacc[MA], gacc[MA];
 #pragma unroll
-  for (int y = 0; y < MA; ++y) sacc[y] = CT(0);
+  for (int y = 0; y < MA; ++y) { sacc[y] = CT(0); gacc[y] = CT(0); }
 
   for (int64_t i0 = row0; i0 < row1; i0 += TRA) {
     __syncthreads();
@@ -224,10 +240,14 @@ __device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, i
       for (int x = 0; x < MA; ++x)
 #pragma unroll
         for (int y = 0; y < MA; ++y) acc[x][y] = fma(a[x], v[y], acc[x][y]);
-      if (want_s && ((ii / RG) % NG) == tk) {
+      if (((ii / RG) % NG) == tk) {
         const CT ri = sR[ii];
 #pragma unroll
-        for (int y = 0; y < MA; ++y) sacc[y] = fma(ri * v[y], v[y], sacc[y]);
+        for (int y = 0; y < MA; ++y) {
+          sacc[y] = fma(ri * v[y], v[y], sacc[y]);
+          const CT gv = PC ? ri * v[y] : v[y];   // preconditioned: v = b / r, so r v = b
+          gacc[y] = fma(gv, gv, gacc[y]);
+        }
       }
     }
   }
@@ -261,12 +281,19 @@ __device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, i
   }
   __syncthreads();
 #pragma unroll
-  for (int y = 0; y < MA; ++y) red[(g * NG + tk) * NT + j0 + y] = (double)sacc[y];
+  for (int y = 0; y < MA; ++y) {
+    red[(g * NG + tk) * NT + j0 + y] = (double)sacc[y];
+    red[RG * NG * NT + (g * NG + tk) * NT + j0 + y] = (double)gacc[y];
+  }
   __syncthreads();
   if (t < N) {
-    double s = 0.0;
-    for (int q = 0; q < RG * NG; ++q) s += red[q * NT + t];
+    double s = 0.0, q2 = 0.0;
+    for (int q = 0; q < RG * NG; ++q) {
+      s += red[q * NT + t];
+      q2 += red[RG * NG * NT + q * NT + t];
+    }
     out[N * N + t] = want_s ? s : 0.0;
+    out[N * N + N + t] = q2;
   }
   __syncthreads();
 }
@@ -377,64 +404,247 @@ __device__ __forceinline__ void stage_T(const double* __restrict__ Tred, int N, 
   __syncthreads();
 }
 
-// ------------------------------------------------------------------ element operators
-// CG pass A: P = Res + beta P (P = Res on the first step of an inner solve; frozen columns
-// keep P).
-template <typename VT>
-struct ProCG {
-  VT* P;
-  const VT* Res;
-  const VT* beta;   // shared, VT copy of beta_j (0 beyond N)
-  const int* active;
-  int N;
-  bool first;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, VT (&v)[4], bool vec) {
-    VT res[4];
-    ld4<VT>(res, Res + i * N, j0, N, vec);
-    if (first) {
+// ------------------------------------------------------------------ fused CG pass
+// Chronopoulos-Gear form of CG (algebraically the Hestenes-Stiefel recurrences): with
+// s = S p carried along, u = S r, gamma = (r, r) and delta = (r, S r) =
+// ||HA^T r||^2/(N-1) + sum_i r_i r_i^2, a step needs only one reduction:
+//   beta = gamma/gamma_old, alpha = gamma / (delta - beta gamma/alpha_old),
+//   p = r + beta p, s = u + beta s, x += alpha p, r -= alpha s.
+// One pass over the CTA's rows does the step and, on the same shared-memory tile, the
+// partial HA^T r_new, sum r_i r_new^2 and sum r_new^2 of the next step: out = [T | sig | gam].
+//
+// With the Jacobi preconditioner M = R (PC), the step is the preconditioned form with
+// z = R^{-1} r: w = S z = HA (HA^T z)/(N-1) + r, gamma = (r, z), delta = (z, S z) =
+// ||HA^T z||^2/(N-1) + gamma, p = z + beta p, s = w + beta s, and the next partials are
+// [HA^T z_new | (r_new, z_new) | (r_new, r_new)].
+template <typename CT, int NT, bool PC = false>
+__device__ __forceinline__ void passF(const CT* __restrict__ HA, int64_t row0, int64_t row1, int N,
+                                      CT* X, CT* Res, CT* P, CT* Sv, const CT* __restrict__ rv,
+                                      const CT* sT, const CT* alpha, const CT* beta, CT vinv,
+                                      unsigned char* tiles, double* __restrict__ out) {
+  constexpr int LD = NT + 16 / (int)sizeof(CT);
+  constexpr int MR = FTile<CT, NT>::MR, TR = FTile<CT, NT>::TR, C4 = NT / 4;
+  constexpr int NJ = NT / 4, NI = kThreads / NJ;
+  static_assert(NI * MR == TR, "fused tile");
+  constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
+  CT* sH = reinterpret_cast<CT*>(tiles);
+  CT* sR = sH + TR * LD;
+  CT* sP = sR + TR * LD;
+  CT* sS = sP + TR * LD;
+  CT* sX = sS + TR * LD;
+  CT* sRv = sX + TR * LD;
+  const int t = threadIdx.x;
+  const int tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * MR;                  // update map
+  const int g = t / TPG, u = t % TPG, gj = u % NG, gk = u / NG, k0 = gk * MA, ja = gj * MA;  // Gram map
+  const bool vec = (N & 3) == 0;
+  CT accT[MA][MA];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) v[y] = res[y];
-    } else {
-      VT p[4];
-      ld4<VT>(p, P + i * N, j0, N, vec);
+  for (int x = 0; x < MA; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) v[y] = active[j0 + y] ? fma(beta[j0 + y], p[y], res[y]) : p[y];
-    }
-    st4<VT>(P + i * N, j0, N, vec, v);
-  }
-};
+    for (int y = 0; y < MA; ++y) accT[x][y] = CT(0);
+  CT sig[4] = {CT(0), CT(0), CT(0), CT(0)}, gam[4] = {CT(0), CT(0), CT(0), CT(0)};
+  CT al[4], be[4];
+#pragma unroll
+  for (int y = 0; y < 4; ++y) { al[y] = alpha[j0 + y]; be[y] = beta[j0 + y]; }
 
-// CG pass B: q = HA T/(N-1) + r p; x += alpha p; res -= alpha q; rr += res^2.
-template <typename VT>
-struct EpiCG {
+  for (int64_t i0 = row0; i0 < row1; i0 += TR) {
+    __syncthreads();
+#pragma unroll
+    for (int c = t; c < TR * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      CT a[4] = {CT(0), CT(0), CT(0), CT(0)}, rr[4] = {CT(0), CT(0), CT(0), CT(0)};
+      CT pp[4] = {CT(0), CT(0), CT(0), CT(0)}, ss[4] = {CT(0), CT(0), CT(0), CT(0)};
+      CT xx[4] = {CT(0), CT(0), CT(0), CT(0)};
+      if (i < row1 && c0 < N) {
+        ld4<CT>(a, HA + i * N, c0, N, vec);
+        ld4<CT>(rr, Res + i * N, c0, N, vec);
+        ld4<CT>(pp, P + i * N, c0, N, vec);
+        ld4<CT>(ss, Sv + i * N, c0, N, vec);
+        ld4<CT>(xx, X + i * N, c0, N, vec);
+      }
+      store_vec4<CT>(sH + ii * LD + c0, a);
+      store_vec4<CT>(sR + ii * LD + c0, rr);
+      store_vec4<CT>(sP + ii * LD + c0, pp);
+      store_vec4<CT>(sS + ii * LD + c0, ss);
+      store_vec4<CT>(sX + ii * LD + c0, xx);
+    }
+    if (t < TR) {
+      const int64_t i = i0 + t;
+      sRv[t] = i < row1 ? rv[i] : CT(0);
+    }
+    __syncthreads();
+    // u = HA T / (N-1) + r_i r
+    CT acc[MR][4];
+#pragma unroll
+    for (int x = 0; x < MR; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = CT(0);
+    if (N == NT) {
+#pragma unroll 8
+      for (int k = 0; k < NT; ++k) {
+        CT a[MR], bv[4];
+#pragma unroll
+        for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * LD + k];
+        load_vec<CT>(bv, sT + k * LD + j0, 4);
+#pragma unroll
+        for (int x = 0; x < MR; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < N; ++k) {
+        CT a[MR], bv[4];
+#pragma unroll
+        for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * LD + k];
+        load_vec<CT>(bv, sT + k * LD + j0, 4);
+#pragma unroll
+        for (int x = 0; x < MR; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+      }
+    }
+    // the CG step on the thread's MR x 4 fragment
+#pragma unroll
+    for (int x = 0; x < MR; ++x) {
+      const int row = r0 + x;
+      const int64_t i = i0 + row;
+      if (i < row1 && j0 < N) {
+        const CT ri = sRv[row];
+        CT rv4[4], pv4[4], sv4[4], xv4[4], pn[4], sn[4], xn[4], rn[4];
+        load_vec<CT>(rv4, sR + row * LD + j0, 4);
+        load_vec<CT>(pv4, sP + row * LD + j0, 4);
+        load_vec<CT>(sv4, sS + row * LD + j0, 4);
+        load_vec<CT>(xv4, sX + row * LD + j0, 4);
+        const CT rinv = PC ? CT(1) / ri : CT(0);
+        CT zn[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          // plain: z = r, w = S r = HA T/(N-1) + R r; preconditioned: z = r / R, w = HA T/(N-1) + r
+          const CT zz = PC ? rv4[y] * rinv : rv4[y];
+          const CT ww = PC ? fma(acc[x][y], vinv, rv4[y]) : fma(acc[x][y], vinv, ri * rv4[y]);
+          // beta == 0 (first step, frozen columns) selects p = z, s = w without reading the
+          // old p, s (which may hold anything, including NaN bit patterns)
+          pn[y] = be[y] == CT(0) ? zz : fma(be[y], pv4[y], zz);
+          sn[y] = be[y] == CT(0) ? ww : fma(be[y], sv4[y], ww);
+          xn[y] = fma(al[y], pn[y], xv4[y]);
+          rn[y] = fma(-al[y], sn[y], rv4[y]);
+          zn[y] = PC ? rn[y] * rinv : rn[y];
+          sig[y] = PC ? fma(rn[y], zn[y], sig[y]) : fma(ri * rn[y], rn[y], sig[y]);
+          gam[y] = fma(rn[y], rn[y], gam[y]);
+        }
+        st4<CT>(P + i * N, j0, N, vec, pn);
+        st4<CT>(Sv + i * N, j0, N, vec, sn);
+        st4<CT>(X + i * N, j0, N, vec, xn);
+        st4<CT>(Res + i * N, j0, N, vec, rn);
+        store_vec4<CT>(sR + row * LD + j0, zn);
+      }
+    }
+    __syncthreads();
+    // next step's partial Gram HA^T r_new on the same tile
+    const int nrows = (int)imin64(TR, row1 - i0);
+    for (int ii = g; ii < nrows; ii += RG) {
+      CT a[MA], v[MA];
+      load_vec<CT>(a, sH + ii * LD + k0, MA);
+      load_vec<CT>(v, sR + ii * LD + ja, MA);
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) accT[x][y] = fma(a[x], v[y], accT[x][y]);
+    }
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(tiles);
+  if (RG > 1) {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + ja + y] = (double)accT[x][y];
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) {
+          const int k = k0 + x, j = ja + y;
+          double s = 0.0;
+          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
+          if (k < N && j < N) out[k * N + j] = s;
+        }
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) {
+        const int k = k0 + x, j = ja + y;
+        if (k < N && j < N) out[k * N + j] = (double)accT[x][y];
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    red[ti * NT + j0 + y] = (double)sig[y];
+    red[NI * NT + ti * NT + j0 + y] = (double)gam[y];
+  }
+  __syncthreads();
+  if (t < N) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < NI; ++q) {
+      a += red[q * NT + t];
+      b += red[NI * NT + q * NT + t];
+    }
+    out[N * N + t] = a;
+    out[N * N + N + t] = b;
+  }
+  __syncthreads();
+}
+
+// Stage the reduced N x N matrix T (FP64 in global, first N*N entries of Tred) into shared
+// memory as CT with stride NT + 16/sizeof(CT), zero-padded, and return the FP64 column norms
+// ||T_:j||^2 in tn2[j] (thread j owns column j's sum over its rows; fixed order).
+template <typename CT, int NT>
+__device__ __forceinline__ void stage_T_norms(const double* __restrict__ Tred, int N, CT* sT,
+                                              double* tn2, double* scratch) {
+  constexpr int LD = NT + 16 / (int)sizeof(CT), L = kThreads / NT;
+  const int t = threadIdx.x, j = t % NT, k0 = t / NT;
+  double nrm = 0.0;
+  for (int k = k0; k < NT; k += L) {
+    const double v = (k < N && j < N) ? __ldcg(Tred + k * N + j) : 0.0;
+    sT[k * LD + j] = (CT)v;
+    nrm = fma(v, v, nrm);
+  }
+  for (int k = t; k < NT * (LD - NT); k += kThreads) sT[(k / (LD - NT)) * LD + NT + k % (LD - NT)] = CT(0);
+  scratch[t] = nrm;
+  __syncthreads();
+  if (t < NT) {
+    double s = 0.0;
+    for (int q = 0; q < L; ++q) s += scratch[q * NT + t];
+    tn2[t] = s;
+  }
+  __syncthreads();
+}
+
+// Inner-solve set-up pass A: Res = B, X = 0, and V = B (preconditioned: V = B / r) for
+// the first reduction.
+template <typename VT, bool PC>
+struct ProSetup {
+  const VT* B;
   VT* X;
   VT* Res;
-  const VT* P;
   const VT* rv;
-  const VT* alpha;  // shared, VT copy of alpha_j (0 for frozen columns and beyond N)
-  VT vinv;
   int N;
-  static constexpr bool kPrefetch = sizeof(VT) == 4;
-  struct Frag { VT p[4], x[4], res[4]; VT ri; };
-  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
-    ld4<VT>(f.p, P + i * N, j0, N, vec);
-    ld4<VT>(f.x, X + i * N, j0, N, vec);
-    ld4<VT>(f.res, Res + i * N, j0, N, vec);
-    f.ri = rv[i];
-  }
-  __device__ __forceinline__ void apply(int64_t i, int j0, const VT (&acc)[4], Frag& f,
-                                        VT (&rr)[4], bool vec) {
-    VT xn[4], rn[4];
+  __device__ __forceinline__ void operator()(int64_t i, int j0, VT (&v)[4], bool vec) {
+    ld4<VT>(v, B + i * N, j0, N, vec);
+    const VT z[4] = {VT(0), VT(0), VT(0), VT(0)};
+    st4<VT>(X + i * N, j0, N, vec, z);
+    st4<VT>(Res + i * N, j0, N, vec, v);
+    if (PC) {
+      const VT rinv = VT(1) / rv[i];
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const VT al = alpha[j0 + y];
-      const VT q = fma(acc[y], vinv, f.ri * f.p[y]);
-      xn[y] = fma(al, f.p[y], f.x[y]);
-      rn[y] = fma(-al, q, f.res[y]);
-      rr[y] = fma(rn[y], rn[y], rr[y]);
+      for (int y = 0; y < 4; ++y) v[y] *= rinv;
     }
-    st4<VT>(X + i * N, j0, N, vec, xn);
-    st4<VT>(Res + i * N, j0, N, vec, rn);
   }
 };
 
@@ -505,11 +715,11 @@ struct SolveParams {
   void* X;
   void* Res;
   void* P;
+  void* Sv;
   double* Z;
   double* Tpart;
   double* Tred;
   double* rrpart;
-  double* Wacc;
   double* W;
   double tol, inner_tol;
   int max_iter, fixed_iters, max_refine, true_residual;
@@ -518,20 +728,28 @@ struct SolveParams {
   double* col_true;
   int* status;
   unsigned* bar;
+  unsigned long long* prof;  // optional phase timers of CTA 0 (ns), nullptr when off
 };
 
-template <typename VT, int NT>
-__global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(SolveParams p) {
+// Phase timer slots (CTA 0, thread 0): accumulated ns per phase of the solve.
+enum : int { PH_SETUP = 0, PH_PASS, PH_BAR1, PH_RED, PH_BAR2, PH_SCAL, PH_REFRESH, PH_COUNT = 8 };
+
+template <typename VT, int NT, bool PC>
+__global__ void __launch_bounds__(kThreads, ((NT == 128 || (NT == 64 && sizeof(VT) == 8)) ? 1 : 2)) solve_kernel(SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* s_rr = reinterpret_cast<double*>(smem);
-  double* s_bn2 = s_rr + NT;
-  double* s_dn2 = s_bn2 + NT;
+  double* s_gam = reinterpret_cast<double*>(smem);   // (r, r) of the current residual
+  double* s_gold = s_gam + NT;                        // previous (r, r)
+  double* s_sig = s_gold + NT;                        // sum r_i r_ij^2
+  double* s_tn2 = s_sig + NT;                         // ||HA^T r_j||^2
+  double* s_bn2 = s_tn2 + NT;                         // ||b_j||^2 of the inner solve
+  double* s_dn2 = s_bn2 + NT;                         // ||d_j||^2
   double* s_alpha = s_dn2 + NT;
   double* s_beta = s_alpha + NT;
   double* s_itol = s_beta + NT;
   double* s_tmp = s_itol + NT;
   double* s_true = s_tmp + NT;
-  int* s_active = reinterpret_cast<int*>(s_true + NT);
+  double* s_spare = s_true + NT;
+  int* s_active = reinterpret_cast<int*>(s_spare + NT);
   int* s_done = s_active + NT;
   int* s_iters = s_done + NT;
   int* s_flag = s_iters + NT;
@@ -539,12 +757,15 @@ __global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(So
   VT* s_beta_v = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(s_flag + NT) + NT * 8);
   double* scratch = reinterpret_cast<double*>(smem + scalar_bytes<NT>());
   unsigned char* uni = smem + scalar_bytes<NT>() + kThreads * 8;
+  constexpr int LDV = NT + 16 / (int)sizeof(VT);
+  VT* sT = reinterpret_cast<VT*>(uni);
+  unsigned char* tiles = uni + NT * LDV * sizeof(VT);
 
   const int N = p.N, G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int64_t rows_per = (p.m + G - 1) / G;
   const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
   const int64_t row1 = imin64(p.m, row0 + rows_per);
-  const int NE = N * N + N;
+  const int NE = N * N + 2 * N;
   GridBarrier bar{p.bar, reinterpret_cast<int*>(p.bar + 1), p.status, (unsigned)G, 0u};
   const double inv_nm1 = 1.0 / (double)(N - 1);
   const bool refine = (p.mode == 1);
@@ -552,10 +773,21 @@ __global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(So
   VT* X = refine ? static_cast<VT*>(p.X) : reinterpret_cast<VT*>(p.Z);
   VT* Res = static_cast<VT*>(p.Res);
   VT* P = static_cast<VT*>(p.P);
+  VT* Sv = static_cast<VT*>(p.Sv);
   const VT* B = refine ? static_cast<const VT*>(p.B) : reinterpret_cast<const VT*>(p.D);
   const VT* HA = static_cast<const VT*>(p.HA);
   const VT* rv = static_cast<const VT*>(p.rv);
   double* Tp = p.Tpart + (int64_t)b * NE;
+  const bool prof = p.prof != nullptr && b == 0 && t == 0;
+  unsigned long long ph[PH_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long tp = prof ? global_ns() : 0ull;
+  auto tick = [&](int slot) {
+    if (prof) {
+      const unsigned long long now = global_ns();
+      ph[slot] += now - tp;
+      tp = now;
+    }
+  };
   int par = 0;
   bool ok = true;
 
@@ -575,119 +807,121 @@ __global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(So
       s_done[t] = zero ? 1 : 0;
       s_iters[t] = 0;
       s_true[t] = (t < N && s_dn2[t] == 0.0) ? 0.0 : -1.0;
-      s_rr[t] = 0.0;
+      s_gam[t] = 0.0;
       s_bn2[t] = 0.0;
       s_itol[t] = refine ? p.inner_tol : p.tol;
       s_alpha_v[t] = VT(0);
       s_beta_v[t] = VT(0);
     }
-    if (b == 0)
-      for (int e = t; e < N * N; e += kThreads) p.Wacc[e] = 0.0;
     __syncthreads();
   }
+  tick(PH_SETUP);
 
   int outer = 0, total_iter = 0, refinements = 0;
   while (ok) {
-    // ---- inner solve of S X = B from X = 0
-    rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
-      const VT bv = B[i * N + j];
-      X[i * N + j] = VT(0);
-      Res[i * N + j] = bv;
-      acc = fma((double)bv, (double)bv, acc);
-    }, s_tmp, scratch);
-    if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+    // ---- inner solve of S X = B from X = 0: first reduction of [HA^T r | sum r_i r^2 | (r, r)]
+    {
+      ProSetup<VT, PC> pro{B, X, Res, rv, N};
+      passA<VT, NT, ProSetup<VT, PC>, PC>(HA, row0, row1, N, rv, true, pro, uni, Tp);
+    }
     if (!(ok = bar.sync())) break;
-    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_rr, scratch);
-    par ^= 1;
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
+    if (!(ok = bar.sync())) break;
+    stage_T_norms<VT, NT>(p.Tred, N, sT, s_tn2, scratch);
+    // slots: plain CG: s_sig = sum r r_i^2, s_gam = (r, r); preconditioned: s_sig = (r, z)
+    // (the CG gamma), s_gam = (r, r) (the stopping rule's norm)
     if (t < NT) {
-      s_bn2[t] = s_rr[t];
-      s_active[t] = (t < N && !s_done[t] && s_rr[t] > 0.0) ? 1 : 0;
-      s_beta[t] = 0.0;
+      const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;
+      const double gm = t < N ? __ldcg(p.Tred + N * N + N + t) : 0.0;
+      s_sig[t] = sg;
+      s_gam[t] = gm;
+      s_bn2[t] = gm;
+      s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
       s_alpha[t] = 0.0;
+      s_beta[t] = 0.0;
+      s_spare[t] = 0.0;
     }
     __syncthreads();
+    tick(PH_SETUP);
     const int limit = fixed ? p.fixed_iters : (p.max_iter - total_iter);
-    bool first = true;
     int it = 0;
-    for (; it < limit; ++it) {
+    for (;;) {
+      // scalars of this step (identical in every CTA: same sums in the same order)
+      if (t < N) {
+        int a = s_active[t];
+        const double gm = s_gam[t];
+        if (a && it > 0) {
+          if (!isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
+          else if (fixed ? gm == 0.0 : sqrt(gm) <= s_itol[t] * sqrt(s_bn2[t])) a = 0;
+        }
+        double al = 0.0, be = 0.0;
+        if (a) {
+          // CG gamma: (r, r) plain, (r, R^-1 r) preconditioned; delta = (z, S z)
+          const double cg = PC ? s_sig[t] : gm;
+          const double delta = s_tn2[t] * inv_nm1 + s_sig[t];
+          double den = delta;
+          if (it > 0) {
+            be = cg / s_gold[t];
+            den = delta - be * cg / s_alpha[t];
+          }
+          if (!isfinite(den)) { atomicOr(p.status, DS_NONFINITE); a = 0; be = 0.0; }
+          else if (den <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); a = 0; be = 0.0; }
+          else al = cg / den;
+        }
+        s_active[t] = a;
+        s_alpha[t] = al;
+        s_beta[t] = be;
+        s_alpha_v[t] = (VT)al;
+        s_beta_v[t] = (VT)be;
+      }
+      __syncthreads();
       if (t == 0) {
         int any = 0;
         for (int j = 0; j < N; ++j) any |= s_active[j];
-        s_flag[0] = any;
+        s_flag[0] = any && it < limit;
       }
       __syncthreads();
       if (!s_flag[0]) break;
-      // pass A: P = R + beta P (P = R on the first step); T = HA^T P; s_j = sum r_i p_ij^2
-      ProCG<VT> pro{P, Res, s_beta_v, s_active, N, first};
-      passA<VT, NT>(HA, row0, row1, N, rv, true, pro, uni, Tp);
+      tick(PH_SCAL);
+      passF<VT, NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
+                        tiles, Tp);
+      tick(PH_PASS);
       if (!(ok = bar.sync())) break;
+      tick(PH_BAR1);
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
+      tick(PH_RED);
       if (!(ok = bar.sync())) break;
-      // alpha_j = rr_j / (||T_:j||^2/(N-1) + s_j)   (p^T S p, Eq. matvec_decomp)
+      tick(PH_BAR2);
+      stage_T_norms<VT, NT>(p.Tred, N, sT, s_tn2, scratch);
       if (t < N) {
-        double t2 = 0.0;
-#pragma unroll 8
-        for (int k = 0; k < N; ++k) {
-          const double v = __ldcg(p.Tred + k * N + t);
-          t2 = fma(v, v, t2);
-        }
-        const double pSp = t2 * inv_nm1 + __ldcg(p.Tred + N * N + t);
-        double al = 0.0;
         if (s_active[t]) {
-          if (!isfinite(pSp)) { atomicOr(p.status, DS_NONFINITE); s_active[t] = 0; }
-          else if (pSp <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); s_active[t] = 0; }
-          else al = s_rr[t] / pSp;
-        }
-        s_alpha[t] = al;
-        s_alpha_v[t] = (VT)al;
-      }
-      VT* sT = reinterpret_cast<VT*>(uni);
-      stage_T<VT, NT>(p.Tred, N, sT);
-      if (b == 0)
-        for (int e = t; e < N * N; e += kThreads) p.Wacc[e] += __ldcg(p.Tred + e) * s_alpha[e % N];
-      // pass B: q = HA T/(N-1) + r p; x += alpha p; res -= alpha q; rr = ||res||^2
-      constexpr int LDT = NT + 16 / (int)sizeof(VT);
-      EpiCG<VT> epi{X, Res, P, rv, s_alpha_v, (VT)inv_nm1, N};
-      passB<VT, NT>(HA, row0, row1, N, sT, uni + NT * LDT * sizeof(VT), epi, s_tmp);
-      if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
-      if (!(ok = bar.sync())) break;
-      reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
-      par ^= 1;
-      if (t < N && s_active[t]) {
-        const double rn = s_tmp[t];
-        s_iters[t] += 1;
-        if (!isfinite(rn)) { atomicOr(p.status, DS_NONFINITE); s_active[t] = 0; s_alpha_v[t] = VT(0); }
-        else {
-          const double be = rn / s_rr[t];
-          s_beta[t] = be;
-          s_beta_v[t] = (VT)be;
-          s_rr[t] = rn;
-          if (fixed) { if (rn == 0.0) s_active[t] = 0; }
-          else if (sqrt(rn) <= s_itol[t] * sqrt(s_bn2[t])) s_active[t] = 0;
+          s_iters[t] += 1;
+          s_gold[t] = PC ? s_sig[t] : s_gam[t];
+          s_gam[t] = __ldcg(p.Tred + N * N + N + t);
+          s_sig[t] = __ldcg(p.Tred + N * N + t);
         }
       }
-      if (t < N && !s_active[t]) s_alpha_v[t] = VT(0);
       __syncthreads();
-      first = false;
+      tick(PH_SCAL);
+      ++it;
     }
     if (!ok) break;
     total_iter += it;
 
-    if (!refine && !p.true_residual) {
-      if (b == 0)
-        for (int e = t; e < N * N; e += kThreads) p.W[e] = p.Wacc[e] * inv_nm1;
-      break;
-    }
-    // ---- FP64 refresh: Z (+)= X; T = HA^T Z; true residual D - S Z; next right-hand side
+    // ---- FP64 refresh: Z (+)= X; T = HA^T Z; W; true residual D - S Z; next right-hand side
     ProRefresh<VT> pro{p.Z, X, N, refine};
     passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
     if (!(ok = bar.sync())) break;
-    double* sT64 = reinterpret_cast<double*>(uni);
-    stage_T<double, NT>(p.Tred, N, sT64);
     if (b == 0)
       for (int e = t; e < N * N; e += kThreads) p.W[e] = __ldcg(p.Tred + e) * inv_nm1;
+    if (!refine && !p.true_residual) {
+      tick(PH_REFRESH);
+      break;
+    }
+    double* sT64 = reinterpret_cast<double*>(uni);
+    stage_T<double, NT>(p.Tred, N, sT64);
     constexpr int LD64 = NT + 2;
     EpiRefresh<VT> epi{p.Z, p.D, p.r, refine ? static_cast<VT*>(p.B) : nullptr, inv_nm1, N};
     passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
@@ -713,6 +947,7 @@ __global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(So
       s_flag[1] = all;
     }
     __syncthreads();
+    tick(PH_REFRESH);
     if (!refine || fixed || s_flag[1] || outer >= p.max_refine || total_iter >= p.max_iter) break;
     ++outer;
   }
@@ -720,16 +955,20 @@ __global__ void __launch_bounds__(kThreads, (NT == 128 ? 1 : 2)) solve_kernel(So
   if (b == 0) {
     if (t < N) {
       p.col_iters[t] = s_iters[t];
-      const double rec = s_dn2[t] > 0.0 ? sqrt(s_rr[t] / s_dn2[t]) : 0.0;
+      const double rec = s_dn2[t] > 0.0 ? sqrt(s_gam[t] / s_dn2[t]) : 0.0;
       p.col_relres[t] = refine ? s_true[t] : rec;
       p.col_true[t] = s_true[t];
       bool conv;
       if (fixed) conv = true;
       else if (refine) conv = s_true[t] >= 0.0 && s_true[t] <= p.tol;
-      else conv = s_dn2[t] == 0.0 || sqrt(s_rr[t]) <= p.tol * sqrt(s_dn2[t]);
+      else conv = s_dn2[t] == 0.0 || sqrt(s_gam[t]) <= p.tol * sqrt(s_dn2[t]);
       if (!conv && ok) atomicOr(p.status, DS_NOT_CONVERGED);
     }
     if (t == 0) p.status[1] = refinements;
+    if (prof) {
+      ph[PH_REFRESH] += 0;
+      for (int q = 0; q < PH_COUNT; ++q) p.prof[q] = ph[q];
+    }
   }
 }
 
@@ -887,21 +1126,28 @@ template <typename VT, int NT> constexpr int update_smem_bytes() {
 static int pick_nt(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
 
 template <typename VT>
-static void* solve_fn(int NT) {
-  if (NT == 32) return (void*)solve_kernel<VT, 32>;
-  if (NT == 64) return (void*)solve_kernel<VT, 64>;
-  return (void*)solve_kernel<VT, 128>;
+static void* solve_fn(int NT, bool pc) {
+  if (pc) {
+    if (NT == 32) return (void*)solve_kernel<VT, 32, true>;
+    if (NT == 64) return (void*)solve_kernel<VT, 64, true>;
+    return (void*)solve_kernel<VT, 128, true>;
+  }
+  if (NT == 32) return (void*)solve_kernel<VT, 32, false>;
+  if (NT == 64) return (void*)solve_kernel<VT, 64, false>;
+  return (void*)solve_kernel<VT, 128, false>;
 }
+template <typename VT>
 static size_t solve_smem(int NT) {
-  return NT == 32 ? solve_smem_bytes<32>() : (NT == 64 ? solve_smem_bytes<64>() : solve_smem_bytes<128>());
+  return NT == 32 ? solve_smem_bytes<VT, 32>() : (NT == 64 ? solve_smem_bytes<VT, 64>() : solve_smem_bytes<VT, 128>());
 }
 
 cudaError_t plan_solve(enkf_handle_s* h) {
   const int N = h->cfg.N;
   const int NT = pick_nt(N);
   const bool fp64 = h->cfg.precision == ENKF_FP64;
-  void* fn = fp64 ? solve_fn<double>(NT) : solve_fn<float>(NT);
-  const size_t smem = solve_smem(NT);
+  const bool pc = h->cfg.precondition != 0;
+  void* fn = fp64 ? solve_fn<double>(NT, pc) : solve_fn<float>(NT, pc);
+  const size_t smem = fp64 ? solve_smem<double>(NT) : solve_smem<float>(NT);
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int occ = 0;
@@ -959,12 +1205,13 @@ cudaError_t launch_solve(enkf_handle_s* h) {
   p.X = ws.X;
   p.Res = ws.Res;
   p.P = ws.P;
+  p.Sv = ws.Sv;
   p.Z = ws.Z;
   p.Tpart = ws.Tpart;
   p.Tred = ws.Tred;
   p.rrpart = ws.rrpart;
-  p.Wacc = ws.Wacc;
   p.W = ws.W;
+  p.prof = h->prof_enabled ? ws.prof : nullptr;
   p.tol = c.tol;
   p.inner_tol = c.inner_tol;
   p.max_iter = c.max_iter;
@@ -980,7 +1227,8 @@ cudaError_t launch_solve(enkf_handle_s* h) {
   if (err != cudaSuccess) return err;
   err = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);
   if (err != cudaSuccess) return err;
-  void* fn = fp64 ? solve_fn<double>(h->launch.NT) : solve_fn<float>(h->launch.NT);
+  const bool pc = c.precondition != 0;
+  void* fn = fp64 ? solve_fn<double>(h->launch.NT, pc) : solve_fn<float>(h->launch.NT, pc);
   void* args[] = {&p};
   return cudaLaunchCooperativeKernel(fn, dim3(h->launch.G), dim3(kThreads), args,
                                      h->launch.smem, h->stream);

@@ -87,14 +87,14 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
 
   // carve the workspace out of the fixed array
   const size_t mN = size_t(c.m) * c.N;
-  const size_t NE = size_t(c.N) * c.N + c.N;
+  const size_t NE = size_t(c.N) * c.N + 2 * size_t(c.N);
   const bool fp64 = c.precision == ENKF_FP64;
   const size_t vs = fp64 ? 8 : 4;
   struct Part { void** p; size_t bytes; };
   enkf::Workspace& ws = h.ws;
   Part parts[] = {
       {(void**)&ws.HA64, 8 * mN}, {(void**)&ws.D, 8 * mN}, {(void**)&ws.Z, 8 * mN},
-      {(void**)&ws.Res, vs * mN}, {(void**)&ws.P, vs * mN},
+      {(void**)&ws.Res, vs * mN}, {(void**)&ws.P, vs * mN}, {(void**)&ws.Sv, vs * mN},
       {(void**)&ws.HA32, fp64 ? 0 : 4 * mN}, {(void**)&ws.B, fp64 ? 0 : vs * mN},
       {(void**)&ws.X, fp64 ? 0 : vs * mN}, {(void**)&ws.r32, fp64 ? 0 : 4 * size_t(c.m)},
       {(void**)&ws.Tpart, 8 * size_t(h.launch.G) * NE}, {(void**)&ws.Tred, 8 * NE},

@@ -193,3 +193,34 @@ def test_l96_cycling_lockstep(lib):
         err = oracle.rel_frobenius(Xa, ref)
         assert err <= 1e-8, (k, err)
         cyc.ensemble = ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(4096, 64, 1024), (2500, 37, 999), (1600, 20, 400),
+                                   (3000, 100, 700), (500, 2, 130)])
+def test_preconditioned_cg_matches_exact_oracle(lib, prec, shape):
+    """CG preconditioned by R (Jacobi) converges to the same analysis; R^-1/2 S R^-1/2 is the
+    identity plus a rank < N term, so exact CG would end within N steps; with r spread over
+    [0.05, 5] rounding adds some (bounded here by 2N in FP64)."""
+    n, N, m = shape
+    side = int(round(n ** 0.5))
+    p = synth.grf_problem(side, 6.0, N, m, 0.05, 5.0, seed=7 * n + N + m,
+                          dtype=np.float64 if prec == "fp64" else np.float32)
+    an, Xa, st = _run(lib, p, prec, tol=1e-10, precondition=1)
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = _oracle_exact(p, E)
+    err = oracle.rel_frobenius(Xa, ref)
+    assert st["status"] == "ok", st
+    assert err <= (1e-8 if prec == "fp64" else 1e-6), (err, st)
+    if prec == "fp64":
+        assert st["iters_max"] <= 2 * p.N, st
+    an0, Xa0, st0 = _run(lib, p, prec, tol=1e-10, precondition=0)
+    assert st0["iters_max"] >= st["iters_max"]
+
+
+def test_preconditioned_full_size_grf512_N64_m65536_fp32(lib):
+    p = synth.workload("grf512_N64_m65536", 1, dtype=np.float32)
+    an, Xa, st = _run(lib, p, "fp32", seed=1, counter=0, tol=1e-8, precondition=1)
+    E = oracle.obs_perturbations(1, 0, p.r, p.N)
+    err = oracle.rel_frobenius(Xa, _oracle_exact(p, E))
+    assert st["status"] == "ok" and err <= 1e-6, (err, st)
