@@ -65,8 +65,9 @@ typedef enum {
   ENKF_FP64 = 0,        /* FP64 storage and arithmetic throughout (the plain FP64 CG)    */
   ENKF_FP32 = 1,        /* FP32 CG inner solves + FP64 residual refresh (iterative
                            refinement) with FP64 scalar recurrences                      */
-  ENKF_BF16_REFINE = 2, /* BF16 HA contractions on tensor cores, FP32 accumulation,
-                           FP32 vectors, FP32 residual refresh every refresh_every steps */
+  ENKF_BF16_REFINE = 2, /* BF16 HA contractions on tensor cores (tcgen05), FP32
+                           accumulation, FP32 vectors, FP64 scalars; inner solves refined
+                           by an FP32 residual refresh (see refresh_every)              */
   ENKF_FP16_REFINE = 3  /* as ENKF_BF16_REFINE with FP16 HA                              */
 } enkf_precision;
 
@@ -87,7 +88,9 @@ typedef struct enkf_config {
                              mode); tol is then ignored                                  */
   int32_t max_refine;     /* ENKF_FP32: maximum FP64 residual refreshes (default 4)      */
   double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
-  int32_t refresh_every;  /* BF16/FP16 modes: FP32 residual refresh period (default 8)   */
+  int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between FP32 residual
+                             refreshes; 0 (default): each inner solve runs until its
+                             residual fell by inner_tol (at least 2e-2 BF16, 4e-3 FP16)  */
   int32_t perturb_obs;    /* 1: E ~ N(0, R) drawn from (seed, counter); 0: E = 0         */
   int32_t warm_start;     /* 0: start CG from Z = 0; 1: learned warm start (model set)   */
   int32_t true_residual;  /* 1: FP64 true residual check (and W = HA^T Z/(N-1) from the
@@ -96,7 +99,11 @@ typedef struct enkf_config {
   int32_t precondition;   /* ENKF_CGD: 0 plain CG (the paper's method); 1 CG preconditioned
                              by R (Jacobi), which ends within about N steps because
                              R^-1/2 S R^-1/2 is the identity plus a rank < N term        */
-  int32_t reserved[6];    /* must be zero                                                */
+  int32_t lowprec_terms;  /* BF16/FP16 modes: 3 (or 0, the default) splits every operand
+                             into hi + lo parts and forms hi*hi + hi*lo + lo*hi (about 16
+                             significant bits); 1 uses single BF16/FP16 operands, whose
+                             refinement diverges once 2 eps cond(S) > 1                  */
+  int32_t reserved[5];    /* must be zero                                                */
 } enkf_config;
 
 typedef struct enkf_stats {
@@ -113,7 +120,7 @@ typedef struct enkf_stats {
 } enkf_stats;
 
 /* Fill *cfg with defaults for an (n, m, N) problem: ENKF_FP64, ENKF_CGD, tol 1e-8,
-   max_iter 1000, max_refine 4, inner_tol 1e-5, refresh_every 8, perturb_obs 1,
+   max_iter 1000, max_refine 4, inner_tol 1e-5, refresh_every 0, perturb_obs 1,
    true_residual 1. Returns ENKF_ERR_INVALID_ARG when cfg is NULL. */
 enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t N);
 

@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
         ("inner_tol", ctypes.c_double), ("refresh_every", ctypes.c_int32),
         ("perturb_obs", ctypes.c_int32), ("warm_start", ctypes.c_int32),
         ("true_residual", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
-        ("precondition", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("precondition", ctypes.c_int32), ("lowprec_terms", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 

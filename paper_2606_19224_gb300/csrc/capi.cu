@@ -26,7 +26,7 @@ enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
 }
 
 void free_workspace(Workspace& ws) {
-  void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.D, ws.Z, ws.B, ws.X,
+  void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.HA16, ws.D, ws.Z, ws.B, ws.X,
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
   for (void* p : ptrs)
@@ -53,7 +53,7 @@ enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t 
   cfg->fixed_iters = 0;
   cfg->max_refine = 4;
   cfg->inner_tol = 1e-5;
-  cfg->refresh_every = 8;
+  cfg->refresh_every = 0;
   cfg->perturb_obs = 1;
   cfg->warm_start = 0;
   cfg->true_residual = 1;
@@ -92,8 +92,13 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (c.m >= (int64_t(1) << 32) || c.n >= (int64_t(1) << 31))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: m must be < 2^32 and n < 2^31");
   if (c.N > 128) return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: N > 128");
-  if (c.precision != ENKF_FP64 && c.precision != ENKF_FP32)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: precision mode not built in this library");
+  if (c.precision < ENKF_FP64 || c.precision > ENKF_FP16_REFINE)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: unknown precision mode");
+  const bool mixed = c.precision == ENKF_BF16_REFINE || c.precision == ENKF_FP16_REFINE;
+  if (mixed && c.variant != ENKF_CGD)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: the BF16/FP16 modes are built for ENKF_CGD");
+  if (mixed && c.fixed_iters > 0)
+    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: fixed_iters is not offered in the BF16/FP16 modes");
   if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED)
     return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: unknown variant");
   if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
@@ -105,7 +110,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (c.grid_blocks < 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: grid_blocks < 0");
   if (c.precondition != 0 && c.precondition != 1)
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: precondition must be 0 or 1");
-  for (int q = 0; q < 6; ++q)
+  if (c.lowprec_terms != 0 && c.lowprec_terms != 1 && c.lowprec_terms != 3)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: lowprec_terms must be 0, 1 or 3");
+  for (int q = 0; q < 5; ++q)
     if (c.reserved[q]) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: reserved fields must be 0");
   // observation operator and R
   if (h_rowptr[0] != 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr[0] != 0");
@@ -130,7 +137,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   h->nnz = nnz;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (e == cudaSuccess) e = enkf::plan_solve(h);
+  if (e == cudaSuccess) e = mixed ? enkf::plan_solve_mixed(h) : enkf::plan_solve(h);
   if (e != cudaSuccess) {
     enkf_status s = cuda_fail(nullptr, e, "enkf_create: device query / planning");
     delete h;
@@ -177,6 +184,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
     allocs.push_back({(void**)&ws.B, vs * mN});
     allocs.push_back({(void**)&ws.X, vs * mN});
   }
+  if (mixed) allocs.push_back({(void**)&ws.HA16, (size_t)((c.lowprec_terms == 1 ? 2 : 4) * mN)});
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -220,7 +228,8 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
   if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
   if (e == cudaSuccess)
-    e = reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter) : enkf::launch_solve(h);
+    e = reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter)
+                : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
   if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
   if (e == cudaSuccess)

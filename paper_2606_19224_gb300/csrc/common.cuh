@@ -115,7 +115,8 @@ struct Workspace {
   double* r = nullptr;          // [m]
   float* r32 = nullptr;         // [m]     (FP32 mode)
   double* HA64 = nullptr;       // [m][N]
-  float* HA32 = nullptr;        // [m][N]   (FP32 mode)
+  float* HA32 = nullptr;        // [m][N]   (FP32 and mixed modes)
+  void* HA16 = nullptr;         // [m][N]   BF16 or FP16 (mixed modes)
   double* D = nullptr;          // [m][N]
   double* Z = nullptr;          // [m][N]   FP64 solution (FP64 mode: the CG iterate itself)
   void* B = nullptr;            // [m][N]   inner right-hand side (FP32 mode)
@@ -169,6 +170,9 @@ cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y
 cudaError_t plan_solve(enkf_handle_s* h);
 cudaError_t launch_solve(enkf_handle_s* h);
 cudaError_t launch_convert_r(enkf_handle_s* h);
+// kernels_tc.cu: mixed-precision (BF16 / FP16 tensor-core) persistent solve
+cudaError_t plan_solve_mixed(enkf_handle_s* h);
+cudaError_t launch_solve_mixed(enkf_handle_s* h);
 cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa);
 cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa);
 // kernels_reduced.cu: Gram pass + N x N CG of CGD-EnKF-Reduced; V lands in ws.W,

@@ -20,687 +20,14 @@
 // contraction so their latency overlaps it. In the FP32 mode the inner loops contain no
 // FP64 arithmetic (FP64 runs at 1/64 of the FP32 rate on this part): per-thread partial
 // sums are FP32 and only the cross-thread / cross-CTA reductions and the CG scalars are FP64.
-#include "common.cuh"
+#include "cg_device.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
 namespace enkf {
-
-// ------------------------------------------------------------------ tiling
-// NT = padded column count (N <= NT). Pass A (T = HA^T V): MA x MA register tile per
-// thread over (k, j), TRA rows of HA and V staged in shared memory per step, RG row groups.
-// Pass B (Q = HA T): 4 x 4 register tile per thread over (i, j), TRB rows per tile.
-template <int NT> struct Tile;
-template <> struct Tile<32> { static constexpr int MA = 4, TRA = 32, TRB = 128; };
-template <> struct Tile<64> { static constexpr int MA = 4, TRA = 32, TRB = 64; };
-template <> struct Tile<128> { static constexpr int MA = 8, TRA = 16, TRB = 32; };
-
-// Fused CG pass tile: TR rows of HA, r, p, s, x staged per step; MR rows per thread in the
-// update (pass-B mapping, NT/4 column groups of 4).
-template <typename CT, int NT> struct FTile;
-template <int NT> struct FTile<float, NT> { static constexpr int MR = 4, TR = (1024 / NT) * 4; };
-template <> struct FTile<double, 32> { static constexpr int MR = 2, TR = 64; };
-template <> struct FTile<double, 64> { static constexpr int MR = 2, TR = 32; };
-template <> struct FTile<double, 128> { static constexpr int MR = 1, TR = 8; };
-
-// shared scalars: 12 FP64 arrays, 4 int arrays, 2 VT-sized (<= 8 B) arrays, each of length NT
-template <int NT> __host__ __device__ constexpr int scalar_bytes() { return NT * 8 * 12 + NT * 4 * 4 + NT * 8 * 2; }
-template <int NT> __host__ __device__ constexpr int refresh_union_bytes() {
-  constexpr int MA = Tile<NT>::MA, TRA = Tile<NT>::TRA, TRB = Tile<NT>::TRB;
-  constexpr int NG = NT / MA, RG = kThreads / (NG * NG);
-  constexpr int a = 2 * TRA * NT * 8 + TRA * 8;
-  constexpr int a2 = RG * NT * NT * 8;
-  constexpr int a3 = 2 * RG * NG * NT * 8;
-  constexpr int b = NT * (NT + 2) * 8 + TRB * (NT + 2) * 8;
-  constexpr int m1 = a > a2 ? a : a2;
-  constexpr int m2 = m1 > a3 ? m1 : a3;
-  return m2 > b ? m2 : b;
-}
-template <typename CT, int NT> __host__ __device__ constexpr int passF_bytes() {
-  constexpr int LD = NT + 16 / (int)sizeof(CT), TR = FTile<CT, NT>::TR;
-  return NT * LD * (int)sizeof(CT) + 5 * TR * LD * (int)sizeof(CT) + TR * (int)sizeof(CT);
-}
-template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
-  return refresh_union_bytes<NT>() > passF_bytes<VT, NT>() ? refresh_union_bytes<NT>() : passF_bytes<VT, NT>();
-}
-template <typename VT, int NT> __host__ __device__ constexpr int solve_smem_bytes() {
-  return scalar_bytes<NT>() + kThreads * 8 + union_bytes<VT, NT>();
-}
-
-__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
-
-// ------------------------------------------------------------------ 4-wide fragments
-template <typename CT> __device__ __forceinline__ void load_vec(CT* d, const CT* s, int n);
-template <> __device__ __forceinline__ void load_vec<float>(float* d, const float* s, int n) {
-  for (int q = 0; q < n; q += 4) {
-    const float4 v = *reinterpret_cast<const float4*>(s + q);
-    d[q] = v.x; d[q + 1] = v.y; d[q + 2] = v.z; d[q + 3] = v.w;
-  }
-}
-template <> __device__ __forceinline__ void load_vec<double>(double* d, const double* s, int n) {
-  for (int q = 0; q < n; q += 2) {
-    const double2 v = *reinterpret_cast<const double2*>(s + q);
-    d[q] = v.x; d[q + 1] = v.y;
-  }
-}
-template <typename CT> __device__ __forceinline__ void store_vec4(CT* d, const CT* s);
-template <> __device__ __forceinline__ void store_vec4<float>(float* d, const float* s) {
-  *reinterpret_cast<float4*>(d) = make_float4(s[0], s[1], s[2], s[3]);
-}
-template <> __device__ __forceinline__ void store_vec4<double>(double* d, const double* s) {
-  *reinterpret_cast<double2*>(d) = make_double2(s[0], s[1]);
-  *reinterpret_cast<double2*>(d + 2) = make_double2(s[2], s[3]);
-}
-// row pointer p, columns j0..j0+3 (vec: N % 4 == 0, so the 4 columns exist and are aligned)
-template <typename CT>
-__device__ __forceinline__ void ld4(CT (&d)[4], const CT* p, int j0, int N, bool vec) {
-  if (vec) { load_vec<CT>(d, p + j0, 4); return; }
-#pragma unroll
-  for (int y = 0; y < 4; ++y) d[y] = (j0 + y < N) ? p[j0 + y] : CT(0);
-}
-template <typename CT>
-__device__ __forceinline__ void st4(CT* p, int j0, int N, bool vec, const CT (&s)[4]) {
-  if (vec) { store_vec4<CT>(p + j0, s); return; }
-#pragma unroll
-  for (int y = 0; y < 4; ++y)
-    if (j0 + y < N) p[j0 + y] = s[y];
-}
-
-// ------------------------------------------------------------------ reductions
-// Block partial of a per-column sum over the CTA's rows: f(i, j, acc) is called once per
-// element (i in [row0,row1), j < N); the per-column totals land in out[0..NT).
-template <int NT, class F>
-__device__ __forceinline__ void rows_reduce(int64_t row0, int64_t row1, int N, F f, double* out,
-                                            double* scratch) {
-  constexpr int L = kThreads / NT;
-  const int t = threadIdx.x, j = t % NT, lane = t / NT;
-  double acc = 0.0;
-  if (j < N)
-    for (int64_t i = row0 + lane; i < row1; i += L) f(i, j, acc);
-  scratch[t] = acc;
-  __syncthreads();
-  if (t < NT) {
-    double s = 0.0;
-    for (int q = 0; q < L; ++q) s += scratch[q * NT + t];
-    out[t] = s;
-  }
-  __syncthreads();
-}
-
-// Every CTA sums the G block partials part[b*NT + j] (b < G, j < N) in the same fixed order,
-// so all CTAs obtain bitwise identical totals (and take identical decisions).
-template <int NT>
-__device__ __forceinline__ void reduce_all(const double* __restrict__ part, int G, int N,
-                                           double* out, double* scratch) {
-  constexpr int Q = kThreads / NT;
-  const int t = threadIdx.x, j = t % NT, q = t / NT;
-  double s = 0.0;
-  if (j < N) {
-    const int b0 = (int)((int64_t)q * G / Q), b1 = (int)((int64_t)(q + 1) * G / Q);
-#pragma unroll 8
-    for (int b = b0; b < b1; ++b) s += __ldcg(part + (int64_t)b * NT + j);
-  }
-  scratch[t] = s;
-  __syncthreads();
-  if (t < NT) {
-    double v = 0.0;
-    for (int qq = 0; qq < Q; ++qq) v += scratch[qq * NT + t];
-    out[t] = v;
-  }
-  __syncthreads();
-}
-
-// CTA b sums its slice of the NE-long partial vectors part[g*NE + e] over g < G (fixed order)
-// and writes red[e].
-__device__ __forceinline__ void reduce_slice(const double* __restrict__ part, int G, int NE,
-                                             double* __restrict__ red, double* scratch) {
-  const int t = threadIdx.x;
-  const int chunk = (NE + G - 1) / G;
-  const int e0 = blockIdx.x * chunk;
-  const int cnt = min(NE, e0 + chunk) - e0;
-  if (cnt <= 0) return;
-  if (cnt >= kThreads) {
-    for (int e = e0 + t; e < e0 + cnt; e += kThreads) {
-      double s = 0.0;
-#pragma unroll 8
-      for (int g = 0; g < G; ++g) s += __ldcg(part + (int64_t)g * NE + e);
-      red[e] = s;
-    }
-    return;
-  }
-  const int parts = kThreads / cnt;
-  const int q = t / cnt, el = t % cnt;
-  double s = 0.0;
-  if (q < parts) {
-    const int g0 = (int)((int64_t)q * G / parts), g1 = (int)((int64_t)(q + 1) * G / parts);
-#pragma unroll 8
-    for (int g = g0; g < g1; ++g) s += __ldcg(part + (int64_t)g * NE + e0 + el);
-  }
-  scratch[t] = s;
-  __syncthreads();
-  if (t < cnt) {
-    double v = 0.0;
-    for (int qq = 0; qq < parts; ++qq) v += scratch[qq * cnt + t];
-    red[e0 + t] = v;
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------------ pass A
-// out[k*N + j] = sum_i HA[i][k] V[i][j] over the CTA's rows and (want_s)
-// out[N*N + j] = sum_i r_i V[i][j]^2 and out[N*N + N + j] = sum_i V[i][j]^2, where
-// pro(i, j0, v) produces (and may store) the four values V[i][j0..j0+3]. Per-thread partial
-// sums are kept in CT.
-template <typename CT, int NT, class Pro, bool PC = false>
-__device__ __forceinline__ void passA(const CT* __restrict__ HA, int64_t row0, int64_t row1,
-                                      int N, const CT* __restrict__ rv, bool want_s, Pro& pro,
-                                      unsigned char* uni, double* __restrict__ out) {
-  constexpr int MA = Tile<NT>::MA, TRA = Tile<NT>::TRA;
-  constexpr int NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG, C4 = NT / 4;
-  CT* sA = reinterpret_cast<CT*>(uni);
-  CT* sV = sA + TRA * NT;
-  CT* sR = sV + TRA * NT;
-  const int t = threadIdx.x, g = t / TPG, u = t % TPG, tj = u % NG, tk = u / NG;
-  const int k0 = tk * MA, j0 = tj * MA;
-  const bool vec = (N & 3) == 0;
-  CT acc[MA][MA];
-#pragma unroll
-  for (int x = 0; x < MA; ++x)
-#pragma unroll
-    for (int y = 0; y < MA; ++y) acc[x][y] = CT(0);
-  CT sacc[MA], gacc[MA];
-#pragma unroll
-  for (int y = 0; y < MA; ++y) { sacc[y] = CT(0); gacc[y] = CT(0); }
-
-  for (int64_t i0 = row0; i0 < row1; i0 += TRA) {
-    __syncthreads();
-#pragma unroll
-    for (int c = t; c < TRA * C4; c += kThreads) {
-      const int ii = c / C4, c0 = (c % C4) * 4;
-      const int64_t i = i0 + ii;
-      CT a[4] = {CT(0), CT(0), CT(0), CT(0)}, v[4] = {CT(0), CT(0), CT(0), CT(0)};
-      if (i < row1 && c0 < N) {
-        ld4<CT>(a, HA + i * N, c0, N, vec);
-        pro(i, c0, v, vec);
-      }
-      store_vec4<CT>(sA + ii * NT + c0, a);
-      store_vec4<CT>(sV + ii * NT + c0, v);
-    }
-    if (t < TRA) {
-      const int64_t i = i0 + t;
-      sR[t] = (want_s && i < row1) ? rv[i] : CT(0);
-    }
-    __syncthreads();
-    const int nrows = (int)imin64(TRA, row1 - i0);
-    for (int ii = g; ii < nrows; ii += RG) {
-      CT a[MA], v[MA];
-      load_vec<CT>(a, sA + ii * NT + k0, MA);
-      load_vec<CT>(v, sV + ii * NT + j0, MA);
-#pragma unroll
-      for (int x = 0; x < MA; ++x)
-#pragma unroll
-        for (int y = 0; y < MA; ++y) acc[x][y] = fma(a[x], v[y], acc[x][y]);
-      if (((ii / RG) % NG) == tk) {
-        const CT ri = sR[ii];
-#pragma unroll
-        for (int y = 0; y < MA; ++y) {
-          sacc[y] = fma(ri * v[y], v[y], sacc[y]);
-          const CT gv = PC ? ri * v[y] : v[y];   // preconditioned: v = b / r, so r v = b
-          gacc[y] = fma(gv, gv, gacc[y]);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(uni);
-  if (RG > 1) {
-#pragma unroll
-    for (int x = 0; x < MA; ++x)
-#pragma unroll
-      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + j0 + y] = (double)acc[x][y];
-    __syncthreads();
-    if (g == 0) {
-#pragma unroll
-      for (int x = 0; x < MA; ++x)
-#pragma unroll
-        for (int y = 0; y < MA; ++y) {
-          const int k = k0 + x, j = j0 + y;
-          double s = 0.0;
-          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
-          if (k < N && j < N) out[k * N + j] = s;
-        }
-    }
-  } else {
-#pragma unroll
-    for (int x = 0; x < MA; ++x)
-#pragma unroll
-      for (int y = 0; y < MA; ++y) {
-        const int k = k0 + x, j = j0 + y;
-        if (k < N && j < N) out[k * N + j] = (double)acc[x][y];
-      }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int y = 0; y < MA; ++y) {
-    red[(g * NG + tk) * NT + j0 + y] = (double)sacc[y];
-    red[RG * NG * NT + (g * NG + tk) * NT + j0 + y] = (double)gacc[y];
-  }
-  __syncthreads();
-  if (t < N) {
-    double s = 0.0, q2 = 0.0;
-    for (int q = 0; q < RG * NG; ++q) {
-      s += red[q * NT + t];
-      q2 += red[RG * NG * NT + q * NT + t];
-    }
-    out[N * N + t] = want_s ? s : 0.0;
-    out[N * N + N + t] = q2;
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------------ pass B
-// For each of the CTA's rows i and 4-column fragment j0: acc[y] = sum_k HA[i][k] T[k][j0+y];
-// epi.prefetch loads the fragment's operands before the contraction, epi.apply updates the
-// fragment and accumulates squared residuals into rr[y] (CT). rr_out[j] = block sum (FP64).
-template <typename CT, int NT, class Epi>
-__device__ __forceinline__ void passB(const CT* __restrict__ HA, int64_t row0, int64_t row1,
-                                      int N, const CT* sT, unsigned char* sHbytes, Epi& epi,
-                                      double* rr_out) {
-  constexpr int PB = 16 / (int)sizeof(CT), LD = NT + PB, TRB = Tile<NT>::TRB, C4 = NT / 4;
-  constexpr int NJ = NT / 4, NI = kThreads / NJ;
-  static_assert(NI * 4 == TRB, "tile");
-  CT* sH = reinterpret_cast<CT*>(sHbytes);
-  const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * 4;
-  const bool vec = (N & 3) == 0;
-  CT rr[4] = {CT(0), CT(0), CT(0), CT(0)};
-  for (int64_t i0 = row0; i0 < row1; i0 += TRB) {
-    __syncthreads();
-#pragma unroll
-    for (int c = t; c < TRB * C4; c += kThreads) {
-      const int ii = c / C4, c0 = (c % C4) * 4;
-      const int64_t i = i0 + ii;
-      CT a[4] = {CT(0), CT(0), CT(0), CT(0)};
-      if (i < row1 && c0 < N) ld4<CT>(a, HA + i * N, c0, N, vec);
-#pragma unroll
-      for (int y = 0; y < 4; ++y) sH[ii * LD + c0 + y] = a[y];
-    }
-    // FP32 fragments are loaded before the contraction (latency overlap); FP64 passes are
-    // DFMA-bound, so their fragments are loaded just before use to save registers
-    constexpr int NF = Epi::kPrefetch ? 4 : 1;
-    typename Epi::Frag frag[NF];
-    if constexpr (Epi::kPrefetch) {
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const int64_t i = i0 + r0 + x;
-        if (i < row1 && j0 < N) epi.prefetch(i, j0, frag[x], vec);
-      }
-    }
-    __syncthreads();
-    CT acc[4][4];
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = CT(0);
-    if (N == NT) {
-#pragma unroll 8
-      for (int k = 0; k < NT; ++k) {
-        CT a[4], bv[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) a[x] = sH[(r0 + x) * LD + k];
-        load_vec<CT>(bv, sT + k * LD + j0, 4);
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
-      }
-    } else {
-#pragma unroll 4
-      for (int k = 0; k < N; ++k) {
-        CT a[4], bv[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) a[x] = sH[(r0 + x) * LD + k];
-        load_vec<CT>(bv, sT + k * LD + j0, 4);
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
-      }
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const int64_t i = i0 + r0 + x;
-      if (i < row1 && j0 < N) {
-        if constexpr (Epi::kPrefetch) {
-          epi.apply(i, j0, acc[x], frag[x], rr, vec);
-        } else {
-          epi.prefetch(i, j0, frag[0], vec);
-          epi.apply(i, j0, acc[x], frag[0], rr, vec);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(sHbytes);
-#pragma unroll
-  for (int y = 0; y < 4; ++y) red[ti * NT + j0 + y] = (double)rr[y];
-  __syncthreads();
-  if (t < NT) {
-    double s = 0.0;
-    for (int q = 0; q < NI; ++q) s += red[q * NT + t];
-    rr_out[t] = s;
-  }
-  __syncthreads();
-}
-
-// Stage the reduced N x N matrix (FP64 in global) into shared memory as CT with stride
-// NT + 16/sizeof(CT), zero-padded to NT x NT.
-template <typename CT, int NT>
-__device__ __forceinline__ void stage_T(const double* __restrict__ Tred, int N, CT* sT) {
-  constexpr int LD = NT + 16 / (int)sizeof(CT);
-  for (int e = threadIdx.x; e < NT * LD; e += kThreads) {
-    const int k = e / LD, j = e % LD;
-    sT[e] = (k < N && j < N) ? (CT)__ldcg(Tred + k * N + j) : CT(0);
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------------ fused CG pass
-// Chronopoulos-Gear form of CG (algebraically the Hestenes-Stiefel recurrences): with
-// s = S p carried along, u = S r, gamma = (r, r) and delta = (r, S r) =
-// ||HA^T r||^2/(N-1) + sum_i r_i r_i^2, a step needs only one reduction:
-//   beta = gamma/gamma_old, alpha = gamma / (delta - beta gamma/alpha_old),
-//   p = r + beta p, s = u + beta s, x += alpha p, r -= alpha s.
-// One pass over the CTA's rows does the step and, on the same shared-memory tile, the
-// partial HA^T r_new, sum r_i r_new^2 and sum r_new^2 of the next step: out = [T | sig | gam].
-//
-// With the Jacobi preconditioner M = R (PC), the step is the preconditioned form with
-// z = R^{-1} r: w = S z = HA (HA^T z)/(N-1) + r, gamma = (r, z), delta = (z, S z) =
-// ||HA^T z||^2/(N-1) + gamma, p = z + beta p, s = w + beta s, and the next partials are
-// [HA^T z_new | (r_new, z_new) | (r_new, r_new)].
-template <typename CT, int NT, bool PC = false>
-__device__ __forceinline__ void passF(const CT* __restrict__ HA, int64_t row0, int64_t row1, int N,
-                                      CT* X, CT* Res, CT* P, CT* Sv, const CT* __restrict__ rv,
-                                      const CT* sT, const CT* alpha, const CT* beta, CT vinv,
-                                      unsigned char* tiles, double* __restrict__ out) {
-  constexpr int LD = NT + 16 / (int)sizeof(CT);
-  constexpr int MR = FTile<CT, NT>::MR, TR = FTile<CT, NT>::TR, C4 = NT / 4;
-  constexpr int NJ = NT / 4, NI = kThreads / NJ;
-  static_assert(NI * MR == TR, "fused tile");
-  constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
-  CT* sH = reinterpret_cast<CT*>(tiles);
-  CT* sR = sH + TR * LD;
-  CT* sP = sR + TR * LD;
-  CT* sS = sP + TR * LD;
-  CT* sX = sS + TR * LD;
-  CT* sRv = sX + TR * LD;
-  const int t = threadIdx.x;
-  const int tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * MR;                  // update map
-  const int g = t / TPG, u = t % TPG, gj = u % NG, gk = u / NG, k0 = gk * MA, ja = gj * MA;  // Gram map
-  const bool vec = (N & 3) == 0;
-  CT accT[MA][MA];
-#pragma unroll
-  for (int x = 0; x < MA; ++x)
-#pragma unroll
-    for (int y = 0; y < MA; ++y) accT[x][y] = CT(0);
-  CT sig[4] = {CT(0), CT(0), CT(0), CT(0)}, gam[4] = {CT(0), CT(0), CT(0), CT(0)};
-  CT al[4], be[4];
-#pragma unroll
-  for (int y = 0; y < 4; ++y) { al[y] = alpha[j0 + y]; be[y] = beta[j0 + y]; }
-
-  for (int64_t i0 = row0; i0 < row1; i0 += TR) {
-    __syncthreads();
-#pragma unroll
-    for (int c = t; c < TR * C4; c += kThreads) {
-      const int ii = c / C4, c0 = (c % C4) * 4;
-      const int64_t i = i0 + ii;
-      CT a[4] = {CT(0), CT(0), CT(0), CT(0)}, rr[4] = {CT(0), CT(0), CT(0), CT(0)};
-      CT pp[4] = {CT(0), CT(0), CT(0), CT(0)}, ss[4] = {CT(0), CT(0), CT(0), CT(0)};
-      CT xx[4] = {CT(0), CT(0), CT(0), CT(0)};
-      if (i < row1 && c0 < N) {
-        ld4<CT>(a, HA + i * N, c0, N, vec);
-        ld4<CT>(rr, Res + i * N, c0, N, vec);
-        ld4<CT>(pp, P + i * N, c0, N, vec);
-        ld4<CT>(ss, Sv + i * N, c0, N, vec);
-        ld4<CT>(xx, X + i * N, c0, N, vec);
-      }
-      store_vec4<CT>(sH + ii * LD + c0, a);
-      store_vec4<CT>(sR + ii * LD + c0, rr);
-      store_vec4<CT>(sP + ii * LD + c0, pp);
-      store_vec4<CT>(sS + ii * LD + c0, ss);
-      store_vec4<CT>(sX + ii * LD + c0, xx);
-    }
-    if (t < TR) {
-      const int64_t i = i0 + t;
-      sRv[t] = i < row1 ? rv[i] : CT(0);
-    }
-    __syncthreads();
-    // u = HA T / (N-1) + r_i r
-    CT acc[MR][4];
-#pragma unroll
-    for (int x = 0; x < MR; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = CT(0);
-    if (N == NT) {
-#pragma unroll 8
-      for (int k = 0; k < NT; ++k) {
-        CT a[MR], bv[4];
-#pragma unroll
-        for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * LD + k];
-        load_vec<CT>(bv, sT + k * LD + j0, 4);
-#pragma unroll
-        for (int x = 0; x < MR; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
-      }
-    } else {
-#pragma unroll 4
-      for (int k = 0; k < N; ++k) {
-        CT a[MR], bv[4];
-#pragma unroll
-        for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * LD + k];
-        load_vec<CT>(bv, sT + k * LD + j0, 4);
-#pragma unroll
-        for (int x = 0; x < MR; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
-      }
-    }
-    // the CG step on the thread's MR x 4 fragment
-#pragma unroll
-    for (int x = 0; x < MR; ++x) {
-      const int row = r0 + x;
-      const int64_t i = i0 + row;
-      if (i < row1 && j0 < N) {
-        const CT ri = sRv[row];
-        CT rv4[4], pv4[4], sv4[4], xv4[4], pn[4], sn[4], xn[4], rn[4];
-        load_vec<CT>(rv4, sR + row * LD + j0, 4);
-        load_vec<CT>(pv4, sP + row * LD + j0, 4);
-        load_vec<CT>(sv4, sS + row * LD + j0, 4);
-        load_vec<CT>(xv4, sX + row * LD + j0, 4);
-        const CT rinv = PC ? CT(1) / ri : CT(0);
-        CT zn[4];
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          // plain: z = r, w = S r = HA T/(N-1) + R r; preconditioned: z = r / R, w = HA T/(N-1) + r
-          const CT zz = PC ? rv4[y] * rinv : rv4[y];
-          const CT ww = PC ? fma(acc[x][y], vinv, rv4[y]) : fma(acc[x][y], vinv, ri * rv4[y]);
-          // beta == 0 (first step, frozen columns) selects p = z, s = w without reading the
-          // old p, s (which may hold anything, including NaN bit patterns)
-          pn[y] = be[y] == CT(0) ? zz : fma(be[y], pv4[y], zz);
-          sn[y] = be[y] == CT(0) ? ww : fma(be[y], sv4[y], ww);
-          xn[y] = fma(al[y], pn[y], xv4[y]);
-          rn[y] = fma(-al[y], sn[y], rv4[y]);
-          zn[y] = PC ? rn[y] * rinv : rn[y];
-          sig[y] = PC ? fma(rn[y], zn[y], sig[y]) : fma(ri * rn[y], rn[y], sig[y]);
-          gam[y] = fma(rn[y], rn[y], gam[y]);
-        }
-        st4<CT>(P + i * N, j0, N, vec, pn);
-        st4<CT>(Sv + i * N, j0, N, vec, sn);
-        st4<CT>(X + i * N, j0, N, vec, xn);
-        st4<CT>(Res + i * N, j0, N, vec, rn);
-        store_vec4<CT>(sR + row * LD + j0, zn);
-      }
-    }
-    __syncthreads();
-    // next step's partial Gram HA^T r_new on the same tile
-    const int nrows = (int)imin64(TR, row1 - i0);
-    for (int ii = g; ii < nrows; ii += RG) {
-      CT a[MA], v[MA];
-      load_vec<CT>(a, sH + ii * LD + k0, MA);
-      load_vec<CT>(v, sR + ii * LD + ja, MA);
-#pragma unroll
-      for (int x = 0; x < MA; ++x)
-#pragma unroll
-        for (int y = 0; y < MA; ++y) accT[x][y] = fma(a[x], v[y], accT[x][y]);
-    }
-  }
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(tiles);
-  if (RG > 1) {
-#pragma unroll
-    for (int x = 0; x < MA; ++x)
-#pragma unroll
-      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + ja + y] = (double)accT[x][y];
-    __syncthreads();
-    if (g == 0) {
-#pragma unroll
-      for (int x = 0; x < MA; ++x)
-#pragma unroll
-        for (int y = 0; y < MA; ++y) {
-          const int k = k0 + x, j = ja + y;
-          double s = 0.0;
-          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
-          if (k < N && j < N) out[k * N + j] = s;
-        }
-    }
-  } else {
-#pragma unroll
-    for (int x = 0; x < MA; ++x)
-#pragma unroll
-      for (int y = 0; y < MA; ++y) {
-        const int k = k0 + x, j = ja + y;
-        if (k < N && j < N) out[k * N + j] = (double)accT[x][y];
-      }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int y = 0; y < 4; ++y) {
-    red[ti * NT + j0 + y] = (double)sig[y];
-    red[NI * NT + ti * NT + j0 + y] = (double)gam[y];
-  }
-  __syncthreads();
-  if (t < N) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < NI; ++q) {
-      a += red[q * NT + t];
-      b += red[NI * NT + q * NT + t];
-    }
-    out[N * N + t] = a;
-    out[N * N + N + t] = b;
-  }
-  __syncthreads();
-}
-
-// Stage the reduced N x N matrix T (FP64 in global, first N*N entries of Tred) into shared
-// memory as CT with stride NT + 16/sizeof(CT), zero-padded, and return the FP64 column norms
-// ||T_:j||^2 in tn2[j] (thread j owns column j's sum over its rows; fixed order).
-template <typename CT, int NT>
-__device__ __forceinline__ void stage_T_norms(const double* __restrict__ Tred, int N, CT* sT,
-                                              double* tn2, double* scratch) {
-  constexpr int LD = NT + 16 / (int)sizeof(CT), L = kThreads / NT;
-  const int t = threadIdx.x, j = t % NT, k0 = t / NT;
-  double nrm = 0.0;
-  for (int k = k0; k < NT; k += L) {
-    const double v = (k < N && j < N) ? __ldcg(Tred + k * N + j) : 0.0;
-    sT[k * LD + j] = (CT)v;
-    nrm = fma(v, v, nrm);
-  }
-  for (int k = t; k < NT * (LD - NT); k += kThreads) sT[(k / (LD - NT)) * LD + NT + k % (LD - NT)] = CT(0);
-  scratch[t] = nrm;
-  __syncthreads();
-  if (t < NT) {
-    double s = 0.0;
-    for (int q = 0; q < L; ++q) s += scratch[q * NT + t];
-    tn2[t] = s;
-  }
-  __syncthreads();
-}
-
-// Inner-solve set-up pass A: Res = B, X = 0, and V = B (preconditioned: V = B / r) for
-// the first reduction.
-template <typename VT, bool PC>
-struct ProSetup {
-  const VT* B;
-  VT* X;
-  VT* Res;
-  const VT* rv;
-  int N;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, VT (&v)[4], bool vec) {
-    ld4<VT>(v, B + i * N, j0, N, vec);
-    const VT z[4] = {VT(0), VT(0), VT(0), VT(0)};
-    st4<VT>(X + i * N, j0, N, vec, z);
-    st4<VT>(Res + i * N, j0, N, vec, v);
-    if (PC) {
-      const VT rinv = VT(1) / rv[i];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) v[y] *= rinv;
-    }
-  }
-};
-
-// Refresh pass A (FP64): Z += X (refinement) and V = Z.
-template <typename VT>
-struct ProRefresh {
-  double* Z;
-  const VT* X;
-  int N;
-  bool accumulate;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, double (&v)[4], bool vec) {
-    ld4<double>(v, Z + i * N, j0, N, vec);
-    if (accumulate) {
-      VT x[4];
-      ld4<VT>(x, X + i * N, j0, N, vec);
-#pragma unroll
-      for (int y = 0; y < 4; ++y) v[y] += (double)x[y];
-      st4<double>(Z + i * N, j0, N, vec, v);
-    }
-  }
-};
-
-// Refresh pass B (FP64): true residual D - (HA T/(N-1) + r Z); optionally the next
-// right-hand side B = (VT) residual.
-template <typename VT>
-struct EpiRefresh {
-  const double* Z;
-  const double* D;
-  const double* r;
-  VT* B;
-  double inv;
-  int N;
-  static constexpr bool kPrefetch = false;
-  struct Frag { double z[4], d[4]; double ri; };
-  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
-    ld4<double>(f.z, Z + i * N, j0, N, vec);
-    ld4<double>(f.d, D + i * N, j0, N, vec);
-    f.ri = r[i];
-  }
-  __device__ __forceinline__ void apply(int64_t i, int j0, const double (&acc)[4], Frag& f,
-                                        double (&rr)[4], bool vec) {
-    double rt[4];
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const double q = fma(acc[y], inv, f.ri * f.z[y]);
-      rt[y] = f.d[y] - q;
-      rr[y] = fma(rt[y], rt[y], rr[y]);
-    }
-    if (B) {
-      VT b[4];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) b[y] = (VT)rt[y];
-      st4<VT>(B + i * N, j0, N, vec, b);
-    }
-  }
-};
 
 struct SolveParams {
   int64_t m;
@@ -979,7 +306,8 @@ __global__ void __launch_bounds__(kThreads) innov_kernel(
     const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
     const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
     double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
-    float* __restrict__ B32) {
+    float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
+    int split_lo) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -1014,6 +342,17 @@ __global__ void __launch_bounds__(kThreads) innov_kernel(
         D[e] = d;
         if (HA32) HA32[e] = (float)ha;
         if (B32) B32[e] = (float)d;
+        // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
+        if (HAb) {
+          const __nv_bfloat16 hi = __double2bfloat16(ha);
+          HAb[e] = hi;
+          if (split_lo) HAb[m * N + e] = __double2bfloat16(ha - (double)__bfloat162float(hi));
+        }
+        if (HAh) {
+          const __half hi = __double2half(ha);
+          HAh[e] = hi;
+          if (split_lo) HAh[m * N + e] = __double2half(ha - (double)__half2float(hi));
+        }
       }
     }
   }
@@ -1173,11 +512,14 @@ cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y
   if (fp64)
     innov_kernel<double><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const double*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
-        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr);
+        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr, nullptr, nullptr, 0);
   else
     innov_kernel<float><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const float*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
-        c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B));
+        c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B),
+        c.precision == ENKF_BF16_REFINE ? static_cast<__nv_bfloat16*>(ws.HA16) : nullptr,
+        c.precision == ENKF_FP16_REFINE ? static_cast<__half*>(ws.HA16) : nullptr,
+        c.lowprec_terms != 1 ? 1 : 0);
   return cudaGetLastError();
 }
 

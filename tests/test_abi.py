@@ -75,7 +75,7 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(case):
     elif case == "tol":
         cfg.tol = 0.0
     elif case == "reserved":
-        cfg.reserved[2] = 1
+        cfg.reserved[1] = 1
     st, h, msg = _create(cfg, rowptr, col, w, r)
     assert st == expect and not h.value and msg
 
