@@ -26,7 +26,7 @@ enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
 }
 
 void free_workspace(Workspace& ws) {
-  void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.HA16, ws.D, ws.Z, ws.B, ws.X,
+  void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.HA16, ws.HAdf, ws.Ddf, ws.Zdf, ws.D, ws.Z, ws.B, ws.X,
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
   for (void* p : ptrs)
@@ -183,6 +183,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
     allocs.push_back({(void**)&ws.r32, sizeof(float) * c.m});
     allocs.push_back({(void**)&ws.B, vs * mN});
     allocs.push_back({(void**)&ws.X, vs * mN});
+    allocs.push_back({(void**)&ws.HAdf, 8 * (size_t)mN});
+    allocs.push_back({(void**)&ws.Ddf, 8 * (size_t)mN});
+    allocs.push_back({(void**)&ws.Zdf, 8 * (size_t)mN});
   }
   if (mixed) allocs.push_back({(void**)&ws.HA16, (size_t)((c.lowprec_terms == 1 ? 2 : 4) * mN)});
   for (auto& a : allocs) {

@@ -50,6 +50,63 @@ template <typename VT, int NT> __host__ __device__ constexpr int solve_smem_byte
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+
+// ------------------------------------------------------------------ double-float arithmetic
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2 (about 44
+// significant bits). Products and sums use the error-free transformations of Dekker and
+// Knuth (TwoProd through FMA, TwoSum, Fast2Sum), written with the _rn intrinsics so that the
+// compiler cannot contract or reorder them. On this GPU FP32 issues at 64x the FP64 rate, so
+// a double-float multiply-add (15 FP32 instructions) is about 4x faster than a native DFMA.
+struct __align__(8) df32 {
+  float hi, lo;
+  __host__ __device__ df32() : hi(0.f), lo(0.f) {}
+  __device__ explicit df32(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+  __device__ df32(float h, float l) : hi(h), lo(l) {}
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ df32 df_fast2sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df32(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// c + a b
+__device__ __forceinline__ df32 fma(const df32& a, const df32& b, const df32& c) {
+  const float ph = __fmul_rn(a.hi, b.hi);
+  float pl = __fmaf_rn(a.hi, b.hi, -ph);
+  pl = __fmaf_rn(a.hi, b.lo, pl);
+  pl = __fmaf_rn(a.lo, b.hi, pl);
+  float s, e;
+  df_two_sum(c.hi, ph, s, e);
+  e = __fadd_rn(e, __fadd_rn(c.lo, pl));
+  return df_fast2sum(s, e);
+}
+// keep the FP32 / FP64 fma overloads visible next to the double-float one
+using ::fma;
+
+__device__ __forceinline__ df32 operator+(const df32& a, const df32& b) {
+  float s, e;
+  df_two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_fast2sum(s, e);
+}
+__device__ __forceinline__ df32 operator-(const df32& a) { return df32(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(const df32& a, const df32& b) { return a + (-b); }
+__device__ __forceinline__ df32 operator*(const df32& a, const df32& b) {
+  const float ph = __fmul_rn(a.hi, b.hi);
+  float pl = __fmaf_rn(a.hi, b.hi, -ph);
+  pl = __fmaf_rn(a.hi, b.lo, pl);
+  pl = __fmaf_rn(a.lo, b.hi, pl);
+  return df_fast2sum(ph, pl);
+}
+__device__ __forceinline__ df32& operator+=(df32& a, const df32& b) { a = a + b; return a; }
+
 // ------------------------------------------------------------------ 4-wide fragments
 template <typename CT> __device__ __forceinline__ void load_vec(CT* d, const CT* s, int n);
 template <> __device__ __forceinline__ void load_vec<float>(float* d, const float* s, int n) {
@@ -64,6 +121,13 @@ template <> __device__ __forceinline__ void load_vec<double>(double* d, const do
     d[q] = v.x; d[q + 1] = v.y;
   }
 }
+template <> __device__ __forceinline__ void load_vec<df32>(df32* d, const df32* s, int n) {
+  for (int q = 0; q < n; q += 2) {
+    const float4 v = *reinterpret_cast<const float4*>(s + q);
+    d[q] = df32(v.x, v.y);
+    d[q + 1] = df32(v.z, v.w);
+  }
+}
 template <typename CT> __device__ __forceinline__ void store_vec4(CT* d, const CT* s);
 template <> __device__ __forceinline__ void store_vec4<float>(float* d, const float* s) {
   *reinterpret_cast<float4*>(d) = make_float4(s[0], s[1], s[2], s[3]);
@@ -71,6 +135,10 @@ template <> __device__ __forceinline__ void store_vec4<float>(float* d, const fl
 template <> __device__ __forceinline__ void store_vec4<double>(double* d, const double* s) {
   *reinterpret_cast<double2*>(d) = make_double2(s[0], s[1]);
   *reinterpret_cast<double2*>(d + 2) = make_double2(s[2], s[3]);
+}
+template <> __device__ __forceinline__ void store_vec4<df32>(df32* d, const df32* s) {
+  *reinterpret_cast<float4*>(d) = make_float4(s[0].hi, s[0].lo, s[1].hi, s[1].lo);
+  *reinterpret_cast<float4*>(d + 2) = make_float4(s[2].hi, s[2].lo, s[3].hi, s[3].lo);
 }
 // row pointer p, columns j0..j0+3 (vec: N % 4 == 0, so the 4 columns exist and are aligned)
 template <typename CT>
@@ -683,5 +751,56 @@ struct EpiRefresh {
   }
 };
 
+
+// Double-float refresh, pass A: Z += X (X is the inner solve's correction, Z the solution in
+// double-float) and V = Z, for T = HA^T Z.
+template <typename VT>
+struct ProRefreshDF {
+  df32* Z;
+  const VT* X;
+  int N;
+  bool accumulate;
+  __device__ __forceinline__ void operator()(int64_t i, int j0, df32 (&v)[4], bool vec) {
+    ld4<df32>(v, Z + i * N, j0, N, vec);
+    if (accumulate) {
+      VT x[4];
+      ld4<VT>(x, X + i * N, j0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) v[y] = v[y] + df32((float)x[y], 0.f);
+      st4<df32>(Z + i * N, j0, N, vec, v);
+    }
+  }
+};
+
+// Double-float refresh, pass B: the true residual D - (HA T' + r Z) with T' = T/(N-1) staged
+// in double-float; writes the next right-hand side B (float) and accumulates ||residual||^2.
+template <typename VT>
+struct EpiRefreshDF {
+  const df32* Z;
+  const df32* D;
+  const double* r;
+  VT* B;
+  int N;
+  df32 inv;   // 1/(N-1)
+  static constexpr bool kPrefetch = false;
+  struct Frag { df32 z[4], d[4]; df32 ri; };
+  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
+    ld4<df32>(f.z, Z + i * N, j0, N, vec);
+    ld4<df32>(f.d, D + i * N, j0, N, vec);
+    f.ri = df32(r[i]);
+  }
+  __device__ __forceinline__ void apply(int64_t i, int j0, const df32 (&acc)[4], Frag& f,
+                                        df32 (&rr)[4], bool vec) {
+    VT b[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const df32 q = fma(f.ri, f.z[y], acc[y] * inv);
+      const df32 rt = f.d[y] - q;
+      rr[y].hi = __fmaf_rn(rt.hi, rt.hi, rr[y].hi);   // the norm only needs float accuracy
+      b[y] = (VT)rt.hi;
+    }
+    if (B) st4<VT>(B + i * N, j0, N, vec, b);
+  }
+};
 
 }  // namespace enkf

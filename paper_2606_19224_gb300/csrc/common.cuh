@@ -117,6 +117,9 @@ struct Workspace {
   double* HA64 = nullptr;       // [m][N]
   float* HA32 = nullptr;        // [m][N]   (FP32 and mixed modes)
   void* HA16 = nullptr;         // [m][N]   BF16 or FP16 (mixed modes)
+  void* HAdf = nullptr;         // [m][N]   double-float HA, D and solution (FP32, mixed modes)
+  void* Ddf = nullptr;
+  void* Zdf = nullptr;
   double* D = nullptr;          // [m][N]
   double* Z = nullptr;          // [m][N]   FP64 solution (FP64 mode: the CG iterate itself)
   void* B = nullptr;            // [m][N]   inner right-hand side (FP32 mode)

@@ -44,6 +44,9 @@ struct SolveParams {
   void* P;
   void* Sv;
   double* Z;
+  const df32* HAdf;   // HA and D in double-float, and the double-float solution (FP32 mode)
+  const df32* Ddf;
+  df32* Zdf;
   double* Tpart;
   double* Tred;
   double* rrpart;
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, ((NT == 128 || (NT == 64 && sizeof(V
   rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
     const double d = p.D[i * N + j];
     acc = fma(d, d, acc);
-    if (refine) p.Z[i * N + j] = 0.0;
+    if (refine) p.Zdf[i * N + j] = df32(0.f, 0.f);
   }, s_tmp, scratch);
   if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
   ok = bar.sync();
@@ -235,9 +238,15 @@ __global__ void __launch_bounds__(kThreads, ((NT == 128 || (NT == 64 && sizeof(V
     if (!ok) break;
     total_iter += it;
 
-    // ---- FP64 refresh: Z (+)= X; T = HA^T Z; W; true residual D - S Z; next right-hand side
-    ProRefresh<VT> pro{p.Z, X, N, refine};
-    passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
+    // ---- refresh: Z (+)= X; T = HA^T Z; W = T/(N-1); true residual D - S Z; next right-hand
+    // side. FP64 in the FP64 mode; double-float (FP32 pairs) in the FP32 mode.
+    if constexpr (sizeof(VT) == 8) {
+      ProRefresh<VT> pro{p.Z, X, N, refine};
+      passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
+    } else {
+      ProRefreshDF<VT> pro{p.Zdf, X, N, true};
+      passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
+    }
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
     if (!(ok = bar.sync())) break;
@@ -247,11 +256,19 @@ __global__ void __launch_bounds__(kThreads, ((NT == 128 || (NT == 64 && sizeof(V
       tick(PH_REFRESH);
       break;
     }
-    double* sT64 = reinterpret_cast<double*>(uni);
-    stage_T<double, NT>(p.Tred, N, sT64);
-    constexpr int LD64 = NT + 2;
-    EpiRefresh<VT> epi{p.Z, p.D, p.r, refine ? static_cast<VT*>(p.B) : nullptr, inv_nm1, N};
-    passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
+    if constexpr (sizeof(VT) == 8) {
+      double* sT64 = reinterpret_cast<double*>(uni);
+      stage_T<double, NT>(p.Tred, N, sT64);
+      constexpr int LD64 = NT + 2;
+      EpiRefresh<VT> epi{p.Z, p.D, p.r, nullptr, inv_nm1, N};
+      passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
+    } else {
+      df32* sTd = reinterpret_cast<df32*>(uni);
+      stage_T<df32, NT>(p.Tred, N, sTd);
+      constexpr int LDD = NT + 2;
+      EpiRefreshDF<VT> epi{p.Zdf, p.Ddf, p.r, static_cast<VT*>(p.B), N, df32(inv_nm1)};
+      passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+    }
     if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
     if (!(ok = bar.sync())) break;
     reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
@@ -307,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) innov_kernel(
     const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
     double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
     float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
-    int split_lo) {
+    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -342,6 +359,8 @@ __global__ void __launch_bounds__(kThreads) innov_kernel(
         D[e] = d;
         if (HA32) HA32[e] = (float)ha;
         if (B32) B32[e] = (float)d;
+        if (HAdf) HAdf[e] = df32(ha);
+        if (Ddf) Ddf[e] = df32(d);
         // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
         if (HAb) {
           const __nv_bfloat16 hi = __double2bfloat16(ha);
@@ -512,14 +531,14 @@ cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y
   if (fp64)
     innov_kernel<double><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const double*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
-        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr, nullptr, nullptr, 0);
+        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr, nullptr, nullptr, 0, nullptr, nullptr);
   else
     innov_kernel<float><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const float*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
         c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B),
         c.precision == ENKF_BF16_REFINE ? static_cast<__nv_bfloat16*>(ws.HA16) : nullptr,
         c.precision == ENKF_FP16_REFINE ? static_cast<__half*>(ws.HA16) : nullptr,
-        c.lowprec_terms != 1 ? 1 : 0);
+        c.lowprec_terms != 1 ? 1 : 0, static_cast<df32*>(ws.HAdf), static_cast<df32*>(ws.Ddf));
   return cudaGetLastError();
 }
 
@@ -549,6 +568,9 @@ cudaError_t launch_solve(enkf_handle_s* h) {
   p.P = ws.P;
   p.Sv = ws.Sv;
   p.Z = ws.Z;
+  p.HAdf = static_cast<const df32*>(ws.HAdf);
+  p.Ddf = static_cast<const df32*>(ws.Ddf);
+  p.Zdf = static_cast<df32*>(ws.Zdf);
   p.Tpart = ws.Tpart;
   p.Tred = ws.Tred;
   p.rrpart = ws.rrpart;

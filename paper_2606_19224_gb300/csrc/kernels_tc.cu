@@ -5,10 +5,11 @@
 //   u = HA T / (N-1)          one M=128 x N x K=N MMA per 128-row tile (D in TMEM)
 //   T_next = HA^T z_next      one M=128 (k, zero-padded) x N x K=128 MMA per tile,
 //                             accumulated in TMEM across the CTA's tiles
-// Each inner CG solve runs until its residual fell by a precision-dependent factor (or for
-// at most `refresh_every` steps); then the residual is recomputed in FP32 on CUDA cores,
-// r = D - S x, and the next inner solve starts from it (iterative refinement of the
-// low-precision solve).
+// Each inner CG solve (for a correction, from zero) runs until its residual fell by a
+// precision-dependent factor (or for at most `refresh_every` steps); then the correction is
+// added to the solution, kept in double-float (FP32 pairs), and the true residual D - S Z is
+// recomputed in double-float on CUDA cores as the next inner right-hand side (iterative
+// refinement of the low-precision solve, with an FP64-grade final residual check).
 //
 // Operands are staged by this kernel into shared memory in the canonical K-major,
 // no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, K-direction core stride
@@ -297,70 +298,6 @@ __device__ void passF_tc(const T16* __restrict__ HAhi, const T16* __restrict__ H
   __syncthreads();
 }
 
-// ------------------------------------------------------------------ FP32 helper operators
-// V = z(r): r (plain) or r / R (preconditioned), for the restart reduction.
-template <bool PC>
-struct ProZ {
-  const float* Res;
-  const float* rv;
-  int N;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, float (&v)[4], bool vec) {
-    ld4<float>(v, Res + i * N, j0, N, vec);
-    if (PC) {
-      const float rinv = 1.f / rv[i];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) v[y] *= rinv;
-    }
-  }
-};
-// V = X (FP32), for T_x = HA^T x in the refresh.
-struct ProX {
-  const float* X;
-  int N;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, float (&v)[4], bool vec) {
-    ld4<float>(v, X + i * N, j0, N, vec);
-  }
-};
-// FP32 refresh: Res = D - (HA T_x/(N-1) + r x), rr = ||Res||^2.
-struct EpiResid32 {
-  const float* X;
-  const float* D32;
-  float* Res;
-  const float* rv;
-  float inv;
-  int N;
-  static constexpr bool kPrefetch = true;
-  struct Frag { float x[4], d[4]; float ri; };
-  __device__ __forceinline__ void prefetch(int64_t i, int j0, Frag& f, bool vec) {
-    ld4<float>(f.x, X + i * N, j0, N, vec);
-    ld4<float>(f.d, D32 + i * N, j0, N, vec);
-    f.ri = rv[i];
-  }
-  __device__ __forceinline__ void apply(int64_t i, int j0, const float (&acc)[4], Frag& f,
-                                        float (&rr)[4], bool vec) {
-    float r[4];
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      r[y] = f.d[y] - fmaf(acc[y], inv, f.ri * f.x[y]);
-      rr[y] = fmaf(r[y], r[y], rr[y]);
-    }
-    st4<float>(Res + i * N, j0, N, vec, r);
-  }
-};
-// X (FP32) -> Z (FP64) for the optional FP64 true-residual check.
-struct ProXtoZ {
-  const float* X;
-  double* Z;
-  int N;
-  __device__ __forceinline__ void operator()(int64_t i, int j0, double (&v)[4], bool vec) {
-    float x[4];
-    ld4<float>(x, X + i * N, j0, N, vec);
-#pragma unroll
-    for (int y = 0; y < 4; ++y) v[y] = (double)x[y];
-    st4<double>(Z + i * N, j0, N, vec, v);
-  }
-};
-
 // Stage T^T/(N-1) scaled per column (ts_j = 1/rms_k(T_kj/(N-1))) into the B operand of the
 // u MMA (rows j, K-major over k); also the FP64 column norms ||T_:j||^2.
 template <typename T16, int NT, int TERMS>
@@ -399,22 +336,23 @@ struct MixedParams {
   int N;
   const void* HA16;
   const float* HA32;
-  const double* HA64;
+  const df32* HAdf;
+  const df32* Ddf;
+  df32* Zdf;
   const double* D;
-  const float* D32;
+  float* B;         // right-hand side of the current inner solve (D, then refreshed residuals)
   const double* r;
   const float* r32;
   float* X;
   float* Res;
   float* P;
   float* Sv;
-  double* Z;
   double* Tpart;
   double* Tred;
   double* rrpart;
   double* W;
   double tol, inner_tol, itol_floor;
-  int max_iter, refresh_every, true_residual;
+  int max_iter, refresh_every;
   int* col_iters;
   double* col_relres;
   double* col_true;
@@ -483,12 +421,11 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   int par = 0;
   bool ok = true;
 
-  // ---- ||d_j||^2 (FP64), X = 0, Res = D
+  // ---- ||d_j||^2 (FP64) and Z = 0 (double-float solution accumulator)
   rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
     const double d = p.D[i * N + j];
     acc = fma(d, d, acc);
-    p.X[i * N + j] = 0.f;
-    p.Res[i * N + j] = p.D32[i * N + j];
+    p.Zdf[i * N + j] = df32(0.f, 0.f);
   }, s_tmp, scratch);
   if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
   ok = bar.sync();
@@ -498,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     if (t < NT) {
       s_done[t] = (t >= N || s_dn2[t] == 0.0) ? 1 : 0;
       s_iters[t] = 0;
-      s_true[t] = -1.0;
+      s_true[t] = (t < N && s_dn2[t] == 0.0) ? 0.0 : -1.0;
       s_rel[t] = (t < N && s_dn2[t] > 0.0) ? 1.0 : 0.0;
       s_prev[t] = 2.0;
       s_alpha_v[t] = 0.f;
@@ -509,10 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   }
   int total = 0, cycles = 0;
   while (ok) {
-    // ---- restart: first reduction of [HA^T z | slot A | slot B] with FP32 HA
+    // ---- inner solve of S X = B from X = 0: first reduction of [HA^T z | slot A | slot B]
     {
-      ProZ<PC> pro{p.Res, p.r32, N};
-      passA<float, NT, ProZ<PC>, PC>(p.HA32, row0, row1, N, p.r32, true, pro, uni, Tp);
+      ProSetup<float, PC> pro{p.B, p.X, p.Res, p.r32, N};
+      passA<float, NT, ProSetup<float, PC>, PC>(p.HA32, row0, row1, N, p.r32, true, pro, uni, Tp);
     }
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
@@ -548,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
           }
           // p^T S p = delta - beta gamma/alpha_old cancels; with BF16/FP16 contractions a
           // small or non-positive value means the low-precision recurrences have drifted:
-          // this column's inner solve ends here and the FP32 refresh restarts it
+          // this column's inner solve ends here and the refresh restarts it
           if (!isfinite(den) || !(den > 0.05 * delta)) { a = 0; be = 0.0; }
           else al = cg / den;
         }
@@ -567,9 +504,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       }
       __syncthreads();
       if (!s_flag[0]) break;
-      passF_tc<T16, NT, PC, TERMS>(HAhi, HAlo, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v, s_beta_v,
-                            s_zs, s_ts, sAu, sBu, sAg, sBg, sacc, tmem, &mbar[0], &mbar[1], ph_u, ph_g,
-                            p.status, ok, Tp);
+      passF_tc<T16, NT, PC, TERMS>(HAhi, HAlo, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+                                   s_beta_v, s_zs, s_ts, sAu, sBu, sAg, sBg, sacc, tmem, &mbar[0],
+                                   &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       if (!(ok = bar.sync() && ok)) break;
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
       if (!(ok = bar.sync())) break;
@@ -586,22 +523,22 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     if (!ok) break;
     total += it;
     ++cycles;
-    // ---- FP32 refresh: T_x = HA^T x; W = T_x/(N-1); Res = D - S x
+    // ---- double-float refresh: Z += X; T = HA^T Z; W; true residual D - S Z -> next B
     {
-      ProX pro{p.X, N};
-      passA<float, NT>(p.HA32, row0, row1, N, p.r32, false, pro, uni, Tp);
+      ProRefreshDF<float> pro{p.Zdf, p.X, N, true};
+      passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
     }
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
     if (!(ok = bar.sync())) break;
     if (b == 0)
       for (int e = t; e < N * N; e += kThreads) p.W[e] = __ldcg(p.Tred + e) * inv_nm1;
-    float* sT32 = reinterpret_cast<float*>(uni);
-    stage_T<float, NT>(p.Tred, N, sT32);
     {
-      constexpr int LD32 = NT + 4;
-      EpiResid32 epi{p.X, p.D32, p.Res, p.r32, (float)inv_nm1, N};
-      passB<float, NT>(p.HA32, row0, row1, N, sT32, uni + NT * LD32 * sizeof(float), epi, s_tmp);
+      df32* sTd = reinterpret_cast<df32*>(uni);
+      stage_T<df32, NT>(p.Tred, N, sTd);
+      constexpr int LDD = NT + 2;
+      EpiRefreshDF<float> epi{p.Zdf, p.Ddf, p.r, p.B, N, df32(inv_nm1)};
+      passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
     }
     if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
     if (!(ok = bar.sync())) break;
@@ -610,8 +547,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     if (t < N) {
       const double rel = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
       s_rel[t] = rel;
+      s_true[t] = rel;
       if (!s_done[t]) {
-        // converged, or stalled at the FP32 refresh's floor (no halving over a cycle)
+        // converged, or stalled (no halving over a cycle)
         if (rel <= p.tol || (cycles >= 2 && rel > 0.5 * s_prev[t])) s_done[t] = 1;
       }
       s_prev[t] = rel;
@@ -629,31 +567,6 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     }
     __syncthreads();
     if (s_flag[1]) break;
-  }
-
-  // ---- optional FP64 true residual of the final x, and W from FP64 HA
-  if (ok && p.true_residual) {
-    ProXtoZ pro{p.X, p.Z, N};
-    passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
-    if ((ok = bar.sync())) {
-      reduce_slice(p.Tpart, G, NE, p.Tred, scratch);
-      ok = bar.sync();
-    }
-    if (ok) {
-      if (b == 0)
-        for (int e = t; e < N * N; e += kThreads) p.W[e] = __ldcg(p.Tred + e) * inv_nm1;
-      double* sT64 = reinterpret_cast<double*>(uni);
-      stage_T<double, NT>(p.Tred, N, sT64);
-      constexpr int LD64 = NT + 2;
-      EpiRefresh<double> epi{p.Z, p.D, p.r, nullptr, inv_nm1, N};
-      passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
-      if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
-      if ((ok = bar.sync())) {
-        reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
-        if (t < N) s_true[t] = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
-        __syncthreads();
-      }
-    }
   }
 
   if (b == 0 && t < N) {
@@ -727,16 +640,17 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.N = c.N;
   p.HA16 = ws.HA16;
   p.HA32 = ws.HA32;
-  p.HA64 = ws.HA64;
+  p.HAdf = static_cast<const df32*>(ws.HAdf);
+  p.Ddf = static_cast<const df32*>(ws.Ddf);
+  p.Zdf = static_cast<df32*>(ws.Zdf);
   p.D = ws.D;
-  p.D32 = static_cast<const float*>(ws.B);
+  p.B = static_cast<float*>(ws.B);
   p.r = ws.r;
   p.r32 = ws.r32;
   p.X = static_cast<float*>(ws.X);
   p.Res = static_cast<float*>(ws.Res);
   p.P = static_cast<float*>(ws.P);
   p.Sv = static_cast<float*>(ws.Sv);
-  p.Z = ws.Z;
   p.Tpart = ws.Tpart;
   p.Tred = ws.Tred;
   p.rrpart = ws.rrpart;
@@ -747,7 +661,6 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.itol_floor = mixed_split(c) ? 1e-3 : (c.precision == ENKF_BF16_REFINE ? 2e-2 : 4e-3);
   p.max_iter = c.max_iter;
   p.refresh_every = c.refresh_every;
-  p.true_residual = c.true_residual;
   p.col_iters = ws.col_iters;
   p.col_relres = ws.col_relres;
   p.col_true = ws.col_true;

@@ -97,6 +97,8 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
       {(void**)&ws.Res, vs * mN}, {(void**)&ws.P, vs * mN}, {(void**)&ws.Sv, vs * mN},
       {(void**)&ws.HA32, fp64 ? 0 : 4 * mN}, {(void**)&ws.B, fp64 ? 0 : vs * mN},
       {(void**)&ws.X, fp64 ? 0 : vs * mN}, {(void**)&ws.r32, fp64 ? 0 : 4 * size_t(c.m)},
+      {(void**)&ws.HAdf, fp64 ? 0 : 8 * mN}, {(void**)&ws.Ddf, fp64 ? 0 : 8 * mN},
+      {(void**)&ws.Zdf, fp64 ? 0 : 8 * mN},
       {(void**)&ws.Tpart, 8 * size_t(h.launch.G) * NE}, {(void**)&ws.Tred, 8 * NE},
       {(void**)&ws.rrpart, 8 * 2 * size_t(h.launch.G) * h.launch.NT},
       {(void**)&ws.Wacc, 8 * size_t(c.N) * c.N}, {(void**)&ws.W, 8 * size_t(c.N) * c.N},

@@ -30,19 +30,20 @@ def test_split_mixed_matches_exact_oracle(lib, prec, pc, shape):
     n, N, m = shape
     side = int(round(n ** 0.5))
     p = synth.grf_problem(side, 6.0, N, m, 0.25, 1.0, seed=11 * n + N + m, dtype=np.float32)
-    an, Xa, st = _run(lib, p, prec, tol=1e-5, precondition=pc, true_residual=1)
+    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=pc)
     E = oracle.obs_perturbations(7, 3, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
     err = oracle.rel_frobenius(Xa, ref)
     assert st["status"] == "ok", st
     assert err <= 1e-4, (err, st)
-    assert 0 < st["true_relres_max"] <= 1e-4, st
+    # the refinement's residual is recomputed in double-float (FP64-grade) each cycle
+    assert 0 < st["true_relres_max"] <= 1e-8, st
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_single_term_mixed_on_a_well_conditioned_case(lib, prec):
     p = synth.grf_problem(64, 6.0, 64, 1024, 0.25, 1.0, seed=5, dtype=np.float32)
-    an, Xa, st = _run(lib, p, prec, tol=1e-5, precondition=1, lowprec_terms=1, true_residual=1)
+    an, Xa, st = _run(lib, p, prec, tol=1e-6, precondition=1, lowprec_terms=1)
     E = oracle.obs_perturbations(7, 3, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
     assert oracle.rel_frobenius(Xa, ref) <= 1e-4
