@@ -1,0 +1,154 @@
+"""Pins of the warm-start oracle (oracle/warmstart.py) to facts outside itself: a normal-table
+value of Phi, finite differences (brute force) for every gradient entry, the closed form of
+Adam's first step, and the identity R Z = D - HA W of the exact solve of S Z = D
+(Eq. matvec_decomp with W = HA^T Z/(N-1))."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import warmstart as ws
+
+
+def test_gelu_values():
+    # x Phi(x) with Phi(1.959964) = 0.975 (standard normal table) and Phi(0) = 1/2
+    x = 1.959963984540054
+    assert abs(ws.gelu(np.array(x)) / x - 0.975) < 1e-12
+    assert ws.gelu(np.array(0.0)) == 0.0
+    xs = np.linspace(-6, 6, 101)
+    assert np.allclose(ws.gelu(xs) - ws.gelu(-xs), xs, atol=1e-15, rtol=0)   # x(Phi(x) + Phi(-x)) = x
+    assert abs(ws.gelu_grad(np.array(0.0)) - 0.5) < 1e-15
+
+
+def test_gelu_grad_finite_difference():
+    xs = np.linspace(-5, 5, 41)
+    h = 1e-6
+    fd = (ws.gelu(xs + h) - ws.gelu(xs - h)) / (2 * h)
+    assert np.max(np.abs(fd - ws.gelu_grad(xs))) < 1e-8
+
+
+def _tiny(seed=0, shape=(5, 4, 2, 3), B=7):
+    rng = np.random.default_rng(seed)
+    P = ws.param_count(*shape)
+    theta = rng.standard_normal(P) * 0.7
+    Ws, mu_in, sd_in, mu_out, sd_out = ws.unpack(theta, *shape)
+    # standardisation entries: positive scales
+    off = P - 2 * shape[0] - 2 * shape[3]
+    theta[off + shape[0]:off + 2 * shape[0]] = rng.uniform(0.5, 2.0, shape[0])
+    theta[P - shape[3]:] = rng.uniform(0.5, 2.0, shape[3])
+    X = rng.standard_normal((B, shape[0])) * 2
+    T = rng.standard_normal((B, shape[3]))
+    return theta, shape, X, T
+
+
+def test_param_count_layout():
+    assert ws.param_count(5, 4, 2, 3) == (4 * 5 + 4) + (4 * 4 + 4) + (3 * 4 + 3) + 2 * 5 + 2 * 3
+    assert ws.param_count(1088, 512, 3, 64) == 1088 * 512 + 512 + 2 * (512 * 512 + 512) + 512 * 64 + 64 + 2 * 1088 + 2 * 64
+
+
+def test_loss_grad_matches_finite_differences():
+    theta, shape, X, T = _tiny()
+    L, g = ws.loss_grad(theta, shape, X, T)
+    h = 1e-6
+    trained = ws.param_count(*shape) - 2 * shape[0] - 2 * shape[3]
+    fd = np.zeros(trained)
+    for k in range(trained):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd[k] = (ws.loss_grad(tp, shape, X, T)[0] - ws.loss_grad(tm, shape, X, T)[0]) / (2 * h)
+    assert np.max(np.abs(fd - g[:trained])) < 1e-7 * max(1.0, np.max(np.abs(fd)))
+    assert np.all(g[trained:] == 0)
+
+
+def test_loss_with_zero_weights_is_bias_fit():
+    theta, shape, X, T = _tiny(1)
+    Ws, mu_in, sd_in, mu_out, sd_out = ws.unpack(theta, *shape)
+    W, b = Ws[-1]
+    theta2 = theta.copy()
+    # zero the output weights: the prediction is the output bias for every row
+    off = sum(o * i + o for i, o in ws.layer_dims(*shape)[:-1])
+    o, i = ws.layer_dims(*shape)[-1][1], ws.layer_dims(*shape)[-1][0]
+    theta2[off:off + o * i] = 0.0
+    L, _ = ws.loss_grad(theta2, shape, X, T)
+    t_std = (T - mu_out) / sd_out
+    assert abs(L - np.mean((b[None, :] - t_std) ** 2)) < 1e-14
+    Y = ws.forward(theta2, shape, X)
+    assert np.allclose(Y, mu_out + sd_out * b, rtol=1e-15, atol=1e-15)
+
+
+def test_adam_first_steps_closed_form():
+    # bias correction makes every step of a constant gradient exactly lr * g / (|g| + eps)
+    g = np.array([3.0, -0.25, 1e-3])
+    theta = np.zeros(3)
+    m = np.zeros(3)
+    v = np.zeros(3)
+    lr, eps = 1e-2, 1e-8
+    for step in (1, 2, 3):
+        theta, m, v = ws.adam(theta, g, m, v, step, lr, eps=eps)
+        assert np.allclose(theta, -step * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+    # and it minimises a quadratic
+    th, m, v = np.array([5.0]), np.zeros(1), np.zeros(1)
+    for step in range(1, 3001):
+        th, m, v = ws.adam(th, th.copy(), m, v, step, 0.05)
+    assert abs(th[0]) < 1e-2
+
+
+def test_standardization():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((50, 4)) * [1, 2, 3, 0] + [0, 1, -2, 7]
+    T = rng.standard_normal((50, 2))
+    mx, sx, mt, st = ws.standardization(X, T)
+    assert np.allclose(mx, X.mean(0)) and np.allclose(sx[:3], X.std(0)[:3]) and sx[3] == 1.0
+    assert np.allclose(mt, T.mean(0)) and np.allclose(st, T.std(0))
+
+
+def test_sketch_indices():
+    assert ws.sketch_indices(10, 4).tolist() == [0, 2, 5, 7]
+    assert ws.sketch_indices(3, 6).tolist() == [0, 0, 1, 1, 2, 2]
+
+
+def _small_problem(seed=3, n=300, N=12, m=80):
+    rng = np.random.default_rng(seed)
+    Xf = rng.standard_normal((n, N)) + rng.standard_normal(n)[:, None]
+    rowptr = np.arange(m + 1, dtype=np.int32)
+    col = np.sort(rng.choice(n, m, replace=False)).astype(np.int32)
+    w = np.ones(m)
+    r = rng.uniform(0.5, 1.5, m)
+    y = rng.standard_normal(m)
+    E = rng.standard_normal((m, N)) * np.sqrt(r)[:, None]
+    return Xf, rowptr, col, w, r, y, E
+
+
+def test_exact_target_decodes_to_exact_solution():
+    Xf, rowptr, col, w, r, y, E = _small_problem()
+    N = Xf.shape[1]
+    Xa, info = oracle.cgd_enkf(Xf, rowptr, col, w, r, y, E, tol=1e-14)
+    HA, D, Z = info["Zhat"], info["D"], info["Z"]
+    # Z from an explicit dense solve of S Z = D (not from CG)
+    S = HA @ HA.T / (N - 1) + np.diag(r)
+    Zd = np.linalg.solve(S, D)
+    assert np.max(np.abs(Z - Zd)) < 1e-9 * np.max(np.abs(Zd))
+    W = HA.T @ Zd / (N - 1)
+    Z0 = ws.decode(HA, D, r, W)
+    assert np.max(np.abs(Z0 - Zd)) < 1e-10 * np.max(np.abs(Zd))
+    # and the features' g satisfies (I + HA^T R^-1 HA/(N-1)) c_j = g_j for c_j = W e_j
+    F, s = ws.features(HA, D, r, 16)
+    g = F[:, 16:].T * s[None, :]
+    G = np.eye(N) + HA.T @ (HA / r[:, None]) / (N - 1)
+    assert np.max(np.abs(G @ W - g)) < 1e-10 * np.max(np.abs(g))
+    T = ws.targets(W, s)
+    assert np.allclose(T * s[:, None], W.T)
+
+
+def test_decoded_residual_lies_in_span_of_HA():
+    Xf, rowptr, col, w, r, y, E = _small_problem(4)
+    N = Xf.shape[1]
+    _, info = oracle.cgd_enkf(Xf, rowptr, col, w, r, y, E, tol=1e-12)
+    HA, D = info["Zhat"], info["D"]
+    C = np.random.default_rng(0).standard_normal((N, N))
+    Z0 = ws.decode(HA, D, r, C)
+    res = D - (HA @ (HA.T @ Z0) / (N - 1) + r[:, None] * Z0)
+    coef, *_ = np.linalg.lstsq(HA, res, rcond=None)
+    assert np.max(np.abs(HA @ coef - res)) < 1e-10 * np.max(np.abs(res))
