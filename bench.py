@@ -31,6 +31,21 @@ WORKLOAD = "grf512_N64_m65536"
 METRIC = "analysis steps/s and HBM-roofline fraction vs plain FP64 GPU CG at stated error"
 UNIT = "analyses/s"
 L2_FLUSH_BYTES = 256 << 20
+BATCH_WORKLOAD = "batched256_grf"
+
+
+def B_ITER(m, N):
+    """Algorithmic DRAM bytes of one fused FP32 CG step (Chronopoulos-Gear form): HA read
+    once (4 m N), the iterate, residual, direction and S-direction read and written
+    (4 x 8 m N), r read (4 m)."""
+    return 36 * m * N + 4 * m
+
+
+def B_REF(m, N):
+    """Algorithmic DRAM bytes of one double-float residual refresh: pass A reads HA (8 m N),
+    reads and writes Z (16 m N) and reads X (4 m N); pass B reads HA, Z and D (24 m N) and
+    writes the next right-hand side (4 m N)."""
+    return 56 * m * N
 
 # DRAM bytes (read + write) of one solve_kernel launch on this workload, from the ncu capture
 # summarised in profiles/solve_kernel_grf512_N64_m65536.md, and the hash of the kernel source
@@ -40,7 +55,7 @@ NCU_TRAFFIC = {"fp32": {"bytes": 4.126482e9, "src_sha": None}}
 
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("kernels_fp.cu", "common.cuh"):
+    for f in ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"):
         with open(os.path.join(ROOT, "paper_2606_19224_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -303,8 +318,8 @@ def run_ours(args):
     mN = m * N
     it_avg = float(np.mean(iters))
     ref_avg = float(np.mean(refines))
-    b_iter = 2 * mN * 4 + 8 * mN * 4 + 2 * m * 8          # per CG step (the plain CG count)
-    b_ref = 56 * mN                                       # FP64 refresh: HA64 x2, Z, D, X, B
+    b_iter = B_ITER(m, N)
+    b_ref = B_REF(m, N)
     alg_bytes = it_avg * b_iter + ref_avg * b_ref
     solve_avg_ms = float(np.mean(solve_ms))
     peak, peak_src = _peaks()
@@ -340,6 +355,138 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def _gen_problem(args):
+    import numpy as np
+    import synth
+    spec, seed, i = args
+    return synth.grf_problem(spec["side"], spec["ell"], spec["N"], spec["m"], 0.5, 1.5, seed, dtype=np.float32,
+                             sub=1000 + i)
+
+
+def run_batched(args):
+    """256 independent analyses of uneven size (n log-uniform in [4096, 262144], m = n/4,
+    N in {16, 32, 64, 128}, GRF ensembles with correlation length U[4, 32], r ~ U[0.5, 1.5])
+    in one persistent launch replayed from a CUDA graph; FP32 with Jacobi preconditioning,
+    tol 1e-8. value = analyses/s."""
+    import multiprocessing as mp
+    import numpy as np
+    import synth
+    ws, rank, local = _dist()
+    seed = args.seed + 1000 * rank
+    specs = synth.problems.batched_problem_specs(256, seed)
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any GPU call
+        probs = pool.map(_gen_problem, [(sp, seed, i) for i, sp in enumerate(specs)])
+    gen_s = time.time() - t0
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2606_19224_gb300 as enkf
+    ba = enkf.BatchAnalysis([dict(n=p.n, m=p.m, N=p.N, rowptr=p.rowptr, col=p.col, w=p.w, r=p.r) for p in probs],
+                            tol=1e-8)
+    Xf = [torch.from_numpy(p.Xf).to(dev) for p in probs]
+    y = [torch.from_numpy(p.y).to(dev) for p in probs]
+    out = [torch.empty_like(x) for x in Xf]
+    seeds = [seed + i for i in range(len(probs))]
+    tune_ms = ba.tune(Xf, y, seeds, None, out=out)
+    plan = ba.plan()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        ba.analyze(Xf, y, seeds, [k] * len(probs), out=out)
+    st = ba.stats()
+    if np.any(st["status"] != 0):
+        raise SystemExit(f"warm-up batch failed: {st['status']}")
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters, refs = [], []
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ba.analyze(Xf, y, seeds, [args.warmup + k] * len(probs), out=out)
+        ev[k][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    st = ba.stats()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    count = len(probs)
+    value = ws * count * args.steps / (ms / 1e3)
+    # end to end: pinned host inputs copied in, the batched call, results copied out
+    Xh = [torch.from_numpy(p.Xf).pin_memory() for p in probs]
+    yh = [torch.from_numpy(p.y).pin_memory() for p in probs]
+    Xo = [torch.empty_like(x).pin_memory() for x in Xh]
+    e2e_steps = max(2, args.steps // 4)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        for a, b in zip(Xf, Xh):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(y, yh):
+            a.copy_(b, non_blocking=True)
+        ba.analyze(Xf, y, seeds, [k] * count, out=out)
+        for a, b in zip(Xo, out):
+            a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * count * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in Xh) + sum(v.numel() * 8 for v in yh)),
+           "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in Xo))}
+    if rank != 0:
+        return
+    # accuracy: a sample of problems against the exact FP64 analysis
+    import oracle
+    ba.analyze(Xf, y, seeds, [0] * count, out=out)
+    torch.cuda.synchronize()
+    errs = []
+    order = sorted(range(count), key=lambda i: probs[i].m)
+    for i in order[::max(1, count // 8)][:8]:
+        p = probs[i]
+        E = oracle.obs_perturbations(seeds[i], 0, p.r, p.N)
+        ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+        errs.append(oracle.rel_frobenius(out[i].double().cpu().numpy(), ref))
+    # roofline: algorithmic bytes of all problems of one launch over the launch time
+    alg = 0.0
+    for i, p in enumerate(probs):
+        alg += st["iters_max"][i] * B_ITER(p.m, p.N) + st["refinements"][i] * B_REF(p.m, p.N)
+        alg += 4 * p.n * p.N * 2 + 32 * p.m * p.N   # update (X_f in, X_a out); innovations out (HA, B, D, HA and D double-float)
+    launch_ms = ms / args.steps
+    peak, peak_src = _peaks()
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded GRF ensembles, random point observations)",
+            "config": {"workload": BATCH_WORKLOAD, "problems": count,
+                       "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+                       "sum_mN": int(sum(p.m * p.N for p in probs)), "tol": 1e-8,
+                       "precision": "fp32 CG + double-float refresh, preconditioned by R",
+                       "plan": plan, "tune_ms": tune_ms, "l2": "flushed between steps",
+                       "generation_s": gen_s},
+            "error": {"rel_frobenius_vs_fp64_oracle_max": max(errs), "sampled_problems": len(errs),
+                      "status_ok": int(np.sum(st["status"] == 0))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel<128>",
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms},
+            "e2e": e2e, "gpu_launches": args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,11 +496,14 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD])
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -92,7 +92,8 @@ typedef struct enkf_config {
                              refreshes; 0 (default): each inner solve runs until its
                              residual fell by inner_tol (at least 2e-2 BF16, 4e-3 FP16)  */
   int32_t perturb_obs;    /* 1: E ~ N(0, R) drawn from (seed, counter); 0: E = 0         */
-  int32_t warm_start;     /* 0: start CG from Z = 0; 1: learned warm start (model set)   */
+  int32_t warm_start;     /* 0: start CG from Z = 0; 1: learned warm start from the model
+                             attached by enkf_set_warm_model (ENKF_CGD, ENKF_FP32 only) */
   int32_t true_residual;  /* 1: FP64 true residual check (and W = HA^T Z/(N-1) from the
                              final Z) after an FP64 solve; always on in ENKF_FP32        */
   int32_t grid_blocks;    /* 0: automatic persistent-grid size; > 0: use this many CTAs  */
@@ -116,7 +117,11 @@ typedef struct enkf_stats {
                                 ||d_j - S z_j|| / ||d_j||; -1 when not computed          */
   int32_t columns_converged; /* columns that met tol                                     */
   int32_t grid_blocks;       /* persistent-grid size used                                */
-  double reserved[4];
+  double warm_relres_max;    /* learned warm start: max over columns of the start's true
+                                relative residual ||d_j - S z0_j|| / ||d_j||; -1 if off   */
+  double warm_fallbacks;     /* columns whose start was rejected (non-finite or more than
+                                1e3 times the zero start's residual) and began at 0      */
+  double reserved[2];
 } enkf_stats;
 
 /* Fill *cfg with defaults for an (n, m, N) problem: ENKF_FP64, ENKF_CGD, tol 1e-8,
@@ -220,6 +225,152 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
                                  const void* d_Xf, const double* d_y, uint64_t seed,
                                  uint64_t counter, void* d_Xa, void* cuda_stream,
                                  enkf_stats* out_stats);
+
+/* ---------------------------------------------------------------- batched analyses
+   Many independent analyses of uneven shape (n, m, N differ per problem) in ONE persistent
+   cooperative kernel launch, replayed from a CUDA graph. The paper analyses one problem at
+   a time; this is the same per-problem computation (innovations, the CG solve of S Z = D with
+   the matrix-free product, X_a = X_f + A HA^T Z / (N - 1)) scheduled for throughput. Every
+   problem uses ENKF_CGD in ENKF_FP32 with precondition = 1 (Jacobi by R), fixed_iters = 0,
+   and the same perturb_obs. A batched handle accepts only the enkf_batch_* calls,
+   enkf_last_error and enkf_destroy; the single-analysis calls reject it with
+   ENKF_ERR_INVALID_ARG. */
+
+/* Create a batched handle for `count` problems. cfgs[count] are HOST configs, each checked
+   as by enkf_create; h_rowptr, h_col, h_w and r_diag are HOST arrays of `count` HOST
+   pointers to each problem's CSR operator and R diagonal (copied to the device). cfgs[0]
+   .grid_blocks > 0 caps the persistent grid. Allocates one device arena (about 56 m N bytes
+   per problem, plus O(grid N_max^2)) and plans the launch: problems worth at least 1.5 CTAs
+   of the grid get their own team of CTAs, the rest are packed onto single-CTA teams. If the
+   environment variable ENKF_TUNE_CACHE names a file holding a tuning result for this batch
+   (written by enkf_batch_tune), that plan is used. Errors as enkf_create, with the index of
+   the failing problem in enkf_last_error(NULL). */
+enkf_status enkf_batch_create(int32_t count, const enkf_config* cfgs,
+                              const int32_t* const* h_rowptr, const int32_t* const* h_col,
+                              const double* const* h_w, const double* const* r_diag,
+                              void* cuda_stream, enkf_handle* out);
+
+/* One batched analysis on the handle's stream. d_Xf, d_y, d_Xa are HOST arrays of `count`
+   DEVICE pointers: X_f [n_i][N_i] FP32, y [m_i] FP64, X_a [n_i][N_i] FP32 (X_a == X_f is
+   allowed, partial overlap is not). seeds / counters (HOST arrays of `count`, NULL means
+   0) select each problem's perturbation stream exactly as enkf_analyze does. The pointer
+   table is copied to the device only when it differs from the previous call's. The first
+   call after create (or after a plan change) captures the launch into a CUDA graph; make
+   it before any capture of the caller's own. Never allocates device memory after that. */
+enkf_status enkf_batch_analyze(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
+                               const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa);
+
+/* Autotune the plan on real inputs (arguments as enkf_batch_analyze): times a few team
+   sizings (alpha in {1, 0.85, 0.7, 0.55, 1.2}: a big problem's team is alpha times its
+   cost share of the grid), keeps the fastest, and appends it to the ENKF_TUNE_CACHE file if
+   that variable is set. Runs several analyses (X_a holds the last one's result);
+   synchronises the stream. *best_ms (HOST, may be NULL) receives the best mean time. */
+enkf_status enkf_batch_tune(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
+                            const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa,
+                            double* best_ms);
+
+/* Synchronise and report the last batched analysis per problem into HOST arrays of length
+   count (any may be NULL): enkf_status, max CG iterations over columns, max recursive
+   relative residual, refreshes performed. Returns the first problem's non-OK status, or
+   ENKF_OK. */
+enkf_status enkf_batch_get_stats(enkf_handle h, int32_t* status, int32_t* iters_max,
+                                 double* relres_max, int32_t* refinements);
+
+/* The handle's current plan: persistent grid size, number of teams, team sizing alpha, and
+   whether analyses replay a CUDA graph (1) or launch directly because capture was refused
+   (0; checked at the first analysis) (HOST outputs, any may be NULL). */
+enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, double* alpha,
+                                int32_t* graphed);
+
+/* The planner alone, on the host (no GPU needed). A problem costs m N^2 (N + 8) + 2 n N^2;
+   one whose share of the total cost times max_grid is at least 1.5 gets a team of
+   min(floor(alpha * that), ceil(m / 64)) CTAs when that is >= 2 and fits (largest first,
+   leaving at least one CTA); the others go longest-first to the least-loaded of the
+   remaining single-CTA teams. For `count` problem shapes (only n, m, N of cfgs are read), a
+   grid of at most max_grid CTAs and team sizing alpha > 0, fill HOST
+   arrays cta_team[grid], cta_rank[grid] (team of each CTA and its rank in it; a team's CTAs
+   are contiguous), team_size[teams], team_first[teams + 1] (offsets into order) and
+   order[count] (problems in team order; every problem exactly once). Arrays of max_grid,
+   max_grid, max_grid, max_grid + 1 and count entries are always large enough; any may be
+   NULL. *grid and *teams receive the sizes. */
+enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
+                            int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
+                            int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams);
+
+/* ---------------------------------------------------------------- learned warm start
+   The paper's CG starts from zero. Every solution column of S Z = D has the form
+   z_j = R^{-1}(d_j - HA c_j) with c_j = W e_j, W = HA^T Z/(N-1) (rearranging S Z = D), so a
+   small MLP predicts c_j per column from features f_j = [d_j(sketch)/s_j, g_j/s_j]: a
+   sketch of K rows i_k = floor(k m / K), s_j the RMS of d_j over the sketch (1 if 0),
+   g_j = HA^T R^{-1} d_j/(N-1). The prediction is decoded into the start
+   z0_j = R^{-1}(d_j - HA c_j) (residual in span(HA)); the start's true residual is measured
+   and a column whose start is non-finite or more than 1e3 times worse than z_j = 0 starts
+   from 0 instead. The network: inputs standardised per feature, `layers` hidden layers of
+   width `hidden` with GELU (x Phi(x)), linear output of the standardised c_j/s_j; trained
+   with mean squared error and Adam (Kingma & Ba 2015). All of it runs in this library's
+   kernels (FP32). */
+typedef struct enkf_mlp_shape {
+  int32_t in_dim;   /* K + N                     */
+  int32_t hidden;   /* hidden width (e.g. 512)   */
+  int32_t layers;   /* hidden layers, 1..7       */
+  int32_t out_dim;  /* N                         */
+} enkf_mlp_shape;
+
+/* Number of FP32 parameters. Layout: for each layer (hidden layers, then the output) the
+   weight [out][in] row-major followed by the bias [out]; then mu_in [in_dim], sd_in [in_dim],
+   mu_out [out_dim], sd_out [out_dim] (standardisation, set by enkf_mlp_standardize, not
+   trained). The trained prefix is the count minus 2 (in_dim + out_dim). -1 for a bad shape. */
+int64_t enkf_mlp_param_count(const enkf_mlp_shape* shape);
+
+/* Device scratch bytes the MLP calls need for `batch` rows (-1 for bad arguments). */
+int64_t enkf_mlp_work_bytes(const enkf_mlp_shape* shape, int32_t batch);
+
+/* Y [batch][out_dim] = mu_out + sd_out * MLP((X[rows[b]] - mu_in) / sd_in), all DEVICE FP32
+   (d_rows: DEVICE int32 [batch] row indices into X, NULL for rows 0..batch-1); d_work of
+   enkf_mlp_work_bytes(shape, batch) bytes. Enqueued on cuda_stream. */
+enkf_status enkf_mlp_forward(const enkf_mlp_shape* shape, const float* d_params, const float* d_X,
+                             const int32_t* d_rows, int32_t batch, float* d_Y, void* d_work,
+                             void* cuda_stream);
+
+/* Loss L = mean over the batch x out_dim entries of (y_std - (T[rows[b]] - mu_out)/sd_out)^2
+   into d_loss (DEVICE float, may be NULL) and its gradient into d_grad (DEVICE, the trained
+   prefix of the parameter layout is overwritten). Enqueued on cuda_stream. */
+enkf_status enkf_mlp_loss_grad(const enkf_mlp_shape* shape, const float* d_params, const float* d_X,
+                               const float* d_T, const int32_t* d_rows, int32_t batch,
+                               float* d_grad, float* d_loss, void* d_work, void* cuda_stream);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1, with bias correction at step >= 1) on the
+   first `count` entries of d_params with gradient d_grad and moments d_m, d_v (DEVICE FP32,
+   zero before step 1). */
+enkf_status enkf_mlp_adam(int64_t count, float* d_params, const float* d_grad, float* d_m,
+                          float* d_v, int32_t step, float lr, float beta1, float beta2, float eps,
+                          void* cuda_stream);
+
+/* One training epoch: for each of floor(rows / batch) minibatches (rows d_perm[q batch ..]
+   of d_X [rows][in_dim] and d_T [rows][out_dim]) a loss/gradient pass and an Adam step
+   (lr, beta1 0.9, beta2 0.999, eps 1e-8, step numbers step0 + 1, ...). d_losses (DEVICE,
+   may be NULL) receives each minibatch's loss; d_grad holds param_count floats; d_work
+   enkf_mlp_work_bytes(shape, batch) bytes. */
+enkf_status enkf_mlp_train_epoch(const enkf_mlp_shape* shape, float* d_params, float* d_m, float* d_v,
+                                 const float* d_X, const float* d_T, const int32_t* d_perm,
+                                 int64_t rows, int32_t batch, int32_t step0, float lr,
+                                 float* d_losses, float* d_grad, void* d_work, void* cuda_stream);
+
+/* Set the standardisation entries of d_params to the per-column mean and standard
+   deviation (population form, 1 where 0) of d_X [rows][in_dim] and d_T [rows][out_dim]. */
+enkf_status enkf_mlp_standardize(const enkf_mlp_shape* shape, float* d_params, const float* d_X,
+                                 const float* d_T, int64_t rows, void* cuda_stream);
+
+/* Training pairs from the handle's last analysis (ENKF_CGD, ENKF_FP32): d_F [N][K + N]
+   features of its N innovation columns for a sketch of K >= 1 rows and, if d_T is not NULL,
+   d_T [N][N] the targets c_j / s_j with c_j = W e_j of the solve (DEVICE FP32). */
+enkf_status enkf_warm_features(enkf_handle h, int32_t K, float* d_F, float* d_T);
+
+/* Attach a model to the handle (d_params DEVICE, caller-owned, must stay valid while
+   analyses with cfg.warm_start = 1 run; NULL detaches). shape->out_dim must be N and
+   in_dim = K + N. Allocates the handle's feature and activation buffers (analyses allocate
+   nothing). */
+enkf_status enkf_set_warm_model(enkf_handle h, const enkf_mlp_shape* shape, const float* d_params);
 
 /* Release the handle and all device memory it owns (synchronises its stream first).
    NULL is accepted. */

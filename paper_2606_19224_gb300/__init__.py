@@ -24,7 +24,11 @@ EXPORTS = (
     "enkf_analyze_host", "enkf_get_stats", "enkf_get_column_stats", "enkf_copy_intermediates",
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
     "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
-    "enkf_get_solve_phases",
+    "enkf_get_solve_phases", "enkf_batch_create", "enkf_batch_analyze", "enkf_batch_tune",
+    "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan",
+    "enkf_mlp_param_count", "enkf_mlp_work_bytes", "enkf_mlp_forward", "enkf_mlp_loss_grad",
+    "enkf_mlp_adam", "enkf_mlp_train_epoch", "enkf_mlp_standardize", "enkf_warm_features",
+    "enkf_set_warm_model",
 )
 
 
@@ -46,8 +50,14 @@ class Stats(ctypes.Structure):
         ("status", ctypes.c_int32), ("iters_max", ctypes.c_int32), ("iters_min", ctypes.c_int32),
         ("refinements", ctypes.c_int32), ("relres_max", ctypes.c_double),
         ("true_relres_max", ctypes.c_double), ("columns_converged", ctypes.c_int32),
-        ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_double * 4),
+        ("grid_blocks", ctypes.c_int32), ("warm_relres_max", ctypes.c_double),
+        ("warm_fallbacks", ctypes.c_double), ("reserved", ctypes.c_double * 2),
     ]
+
+
+class MlpShape(ctypes.Structure):
+    _fields_ = [("in_dim", ctypes.c_int32), ("hidden", ctypes.c_int32), ("layers", ctypes.c_int32),
+                ("out_dim", ctypes.c_int32)]
 
 
 class EnKFError(RuntimeError):
@@ -89,6 +99,24 @@ def load(path: str = None):
         "enkf_get_solve_phases": (i32, [vp, vp]),
         "enkf_analyze_noalloc": (i32, [ctypes.POINTER(Config), vp, vp, vp, vp, vp, dp, u64, u64,
                                        vp, vp, ctypes.POINTER(Stats)]),
+        "enkf_batch_create": (i32, [i32, ctypes.POINTER(Config), vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "enkf_batch_analyze": (i32, [vp, vp, vp, vp, vp, vp]),
+        "enkf_batch_tune": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "enkf_batch_get_stats": (i32, [vp, vp, vp, vp, vp]),
+        "enkf_batch_get_plan": (i32, [vp, vp, vp, vp, vp]),
+        "enkf_mlp_param_count": (i64, [ctypes.POINTER(MlpShape)]),
+        "enkf_mlp_work_bytes": (i64, [ctypes.POINTER(MlpShape), i32]),
+        "enkf_mlp_forward": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, i32, vp, vp, vp]),
+        "enkf_mlp_loss_grad": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, vp, i32, vp, vp, vp, vp]),
+        "enkf_mlp_adam": (i32, [i64, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, vp]),
+        "enkf_mlp_train_epoch": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, vp, vp, vp, i64, i32, i32,
+                                       ctypes.c_float, vp, vp, vp, vp]),
+        "enkf_mlp_standardize": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, i64, vp]),
+        "enkf_warm_features": (i32, [vp, i32, vp, vp]),
+        "enkf_set_warm_model": (i32, [vp, ctypes.POINTER(MlpShape), vp]),
+        "enkf_batch_plan": (i32, [i32, ctypes.POINTER(Config), i32, ctypes.c_double, vp, vp, vp, vp, vp,
+                                  vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -181,7 +209,24 @@ class Analysis:
         return dict(status=STATUS.get(s.status, s.status), iters_max=s.iters_max,
                     iters_min=s.iters_min, refinements=s.refinements, relres_max=s.relres_max,
                     true_relres_max=s.true_relres_max, columns_converged=s.columns_converged,
-                    grid_blocks=s.grid_blocks)
+                    grid_blocks=s.grid_blocks, warm_relres_max=s.warm_relres_max,
+                    warm_fallbacks=int(s.warm_fallbacks))
+
+    def warm_features(self, K, targets=True):
+        """Training pairs of the last analysis: (F [N][K + N], T [N][N] or None), device FP32."""
+        import torch
+        F = torch.empty((self.N, K + self.N), dtype=torch.float32, device="cuda")
+        T = torch.empty((self.N, self.N), dtype=torch.float32, device="cuda") if targets else None
+        _check(load().enkf_warm_features(self.h, K, _ptr(F), _ptr(T)), self.h)
+        return F, T
+
+    def set_warm_model(self, shape, params):
+        """Attach an MLP (shape: MlpShape or (in, hidden, layers, out); params: device FP32,
+        kept referenced here) for analyses with warm_start=1; params=None detaches."""
+        if not isinstance(shape, MlpShape):
+            shape = MlpShape(*shape)
+        self._warm_params = params
+        _check(load().enkf_set_warm_model(self.h, ctypes.byref(shape), _ptr(params)), self.h)
 
     def column_stats(self):
         import numpy as np
@@ -263,3 +308,185 @@ def analyze_noalloc(cfg, rowptr, col, w, r, Xf, y, seed=0, counter=0, out=None, 
                                      _stream_handle(stream), ctypes.byref(s))
     return out, dict(status=STATUS.get(st, st), iters_max=s.iters_max, refinements=s.refinements,
                      true_relres_max=s.true_relres_max, grid_blocks=s.grid_blocks)
+
+
+def _ptr_array(items, ctype=ctypes.c_void_p):
+    arr = (ctype * len(items))()
+    for i, x in enumerate(items):
+        arr[i] = x
+    return arr
+
+
+def batch_plan(shapes, max_grid, alpha=1.0):
+    """The batched launch planner alone (host only): shapes is a list of (n, m, N). Returns
+    dict(grid, teams, cta_team, cta_rank, team_size, team_first, order) as numpy arrays."""
+    import numpy as np
+    cfgs = (Config * len(shapes))()
+    for i, (n, m, N) in enumerate(shapes):
+        cfgs[i].n, cfgs[i].m, cfgs[i].N = n, m, N
+    out = {k: np.zeros(max_grid + 1, dtype=np.int32) for k in ("cta_team", "cta_rank", "team_size", "team_first")}
+    order = np.zeros(len(shapes), dtype=np.int32)
+    grid, teams = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().enkf_batch_plan(len(shapes), cfgs, max_grid, alpha, out["cta_team"].ctypes.data,
+                                  out["cta_rank"].ctypes.data, out["team_size"].ctypes.data,
+                                  out["team_first"].ctypes.data, order.ctypes.data, ctypes.byref(grid),
+                                  ctypes.byref(teams)))
+    g, t = grid.value, teams.value
+    return dict(grid=g, teams=t, cta_team=out["cta_team"][:g], cta_rank=out["cta_rank"][:g],
+                team_size=out["team_size"][:t], team_first=out["team_first"][:t + 1], order=order)
+
+
+class BatchAnalysis:
+    """Many problems of uneven (n, m, N) analysed in one persistent launch replayed from a
+    CUDA graph (enkf_batch_create / enkf_batch_analyze). problems: list of dicts with n, m, N,
+    rowptr, col, w, r (host arrays). FP32 with Jacobi preconditioning."""
+
+    def __init__(self, problems, stream=None, tol=1e-8, perturb_obs=1, grid_blocks=0, **config):
+        import numpy as np
+        import torch
+        if not torch.cuda.is_available():
+            raise EnKFError(2, "no CUDA device")
+        lib = load()
+        self.count = len(problems)
+        self.cfgs = (Config * self.count)()
+        self._keep = []
+        rp, cl, ww, rr = [], [], [], []
+        for i, p in enumerate(problems):
+            kw = dict(precision=FP32, precondition=1, tol=tol, perturb_obs=perturb_obs, grid_blocks=grid_blocks)
+            kw.update(config)
+            c = default_config(p["n"], p["m"], p["N"], **kw)
+            self.cfgs[i] = c
+            arrs = (np.ascontiguousarray(p["rowptr"], dtype=np.int32), np.ascontiguousarray(p["col"], dtype=np.int32),
+                    np.ascontiguousarray(p["w"], dtype=np.float64), np.ascontiguousarray(p["r"], dtype=np.float64))
+            self._keep.append(arrs)
+            rp.append(arrs[0].ctypes.data)
+            cl.append(arrs[1].ctypes.data)
+            ww.append(arrs[2].ctypes.data)
+            rr.append(arrs[3].ctypes.data)
+        self.shapes = [(p["n"], p["m"], p["N"]) for p in problems]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib.enkf_batch_create(self.count, self.cfgs, _ptr_array(rp), _ptr_array(cl), _ptr_array(ww),
+                                   _ptr_array(rr), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(st, None)
+        self.h = h
+
+    def _tables(self, Xf, y, seeds, counters, out):
+        import torch
+        if out is None:
+            out = [torch.empty_like(x) for x in Xf]
+        tabs = (_ptr_array([x.data_ptr() for x in Xf]), _ptr_array([v.data_ptr() for v in y]),
+                _ptr_array([o.data_ptr() for o in out]))
+        sd = _ptr_array([int(v) for v in seeds], ctypes.c_uint64) if seeds is not None else None
+        ct = _ptr_array([int(v) for v in counters], ctypes.c_uint64) if counters is not None else None
+        return out, tabs, sd, ct
+
+    def analyze(self, Xf, y, seeds=None, counters=None, out=None):
+        """Xf: list of device FP32 [n_i][N_i]; y: list of device FP64 [m_i]. Returns X_a list."""
+        out, (a, b, c), sd, ct = self._tables(Xf, y, seeds, counters, out)
+        _check(load().enkf_batch_analyze(self.h, a, b, sd, ct, c), self.h)
+        return out
+
+    def tune(self, Xf, y, seeds=None, counters=None, out=None):
+        out, (a, b, c), sd, ct = self._tables(Xf, y, seeds, counters, out)
+        best = ctypes.c_double()
+        _check(load().enkf_batch_tune(self.h, a, b, sd, ct, c, ctypes.byref(best)), self.h)
+        return best.value
+
+    def stats(self):
+        import numpy as np
+        st = np.zeros(self.count, dtype=np.int32)
+        it = np.zeros(self.count, dtype=np.int32)
+        rel = np.zeros(self.count, dtype=np.float64)
+        ref = np.zeros(self.count, dtype=np.int32)
+        load().enkf_batch_get_stats(self.h, st.ctypes.data, it.ctypes.data, rel.ctypes.data, ref.ctypes.data)
+        return dict(status=st, iters_max=it, relres_max=rel, refinements=ref)
+
+    def plan(self):
+        g, t, a, gr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+        _check(load().enkf_batch_get_plan(self.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(a),
+                                          ctypes.byref(gr)), self.h)
+        return dict(grid=g.value, teams=t.value, alpha=a.value, graphed=gr.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().enkf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- learned warm start (MLP)
+def _shape(shape):
+    return shape if isinstance(shape, MlpShape) else MlpShape(*shape)
+
+
+def mlp_param_count(shape):
+    """Total FP32 parameters of the layout; the trained prefix is this minus 2 (in + out)."""
+    return int(load().enkf_mlp_param_count(ctypes.byref(_shape(shape))))
+
+
+def mlp_trained_count(shape):
+    s = _shape(shape)
+    return mlp_param_count(s) - 2 * (s.in_dim + s.out_dim)
+
+
+def _work(shape, batch):
+    import torch
+    nb = int(load().enkf_mlp_work_bytes(ctypes.byref(_shape(shape)), batch))
+    if nb < 0:
+        raise EnKFError(1, "bad MLP shape or batch")
+    return torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+
+def mlp_forward(shape, params, X, rows=None, stream=None):
+    """Raw predictions Y [batch][out] for rows X (or X[rows]), device FP32."""
+    import torch
+    s = _shape(shape)
+    B = rows.numel() if rows is not None else X.shape[0]
+    Y = torch.empty((B, s.out_dim), dtype=torch.float32, device="cuda")
+    work = _work(s, B)
+    _check(load().enkf_mlp_forward(ctypes.byref(s), _ptr(params), _ptr(X), _ptr(rows), B, _ptr(Y), _ptr(work),
+                                   _stream_handle(stream)))
+    return Y
+
+
+def mlp_loss_grad(shape, params, X, T, rows=None, stream=None):
+    """(loss tensor [1], gradient [param_count]) of the standardised MSE on a minibatch."""
+    import torch
+    s = _shape(shape)
+    B = rows.numel() if rows is not None else X.shape[0]
+    grad = torch.zeros(mlp_param_count(s), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = _work(s, B)
+    _check(load().enkf_mlp_loss_grad(ctypes.byref(s), _ptr(params), _ptr(X), _ptr(T), _ptr(rows), B, _ptr(grad),
+                                     _ptr(loss), _ptr(work), _stream_handle(stream)))
+    return loss, grad
+
+
+def mlp_adam(count, params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().enkf_mlp_adam(count, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1, beta2, eps,
+                                _stream_handle(stream)))
+
+
+def mlp_standardize(shape, params, X, T, stream=None):
+    _check(load().enkf_mlp_standardize(ctypes.byref(_shape(shape)), _ptr(params), _ptr(X), _ptr(T), X.shape[0],
+                                       _stream_handle(stream)))
+
+
+def mlp_train_epoch(shape, params, m, v, X, T, perm, batch, step0, lr, stream=None):
+    """One epoch of minibatch Adam over rows perm (device int32); returns per-batch losses."""
+    import torch
+    s = _shape(shape)
+    rows = perm.numel()
+    losses = torch.zeros(rows // batch, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(mlp_param_count(s), dtype=torch.float32, device="cuda")
+    work = _work(s, batch)
+    _check(load().enkf_mlp_train_epoch(ctypes.byref(s), _ptr(params), _ptr(m), _ptr(v), _ptr(X), _ptr(T),
+                                       _ptr(perm), rows, batch, step0, lr, _ptr(losses), _ptr(grad), _ptr(work),
+                                       _stream_handle(stream)))
+    return losses

@@ -28,10 +28,66 @@ enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
 void free_workspace(Workspace& ws) {
   void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.HA16, ws.HAdf, ws.Ddf, ws.Zdf, ws.D, ws.Z, ws.B, ws.X,
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
-                  ws.col_relres, ws.col_true, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
+                  ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace{};
+}
+
+// Argument checks shared by enkf_create and enkf_batch_create; on failure the message is
+// left in msg (without the caller's prefix).
+enkf_status check_problem(const enkf_config& c, const int32_t* h_rowptr, const int32_t* h_col,
+                          const double* h_w, const double* r_diag, std::string& msg) {
+  auto bad = [&](enkf_status s, const char* m) { msg = m; return s; };
+  if (!h_rowptr || !r_diag) return bad(ENKF_ERR_INVALID_ARG, "NULL rowptr or r");
+  if (c.n < 1 || c.m < 1 || c.N < 2)
+    return bad(ENKF_ERR_INVALID_ARG, "need n >= 1, m >= 1, N >= 2");
+  if (c.m >= (int64_t(1) << 32) || c.n >= (int64_t(1) << 31))
+    return bad(ENKF_ERR_INVALID_ARG, "m must be < 2^32 and n < 2^31");
+  if (c.N > 128) return bad(ENKF_ERR_UNSUPPORTED, "N > 128");
+  if (c.precision < ENKF_FP64 || c.precision > ENKF_FP16_REFINE)
+    return bad(ENKF_ERR_UNSUPPORTED, "unknown precision mode");
+  const bool mixed = c.precision == ENKF_BF16_REFINE || c.precision == ENKF_FP16_REFINE;
+  if (mixed && c.variant != ENKF_CGD)
+    return bad(ENKF_ERR_UNSUPPORTED, "the BF16/FP16 modes are built for ENKF_CGD");
+  if (mixed && c.fixed_iters > 0)
+    return bad(ENKF_ERR_UNSUPPORTED, "fixed_iters is not offered in the BF16/FP16 modes");
+  if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED)
+    return bad(ENKF_ERR_UNSUPPORTED, "unknown variant");
+  if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
+    return bad(ENKF_ERR_INVALID_ARG, "bad iteration limits");
+  if (c.fixed_iters == 0 && !(c.tol > 0.0 && std::isfinite(c.tol)))
+    return bad(ENKF_ERR_INVALID_ARG, "tol must be positive and finite");
+  if (c.precision == ENKF_FP32 && !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
+    return bad(ENKF_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+  if (c.grid_blocks < 0) return bad(ENKF_ERR_INVALID_ARG, "grid_blocks < 0");
+  if (c.precondition != 0 && c.precondition != 1)
+    return bad(ENKF_ERR_INVALID_ARG, "precondition must be 0 or 1");
+  if (c.lowprec_terms != 0 && c.lowprec_terms != 1 && c.lowprec_terms != 3)
+    return bad(ENKF_ERR_INVALID_ARG, "lowprec_terms must be 0, 1 or 3");
+  if (c.warm_start != 0 && c.warm_start != 1) return bad(ENKF_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+  if (c.warm_start && (c.precision != ENKF_FP32 || c.variant != ENKF_CGD || c.fixed_iters > 0))
+    return bad(ENKF_ERR_UNSUPPORTED, "the learned warm start runs in ENKF_CGD / ENKF_FP32 without fixed_iters");
+  for (int q = 0; q < 5; ++q)
+    if (c.reserved[q]) return bad(ENKF_ERR_INVALID_ARG, "reserved fields must be 0");
+  // observation operator and R
+  if (h_rowptr[0] != 0) return bad(ENKF_ERR_INVALID_ARG, "rowptr[0] != 0");
+  for (int64_t i = 0; i < c.m; ++i)
+    if (h_rowptr[i + 1] < h_rowptr[i])
+      return bad(ENKF_ERR_INVALID_ARG, "rowptr decreases");
+  const int64_t nnz = h_rowptr[c.m];
+  if (nnz > 0 && (!h_col || !h_w))
+    return bad(ENKF_ERR_INVALID_ARG, "NULL col/w with nnz > 0");
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (h_col[k] < 0 || h_col[k] >= c.n)
+      return bad(ENKF_ERR_INVALID_ARG, "column index outside [0, n)");
+    if (!std::isfinite(h_w[k])) return bad(ENKF_ERR_INVALID_ARG, "non-finite weight");
+  }
+  for (int64_t i = 0; i < c.m; ++i)
+    if (!(r_diag[i] > 0.0) || !std::isfinite(r_diag[i]))
+      return bad(ENKF_ERR_INVALID_ARG, "r must be positive and finite");
+
+  return ENKF_OK;
 }
 
 size_t elem_size(const enkf_config& c) { return c.precision == ENKF_FP64 ? 8 : 4; }
@@ -87,50 +143,13 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (!cfg || !out || !h_rowptr || !r_diag)
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: NULL argument");
   const enkf_config c = *cfg;
-  if (c.n < 1 || c.m < 1 || c.N < 2)
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: need n >= 1, m >= 1, N >= 2");
-  if (c.m >= (int64_t(1) << 32) || c.n >= (int64_t(1) << 31))
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: m must be < 2^32 and n < 2^31");
-  if (c.N > 128) return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: N > 128");
-  if (c.precision < ENKF_FP64 || c.precision > ENKF_FP16_REFINE)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: unknown precision mode");
-  const bool mixed = c.precision == ENKF_BF16_REFINE || c.precision == ENKF_FP16_REFINE;
-  if (mixed && c.variant != ENKF_CGD)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: the BF16/FP16 modes are built for ENKF_CGD");
-  if (mixed && c.fixed_iters > 0)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: fixed_iters is not offered in the BF16/FP16 modes");
-  if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED)
-    return fail(nullptr, ENKF_ERR_UNSUPPORTED, "enkf_create: unknown variant");
-  if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: bad iteration limits");
-  if (c.fixed_iters == 0 && !(c.tol > 0.0 && std::isfinite(c.tol)))
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: tol must be positive and finite");
-  if (c.precision == ENKF_FP32 && !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: inner_tol must be in (0, 1)");
-  if (c.grid_blocks < 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: grid_blocks < 0");
-  if (c.precondition != 0 && c.precondition != 1)
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: precondition must be 0 or 1");
-  if (c.lowprec_terms != 0 && c.lowprec_terms != 1 && c.lowprec_terms != 3)
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: lowprec_terms must be 0, 1 or 3");
-  for (int q = 0; q < 5; ++q)
-    if (c.reserved[q]) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: reserved fields must be 0");
-  // observation operator and R
-  if (h_rowptr[0] != 0) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr[0] != 0");
-  for (int64_t i = 0; i < c.m; ++i)
-    if (h_rowptr[i + 1] < h_rowptr[i])
-      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: rowptr decreases");
-  const int64_t nnz = h_rowptr[c.m];
-  if (nnz > 0 && (!h_col || !h_w))
-    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: NULL col/w with nnz > 0");
-  for (int64_t k = 0; k < nnz; ++k) {
-    if (h_col[k] < 0 || h_col[k] >= c.n)
-      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: column index outside [0, n)");
-    if (!std::isfinite(h_w[k])) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: non-finite weight");
+  {
+    std::string msg;
+    const enkf_status cs = check_problem(c, h_rowptr, h_col, h_w, r_diag, msg);
+    if (cs != ENKF_OK) return fail(nullptr, cs, "enkf_create: " + msg);
   }
-  for (int64_t i = 0; i < c.m; ++i)
-    if (!(r_diag[i] > 0.0) || !std::isfinite(r_diag[i]))
-      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: r must be positive and finite");
-
+  const bool mixed = c.precision == ENKF_BF16_REFINE || c.precision == ENKF_FP16_REFINE;
+  const int64_t nnz = h_rowptr[c.m];
   auto* h = new enkf_handle_s();
   h->cfg = c;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -164,6 +183,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       {(void**)&ws.col_iters, sizeof(int32_t) * c.N},
       {(void**)&ws.col_relres, sizeof(double) * c.N},
       {(void**)&ws.col_true, sizeof(double) * c.N},
+      {(void**)&ws.col_warm, sizeof(double) * c.N},
       {(void**)&ws.status, sizeof(int32_t) * 4},
       {(void**)&ws.bar, sizeof(unsigned) * 4},
       {(void**)&ws.stage_Xf, vs * c.n * c.N},
@@ -217,6 +237,7 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
                                 const double* d_E, int emode, uint64_t seed, uint64_t counter,
                                 void* d_Xa) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "analyze: batched handle (use the enkf_batch_* calls)");
   if (!d_Xf || !d_y || !d_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze: NULL X_f, y or X_a");
   const auto& c = h->cfg;
   const size_t xb = elem_size(c) * c.n * c.N;
@@ -227,8 +248,14 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   cudaError_t e = cudaSuccess;
   const bool reduced = c.variant == ENKF_CGD_REDUCED;
   if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
+  if (c.warm_start && !enkf::warm_ready(h))
+    return fail(h, ENKF_ERR_INVALID_ARG, "analyze: warm_start = 1 but no model attached (enkf_set_warm_model)");
   if (e == cudaSuccess && !reduced) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
+  if (c.warm_start) {
+    e = enkf::warm_prepare(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze: learned warm start");
+  }
   if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
   if (e == cudaSuccess)
     e = reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter)
@@ -261,6 +288,7 @@ enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d
 enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y, uint64_t seed,
                               uint64_t counter, void* h_Xa) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze_host: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "analyze_host: batched handle (use the enkf_batch_* calls)");
   if (!h_Xf || !h_y || !h_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze_host: NULL buffer");
   const auto& c = h->cfg;
   const size_t xb = elem_size(c) * c.n * c.N;
@@ -278,6 +306,7 @@ enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y
 
 enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres, double* true_relres) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "get_column_stats: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "get_column_stats: batched handle (use the enkf_batch_* calls)");
   cudaError_t e = cudaStreamSynchronize(h->stream);
   const int N = h->cfg.N;
   if (e == cudaSuccess && iters) e = cudaMemcpy(iters, h->ws.col_iters, sizeof(int32_t) * N, cudaMemcpyDeviceToHost);
@@ -289,6 +318,7 @@ enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
 
 enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out) {
   if (!h || !out) return fail(h, ENKF_ERR_INVALID_ARG, "get_stats: NULL argument");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "get_stats: batched handle (use enkf_batch_get_stats)");
   std::memset(out, 0, sizeof(*out));
   const int N = h->cfg.N;
   std::vector<int32_t> it(N);
@@ -310,6 +340,15 @@ enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out) {
   }
   const int bits = st[0];
   out->refinements = st[1];
+  out->warm_relres_max = -1.0;
+  out->warm_fallbacks = 0.0;
+  if (h->cfg.warm_start) {
+    std::vector<double> wr(N);
+    e = cudaMemcpy(wr.data(), h->ws.col_warm, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_stats");
+    for (int j = 0; j < N; ++j) out->warm_relres_max = std::max(out->warm_relres_max, wr[j]);
+    out->warm_fallbacks = st[2];
+  }
   out->grid_blocks = h->launch.G;
   enkf_status status = ENKF_OK;
   if (bits & enkf::DS_TIMEOUT) status = ENKF_ERR_TIMEOUT;
@@ -326,6 +365,7 @@ enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out) {
 
 enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z, double* d_W) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "copy_intermediates: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "copy_intermediates: batched handle (use the enkf_batch_* calls)");
   const auto& c = h->cfg;
   const size_t mN = sizeof(double) * c.m * c.N;
   cudaError_t e = cudaSuccess;
@@ -358,6 +398,7 @@ enkf_status enkf_draw_perturbations(uint64_t seed, uint64_t counter, const doubl
 
 enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "set_phase_timing: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "set_phase_timing: batched handle (use the enkf_batch_* calls)");
   if (enable && !h->ev[0]) {
     for (auto& ev : h->ev) {
       cudaError_t e = cudaEventCreate(&ev);
@@ -390,9 +431,220 @@ enkf_status enkf_get_phase_times(enkf_handle h, float* ms) {
   return ENKF_OK;
 }
 
+// ------------------------------------------------------------------ batched analyses
+enkf_status enkf_batch_create(int32_t count, const enkf_config* cfgs,
+                              const int32_t* const* h_rowptr, const int32_t* const* h_col,
+                              const double* const* h_w, const double* const* r_diag,
+                              void* cuda_stream, enkf_handle* out) {
+  if (out) *out = nullptr;
+  if (!cfgs || !out || !h_rowptr || !h_col || !h_w || !r_diag || count < 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_create: NULL argument or count < 1");
+  for (int32_t i = 0; i < count; ++i) {
+    const enkf_config& c = cfgs[i];
+    std::string msg;
+    const enkf_status cs = check_problem(c, h_rowptr[i], h_col[i], h_w[i], r_diag[i], msg);
+    const std::string who = "enkf_batch_create: problem " + std::to_string(i) + ": ";
+    if (cs != ENKF_OK) return fail(nullptr, cs, who + msg);
+    if (c.precision != ENKF_FP32 || c.variant != ENKF_CGD || c.precondition != 1 || c.fixed_iters != 0)
+      return fail(nullptr, ENKF_ERR_UNSUPPORTED,
+                  who + "batches run ENKF_CGD in ENKF_FP32 with precondition = 1 and fixed_iters = 0");
+    if (c.perturb_obs != cfgs[0].perturb_obs)
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, who + "perturb_obs differs from problem 0");
+  }
+  auto* h = new enkf_handle_s();
+  h->cfg = cfgs[0];
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  std::string err = "enkf_batch_create: device query";
+  if (e == cudaSuccess) e = enkf::batch_build(h, count, cfgs, h_rowptr, h_col, h_w, r_diag, err);
+  if (e != cudaSuccess) {
+    enkf_status s = cuda_fail(nullptr, e, err.c_str());
+    enkf::batch_free(h);
+  enkf::warm_free(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return ENKF_OK;
+}
+
+static enkf_status batch_args(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
+                              void* const* d_Xa, const char* who) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, std::string(who) + ": NULL handle");
+  if (!h->batch) return fail(h, ENKF_ERR_INVALID_ARG, std::string(who) + ": not a batched handle");
+  if (!d_Xf || !d_y || !d_Xa) return fail(h, ENKF_ERR_INVALID_ARG, std::string(who) + ": NULL pointer array");
+  const int count = enkf::batch_count(h);
+  for (int i = 0; i < count; ++i) {
+    if (!d_Xf[i] || !d_y[i] || !d_Xa[i])
+      return fail(h, ENKF_ERR_INVALID_ARG, std::string(who) + ": NULL X_f, y or X_a of problem " + std::to_string(i));
+    const size_t xb = enkf::batch_state_bytes(h, i);
+    const char* a = static_cast<const char*>(d_Xf[i]);
+    const char* b = static_cast<const char*>(d_Xa[i]);
+    if (a != b && a < b + xb && b < a + xb)
+      return fail(h, ENKF_ERR_INVALID_ARG, std::string(who) + ": X_a partially overlaps X_f in problem " + std::to_string(i));
+  }
+  return ENKF_OK;
+}
+
+enkf_status enkf_batch_analyze(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
+                               const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa) {
+  enkf_status s = batch_args(h, d_Xf, d_y, d_Xa, "enkf_batch_analyze");
+  if (s != ENKF_OK) return s;
+  cudaError_t e = enkf::batch_analyze(h, d_Xf, d_y, seeds, counters, d_Xa);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_batch_analyze");
+  h->has_result = true;
+  return ENKF_OK;
+}
+
+enkf_status enkf_batch_tune(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
+                            const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa,
+                            double* best_ms) {
+  enkf_status s = batch_args(h, d_Xf, d_y, d_Xa, "enkf_batch_tune");
+  if (s != ENKF_OK) return s;
+  double alpha = 0.0;
+  cudaError_t e = enkf::batch_tune(h, d_Xf, d_y, seeds, counters, d_Xa, &alpha, best_ms);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_batch_tune");
+  h->has_result = true;
+  return ENKF_OK;
+}
+
+enkf_status enkf_batch_get_stats(enkf_handle h, int32_t* status, int32_t* iters_max,
+                                 double* relres_max, int32_t* refinements) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_get_stats: NULL handle");
+  if (!h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_stats: not a batched handle");
+  if (!h->has_result) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_stats: no analysis yet");
+  const int count = enkf::batch_count(h);
+  std::vector<int32_t> st(count);
+  cudaError_t e = enkf::batch_stats(h, st.data(), iters_max, relres_max, refinements);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_batch_get_stats");
+  enkf_status worst = ENKF_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = st[i];
+    if (worst == ENKF_OK && st[i] != ENKF_OK) worst = (enkf_status)st[i];
+  }
+  return worst;
+}
+
+enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, double* alpha,
+                                int32_t* graphed) {
+  if (!h || !h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_plan: not a batched handle");
+  const enkf::BatchPlanOut p = enkf::batch_info(h);
+  if (grid) *grid = p.grid;
+  if (teams) *teams = p.teams;
+  if (alpha) *alpha = p.alpha;
+  if (graphed) *graphed = p.graphed;
+  return ENKF_OK;
+}
+
+enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
+                            int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
+                            int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams) {
+  if (count < 1 || !cfgs || max_grid < 1 || !(alpha > 0.0))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: bad argument");
+  for (int32_t i = 0; i < count; ++i)
+    if (cfgs[i].m < 1 || cfgs[i].n < 1 || cfgs[i].N < 2 || cfgs[i].N > 128)
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: bad problem shape");
+  enkf::BatchPlanOut p;
+  if (!enkf::batch_plan_host(count, cfgs, max_grid, alpha, cta_team, cta_rank, team_size, team_first,
+                             order, &p))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: planning failed");
+  if (grid) *grid = p.grid;
+  if (teams) *teams = p.teams;
+  return ENKF_OK;
+}
+
+// ------------------------------------------------------------------ learned warm start
+int64_t enkf_mlp_param_count(const enkf_mlp_shape* shape) { return enkf::mlp_param_count(shape); }
+
+int64_t enkf_mlp_work_bytes(const enkf_mlp_shape* shape, int32_t batch) {
+  return enkf::mlp_work_bytes(shape, batch);
+}
+
+enkf_status enkf_mlp_forward(const enkf_mlp_shape* shape, const float* d_params, const float* d_X,
+                             const int32_t* d_rows, int32_t batch, float* d_Y, void* d_work,
+                             void* cuda_stream) {
+  if (enkf::mlp_param_count(shape) < 0 || !d_params || !d_X || !d_Y || !d_work || batch < 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_mlp_forward: bad argument");
+  cudaError_t e = enkf::mlp_forward(shape, d_params, d_X, d_rows, batch, d_Y, d_work,
+                                    static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(nullptr, e, "enkf_mlp_forward");
+}
+
+enkf_status enkf_mlp_loss_grad(const enkf_mlp_shape* shape, const float* d_params, const float* d_X,
+                               const float* d_T, const int32_t* d_rows, int32_t batch,
+                               float* d_grad, float* d_loss, void* d_work, void* cuda_stream) {
+  if (enkf::mlp_param_count(shape) < 0 || !d_params || !d_X || !d_T || !d_grad || !d_work || batch < 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_mlp_loss_grad: bad argument");
+  cudaError_t e = enkf::mlp_loss_grad(shape, d_params, d_X, d_T, d_rows, batch, d_grad, d_loss, d_work,
+                                      static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(nullptr, e, "enkf_mlp_loss_grad");
+}
+
+enkf_status enkf_mlp_adam(int64_t count, float* d_params, const float* d_grad, float* d_m, float* d_v,
+                          int32_t step, float lr, float beta1, float beta2, float eps, void* cuda_stream) {
+  if (count < 1 || !d_params || !d_grad || !d_m || !d_v || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_mlp_adam: bad argument");
+  cudaError_t e = enkf::mlp_adam(count, d_params, d_grad, d_m, d_v, step, lr, beta1, beta2, eps,
+                                 static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(nullptr, e, "enkf_mlp_adam");
+}
+
+enkf_status enkf_mlp_train_epoch(const enkf_mlp_shape* shape, float* d_params, float* d_m, float* d_v,
+                                 const float* d_X, const float* d_T, const int32_t* d_perm,
+                                 int64_t rows, int32_t batch, int32_t step0, float lr,
+                                 float* d_losses, float* d_grad, void* d_work, void* cuda_stream) {
+  if (enkf::mlp_param_count(shape) < 0 || !d_params || !d_m || !d_v || !d_X || !d_T || !d_perm || !d_grad ||
+      !d_work || batch < 1 || rows < batch || step0 < 0)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_mlp_train_epoch: bad argument");
+  cudaError_t e = enkf::mlp_train_epoch(shape, d_params, d_m, d_v, d_X, d_T, d_perm, rows, batch, step0, lr,
+                                        d_losses, d_work, d_grad, static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(nullptr, e, "enkf_mlp_train_epoch");
+}
+
+enkf_status enkf_mlp_standardize(const enkf_mlp_shape* shape, float* d_params, const float* d_X,
+                                 const float* d_T, int64_t rows, void* cuda_stream) {
+  if (enkf::mlp_param_count(shape) < 0 || !d_params || !d_X || !d_T || rows < 1)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_mlp_standardize: bad argument");
+  cudaError_t e = enkf::mlp_standardize(shape, d_params, d_X, d_T, rows, static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(nullptr, e, "enkf_mlp_standardize");
+}
+
+enkf_status enkf_warm_features(enkf_handle h, int32_t K, float* d_F, float* d_T) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_warm_features: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_warm_features: batched handle");
+  if (h->cfg.precision != ENKF_FP32 || h->cfg.variant != ENKF_CGD)
+    return fail(h, ENKF_ERR_UNSUPPORTED, "enkf_warm_features: needs ENKF_CGD in ENKF_FP32");
+  if (!h->has_result) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_warm_features: no analysis yet");
+  if (K < 1 || !d_F) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_warm_features: K < 1 or NULL d_F");
+  cudaError_t e = enkf::warm_features(h, K, d_F, d_T);
+  return e == cudaSuccess ? ENKF_OK : cuda_fail(h, e, "enkf_warm_features");
+}
+
+enkf_status enkf_set_warm_model(enkf_handle h, const enkf_mlp_shape* shape, const float* d_params) {
+  if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_set_warm_model: NULL handle");
+  if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_set_warm_model: batched handle");
+  if (h->cfg.precision != ENKF_FP32 || h->cfg.variant != ENKF_CGD)
+    return fail(h, ENKF_ERR_UNSUPPORTED, "enkf_set_warm_model: needs ENKF_CGD in ENKF_FP32");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_set_warm_model");
+  if (!d_params) {
+    enkf::warm_free(h);
+    return ENKF_OK;
+  }
+  std::string err;
+  e = enkf::warm_set_model(h, shape, d_params, err);
+  if (e == cudaErrorInvalidValue) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_set_warm_model: " + err);
+  if (e != cudaSuccess) return cuda_fail(h, e, ("enkf_set_warm_model: " + err).c_str());
+  return ENKF_OK;
+}
+
 enkf_status enkf_destroy(enkf_handle h) {
   if (!h) return ENKF_OK;
   cudaStreamSynchronize(h->stream);
+  enkf::batch_free(h);
+  enkf::warm_free(h);
   for (auto& ev : h->ev)
     if (ev) cudaEventDestroy(ev);
   free_workspace(h->ws);

@@ -199,13 +199,14 @@ __device__ __forceinline__ void reduce_all(const double* __restrict__ part, int 
   __syncthreads();
 }
 
-// CTA b sums its slice of the NE-long partial vectors part[g*NE + e] over g < G (fixed order)
-// and writes red[e].
+// CTA b (of G) sums its slice of the NE-long partial vectors part[g*NE + e] over g < G (fixed
+// order) and writes red[e].
 __device__ __forceinline__ void reduce_slice(const double* __restrict__ part, int G, int NE,
-                                             double* __restrict__ red, double* scratch) {
+                                             double* __restrict__ red, double* scratch,
+                                             int b) {
   const int t = threadIdx.x;
   const int chunk = (NE + G - 1) / G;
-  const int e0 = blockIdx.x * chunk;
+  const int e0 = b * chunk;
   const int cnt = min(NE, e0 + chunk) - e0;
   if (cnt <= 0) return;
   if (cnt >= kThreads) {

@@ -135,12 +135,16 @@ struct Workspace {
   int32_t* col_iters = nullptr; // [N]
   double* col_relres = nullptr; // [N]
   double* col_true = nullptr;   // [N]
+  double* col_warm = nullptr;   // [N] true relative residual of a learned start (FP32 mode)
   int32_t* status = nullptr;    // [4]: status bits, refinements, grid, spare
   unsigned* bar = nullptr;      // [4]: barrier counter, abort flag, spare
   void* stage_Xf = nullptr;     // host-API staging [n][N]
   double* stage_y = nullptr;    // [m]
   unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
 };
+
+struct BatchState;   // kernels_batch.cu: plan, arena and graph of a batched handle
+struct WarmState;    // kernels_mlp.cu: learned warm-start model and buffers
 
 struct SolveLaunch {
   int G = 0;          // persistent grid size
@@ -164,6 +168,8 @@ struct enkf_handle_s {
   bool timed = false;
   bool prof_enabled = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  enkf::BatchState* batch = nullptr;   // non-NULL for a handle made by enkf_batch_create
+  enkf::WarmState* warm = nullptr;     // learned warm start (enkf_set_warm_model / enkf_warm_features)
 };
 
 namespace enkf {
@@ -183,6 +189,48 @@ cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa);
 int reduced_grid(const enkf_handle_s* h);
 cudaError_t launch_reduced(enkf_handle_s* h, const void* Xf, const double* y, const double* E,
                            int emode, uint64_t seed, uint64_t counter);
+// kernels_batch.cu: batched analyses (planner, arena, persistent kernel, graph, tuner)
+struct BatchPlanOut {
+  int grid = 0, teams = 0;
+  double alpha = 0.0;
+  int graphed = 0;
+};
+bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha,
+                     int* cta_team, int* cta_rank, int* team_size, int* team_first, int* order,
+                     BatchPlanOut* out);
+cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
+                        const int32_t* const* rowptr, const int32_t* const* col,
+                        const double* const* w, const double* const* r, std::string& err);
+cudaError_t batch_analyze(enkf_handle_s* h, const void* const* Xf, const double* const* y,
+                          const uint64_t* seeds, const uint64_t* counters, void* const* Xa);
+cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
+                       const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
+                       double* best_alpha, double* best_ms);
+cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, double* relres_max,
+                        int32_t* refinements);
+BatchPlanOut batch_info(const enkf_handle_s* h);
+int batch_count(const enkf_handle_s* h);
+size_t batch_state_bytes(const enkf_handle_s* h, int i);   // bytes of X_f of problem i
+void batch_free(enkf_handle_s* h);
+// kernels_mlp.cu: the MLP of the learned warm start and its use in an analysis
+cudaError_t warm_features(enkf_handle_s* h, int K, float* F, float* T);
+cudaError_t warm_set_model(enkf_handle_s* h, const enkf_mlp_shape* shape, const float* params, std::string& err);
+bool warm_ready(const enkf_handle_s* h);
+cudaError_t warm_prepare(enkf_handle_s* h);
+void warm_free(enkf_handle_s* h);
+int64_t mlp_param_count(const enkf_mlp_shape* s);
+int64_t mlp_work_bytes(const enkf_mlp_shape* s, int B);
+cudaError_t mlp_forward(const enkf_mlp_shape* s, const float* P, const float* X, const int32_t* rows, int B,
+                        float* Y, void* work, cudaStream_t st);
+cudaError_t mlp_loss_grad(const enkf_mlp_shape* s, const float* P, const float* X, const float* T,
+                          const int32_t* rows, int B, float* grad, float* loss, void* work, cudaStream_t st);
+cudaError_t mlp_adam(int64_t count, float* P, const float* g, float* m, float* v, int step, float lr, float b1,
+                     float b2, float eps, cudaStream_t st);
+cudaError_t mlp_train_epoch(const enkf_mlp_shape* s, float* P, float* m, float* v, const float* X, const float* T,
+                            const int32_t* perm, int64_t rows, int B, int step0, float lr, float* losses,
+                            void* work, float* grad, cudaStream_t st);
+cudaError_t mlp_standardize(const enkf_mlp_shape* s, float* P, const float* X, const float* T, int64_t rows,
+                            cudaStream_t st);
 cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r,
                                       int64_t m, int N, double* E, cudaStream_t s);
 }  // namespace enkf

@@ -1,0 +1,562 @@
+// Batched analyses: many independent CGD-EnKF problems of uneven (n, m, N) in one persistent
+// cooperative launch, replayed from a CUDA graph. Each problem is the analysis of Fig. 2 /
+// Algorithm 1 (innovations, CG solve of S Z = D with the matrix-free product of the
+// matvec decomposition, X_a = X_f + A HA^T Z / (N - 1)), in the FP32-with-refresh mode.
+//
+// Planning (host): a problem is costed at m N^2 (N + 8) + 2 n N^2 (about N preconditioned
+// steps of 4 m N^2 flops each, plus the update). Problems worth at least 1.5 CTAs of the
+// grid get a team of CTAs of their own, sized by alpha times their cost share; the rest are
+// packed onto single-CTA teams longest-processing-time first. Every team walks its list of
+// problems; for each it runs the innovations over its rows, the persistent CG solve with a
+// bounded barrier over the team's CTAs only, and the ensemble update. The tuner times a few
+// alpha values on the caller's inputs and keeps the fastest; the choice can be cached in the
+// text file named by the ENKF_TUNE_CACHE environment variable.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "solve_body.cuh"
+
+namespace enkf {
+
+struct BatchProblem {
+  SolveParams sp;
+  int64_t n;
+  int NT;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* w;
+};
+struct BatchIO {
+  const float* Xf;
+  const double* y;
+  float* Xa;
+  uint64_t seed, counter;
+};
+
+// The per-problem phases as separate (not inlined) device functions, so that each gets the
+// register allocation of its own loop nest instead of the union of all of them.
+template <int NT>
+__device__ __noinline__ void batch_solve(const SolveParams& sp, int G, int rank, GridBarrier& bar,
+                                         unsigned char* smem) {
+  solve_body<float, NT, true>(sp, G, rank, bar, smem);
+}
+template <int NT>
+__device__ __noinline__ void batch_update(const BatchIO& io, const double* W, int64_t n, int N,
+                                          int rank, int G, unsigned char* smem) {
+  update_rows<float, NT, 0>(io.Xf, io.Xa, W, n, N, rank, G, smem);
+}
+
+// NTMAX bounds the column tile of every problem in the batch; batches with N <= 64 fit two
+// CTAs per SM like the single-analysis FP32 solve. The solve is the Jacobi-preconditioned
+// (M = R) form.
+template <int NTMAX>
+__global__ void __launch_bounds__(kThreads, NTMAX == 128 ? 1 : 2) batch_kernel(
+    const BatchProblem* __restrict__ probs, const BatchIO* __restrict__ io,
+    const int* __restrict__ cta_team, const int* __restrict__ cta_rank,
+    const int* __restrict__ team_size, const int* __restrict__ team_first,
+    const int* __restrict__ order, int perturb) {
+  constexpr int NT2 = NTMAX >= 64 ? 64 : 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SolveParams s_sp;
+  __shared__ BatchIO s_io;
+  __shared__ int64_t s_n;
+  __shared__ int s_nt;
+  const int team = cta_team[blockIdx.x], rank = cta_rank[blockIdx.x], G = team_size[team];
+  const int warp = threadIdx.x >> 5;
+  const int k_end = team_first[team + 1];
+  for (int k = team_first[team]; k < k_end; ++k) {
+    const int pi = order[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_sp = probs[pi].sp;
+      s_io = io[pi];
+      s_n = probs[pi].n;
+      s_nt = probs[pi].NT;
+    }
+    __syncthreads();
+    const SolveParams& sp = s_sp;
+    const int NT = s_nt;
+    GridBarrier bar{sp.bar, reinterpret_cast<int*>(sp.bar + 1), sp.status, (unsigned)G, 0u};
+    // innovations over this CTA's block of observation rows (the solve uses the same blocks)
+    const int64_t rows_per = (sp.m + G - 1) / G;
+    const int64_t r0 = imin64(sp.m, (int64_t)rank * rows_per), r1 = imin64(sp.m, r0 + rows_per);
+    innov_rows<float>(s_io.Xf, probs[pi].rowptr, probs[pi].col, probs[pi].w, s_io.y, sp.r, nullptr,
+                      perturb ? 2 : 0, s_io.seed, s_io.counter, sp.m, sp.N, nullptr,
+                      static_cast<float*>(const_cast<void*>(sp.HA)), const_cast<double*>(sp.D),
+                      static_cast<float*>(sp.B), nullptr, nullptr, 0, const_cast<df32*>(sp.HAdf),
+                      const_cast<df32*>(sp.Ddf), r0, r1, warp, kThreads / 32);
+    bool ok = bar.sync();
+    if (ok) {
+      if (NT == 32) batch_solve<32>(sp, G, rank, bar, smem);
+      else if (NT == 64) batch_solve<NT2>(sp, G, rank, bar, smem);
+      else batch_solve<NTMAX>(sp, G, rank, bar, smem);
+      ok = bar.sync();   // W of this problem complete and visible to the team
+    }
+    if (!ok) {
+      // a barrier of this problem gave up: the team is no longer in step, so it stops here
+      // and flags the problems it has not finished
+      if (rank == 0 && threadIdx.x == 0)
+        for (int q = k; q < k_end; ++q) atomicOr(probs[order[q]].sp.status, DS_TIMEOUT);
+      return;
+    }
+    if (NT == 32) batch_update<32>(s_io, sp.W, s_n, sp.N, rank, G, smem);
+    else if (NT == 64) batch_update<NT2>(s_io, sp.W, s_n, sp.N, rank, G, smem);
+    else batch_update<NTMAX>(s_io, sp.W, s_n, sp.N, rank, G, smem);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct BatchPlan {
+  double alpha = 1.0;
+  int grid = 0;
+  std::vector<int> cta_team, cta_rank, team_size, team_first, order, team_cta0;
+};
+
+struct BatchState {
+  int count = 0;
+  int perturb = 1;
+  int ntmax = 32;
+  int ne_max = 0;
+  size_t smem = 0;
+  int max_grid = 0;
+  std::vector<enkf_config> cfg;
+  void* arena = nullptr;
+  std::vector<BatchProblem> probs;     // host copy (device pointers into the arena)
+  BatchProblem* d_probs = nullptr;
+  BatchIO* d_io = nullptr;
+  BatchIO* h_io = nullptr;             // pinned staging of the per-call table
+  std::vector<BatchIO> last_io;        // table currently on the device
+  cudaEvent_t io_copied = nullptr;     // the last table upload has finished reading h_io
+  int* d_plan = nullptr;               // cta_team | cta_rank | team_size | team_first | order
+                                       // (grid, grid, teams, teams + 1, count entries)
+  int* d_status = nullptr;             // [count][4]: status bits, refinements
+  unsigned* d_bar = nullptr;           // [count][4]: barrier counter, abort flag
+  double* d_team = nullptr;            // Tpart [max_grid][NE], Tred [max_grid][NE], rrpart [max_grid][256]
+  BatchPlan plan;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = true;                // capture works here; else launches go direct
+};
+
+static int nt_of(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
+
+static double problem_cost(const enkf_config& c) {
+  const double m = (double)c.m, N = c.N, n = (double)c.n;
+  return m * N * N * (N + 8.0) + 2.0 * n * N * N;
+}
+
+static BatchPlan make_plan(const std::vector<enkf_config>& cfg, int G, double alpha) {
+  BatchPlan P;
+  P.alpha = alpha;
+  const int count = (int)cfg.size();
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) cost[i] = problem_cost(cfg[i]);
+  const double C = std::accumulate(cost.begin(), cost.end(), 0.0);
+  std::vector<int> idx(count);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  struct Team { int size; double load; std::vector<int> probs; };
+  std::vector<Team> teams;
+  int used = 0;
+  std::vector<int> small;
+  for (int pi : idx) {
+    const double share = G * cost[pi] / C;
+    const int cap = (int)std::max<int64_t>(1, (cfg[pi].m + 63) / 64);   // >= 64 rows per CTA
+    const int k = std::min((int)std::floor(alpha * share), cap);
+    if (share >= 1.5 && k >= 2 && used + k <= G - 1) {
+      teams.push_back({k, cost[pi] / k, {pi}});
+      used += k;
+    } else {
+      small.push_back(pi);
+    }
+  }
+  const size_t first_single = teams.size();
+  const int singles = std::min<int>(G - used, std::max<int>(1, (int)small.size()));
+  for (int s = 0; s < singles; ++s) teams.push_back({1, 0.0, {}});
+  for (int pi : small) {   // LPT onto the single-CTA teams (costs already descending)
+    size_t best = first_single;
+    for (size_t t = first_single + 1; t < teams.size(); ++t)
+      if (teams[t].load < teams[best].load) best = t;
+    teams[best].load += cost[pi];
+    teams[best].probs.push_back(pi);
+  }
+  int cta = 0;
+  P.team_first.push_back(0);
+  for (const Team& t : teams) {
+    if (t.probs.empty()) continue;
+    const int tid = (int)P.team_size.size();
+    P.team_size.push_back(t.size);
+    P.team_cta0.push_back(cta);
+    for (int r = 0; r < t.size; ++r) {
+      P.cta_team.push_back(tid);
+      P.cta_rank.push_back(r);
+    }
+    cta += t.size;
+    for (int pi : t.probs) P.order.push_back(pi);
+    P.team_first.push_back((int)P.order.size());
+  }
+  P.grid = cta;
+  return P;
+}
+
+bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha,
+                     int* cta_team, int* cta_rank, int* team_size, int* team_first, int* order,
+                     BatchPlanOut* out) {
+  if (count < 1 || !cfgs || max_grid < 1) return false;
+  const BatchPlan P = make_plan(std::vector<enkf_config>(cfgs, cfgs + count), max_grid, alpha);
+  auto put = [](const std::vector<int>& v, int* dst) { if (dst) std::copy(v.begin(), v.end(), dst); };
+  put(P.cta_team, cta_team);
+  put(P.cta_rank, cta_rank);
+  put(P.team_size, team_size);
+  put(P.team_first, team_first);
+  put(P.order, order);
+  if (out) *out = BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha};
+  return true;
+}
+
+template <int NTMAX>
+static size_t batch_smem_nt() {
+  return std::max<size_t>(solve_smem_bytes<float, NTMAX>(), update_smem_bytes<float, NTMAX>());
+}
+
+static void* batch_fn(int ntmax) {
+  if (ntmax == 32) return (void*)batch_kernel<32>;
+  if (ntmax == 64) return (void*)batch_kernel<64>;
+  return (void*)batch_kernel<128>;
+}
+
+static void drop_graph(BatchState& B) {
+  if (B.gexec) { cudaGraphExecDestroy(B.gexec); B.gexec = nullptr; }
+  if (B.graph) { cudaGraphDestroy(B.graph); B.graph = nullptr; }
+}
+
+// Install a plan: per-team slices of the reduction buffers, plan arrays on the device.
+static cudaError_t apply_plan(BatchState& B, const BatchPlan& P, cudaStream_t s) {
+  B.plan = P;
+  const size_t NE = (size_t)B.ne_max;
+  for (size_t t = 0; t < P.team_size.size(); ++t) {
+    const size_t c0 = (size_t)P.team_cta0[t];
+    for (int k = P.team_first[t]; k < P.team_first[t + 1]; ++k) {
+      SolveParams& sp = B.probs[P.order[k]].sp;
+      sp.Tpart = B.d_team + c0 * NE;                                   // [team size][NE]
+      sp.Tred = B.d_team + (size_t)B.max_grid * NE + c0 * NE;          // [NE]
+      sp.rrpart = B.d_team + (size_t)2 * B.max_grid * NE + c0 * 256;   // [2][team size][NT]
+    }
+  }
+  std::vector<int> flat;
+  for (const auto* v : {&P.cta_team, &P.cta_rank, &P.team_size, &P.team_first, &P.order})
+    flat.insert(flat.end(), v->begin(), v->end());
+  drop_graph(B);
+  cudaError_t e = cudaStreamSynchronize(s);   // no replay of the old plan is still reading
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B.d_plan, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B.d_probs, B.probs.data(), B.probs.size() * sizeof(BatchProblem), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static cudaError_t enqueue_batch(BatchState& B, cudaStream_t s) {
+  const BatchPlan& P = B.plan;
+  const int nC = (int)P.cta_team.size(), nT = (int)P.team_size.size();
+  int* cta_team = B.d_plan;
+  int* cta_rank = cta_team + nC;
+  int* team_size = cta_rank + nC;
+  int* team_first = team_size + nT;
+  int* order = team_first + nT + 1;
+  cudaError_t e = cudaMemsetAsync(B.d_bar, 0, sizeof(unsigned) * 4 * B.count, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.d_status, 0, sizeof(int) * 4 * B.count, s);
+  if (e != cudaSuccess) return e;
+  const BatchProblem* probs = B.d_probs;
+  const BatchIO* io = B.d_io;
+  int perturb = B.perturb;
+  void* args[] = {&probs, &io, &cta_team, &cta_rank, &team_size, &team_first, &order, &perturb};
+  return cudaLaunchCooperativeKernel(batch_fn(B.ntmax), dim3(P.grid), dim3(kThreads), args,
+                                     B.smem, s);
+}
+
+// One batched analysis: upload the per-call table if it changed, then replay the graph
+// (captured on first use after each plan change).
+static cudaError_t run_batch(enkf_handle_s* h, const std::vector<BatchIO>& io) {
+  BatchState& B = *h->batch;
+  cudaError_t e = cudaSuccess;
+  const bool same = B.last_io.size() == io.size() &&
+                    std::memcmp(B.last_io.data(), io.data(), io.size() * sizeof(BatchIO)) == 0;
+  if (!same) {
+    e = cudaEventSynchronize(B.io_copied);   // the previous upload no longer reads h_io
+    if (e != cudaSuccess) return e;
+    std::memcpy(B.h_io, io.data(), io.size() * sizeof(BatchIO));
+    e = cudaMemcpyAsync(B.d_io, B.h_io, io.size() * sizeof(BatchIO), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(B.io_copied, h->stream);
+    if (e != cudaSuccess) return e;
+    B.last_io = io;
+  }
+  if (!B.graph_ok) return enqueue_batch(B, h->stream);
+  if (!B.gexec) {
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t le = enqueue_batch(B, cap);
+      e = cudaStreamEndCapture(cap, &B.graph);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B.gexec, B.graph, 0);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+      // capture of a cooperative launch refused: the graph is an optimisation, so clear the
+      // error and launch the same work directly from now on
+      cudaGetLastError();
+      drop_graph(B);
+      B.graph_ok = false;
+      return enqueue_batch(B, h->stream);
+    }
+  }
+  return cudaGraphLaunch(B.gexec, h->stream);
+}
+
+static std::string cache_key(const BatchState& B) {
+  std::string key = std::to_string(B.count) + ":" + std::to_string(B.max_grid) + ":";
+  for (const auto& c : B.cfg)
+    key += std::to_string(c.n) + "/" + std::to_string(c.m) + "/" + std::to_string(c.N) + ",";
+  return key;
+}
+
+// ------------------------------------------------------------------ entry-point helpers
+cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
+                        const int32_t* const* rowptr, const int32_t* const* col,
+                        const double* const* w, const double* const* r, std::string& err) {
+  auto* Bp = new BatchState();
+  h->batch = Bp;
+  BatchState& B = *Bp;
+  B.count = count;
+  B.perturb = cfgs[0].perturb_obs;
+  int nmax = 2;
+  for (int i = 0; i < count; ++i) {
+    B.cfg.push_back(cfgs[i]);
+    nmax = std::max(nmax, (int)cfgs[i].N);
+  }
+  B.ntmax = nt_of(nmax);
+  B.ne_max = nmax * nmax + 2 * nmax;
+  B.smem = B.ntmax == 32 ? batch_smem_nt<32>() : B.ntmax == 64 ? batch_smem_nt<64>() : batch_smem_nt<128>();
+  void* fn = batch_fn(B.ntmax);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem);
+  int occ = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, B.smem);
+  if (e != cudaSuccess) { err = "enkf_batch_create: occupancy query"; return e; }
+  if (occ < 1) { err = "enkf_batch_create: kernel does not fit on an SM"; return cudaErrorInvalidConfiguration; }
+  B.max_grid = occ * h->sms;
+  if (h->cfg.grid_blocks > 0) B.max_grid = std::min(B.max_grid, h->cfg.grid_blocks);
+  // one arena: per problem HA, HAdf, D, Ddf, Zdf, B, X, Res, P, Sv, r, r32, rowptr, col, w,
+  // W, column iterations / residuals
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  std::vector<std::vector<size_t>> parts(count);
+  std::vector<size_t> off(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    const auto& c = cfgs[i];
+    const size_t mN = (size_t)c.m * c.N, m = (size_t)c.m, N = (size_t)c.N;
+    const size_t nnz = (size_t)std::max(1, rowptr[i][c.m]);
+    parts[i] = {4 * mN, 8 * mN, 8 * mN, 8 * mN, 8 * mN, 4 * mN, 4 * mN, 4 * mN, 4 * mN, 4 * mN,
+                8 * m, 4 * m, 4 * (m + 1), 4 * nnz, 8 * nnz, 8 * N * N, 4 * N, 8 * N, 8 * N};
+    size_t sz = 0;
+    for (size_t b : parts[i]) sz += al(b);
+    off[i + 1] = off[i] + sz;
+  }
+  const size_t NE = (size_t)B.ne_max;
+  e = cudaMalloc(&B.arena, off[count]);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_probs, sizeof(BatchProblem) * count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_io, sizeof(BatchIO) * count);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&B.h_io, sizeof(BatchIO) * count);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.io_copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_plan, sizeof(int) * (4 * (size_t)B.max_grid + 1 + count));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_status, sizeof(int) * 4 * count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_bar, sizeof(unsigned) * 4 * count);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&B.d_team, sizeof(double) * (2 * (size_t)B.max_grid * NE + (size_t)B.max_grid * 256));
+  if (e != cudaSuccess) { err = "enkf_batch_create: device allocation"; return e; }
+  unsigned char* base = static_cast<unsigned char*>(B.arena);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    const auto& c = cfgs[i];
+    unsigned char* q = base + off[i];
+    std::vector<void*> ptr;
+    for (size_t b : parts[i]) { ptr.push_back(q); q += al(b); }
+    BatchProblem bp{};
+    SolveParams& sp = bp.sp;
+    sp.m = c.m;
+    sp.N = c.N;
+    sp.mode = 1;
+    sp.HA = ptr[0];
+    sp.HA64 = nullptr;
+    sp.HAdf = static_cast<const df32*>(ptr[1]);
+    sp.D = static_cast<const double*>(ptr[2]);
+    sp.Ddf = static_cast<const df32*>(ptr[3]);
+    sp.Zdf = static_cast<df32*>(ptr[4]);
+    sp.B = ptr[5];
+    sp.X = ptr[6];
+    sp.Res = ptr[7];
+    sp.P = ptr[8];
+    sp.Sv = ptr[9];
+    sp.Z = nullptr;
+    sp.r = static_cast<const double*>(ptr[10]);
+    sp.rv = ptr[11];
+    sp.W = static_cast<double*>(ptr[15]);
+    sp.col_iters = static_cast<int*>(ptr[16]);
+    sp.col_relres = static_cast<double*>(ptr[17]);
+    sp.col_true = static_cast<double*>(ptr[18]);
+    sp.tol = c.tol;
+    sp.inner_tol = c.inner_tol;
+    sp.max_iter = c.max_iter;
+    sp.fixed_iters = 0;
+    sp.max_refine = c.max_refine;
+    sp.true_residual = c.true_residual;
+    sp.status = B.d_status + 4 * i;
+    sp.bar = B.d_bar + 4 * i;
+    sp.prof = nullptr;
+    bp.n = c.n;
+    bp.NT = nt_of(c.N);
+    bp.rowptr = static_cast<const int32_t*>(ptr[12]);
+    bp.col = static_cast<const int32_t*>(ptr[13]);
+    bp.w = static_cast<const double*>(ptr[14]);
+    const int64_t nnz = rowptr[i][c.m];
+    e = cudaMemcpy(ptr[12], rowptr[i], 4 * ((size_t)c.m + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ptr[13], col[i], 4 * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ptr[14], w[i], 8 * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ptr[10], r[i], 8 * (size_t)c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      std::vector<float> r32(c.m);
+      for (int64_t k = 0; k < c.m; ++k) r32[k] = (float)r[i][k];
+      e = cudaMemcpy(ptr[11], r32.data(), 4 * (size_t)c.m, cudaMemcpyHostToDevice);
+    }
+    B.probs.push_back(bp);
+  }
+  if (e != cudaSuccess) { err = "enkf_batch_create: upload of the observation operators"; return e; }
+  double alpha = 1.0;
+  if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
+    std::ifstream f(path);
+    const std::string key = cache_key(B);
+    std::string line;
+    while (std::getline(f, line)) {
+      const size_t sp = line.rfind(' ');
+      if (sp != std::string::npos && line.compare(0, sp, key) == 0) alpha = std::atof(line.c_str() + sp + 1);
+    }
+    if (!(alpha > 0.0 && alpha <= 4.0)) alpha = 1.0;
+  }
+  e = apply_plan(B, make_plan(B.cfg, B.max_grid, alpha), h->stream);
+  if (e != cudaSuccess) err = "enkf_batch_create: plan upload";
+  return e;
+}
+
+static std::vector<BatchIO> make_io(const BatchState& B, const void* const* Xf, const double* const* y,
+                                    const uint64_t* seeds, const uint64_t* counters, void* const* Xa) {
+  std::vector<BatchIO> io(B.count);
+  for (int i = 0; i < B.count; ++i)
+    io[i] = BatchIO{static_cast<const float*>(Xf[i]), y[i], static_cast<float*>(Xa[i]),
+                    seeds ? seeds[i] : 0, counters ? counters[i] : 0};
+  return io;
+}
+
+cudaError_t batch_analyze(enkf_handle_s* h, const void* const* Xf, const double* const* y,
+                          const uint64_t* seeds, const uint64_t* counters, void* const* Xa) {
+  return run_batch(h, make_io(*h->batch, Xf, y, seeds, counters, Xa));
+}
+
+cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
+                       const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
+                       double* best_alpha, double* best_ms) {
+  BatchState& B = *h->batch;
+  const std::vector<BatchIO> io = make_io(B, Xf, y, seeds, counters, Xa);
+  const double cand[] = {1.0, 0.85, 0.7, 0.55, 1.2};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 1e300, ba = B.plan.alpha;
+  for (double a : cand) {
+    if (e != cudaSuccess) break;
+    e = apply_plan(B, make_plan(B.cfg, B.max_grid, a), h->stream);
+    if (e == cudaSuccess) e = run_batch(h, io);   // warm-up, captures the graph
+    float tot = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      float ms = 0.f;
+      e = cudaEventRecord(e0, h->stream);
+      if (e == cudaSuccess) e = run_batch(h, io);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (e == cudaSuccess && tot / 3 < best) { best = tot / 3; ba = a; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  e = apply_plan(B, make_plan(B.cfg, B.max_grid, ba), h->stream);
+  if (best_alpha) *best_alpha = ba;
+  if (best_ms) *best_ms = best;
+  if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
+    std::ofstream f(path, std::ios::app);
+    f << cache_key(B) << " " << ba << "\n";
+  }
+  return e;
+}
+
+cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, double* relres_max,
+                        int32_t* refinements) {
+  BatchState& B = *h->batch;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  std::vector<int> st(4 * (size_t)B.count);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), B.d_status, sizeof(int) * 4 * B.count, cudaMemcpyDeviceToHost);
+  for (int i = 0; i < B.count && e == cudaSuccess; ++i) {
+    const SolveParams& sp = B.probs[i].sp;
+    const int N = B.cfg[i].N;
+    std::vector<int> it(N);
+    std::vector<double> rel(N);
+    e = cudaMemcpy(it.data(), sp.col_iters, sizeof(int) * N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rel.data(), sp.col_relres, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    const int bits = st[4 * (size_t)i];
+    int s = ENKF_OK;
+    if (bits & DS_TIMEOUT) s = ENKF_ERR_TIMEOUT;
+    else if (bits & DS_NONFINITE) s = ENKF_ERR_NONFINITE;
+    else if (bits & DS_BREAKDOWN) s = ENKF_ERR_BREAKDOWN;
+    else if (bits & DS_NOT_CONVERGED) s = ENKF_ERR_NOT_CONVERGED;
+    if (status) status[i] = s;
+    if (iters_max) iters_max[i] = *std::max_element(it.begin(), it.end());
+    if (relres_max) relres_max[i] = *std::max_element(rel.begin(), rel.end());
+    if (refinements) refinements[i] = st[4 * (size_t)i + 1];
+  }
+  return e;
+}
+
+BatchPlanOut batch_info(const enkf_handle_s* h) {
+  if (!h->batch) return BatchPlanOut{};
+  const BatchPlan& P = h->batch->plan;
+  return BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha, h->batch->graph_ok ? 1 : 0};
+}
+
+int batch_count(const enkf_handle_s* h) { return h->batch ? h->batch->count : 0; }
+
+size_t batch_state_bytes(const enkf_handle_s* h, int i) {
+  const enkf_config& c = h->batch->cfg[i];
+  return sizeof(float) * (size_t)c.n * (size_t)c.N;
+}
+
+void batch_free(enkf_handle_s* h) {
+  BatchState* B = h->batch;
+  if (!B) return;
+  drop_graph(*B);
+  if (B->io_copied) cudaEventDestroy(B->io_copied);
+  if (B->h_io) cudaFreeHost(B->h_io);
+  void* ptrs[] = {B->arena, B->d_probs, B->d_io, B->d_plan, B->d_status, B->d_bar, B->d_team};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete B;
+  h->batch = nullptr;
+}
+
+}  // namespace enkf

@@ -69,6 +69,8 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
     return noalloc_fail(ENKF_ERR_UNSUPPORTED, "enkf_analyze_noalloc: precision must be FP64 or FP32");
   if (c.variant != ENKF_CGD)
     return noalloc_fail(ENKF_ERR_UNSUPPORTED, "enkf_analyze_noalloc: variant must be ENKF_CGD");
+  if (c.warm_start != 0)
+    return noalloc_fail(ENKF_ERR_UNSUPPORTED, "enkf_analyze_noalloc: no learned warm start (it needs a handle)");
   if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0 || c.grid_blocks < 0)
     return noalloc_fail(ENKF_ERR_INVALID_ARG, "enkf_analyze_noalloc: bad iteration limits");
   if (c.fixed_iters == 0 && !(c.tol > 0.0))

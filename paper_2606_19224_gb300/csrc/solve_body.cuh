@@ -1,0 +1,488 @@
+// The persistent CG solve of one problem by a set of co-resident CTAs, and the row-range
+// forms of the innovation and update steps: shared by the single-analysis kernels
+// (kernels_fp.cu) and the batched kernel (kernels_batch.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "cg_device.cuh"
+
+namespace enkf {
+
+struct SolveParams {
+  int64_t m;
+  int N;
+  int mode;  // 0: FP64 CG (X is the FP64 solution Z); 1: FP32 inner CG + FP64 refresh
+  const void* HA;
+  const double* HA64;
+  const double* D;
+  const double* r;
+  const void* rv;   // r in the inner-solve type
+  void* B;
+  void* X;
+  void* Res;
+  void* P;
+  void* Sv;
+  double* Z;
+  const df32* HAdf;   // HA and D in double-float, and the double-float solution (FP32 mode)
+  const df32* Ddf;
+  df32* Zdf;
+  double* Tpart;
+  double* Tred;
+  double* rrpart;
+  double* W;
+  double tol, inner_tol;
+  int max_iter, fixed_iters, max_refine, true_residual;
+  int* col_iters;
+  double* col_relres;
+  double* col_true;
+  int* status;
+  unsigned* bar;
+  unsigned long long* prof;  // optional phase timers of CTA 0 (ns), nullptr when off
+  int warm;                  // FP32 mode: Zdf holds a starting solution (learned warm start)
+  double* col_warm;          // [N] true relative residual of that start (-1 when not warm)
+};
+
+// Phase timer slots (CTA 0, thread 0): accumulated ns per phase of the solve.
+enum : int { PH_SETUP = 0, PH_PASS, PH_BAR1, PH_RED, PH_BAR2, PH_SCAL, PH_REFRESH, PH_COUNT = 8 };
+
+// The persistent solve of one problem by G co-resident CTAs (this one is number b), with the
+// grid barrier `bar` over exactly those CTAs: the whole grid for one analysis, a team of the
+// grid for batched analyses.
+template <typename VT, int NT, bool PC>
+__device__ void solve_body(const SolveParams& p, const int G, const int b, GridBarrier& bar,
+                           unsigned char* smem) {
+  double* s_gam = reinterpret_cast<double*>(smem);   // (r, r) of the current residual
+  double* s_gold = s_gam + NT;                        // previous (r, r)
+  double* s_sig = s_gold + NT;                        // sum r_i r_ij^2
+  double* s_tn2 = s_sig + NT;                         // ||HA^T r_j||^2
+  double* s_bn2 = s_tn2 + NT;                         // ||b_j||^2 of the inner solve
+  double* s_dn2 = s_bn2 + NT;                         // ||d_j||^2
+  double* s_alpha = s_dn2 + NT;
+  double* s_beta = s_alpha + NT;
+  double* s_itol = s_beta + NT;
+  double* s_tmp = s_itol + NT;
+  double* s_true = s_tmp + NT;
+  double* s_spare = s_true + NT;
+  int* s_active = reinterpret_cast<int*>(s_spare + NT);
+  int* s_done = s_active + NT;
+  int* s_iters = s_done + NT;
+  int* s_flag = s_iters + NT;
+  VT* s_alpha_v = reinterpret_cast<VT*>(s_flag + NT);
+  VT* s_beta_v = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(s_flag + NT) + NT * 8);
+  double* scratch = reinterpret_cast<double*>(smem + scalar_bytes<NT>());
+  unsigned char* uni = smem + scalar_bytes<NT>() + kThreads * 8;
+  constexpr int LDV = NT + 16 / (int)sizeof(VT);
+  VT* sT = reinterpret_cast<VT*>(uni);
+  unsigned char* tiles = uni + NT * LDV * sizeof(VT);
+
+  const int N = p.N, t = threadIdx.x;
+  const int64_t rows_per = (p.m + G - 1) / G;
+  const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
+  const int64_t row1 = imin64(p.m, row0 + rows_per);
+  const int NE = N * N + 2 * N;
+  const double inv_nm1 = 1.0 / (double)(N - 1);
+  const bool refine = (p.mode == 1);
+  const bool fixed = p.fixed_iters > 0;
+  VT* X = refine ? static_cast<VT*>(p.X) : reinterpret_cast<VT*>(p.Z);
+  VT* Res = static_cast<VT*>(p.Res);
+  VT* P = static_cast<VT*>(p.P);
+  VT* Sv = static_cast<VT*>(p.Sv);
+  const VT* B = refine ? static_cast<const VT*>(p.B) : reinterpret_cast<const VT*>(p.D);
+  const VT* HA = static_cast<const VT*>(p.HA);
+  const VT* rv = static_cast<const VT*>(p.rv);
+  double* Tp = p.Tpart + (int64_t)b * NE;
+  const bool prof = p.prof != nullptr && b == 0 && t == 0;
+  unsigned long long ph[PH_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long tp = prof ? global_ns() : 0ull;
+  auto tick = [&](int slot) {
+    if (prof) {
+      const unsigned long long now = global_ns();
+      ph[slot] += now - tp;
+      tp = now;
+    }
+  };
+  int par = 0;
+  bool ok = true;
+
+  // a warm start keeps the given Zdf and begins with a refresh (its true residual)
+  bool warm_pending = refine && p.warm != 0;
+  // ---- ||d_j||^2 (and Z = 0 for the refinement accumulator)
+  rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
+    const double d = p.D[i * N + j];
+    acc = fma(d, d, acc);
+    if (refine && !warm_pending) p.Zdf[i * N + j] = df32(0.f, 0.f);
+  }, s_tmp, scratch);
+  if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+  ok = bar.sync();
+  if (ok) {
+    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_dn2, scratch);
+    par ^= 1;
+    if (t < NT) {
+      const bool zero = (t >= N) || (s_dn2[t] == 0.0);
+      s_done[t] = zero ? 1 : 0;
+      s_iters[t] = 0;
+      s_true[t] = (t < N && s_dn2[t] == 0.0) ? 0.0 : -1.0;
+      s_gam[t] = 0.0;
+      s_bn2[t] = 0.0;
+      s_itol[t] = refine ? p.inner_tol : p.tol;
+      s_alpha_v[t] = VT(0);
+      s_beta_v[t] = VT(0);
+    }
+    __syncthreads();
+  }
+  tick(PH_SETUP);
+
+  int outer = 0, total_iter = 0, refinements = 0;
+  while (ok) {
+   const bool warm_step = warm_pending;
+   if (!warm_step) {
+    // ---- inner solve of S X = B from X = 0: first reduction of [HA^T r | sum r_i r^2 | (r, r)]
+    {
+      ProSetup<VT, PC> pro{B, X, Res, rv, N};
+      passA<VT, NT, ProSetup<VT, PC>, PC>(HA, row0, row1, N, rv, true, pro, uni, Tp);
+    }
+    if (!(ok = bar.sync())) break;
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+    if (!(ok = bar.sync())) break;
+    stage_T_norms<VT, NT>(p.Tred, N, sT, s_tn2, scratch);
+    // slots: plain CG: s_sig = sum r r_i^2, s_gam = (r, r); preconditioned: s_sig = (r, z)
+    // (the CG gamma), s_gam = (r, r) (the stopping rule's norm)
+    if (t < NT) {
+      const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;
+      const double gm = t < N ? __ldcg(p.Tred + N * N + N + t) : 0.0;
+      s_sig[t] = sg;
+      s_gam[t] = gm;
+      s_bn2[t] = gm;
+      s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
+      s_alpha[t] = 0.0;
+      s_beta[t] = 0.0;
+      s_spare[t] = 0.0;
+    }
+    __syncthreads();
+    tick(PH_SETUP);
+    const int limit = fixed ? p.fixed_iters : (p.max_iter - total_iter);
+    int it = 0;
+    for (;;) {
+      // scalars of this step (identical in every CTA: same sums in the same order)
+      if (t < N) {
+        int a = s_active[t];
+        const double gm = s_gam[t];
+        if (a && it > 0) {
+          if (!isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
+          else if (fixed ? gm == 0.0 : sqrt(gm) <= s_itol[t] * sqrt(s_bn2[t])) a = 0;
+        }
+        double al = 0.0, be = 0.0;
+        if (a) {
+          // CG gamma: (r, r) plain, (r, R^-1 r) preconditioned; delta = (z, S z)
+          const double cg = PC ? s_sig[t] : gm;
+          const double delta = s_tn2[t] * inv_nm1 + s_sig[t];
+          double den = delta;
+          if (it > 0) {
+            be = cg / s_gold[t];
+            den = delta - be * cg / s_alpha[t];
+          }
+          if (!isfinite(den)) { atomicOr(p.status, DS_NONFINITE); a = 0; be = 0.0; }
+          else if (den <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); a = 0; be = 0.0; }
+          else al = cg / den;
+        }
+        s_active[t] = a;
+        s_alpha[t] = al;
+        s_beta[t] = be;
+        s_alpha_v[t] = (VT)al;
+        s_beta_v[t] = (VT)be;
+      }
+      __syncthreads();
+      if (t == 0) {
+        int any = 0;
+        for (int j = 0; j < N; ++j) any |= s_active[j];
+        s_flag[0] = any && it < limit;
+      }
+      __syncthreads();
+      if (!s_flag[0]) break;
+      tick(PH_SCAL);
+      passF<VT, NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
+                        tiles, Tp);
+      tick(PH_PASS);
+      if (!(ok = bar.sync())) break;
+      tick(PH_BAR1);
+      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+      tick(PH_RED);
+      if (!(ok = bar.sync())) break;
+      tick(PH_BAR2);
+      stage_T_norms<VT, NT>(p.Tred, N, sT, s_tn2, scratch);
+      if (t < N) {
+        if (s_active[t]) {
+          s_iters[t] += 1;
+          s_gold[t] = PC ? s_sig[t] : s_gam[t];
+          s_gam[t] = __ldcg(p.Tred + N * N + N + t);
+          s_sig[t] = __ldcg(p.Tred + N * N + t);
+        }
+      }
+      __syncthreads();
+      tick(PH_SCAL);
+      ++it;
+    }
+    if (!ok) break;
+    total_iter += it;
+   }
+
+    // ---- refresh: Z (+)= X; T = HA^T Z; W = T/(N-1); true residual D - S Z; next right-hand
+    // side. FP64 in the FP64 mode; double-float (FP32 pairs) in the FP32 mode.
+    if constexpr (sizeof(VT) == 8) {
+      ProRefresh<VT> pro{p.Z, X, N, refine};
+      passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
+    } else {
+      ProRefreshDF<VT> pro{p.Zdf, X, N, !warm_pending};
+      passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
+    }
+    if (!(ok = bar.sync())) break;
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+    if (!(ok = bar.sync())) break;
+    if (b == 0)
+      for (int e = t; e < N * N; e += kThreads) p.W[e] = __ldcg(p.Tred + e) * inv_nm1;
+    if (!refine && !p.true_residual) {
+      tick(PH_REFRESH);
+      break;
+    }
+    if constexpr (sizeof(VT) == 8) {
+      double* sT64 = reinterpret_cast<double*>(uni);
+      stage_T<double, NT>(p.Tred, N, sT64);
+      constexpr int LD64 = NT + 2;
+      EpiRefresh<VT> epi{p.Z, p.D, p.r, nullptr, inv_nm1, N};
+      passB<double, NT>(p.HA64, row0, row1, N, sT64, uni + NT * LD64 * sizeof(double), epi, s_tmp);
+    } else {
+      df32* sTd = reinterpret_cast<df32*>(uni);
+      stage_T<df32, NT>(p.Tred, N, sTd);
+      constexpr int LDD = NT + 2;
+      EpiRefreshDF<VT> epi{p.Zdf, p.Ddf, p.r, static_cast<VT*>(p.B), N, df32(inv_nm1)};
+      passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+    }
+    if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+    if (!(ok = bar.sync())) break;
+    reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
+    par ^= 1;
+    ++refinements;
+    if (warm_pending) {
+      // the start's true residual judges it: a column whose start is non-finite or more than
+      // 1e3 times worse than the zero start (residual d_j) falls back to z_j = 0
+      if (t < NT) {
+        const bool bad = t < N && !(s_tmp[t] <= 1e6 * s_dn2[t]);
+        if (b == 0 && t < N) p.col_warm[t] = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+        s_active[t] = bad ? 1 : 0;   // s_active is free until the next inner solve
+        if (bad) s_tmp[t] = s_dn2[t];
+      }
+      __syncthreads();
+      int nbad = 0;
+      for (int j = 0; j < N; ++j) nbad += s_active[j];
+      if (nbad) {
+        VT* Bv = static_cast<VT*>(p.B);
+        for (int64_t e = (int64_t)t; e < (row1 - row0) * N; e += kThreads) {
+          const int64_t i = row0 + e / N;
+          const int j = (int)(e % N);
+          if (s_active[j]) {
+            p.Zdf[i * N + j] = df32(0.f, 0.f);
+            Bv[i * N + j] = (VT)p.D[i * N + j];
+          }
+        }
+        if (b == 0 && t == 0) p.status[2] = nbad;
+      }
+      __syncthreads();
+      warm_pending = false;
+    }
+    if (t < N) {
+      const double tr = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+      s_true[t] = tr;
+      if (refine) {
+        if (tr <= p.tol) s_done[t] = 1;
+        // next inner solve only has to gain the remaining factor tol/tr (with margin 0.1)
+        s_itol[t] = fmax(p.inner_tol, tr > 0.0 ? 0.1 * p.tol / tr : p.inner_tol);
+        if (s_itol[t] > 0.5) s_itol[t] = 0.5;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      int all = 1;
+      for (int j = 0; j < N; ++j) all &= s_done[j];
+      s_flag[1] = all;
+    }
+    __syncthreads();
+    tick(PH_REFRESH);
+    if (warm_step) {
+      if (s_flag[1]) break;
+      continue;
+    }
+    if (!refine || fixed || s_flag[1] || outer >= p.max_refine || total_iter >= p.max_iter) break;
+    ++outer;
+  }
+
+  if (b == 0) {
+    if (t < N) {
+      p.col_iters[t] = s_iters[t];
+      const double rec = s_dn2[t] > 0.0 ? sqrt(s_gam[t] / s_dn2[t]) : 0.0;
+      p.col_relres[t] = refine ? s_true[t] : rec;
+      p.col_true[t] = s_true[t];
+      bool conv;
+      if (fixed) conv = true;
+      else if (refine) conv = s_true[t] >= 0.0 && s_true[t] <= p.tol;
+      else conv = s_dn2[t] == 0.0 || sqrt(s_gam[t]) <= p.tol * sqrt(s_dn2[t]);
+      if (!conv && ok) atomicOr(p.status, DS_NOT_CONVERGED);
+    }
+    if (t == 0) p.status[1] = refinements;
+    if (prof) {
+      ph[PH_REFRESH] += 0;
+      for (int q = 0; q < PH_COUNT; ++q) p.prof[q] = ph[q];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K1: innovations
+// Rows [i_begin, i_end) of the observation operator, one warp per row: `warp` is this warp's
+// index among `nwarps` warps sharing the range.
+template <typename VT>
+__device__ __forceinline__ void innov_rows(
+    const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
+    const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
+    double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
+    float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
+    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
+    int64_t warp, int64_t nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = i_begin + warp; i < i_end; i += nwarps) {
+    double z[4] = {0.0, 0.0, 0.0, 0.0};
+    const int k0 = rowptr[i], k1 = rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const double wk = w[k];
+      const VT* xr = Xf + (int64_t)col[k] * N;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        if (j < N) z[q] = fma(wk, (double)xr[j], z[q]);
+      }
+    }
+    double s = z[0] + z[1] + z[2] + z[3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double zbar = s / (double)N;
+    const double yi = y[i], sr = sqrt(r[i]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = lane + 32 * q;
+      if (j < N) {
+        const int64_t e = i * N + j;
+        double pert = 0.0;
+        if (emode == 1) pert = E[e];
+        else if (emode == 2) pert = sr * perturbation_normal(i, j, seed, counter);
+        const double ha = z[q] - zbar;
+        const double d = (yi - z[q]) + pert;
+        if (HA64) HA64[e] = ha;
+        D[e] = d;
+        if (HA32) HA32[e] = (float)ha;
+        if (B32) B32[e] = (float)d;
+        if (HAdf) HAdf[e] = df32(ha);
+        if (Ddf) Ddf[e] = df32(d);
+        // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
+        if (HAb) {
+          const __nv_bfloat16 hi = __double2bfloat16(ha);
+          HAb[e] = hi;
+          if (split_lo) HAb[m * N + e] = __double2bfloat16(ha - (double)__bfloat162float(hi));
+        }
+        if (HAh) {
+          const __half hi = __double2half(ha);
+          HAh[e] = hi;
+          if (split_lo) HAh[m * N + e] = __double2half(ha - (double)__half2float(hi));
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K4: final update
+// MODE 0: X_a = X_f + (X_f - xbar 1^T) W (CGD-EnKF, Fig. 2 / Algorithm 1);
+// MODE 1: X_a = X_f W (CGD-EnKF-Reduced, Algorithm 2 with W = V).
+// Row tiles of TRB rows staged in shared memory.
+// Row tiles tile0, tile0 + tstride, ... (TRB rows each) of the update.
+template <typename VT, int NT, int MODE = 0>
+__device__ __forceinline__ void update_rows(const VT* Xf, VT* Xa, const double* __restrict__ W,
+                                            int64_t n, int N, int64_t tile0, int64_t tstride,
+                                            unsigned char* smem) {
+  constexpr int LD = NT + 16 / (int)sizeof(VT), TRB = Tile<NT>::TRB, C4 = NT / 4;
+  constexpr int NJ = NT / 4;
+  VT* sW = reinterpret_cast<VT*>(smem);
+  VT* sX = sW + NT * LD;
+  VT* smean = sX + TRB * LD;
+  const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * 4;
+  const bool vec = (N & 3) == 0;
+  for (int e = t; e < NT * LD; e += kThreads) {
+    const int k = e / LD, j = e % LD;
+    sW[e] = (k < N && j < N) ? (VT)__ldcg(W + k * N + j) : VT(0);   // W may be written by this launch
+  }
+  for (int64_t i0 = tile0 * TRB; i0 < n; i0 += tstride * TRB) {
+    __syncthreads();
+#pragma unroll
+    for (int c = t; c < TRB * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      VT a[4] = {VT(0), VT(0), VT(0), VT(0)};
+      if (i < n && c0 < N) ld4<VT>(a, Xf + i * N, c0, N, vec);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) sX[ii * LD + c0 + y] = a[y];
+    }
+    __syncthreads();
+    if (t < TRB) {
+      VT s = VT(0);
+      for (int k = 0; k < N; ++k) s += sX[t * LD + k];
+      smean[t] = s / (VT)N;
+    }
+    __syncthreads();
+    // original X_f fragments for the output (same threads write X_a, so X_a may alias X_f)
+    VT xf[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) xf[x][y] = sX[(r0 + x) * LD + j0 + y];
+    __syncthreads();
+    if (MODE == 0) {
+      for (int e = t; e < TRB * NT; e += kThreads) {
+        const int ii = e / NT, k = e % NT;
+        if (k < N) sX[ii * LD + k] -= smean[ii];
+      }
+    }
+    __syncthreads();
+    VT acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = VT(0);
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      VT a[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = sX[(r0 + x) * LD + k];
+      load_vec<VT>(bv, sW + k * LD + j0, 4);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t i = i0 + r0 + x;
+      if (i < n && j0 < N) {
+        VT o[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[y] = MODE == 0 ? xf[x][y] + acc[x][y] : acc[x][y];
+        st4<VT>(Xa + i * N, j0, N, vec, o);
+      }
+    }
+  }
+}
+
+template <typename VT, int NT> __host__ __device__ constexpr int update_smem_bytes() {
+  constexpr int LD = NT + 16 / (int)sizeof(VT);
+  return (NT * LD + Tile<NT>::TRB * LD + Tile<NT>::TRB) * (int)sizeof(VT);
+}
+
+}  // namespace enkf
