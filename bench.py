@@ -32,6 +32,7 @@ METRIC = "analysis steps/s and HBM-roofline fraction vs plain FP64 GPU CG at sta
 UNIT = "analyses/s"
 L2_FLUSH_BYTES = 256 << 20
 BATCH_WORKLOAD = "batched256_grf"
+MIXED_WORKLOAD = "grf1024_N128_m262144"
 
 
 def B_ITER(m, N):
@@ -48,9 +49,9 @@ def B_REF(m, N):
     return 56 * m * N
 
 # DRAM bytes (read + write) of one solve_kernel launch on this workload, from the ncu capture
-# summarised in profiles/solve_kernel_grf512_N64_m65536.md, and the hash of the kernel source
+# summarised in profiles/solve_kernel_fp32_grf512_N64_m65536.md, and the hash of the kernel source
 # that capture measured; reported as null once the source has changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 4.126482e9, "src_sha": None}}
+NCU_TRAFFIC = {"fp32": {"bytes": 4.980707e9, "src_sha": "eeca2dd335f5f4ec"}}
 
 
 def _src_hash():
@@ -327,7 +328,7 @@ def run_ours(args):
     tr = NCU_TRAFFIC.get("fp32", {})
     traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash() else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64>",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64,1>",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_ms": solve_avg_ms, "cg_iterations": it_avg, "fp64_refreshes": ref_avg}
 
@@ -336,7 +337,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
-                       "precision": "fp32 CG + fp64 residual refresh",
+                       "precision": "fp32 CG + double-float residual refresh",
                        "solver": "CG preconditioned by R" if args.precondition else "plain CG",
                        "l2": "flushed between steps", "status": last_status["status"]},
             "error": {"rel_frobenius_vs_fp64_oracle": err, "fp64_cg_rel_frobenius": err64,
@@ -463,7 +464,7 @@ def run_batched(args):
     # roofline: algorithmic bytes of all problems of one launch over the launch time
     alg = 0.0
     for i, p in enumerate(probs):
-        alg += st["iters_max"][i] * B_ITER(p.m, p.N) + st["refinements"][i] * B_REF(p.m, p.N)
+        alg += float(st["iters_max"][i]) * B_ITER(p.m, p.N) + float(st["refinements"][i]) * B_REF(p.m, p.N)
         alg += 4 * p.n * p.N * 2 + 32 * p.m * p.N   # update (X_f in, X_a out); innovations out (HA, B, D, HA and D double-float)
     launch_ms = ms / args.steps
     peak, peak_src = _peaks()
@@ -487,6 +488,85 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args):
+    """The mixed-precision workload: 1024 x 1024 GRF (length 24), N = 128, m = 262,144,
+    r ~ U[0.25, 1.0], tol 1e-8. One line per run; `value` is the BF16 tensor-core path
+    (split hi/lo operands, FP32 accumulation in TMEM, double-float refresh); FP16, FP32 and
+    FP64 (preconditioned and plain) are timed beside it with their errors against the exact
+    FP64 oracle analysis."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_2606_19224_gb300 as enkf
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = args.seed + 1000 * rank
+    p = synth.workload(MIXED_WORKLOAD, seed, dtype=np.float32)
+    n, m, N = p.n, p.m, p.N
+    Xf = torch.from_numpy(p.Xf).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    out = torch.empty_like(Xf)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    E = oracle.obs_perturbations(seed, 0, p.r, N) if rank == 0 else None
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E) if rank == 0 else None
+
+    def timed(an, Xd, od, steps, tag):
+        for k in range(args.warmup):
+            an.analyze(Xd, y, seed, k, out=od)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            an.analyze(Xd, y, seed, k, out=od)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        st = an.stats()
+        an.analyze(Xd, y, seed, 0, out=od)
+        err = oracle.rel_frobenius(od.double().cpu().numpy(), ref) if rank == 0 else None
+        return {"ms_per_step": ms, "value": 1e3 / ms, "iters": st["iters_max"], "refinements": st["refinements"],
+                "true_relres_max": st["true_relres_max"], "rel_frobenius_vs_fp64_oracle": err,
+                "status": st["status"], "precision": tag}
+
+    clocks = Clocks(local)
+    clocks.start()
+    res = {}
+    for tag, prec in (("bf16", "bf16"), ("fp16", "fp16"), ("fp32", "fp32")):
+        an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8, precondition=1)
+        res[tag] = timed(an, Xf, out, args.steps, tag)
+        an.close()
+    clk = clocks.stop()
+    X64 = Xf.double()
+    o64 = torch.empty_like(X64)
+    for tag, pc in (("fp64_pc", 1), ("fp64", 0)):
+        an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp64", tol=1e-8, precondition=pc)
+        res[tag] = timed(an, X64, o64, args.fp64_steps, tag)
+        an.close()
+    ms = res["bf16"]["ms_per_step"]
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": ws * 1e3 / ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded 1024x1024 GRF ensemble, random point observations)",
+            "config": {"workload": MIXED_WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
+                       "precision": "BF16 hi/lo split operands on tcgen05, FP32 accumulation, double-float refresh",
+                       "l2": "flushed between steps"},
+            "variants": res, "gpu_launches": 3 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,7 +576,7 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD, MIXED_WORKLOAD])
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")
     args = ap.parse_args()
@@ -504,6 +584,8 @@ def main():
         run_reference(args)
     elif args.workload == BATCH_WORKLOAD:
         run_batched(args)
+    elif args.workload == MIXED_WORKLOAD:
+        run_mixed(args)
     else:
         run_ours(args)
 

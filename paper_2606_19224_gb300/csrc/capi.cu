@@ -351,7 +351,8 @@ enkf_status enkf_get_stats(enkf_handle h, enkf_stats* out) {
   }
   out->grid_blocks = h->launch.G;
   enkf_status status = ENKF_OK;
-  if (bits & enkf::DS_TIMEOUT) status = ENKF_ERR_TIMEOUT;
+  if (bits & enkf::DS_SMEM) status = ENKF_ERR_CUDA;
+  else if (bits & enkf::DS_TIMEOUT) status = ENKF_ERR_TIMEOUT;
   else if (bits & enkf::DS_NONFINITE) status = ENKF_ERR_NONFINITE;
   else if (bits & enkf::DS_BREAKDOWN) status = ENKF_ERR_BREAKDOWN;
   else if (bits & enkf::DS_NOT_CONVERGED) status = ENKF_ERR_NOT_CONVERGED;

@@ -41,8 +41,14 @@ template <typename CT, int NT> __host__ __device__ constexpr int passF_bytes() {
   constexpr int LD = NT + 16 / (int)sizeof(CT), TR = FTile<CT, NT>::TR;
   return NT * LD * (int)sizeof(CT) + 5 * TR * LD * (int)sizeof(CT) + TR * (int)sizeof(CT);
 }
+// FP32 solves with NT <= 64 use the double-buffered fused pass (passF_async)
+template <typename VT, int NT> __host__ __device__ constexpr bool async_passF() {
+  return sizeof(VT) == 4 && NT <= 64;
+}
+template <int NT> __host__ __device__ constexpr int passF_async_bytes();
 template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
-  return refresh_union_bytes<NT>() > passF_bytes<VT, NT>() ? refresh_union_bytes<NT>() : passF_bytes<VT, NT>();
+  constexpr int f = async_passF<VT, NT>() ? passF_async_bytes<NT>() : passF_bytes<VT, NT>();
+  return refresh_union_bytes<NT>() > f ? refresh_union_bytes<NT>() : f;
 }
 template <typename VT, int NT> __host__ __device__ constexpr int solve_smem_bytes() {
   return scalar_bytes<NT>() + kThreads * 8 + union_bytes<VT, NT>();
@@ -647,6 +653,215 @@ __device__ __forceinline__ void passF(const CT* __restrict__ HA, int64_t row0, i
     }
     out[N * N + t] = a;
     out[N * N + N + t] = b;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ fused CG pass, pipelined
+// The FP32 fused step of passF for NT <= 64 with the row tiles double-buffered: the next
+// tile's HA, r, p, s, x and r_i are copied global -> shared with cp.async (16-byte pieces,
+// zero-filled past the CTA's rows and past N) while the current tile is computed. Needs
+// N % 4 == 0 (16-byte aligned rows). The u = HA T contraction reads HA four k at a time.
+// Same arithmetic, partial sums and output as passF (fixed order).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+template <int NT> __host__ __device__ constexpr int passF_async_bytes() {
+  constexpr int LD = NT + 4, TR = FTile<float, NT>::TR;
+  return NT * LD * 4 + 2 * (5 * TR * LD + TR) * 4;
+}
+
+template <int NT, bool PC>
+__device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_t row0, int64_t row1, int N,
+                                            float* X, float* Res, float* P, float* Sv,
+                                            const float* __restrict__ rv, const float* sT,
+                                            const float* alpha, const float* beta, float vinv,
+                                            unsigned char* tiles, double* __restrict__ out) {
+  constexpr int LD = NT + 4;
+  constexpr int MR = FTile<float, NT>::MR, TR = FTile<float, NT>::TR, C4 = NT / 4;
+  constexpr int NJ = NT / 4, NI = kThreads / NJ;
+  static_assert(NI * MR == TR, "fused tile");
+  constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
+  constexpr int BUF = 5 * TR * LD + TR;   // floats per buffer
+  float* const buf0 = reinterpret_cast<float*>(tiles);
+  const int t = threadIdx.x;
+  const int tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * MR;
+  const int g = t / TPG, u = t % TPG, gj = u % NG, gk = u / NG, k0 = gk * MA, ja = gj * MA;
+  float accT[MA][MA];
+#pragma unroll
+  for (int x = 0; x < MA; ++x)
+#pragma unroll
+    for (int y = 0; y < MA; ++y) accT[x][y] = 0.f;
+  float sig[4] = {0.f, 0.f, 0.f, 0.f}, gam[4] = {0.f, 0.f, 0.f, 0.f};
+  float al[4], be[4];
+#pragma unroll
+  for (int y = 0; y < 4; ++y) { al[y] = alpha[j0 + y]; be[y] = beta[j0 + y]; }
+
+  // copy tile starting at row i0 into buffer b
+  auto issue = [&](int64_t i0, int b) {
+    float* sb = buf0 + b * BUF;
+#pragma unroll
+    for (int c = t; c < TR * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      const bool ok = i < row1 && c0 < N;
+      const int64_t off = ok ? i * N + c0 : row0 * N;
+      cp_async16(sb + 0 * TR * LD + ii * LD + c0, HA + off, ok);
+      cp_async16(sb + 1 * TR * LD + ii * LD + c0, Res + off, ok);
+      cp_async16(sb + 2 * TR * LD + ii * LD + c0, P + off, ok);
+      cp_async16(sb + 3 * TR * LD + ii * LD + c0, Sv + off, ok);
+      cp_async16(sb + 4 * TR * LD + ii * LD + c0, X + off, ok);
+    }
+    if (t < TR) {
+      const int64_t i = i0 + t;
+      cp_async4(sb + 5 * TR * LD + t, rv + (i < row1 ? i : row0), i < row1);
+    }
+    cp_async_commit();
+  };
+
+  int b = 0;
+  if (row0 < row1) issue(row0, 0);
+  for (int64_t i0 = row0; i0 < row1; i0 += TR, b ^= 1) {
+    const bool more = i0 + TR < row1;
+    if (more) {
+      issue(i0 + TR, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* sH = buf0 + b * BUF;
+    float* sR = buf0 + b * BUF + TR * LD;
+    const float* sP = sR + TR * LD;
+    const float* sS = sP + TR * LD;
+    const float* sX = sS + TR * LD;
+    const float* sRv = sX + TR * LD;
+    // u = HA T (the 1/(N-1) is applied below); four k per step from float4 rows of HA
+    float acc[MR][4];
+#pragma unroll
+    for (int x = 0; x < MR; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < NT; k += 4) {
+      float4 a4[MR];
+#pragma unroll
+      for (int x = 0; x < MR; ++x) a4[x] = *reinterpret_cast<const float4*>(sH + (r0 + x) * LD + k);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 b4 = *reinterpret_cast<const float4*>(sT + (k + kk) * LD + j0);
+#pragma unroll
+        for (int x = 0; x < MR; ++x) {
+          const float av = kk == 0 ? a4[x].x : kk == 1 ? a4[x].y : kk == 2 ? a4[x].z : a4[x].w;
+          acc[x][0] = fmaf(av, b4.x, acc[x][0]);
+          acc[x][1] = fmaf(av, b4.y, acc[x][1]);
+          acc[x][2] = fmaf(av, b4.z, acc[x][2]);
+          acc[x][3] = fmaf(av, b4.w, acc[x][3]);
+        }
+      }
+    }
+    // the CG step on the thread's MR x 4 fragment (as passF)
+#pragma unroll
+    for (int x = 0; x < MR; ++x) {
+      const int row = r0 + x;
+      const int64_t i = i0 + row;
+      if (i < row1 && j0 < N) {
+        const float ri = sRv[row];
+        const float4 rv4 = *reinterpret_cast<const float4*>(sR + row * LD + j0);
+        const float4 pv4 = *reinterpret_cast<const float4*>(sP + row * LD + j0);
+        const float4 sv4 = *reinterpret_cast<const float4*>(sS + row * LD + j0);
+        const float4 xv4 = *reinterpret_cast<const float4*>(sX + row * LD + j0);
+        const float rvv[4] = {rv4.x, rv4.y, rv4.z, rv4.w}, pvv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+        const float svv[4] = {sv4.x, sv4.y, sv4.z, sv4.w}, xvv[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
+        const float rinv = PC ? 1.f / ri : 0.f;
+        float pn[4], sn[4], xn[4], rn[4], zn[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const float zz = PC ? rvv[y] * rinv : rvv[y];
+          const float ww = PC ? fmaf(acc[x][y], vinv, rvv[y]) : fmaf(acc[x][y], vinv, ri * rvv[y]);
+          pn[y] = be[y] == 0.f ? zz : fmaf(be[y], pvv[y], zz);
+          sn[y] = be[y] == 0.f ? ww : fmaf(be[y], svv[y], ww);
+          xn[y] = fmaf(al[y], pn[y], xvv[y]);
+          rn[y] = fmaf(-al[y], sn[y], rvv[y]);
+          zn[y] = PC ? rn[y] * rinv : rn[y];
+          sig[y] = PC ? fmaf(rn[y], zn[y], sig[y]) : fmaf(ri * rn[y], rn[y], sig[y]);
+          gam[y] = fmaf(rn[y], rn[y], gam[y]);
+        }
+        *reinterpret_cast<float4*>(P + i * N + j0) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        *reinterpret_cast<float4*>(Sv + i * N + j0) = make_float4(sn[0], sn[1], sn[2], sn[3]);
+        *reinterpret_cast<float4*>(X + i * N + j0) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+        *reinterpret_cast<float4*>(Res + i * N + j0) = make_float4(rn[0], rn[1], rn[2], rn[3]);
+        *reinterpret_cast<float4*>(sR + row * LD + j0) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+      }
+    }
+    __syncthreads();
+    // next step's partial Gram HA^T z_new on the same tile (rows past row1 are zero)
+    const int nrows = (int)imin64(TR, row1 - i0);
+    for (int ii = g; ii < nrows; ii += RG) {
+      float a[MA], v[MA];
+      load_vec<float>(a, sH + ii * LD + k0, MA);
+      load_vec<float>(v, sR + ii * LD + ja, MA);
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) accT[x][y] = fmaf(a[x], v[y], accT[x][y]);
+    }
+    __syncthreads();   // this buffer is refilled by the copy issued in the next iteration
+  }
+  double* red = reinterpret_cast<double*>(tiles);
+  if (RG > 1) {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + ja + y] = (double)accT[x][y];
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) {
+          const int k = k0 + x, j = ja + y;
+          double s = 0.0;
+          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
+          if (k < N && j < N) out[k * N + j] = s;
+        }
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) {
+        const int k = k0 + x, j = ja + y;
+        if (k < N && j < N) out[k * N + j] = (double)accT[x][y];
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    red[ti * NT + j0 + y] = (double)sig[y];
+    red[NI * NT + ti * NT + j0 + y] = (double)gam[y];
+  }
+  __syncthreads();
+  if (t < N) {
+    double a = 0.0, bb = 0.0;
+    for (int q = 0; q < NI; ++q) {
+      a += red[q * NT + t];
+      bb += red[NI * NT + q * NT + t];
+    }
+    out[N * N + t] = a;
+    out[N * N + N + t] = bb;
   }
   __syncthreads();
 }

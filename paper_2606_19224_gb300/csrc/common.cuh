@@ -14,7 +14,13 @@ constexpr int kThreads = 256;                          // every kernel here uses
 constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s per grid-barrier wait
 
 // Device status bits (folded into enkf_status by enkf_get_stats).
-enum : int { DS_NOT_CONVERGED = 1, DS_NONFINITE = 2, DS_BREAKDOWN = 4, DS_TIMEOUT = 8 };
+enum : int { DS_NOT_CONVERGED = 1, DS_NONFINITE = 2, DS_BREAKDOWN = 4, DS_TIMEOUT = 8, DS_SMEM = 16 };
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {

@@ -53,11 +53,11 @@ __device__ __noinline__ void batch_update(const BatchIO& io, const double* W, in
   update_rows<float, NT, 0>(io.Xf, io.Xa, W, n, N, rank, G, smem);
 }
 
-// NTMAX bounds the column tile of every problem in the batch; batches with N <= 64 fit two
-// CTAs per SM like the single-analysis FP32 solve. The solve is the Jacobi-preconditioned
-// (M = R) form.
+// NTMAX bounds the column tile of every problem in the batch. One CTA per SM (the
+// double-buffered fused pass takes most of the shared memory). The solve is the
+// Jacobi-preconditioned (M = R) form.
 template <int NTMAX>
-__global__ void __launch_bounds__(kThreads, NTMAX == 128 ? 1 : 2) batch_kernel(
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(
     const BatchProblem* __restrict__ probs, const BatchIO* __restrict__ io,
     const int* __restrict__ cta_team, const int* __restrict__ cta_rank,
     const int* __restrict__ team_size, const int* __restrict__ team_first,
@@ -221,9 +221,19 @@ bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double al
   return true;
 }
 
+// Dynamic shared memory of a batch whose tiles go up to NTMAX: the largest need of any
+// column tile it may run (the NT = 32 and 64 solves use the double-buffered fused pass and
+// need more than the NT = 128 one).
+template <int NT>
+static size_t tile_smem() {
+  return std::max<size_t>(solve_smem_bytes<float, NT>(), update_smem_bytes<float, NT>());
+}
 template <int NTMAX>
 static size_t batch_smem_nt() {
-  return std::max<size_t>(solve_smem_bytes<float, NTMAX>(), update_smem_bytes<float, NTMAX>());
+  size_t s = tile_smem<32>();
+  if (NTMAX >= 64) s = std::max(s, tile_smem<64>());
+  if (NTMAX >= 128) s = std::max(s, tile_smem<128>());
+  return s;
 }
 
 static void* batch_fn(int ntmax) {
@@ -521,7 +531,8 @@ cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, d
     if (e == cudaSuccess) e = cudaMemcpy(rel.data(), sp.col_relres, sizeof(double) * N, cudaMemcpyDeviceToHost);
     const int bits = st[4 * (size_t)i];
     int s = ENKF_OK;
-    if (bits & DS_TIMEOUT) s = ENKF_ERR_TIMEOUT;
+    if (bits & DS_SMEM) s = ENKF_ERR_CUDA;
+    else if (bits & DS_TIMEOUT) s = ENKF_ERR_TIMEOUT;
     else if (bits & DS_NONFINITE) s = ENKF_ERR_NONFINITE;
     else if (bits & DS_BREAKDOWN) s = ENKF_ERR_BREAKDOWN;
     else if (bits & DS_NOT_CONVERGED) s = ENKF_ERR_NOT_CONVERGED;

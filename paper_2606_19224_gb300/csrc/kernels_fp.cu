@@ -27,7 +27,8 @@
 namespace enkf {
 
 template <typename VT, int NT, bool PC>
-__global__ void __launch_bounds__(kThreads, ((NT == 128 || (NT == 64 && sizeof(VT) == 8)) ? 1 : 2)) solve_kernel(SolveParams p) {
+__global__ void __launch_bounds__(kThreads, (NT == 128 || sizeof(VT) == 8 || async_passF<VT, NT>()) ? 1 : 2)
+    solve_kernel(SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   GridBarrier bar{p.bar, reinterpret_cast<int*>(p.bar + 1), p.status, gridDim.x, 0u};
   solve_body<VT, NT, PC>(p, (int)gridDim.x, (int)blockIdx.x, bar, smem);

@@ -87,46 +87,49 @@ struct GemmArgs {
   const float* sd_out;
 };
 
-template <int EPI>
+// TM x TM outputs per thread, (16 TM) x (16 TM) per CTA: TM = 4 for large products, TM = 2
+// when the 64 x 64 grid would leave most SMs idle (the per-analysis inference, batch N).
+template <int EPI, int TM>
 __global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs g) {
-  __shared__ float As[GBK][GBM + 4];
-  __shared__ float Bs[GBK][GBN + 4];
+  constexpr int BM = 16 * TM, BN = 16 * TM;
+  __shared__ float As[GBK][BM + 4];
+  __shared__ float Bs[GBK][BN + 4];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  float acc[4][4] = {};
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[TM][TM] = {};
   for (int k0 = 0; k0 < g.K; k0 += GBK) {
-    for (int e = t; e < GBM * GBK; e += 256) {
+    for (int e = t; e < BM * GBK; e += 256) {
       const int mm = e / GBK, kk = e % GBK;
       const int m = m0 + mm, k = k0 + kk;
       As[kk][mm] = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : 0.f;
     }
-    for (int e = t; e < GBK * GBN; e += 256) {
-      const int kk = e / GBN, nn = e % GBN;
+    for (int e = t; e < GBK * BN; e += 256) {
+      const int kk = e / BN, nn = e % BN;
       const int k = k0 + kk, n = n0 + nn;
       Bs[kk][nn] = (k < g.K && n < g.N) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
-      float a[4], b[4];
+      float a[TM], b[TM];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) a[x] = As[kk][ty * 4 + x];
+      for (int x = 0; x < TM; ++x) a[x] = As[kk][ty * TM + x];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tx * 4 + y];
+      for (int y = 0; y < TM; ++y) b[y] = Bs[kk][tx * TM + y];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < TM; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        for (int y = 0; y < TM; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int m = m0 + ty * 4 + x;
+  for (int x = 0; x < TM; ++x) {
+    const int m = m0 + ty * TM + x;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int n = n0 + tx * 4 + y;
+    for (int y = 0; y < TM; ++y) {
+      const int n = n0 + tx * TM + y;
       if (n >= g.N) continue;
       const int64_t e = (int64_t)m * g.N + n;
       float v = acc[x][y];
@@ -149,8 +152,14 @@ __global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs g) {
 
 template <int EPI>
 static cudaError_t gemm(const GemmArgs& a, cudaStream_t s) {
-  dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
-  mlp_gemm_kernel<EPI><<<grid, 256, 0, s>>>(a);
+  const int64_t big = (int64_t)((a.N + GBN - 1) / GBN) * ((a.M + GBM - 1) / GBM);
+  if (big >= 128) {
+    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
+    mlp_gemm_kernel<EPI, 4><<<grid, 256, 0, s>>>(a);
+  } else {
+    dim3 grid((a.N + 31) / 32, (a.M + 31) / 32);
+    mlp_gemm_kernel<EPI, 2><<<grid, 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -394,10 +403,20 @@ __global__ void __launch_bounds__(kThreads) warm_gram_kernel(const float* __rest
     }
 }
 
+// g[k][j] = sum over the row-block partials in block order (one thread per entry).
+__global__ void warm_reduce_kernel(const double* __restrict__ part, int nparts, int NN, double* __restrict__ g) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NN) return;
+  double s = 0.0;
+#pragma unroll 8
+  for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * NN + e];
+  g[e] = s;
+}
+
 // Features of column j (one CTA per column): sketch values, their RMS s_j, and g_j/s_j.
 __global__ void __launch_bounds__(kThreads) warm_features_kernel(const double* __restrict__ D, int64_t m, int N,
-                                                                 int K, const double* __restrict__ part,
-                                                                 int nparts, float* __restrict__ F,
+                                                                 int K, const double* __restrict__ gsum,
+                                                                 float* __restrict__ F,
                                                                  float* __restrict__ s_out) {
   __shared__ double red[kThreads];
   const int j = blockIdx.x, t = threadIdx.x;
@@ -421,11 +440,7 @@ __global__ void __launch_bounds__(kThreads) warm_features_kernel(const double* _
     const int64_t i = ((int64_t)k * m) / K;
     F[(int64_t)j * in + k] = (float)(D[i * N + j] / sj);
   }
-  for (int k = t; k < N; k += kThreads) {
-    double g = 0.0;
-    for (int b = 0; b < nparts; ++b) g += part[((int64_t)b * N + k) * N + j];
-    F[(int64_t)j * in + K + k] = (float)(g * inv_nm1 / sj);
-  }
+  for (int k = t; k < N; k += kThreads) F[(int64_t)j * in + K + k] = (float)(gsum[k * N + j] * inv_nm1 / sj);
   if (t == 0) s_out[j] = (float)sj;
 }
 
@@ -486,6 +501,7 @@ struct WarmState {
   int K = 0;                       // sketch size of the model (in_dim - N)
   int nparts = 0;
   double* part = nullptr;          // [nparts][N][N]
+  double* gsum = nullptr;          // [N][N] = HA^T R^-1 D
   float* F = nullptr;              // [N][K + N] features of the current analysis
   float* s = nullptr;              // [N] column scales
   float* Y = nullptr;              // [N][N] raw predictions
@@ -501,6 +517,7 @@ static cudaError_t warm_alloc(enkf_handle_s* h, int K) {
   if (!w.part) {
     w.nparts = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)h->sms, (h->cfg.m + 255) / 256));
     e = cudaMalloc((void**)&w.part, sizeof(double) * (size_t)w.nparts * N * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.gsum, sizeof(double) * N * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.s, sizeof(float) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.Y, sizeof(float) * N * N);
   }
@@ -520,7 +537,10 @@ static cudaError_t warm_features_into(enkf_handle_s* h, int K, float* F) {
   warm_gram_kernel<<<w.nparts, kThreads, 0, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r, c.m, c.N, rows_per, w.part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  warm_features_kernel<<<c.N, kThreads, 0, h->stream>>>(h->ws.D, c.m, c.N, K, w.part, w.nparts, F, w.s);
+  warm_reduce_kernel<<<(c.N * c.N + 255) / 256, 256, 0, h->stream>>>(w.part, w.nparts, c.N * c.N, w.gsum);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  warm_features_kernel<<<c.N, kThreads, 0, h->stream>>>(h->ws.D, c.m, c.N, K, w.gsum, F, w.s);
   return cudaGetLastError();
 }
 
@@ -576,7 +596,7 @@ cudaError_t warm_prepare(enkf_handle_s* h) {
 void warm_free(enkf_handle_s* h) {
   WarmState* w = h->warm;
   if (!w) return;
-  void* ptrs[] = {w->part, w->F, w->s, w->Y, w->work};
+  void* ptrs[] = {w->part, w->gsum, w->F, w->s, w->Y, w->work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete w;

@@ -162,8 +162,11 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
   out_stats->refinements = st[1];
   out_stats->columns_converged = conv;
   out_stats->grid_blocks = h.launch.G;
+  out_stats->warm_relres_max = -1.0;
+  out_stats->warm_fallbacks = 0.0;
   enkf_status s = ENKF_OK;
-  if (st[0] & enkf::DS_TIMEOUT) s = ENKF_ERR_TIMEOUT;
+  if (st[0] & enkf::DS_SMEM) s = ENKF_ERR_CUDA;
+  else if (st[0] & enkf::DS_TIMEOUT) s = ENKF_ERR_TIMEOUT;
   else if (st[0] & enkf::DS_NONFINITE) s = ENKF_ERR_NONFINITE;
   else if (st[0] & enkf::DS_BREAKDOWN) s = ENKF_ERR_BREAKDOWN;
   else if (st[0] & enkf::DS_NOT_CONVERGED) s = ENKF_ERR_NOT_CONVERGED;

@@ -78,6 +78,11 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   unsigned char* tiles = uni + NT * LDV * sizeof(VT);
 
   const int N = p.N, t = threadIdx.x;
+  // every CTA of the launch sees the same size, so all of them leave here together
+  if (dynamic_smem_bytes() < (unsigned)solve_smem_bytes<VT, NT>()) {
+    if (t == 0) atomicOr(p.status, DS_SMEM);
+    return;
+  }
   const int64_t rows_per = (p.m + G - 1) / G;
   const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
   const int64_t row1 = imin64(p.m, row0 + rows_per);
@@ -202,8 +207,17 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       __syncthreads();
       if (!s_flag[0]) break;
       tick(PH_SCAL);
-      passF<VT, NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
-                        tiles, Tp);
+      if constexpr (async_passF<VT, NT>()) {
+        if ((N & 3) == 0)
+          passF_async<NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
+                              tiles, Tp);
+        else
+          passF<VT, NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
+                            tiles, Tp);
+      } else {
+        passF<VT, NT, PC>(HA, row0, row1, N, X, Res, P, Sv, rv, sT, s_alpha_v, s_beta_v, (VT)inv_nm1,
+                          tiles, Tp);
+      }
       tick(PH_PASS);
       if (!(ok = bar.sync())) break;
       tick(PH_BAR1);
@@ -338,8 +352,26 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
 }
 
 // ------------------------------------------------------------------ K1: innovations
+// Standard normals of members (j, j + 1), j even, from one Philox block and one Box-Muller
+// pair (the definition of perturbation_normal for both members, computed once).
+__device__ __forceinline__ void perturbation_pair(int64_t i, int j, uint64_t seed, uint64_t counter,
+                                                  double& n_even, double& n_odd) {
+  uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(j >> 1), c2 = (uint32_t)counter, c3 = (uint32_t)(counter >> 32);
+  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint64_t x1 = ((uint64_t)c0 << 21) | (c1 >> 11);
+  const uint64_t x2 = ((uint64_t)c2 << 21) | (c3 >> 11);
+  const double u1 = ((double)x1 + 0.5) * 0x1p-53;
+  const double u2 = (double)x2 * 0x1p-53;
+  const double rho = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincos(6.283185307179586 * u2, &sn, &cs);
+  n_even = rho * cs;
+  n_odd = rho * sn;
+}
+
 // Rows [i_begin, i_end) of the observation operator, one warp per row: `warp` is this warp's
-// index among `nwarps` warps sharing the range.
+// index among `nwarps` warps sharing the range. Lane l owns members 2l, 2l + 1, 2l + 64,
+// 2l + 65, so each perturbation pair is drawn once.
 template <typename VT>
 __device__ __forceinline__ void innov_rows(
     const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -358,7 +390,7 @@ __device__ __forceinline__ void innov_rows(
       const VT* xr = Xf + (int64_t)col[k] * N;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int j = lane + 32 * q;
+        const int j = 2 * lane + (q & 1) + 64 * (q >> 1);
         if (j < N) z[q] = fma(wk, (double)xr[j], z[q]);
       }
     }
@@ -368,13 +400,20 @@ __device__ __forceinline__ void innov_rows(
     const double zbar = s / (double)N;
     const double yi = y[i], sr = sqrt(r[i]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = lane + 32 * q;
-      if (j < N) {
+    for (int h = 0; h < 2; ++h) {
+      const int jp = 2 * lane + 64 * h;   // even member of the pair
+      if (jp >= N) continue;
+      double nrm[2] = {0.0, 0.0};
+      if (emode == 2) perturbation_pair(i, jp, seed, counter, nrm[0], nrm[1]);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int j = jp + b;
+        if (j >= N) continue;
+        const int q = 2 * h + b;
         const int64_t e = i * N + j;
         double pert = 0.0;
         if (emode == 1) pert = E[e];
-        else if (emode == 2) pert = sr * perturbation_normal(i, j, seed, counter);
+        else if (emode == 2) pert = sr * nrm[b];
         const double ha = z[q] - zbar;
         const double d = (yi - z[q]) + pert;
         if (HA64) HA64[e] = ha;

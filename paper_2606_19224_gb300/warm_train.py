@@ -21,30 +21,40 @@ from . import Analysis, MlpShape, mlp_param_count, mlp_standardize, mlp_train_ep
 
 def _problem(side, ell, N, m, seed, draw):
     import synth
-    # ensemble from `seed`, observations / perturbation stream from (seed, draw)
+    # ensemble, observations and perturbation stream from (seed, draw)
     return synth.grf_problem(side, ell, N, m, 0.5, 1.5, seed, dtype=np.float32, sub=draw)
 
 
-def collect_pairs(cfg, seeds, draws, K, log=None):
-    """Run one FP32 analysis per (ensemble seed, draw); return device F [P][K+N], T [P][N]."""
+def _problem_args(a):
+    return _problem(*a)
+
+
+def collect_pairs(cfg, seeds, draws, K, log=None, workers=8):
+    """Run one FP32 analysis per (seed, draw) (inputs generated by a spawn pool while the GPU
+    works); return device F [P][K+N], T [P][N]."""
+    import multiprocessing as mp
     import torch
     Fs, Ts = [], []
-    for s in seeds:
-        an = None
-        for d in range(draws):
-            p = _problem(cfg["side"], cfg["ell"], cfg["N"], cfg["m"], s, d)
+    jobs = [(cfg["side"], cfg["ell"], cfg["N"], cfg["m"], s, d) for s in seeds for d in range(draws)]
+    an = None
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for q, p in enumerate(pool.imap(_problem_args, jobs)):
+            s, d = jobs[q][4], jobs[q][5]
             if an is None:
                 an = Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", precondition=1,
                               tol=cfg["tol"])
-            Xf = torch.from_numpy(p.Xf).cuda()
-            y = torch.from_numpy(p.y).cuda()
-            an.analyze(Xf, y, seed=1000 * s + d, counter=d)
+            else:
+                an.close()
+                an = Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", precondition=1,
+                              tol=cfg["tol"])
+            an.analyze(torch.from_numpy(p.Xf).cuda(), torch.from_numpy(p.y).cuda(), seed=1000 * s + d, counter=d)
             F, T = an.warm_features(K)
             Fs.append(F)
             Ts.append(T)
+            if log and (q + 1) % max(1, len(jobs) // 10) == 0:
+                log(f"pairs: {len(Fs) * cfg['N']}")
+    if an is not None:
         an.close()
-        if log:
-            log(f"pairs from ensemble {s}: {len(Fs) * cfg['N']}")
     return torch.cat(Fs), torch.cat(Ts)
 
 
@@ -95,10 +105,15 @@ def evaluate(cfg, shape, params, seeds, K, reps=5):
                 an.analyze(Xf, y, seed=77 + s, counter=0, out=Xa)
             e1.record()
             torch.cuda.synchronize()
+            an.set_phase_timing(True)
+            an.analyze(Xf, y, seed=77 + s, counter=0, out=Xa)
+            ph = an.phase_times()
+            an.set_phase_timing(False)
             st = an.stats()
             it, _, _ = an.column_stats()
             row[mode] = dict(iters_mean=float(np.mean(it)), iters_max=int(np.max(it)),
-                             ms=e0.elapsed_time(e1) / reps, true_relres_max=st["true_relres_max"],
+                             ms=e0.elapsed_time(e1) / reps, phase_ms=[float(v) for v in ph],
+                             refinements=st["refinements"], true_relres_max=st["true_relres_max"],
                              warm_relres_max=st["warm_relres_max"], warm_fallbacks=st["warm_fallbacks"],
                              status=st["status"])
             row[mode + "_Xa"] = Xa
