@@ -117,8 +117,9 @@ typedef struct enkf_stats {
                                 ||d_j - S z_j|| / ||d_j||; -1 when not computed          */
   int32_t columns_converged; /* columns that met tol                                     */
   int32_t grid_blocks;       /* persistent-grid size used                                */
-  double warm_relres_max;    /* learned warm start: max over columns of the start's true
-                                relative residual ||d_j - S z0_j|| / ||d_j||; -1 if off   */
+  double warm_relres_max;    /* learned warm start: max over columns of the start's
+                                relative residual ||d_j - S z0_j|| / ||d_j|| (evaluated in
+                                FP32 through the N x N identity below); -1 if off         */
   double warm_fallbacks;     /* columns whose start was rejected (non-finite or more than
                                 1e3 times the zero start's residual) and began at 0      */
   double reserved[2];
@@ -303,9 +304,10 @@ enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_
    small MLP predicts c_j per column from features f_j = [d_j(sketch)/s_j, g_j/s_j]: a
    sketch of K rows i_k = floor(k m / K), s_j the RMS of d_j over the sketch (1 if 0),
    g_j = HA^T R^{-1} d_j/(N-1). The prediction is decoded into the start
-   z0_j = R^{-1}(d_j - HA c_j) (residual in span(HA)); the start's true residual is measured
-   and a column whose start is non-finite or more than 1e3 times worse than z_j = 0 starts
-   from 0 instead. The network: inputs standardised per feature, `layers` hidden layers of
+   z0_j = R^{-1}(d_j - HA c_j), whose residual is HA e_j with
+   e_j = c_j + (HA^T R^{-1} HA c_j - HA^T R^{-1} d_j)/(N-1) (so no extra pass over S is needed);
+   a column whose start residual is non-finite or more than 1e3 times that of z_j = 0 starts
+   from 0 instead. The refreshes of the solve then measure the true residual as usual. The network: inputs standardised per feature, `layers` hidden layers of
    width `hidden` with GELU (x Phi(x)), linear output of the standardised c_j/s_j; trained
    with mean squared error and Adam (Kingma & Ba 2015). All of it runs in this library's
    kernels (FP32). */

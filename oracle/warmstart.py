@@ -147,3 +147,12 @@ def targets(W, s):
 def decode(HA, D, r, C):
     """Z0 = R^{-1}(D - HA C), C [N][N] with column j the predicted c_j."""
     return (D - HA @ C) / r[:, None]
+
+
+def start_residual(HA, D, r, C):
+    """Residual of the decoded start, D - S z0 = HA E with
+    E = C + (HA^T R^-1 HA C - HA^T R^-1 D)/(N-1) (from S = HA HA^T/(N-1) + R)."""
+    N = HA.shape[1]
+    Gw = HA.T @ (HA / r[:, None])
+    g = HA.T @ (D / r[:, None])
+    return HA @ (C + (Gw @ C - g) / (N - 1))

@@ -207,7 +207,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
     allocs.push_back({(void**)&ws.Ddf, 8 * (size_t)mN});
     allocs.push_back({(void**)&ws.Zdf, 8 * (size_t)mN});
   }
-  if (mixed) allocs.push_back({(void**)&ws.HA16, (size_t)((c.lowprec_terms == 1 ? 2 : 4) * mN)});
+  if (mixed) allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -221,6 +221,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.w, h_w, sizeof(double) * nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ws.r, r_diag, sizeof(double) * c.m, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ws.status, 0, sizeof(int32_t) * 4);
+  if (e == cudaSuccess && ws.HA16) e = cudaMemset(ws.HA16, 0, enkf::mixed_image_bytes(h));
   if (e == cudaSuccess) e = cudaMemset(ws.bar, 0, sizeof(unsigned) * 4);
   if (e == cudaSuccess) e = enkf::launch_convert_r(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

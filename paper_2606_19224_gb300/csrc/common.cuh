@@ -188,6 +188,7 @@ cudaError_t launch_convert_r(enkf_handle_s* h);
 // kernels_tc.cu: mixed-precision (BF16 / FP16 tensor-core) persistent solve
 cudaError_t plan_solve_mixed(enkf_handle_s* h);
 cudaError_t launch_solve_mixed(enkf_handle_s* h);
+size_t mixed_image_bytes(const enkf_handle_s* h);   // tile images of HA (zeroed at create)
 cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa);
 cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa);
 // kernels_reduced.cu: Gram pass + N x N CG of CGD-EnKF-Reduced; V lands in ws.W,

@@ -130,9 +130,7 @@ cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y
     innov_kernel<float><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const float*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
         c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B),
-        c.precision == ENKF_BF16_REFINE ? static_cast<__nv_bfloat16*>(ws.HA16) : nullptr,
-        c.precision == ENKF_FP16_REFINE ? static_cast<__half*>(ws.HA16) : nullptr,
-        c.lowprec_terms != 1 ? 1 : 0, static_cast<df32*>(ws.HAdf), static_cast<df32*>(ws.Ddf));
+        nullptr, nullptr, 0, static_cast<df32*>(ws.HAdf), static_cast<df32*>(ws.Ddf));
   return cudaGetLastError();
 }
 

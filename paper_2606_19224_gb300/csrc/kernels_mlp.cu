@@ -356,50 +356,66 @@ static cudaError_t mlp_loss_grad_impl(const MlpLayout& L, const float* P, const 
 }
 
 // ------------------------------------------------------------------ warm-start maps
-// Partial N x N products g_part[b][k][j] = sum_{i in block b} HA[i][k] D[i][j] / r_i over row
-// blocks; the feature kernel sums the blocks in a fixed order.
+// Partial N x N products over row blocks: part[b][0][k][j] = sum_{i in block b} HA[i][k] D[i][j] / r_i
+// and part[b][1][k][j] = sum_{i in block b} HA[i][k] HA[i][j] / r_i (FP32 products of the FP32
+// copies, FP32 within a block); the reduce kernel sums the blocks in a fixed order in FP64.
+// AM x AM outputs of each product per thread (AM = NT / 16).
 constexpr int kWarmRows = 32;
 
+template <int AM>
 __global__ void __launch_bounds__(kThreads) warm_gram_kernel(const float* __restrict__ HA,
                                                              const double* __restrict__ D,
-                                                             const double* __restrict__ r, int64_t m, int N,
+                                                             const float* __restrict__ r32, int64_t m, int N,
                                                              int64_t rows_per, double* __restrict__ part) {
-  __shared__ float sH[kWarmRows][129];
-  __shared__ float sD[kWarmRows][129];
+  constexpr int NT = 16 * AM, RW = AM == 8 ? kWarmRows / 2 : kWarmRows;   // static smem < 48 KB
+  __shared__ float sH[RW][NT + 1];
+  __shared__ float sD[RW][NT + 1];
+  __shared__ float sHr[RW][NT + 1];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per, i1 = imin64(m, i0 + rows_per);
-  // each thread owns outputs (k, j) = (t / 16 + 16 a, t % 16 + 16 c) for a, c < 8 (N <= 128)
   const int tk = t / 16, tj = t % 16;
-  float acc[8][8] = {};
-  for (int64_t ib = i0; ib < i1; ib += kWarmRows) {
+  float acc[AM][AM] = {}, accG[AM][AM] = {};
+  for (int64_t ib = i0; ib < i1; ib += RW) {
     __syncthreads();
-    for (int e = t; e < kWarmRows * N; e += kThreads) {
-      const int ii = e / N, k = e % N;
+    for (int e = t; e < RW * NT; e += kThreads) {
+      const int ii = e / NT, k = e % NT;
       const int64_t i = ib + ii;
-      const bool in = i < i1;
-      sH[ii][k] = in ? HA[i * N + k] : 0.f;
-      sD[ii][k] = in ? (float)(D[i * N + k] / r[i]) : 0.f;
+      const bool in = i < i1 && k < N;
+      const float rinv = in ? 1.f / r32[i] : 0.f;
+      const float h = in ? HA[i * N + k] : 0.f;
+      sH[ii][k] = h;
+      sHr[ii][k] = h * rinv;
+      sD[ii][k] = in ? (float)D[i * N + k] * rinv : 0.f;
     }
     __syncthreads();
-    for (int ii = 0; ii < kWarmRows; ++ii) {
-      float h[8], d[8];
+    for (int ii = 0; ii < RW; ++ii) {
+      float h[AM], d[AM], hr[AM];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) h[a] = (tk + 16 * a < N) ? sH[ii][tk + 16 * a] : 0.f;
+      for (int a = 0; a < AM; ++a) h[a] = sH[ii][tk + 16 * a];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) d[c] = (tj + 16 * c < N) ? sD[ii][tj + 16 * c] : 0.f;
+      for (int c = 0; c < AM; ++c) {
+        d[c] = sD[ii][tj + 16 * c];
+        hr[c] = sHr[ii][tj + 16 * c];
+      }
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < AM; ++a)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(h[a], d[c], acc[a][c]);
+        for (int c = 0; c < AM; ++c) {
+          acc[a][c] = fmaf(h[a], d[c], acc[a][c]);
+          accG[a][c] = fmaf(h[a], hr[c], accG[a][c]);
+        }
     }
   }
-  double* out = part + (int64_t)blockIdx.x * N * N;
+  double* out = part + (int64_t)blockIdx.x * 2 * N * N;
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < AM; ++a)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < AM; ++c) {
       const int k = tk + 16 * a, j = tj + 16 * c;
-      if (k < N && j < N) out[k * N + j] = acc[a][c];
+      if (k < N && j < N) {
+        out[k * N + j] = acc[a][c];
+        out[N * N + k * N + j] = accG[a][c];
+      }
     }
 }
 
@@ -453,22 +469,47 @@ __global__ void warm_targets_kernel(const double* __restrict__ W, const float* _
   T[e] = (float)(W[k * N + j] / (double)s[j]);
 }
 
-// Decoder: z0[i][j] = (D[i][j] - sum_k HA[i][k] C[k][j]) / r_i with C[k][j] = Y[j][k] s_j,
-// written as the double-float starting solution of the FP32 solve.
+// Coefficients of column j (one CTA per column): c_j = Y[j] s_j (the prediction in raw units)
+// and e_j = c_j + (Gw c_j - g~_j)/(N-1) with Gw = HA^T R^-1 HA, g~_j = HA^T R^-1 d_j, so that the
+// start z0_j = R^-1 (d_j - HA c_j) has residual d_j - S z0_j = HA e_j (from S = HA HA^T/(N-1) + R).
+__global__ void __launch_bounds__(128) warm_coef_kernel(const float* __restrict__ Y, const float* __restrict__ s,
+                                                        const double* __restrict__ gsum, int N,
+                                                        float* __restrict__ C, float* __restrict__ Ecoef) {
+  __shared__ double sc[128];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const double sj = s[j];
+  for (int k = t; k < N; k += 128) sc[k] = (double)Y[j * N + k] * sj;
+  __syncthreads();
+  const double* g = gsum;                 // [k][j] = HA^T R^-1 D
+  const double* Gw = gsum + N * N;        // [k][l] = HA^T R^-1 HA
+  const double inv = 1.0 / (double)(N - 1);
+  for (int k = t; k < N; k += 128) {
+    double acc = 0.0;
+    for (int l = 0; l < N; ++l) acc = fma(Gw[k * N + l], sc[l], acc);
+    C[k * N + j] = (float)sc[k];
+    Ecoef[k * N + j] = (float)(sc[k] + (acc - g[k * N + j]) * inv);
+  }
+}
+
+// Decoder: z0[i][j] = (d_ij - sum_k HA[i][k] C[k][j]) / r_i as the double-float starting solution
+// of the FP32 solve, and its residual B[i][j] = sum_k HA[i][k] E[k][j] as the first inner
+// right-hand side (FP32; the refreshes recompute the true residual in double-float).
 __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __restrict__ HA,
                                                                const double* __restrict__ D,
-                                                               const double* __restrict__ r, int64_t m, int N,
-                                                               const float* __restrict__ Y,
-                                                               const float* __restrict__ s,
-                                                               df32* __restrict__ Z0) {
-  extern __shared__ float wsm[];   // C [N][N + 1] then a 16-row tile of HA [16][N + 1]
+                                                               const float* __restrict__ r32, int64_t m, int N,
+                                                               const float* __restrict__ C,
+                                                               const float* __restrict__ Ecoef,
+                                                               df32* __restrict__ Z0, float* __restrict__ B) {
+  extern __shared__ float wsm[];   // C [N][N + 1], E [N][N + 1], a 16-row tile of HA [16][N + 1]
   const int LD = N + 1;
   float* sC = wsm;
-  float* sHt = wsm + N * LD;
+  float* sE = wsm + N * LD;
+  float* sHt = wsm + 2 * N * LD;
   const int t = threadIdx.x;
   for (int e = t; e < N * N; e += kThreads) {
     const int k = e / N, j = e % N;
-    sC[k * LD + j] = Y[j * N + k] * s[j];
+    sC[k * LD + j] = C[e];
+    sE[k * LD + j] = Ecoef[e];
   }
   for (int64_t ib = (int64_t)blockIdx.x * 16; ib < m; ib += (int64_t)gridDim.x * 16) {
     __syncthreads();
@@ -482,10 +523,15 @@ __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __re
       const int ii = e / N, j = e % N;
       const int64_t i = ib + ii;
       if (i >= m) continue;
-      float acc = 0.f;
-      for (int k = 0; k < N; ++k) acc = fmaf(sHt[ii * LD + k], sC[k * LD + j], acc);
-      const double z = (D[i * N + j] - (double)acc) / r[i];
-      Z0[i * N + j] = df32(z);
+      float a1 = 0.f, a2 = 0.f;
+      for (int k = 0; k < N; ++k) {
+        const float h = sHt[ii * LD + k];
+        a1 = fmaf(h, sC[k * LD + j], a1);
+        a2 = fmaf(h, sE[k * LD + j], a2);
+      }
+      const float z = ((float)D[i * N + j] - a1) / r32[i];
+      Z0[i * N + j] = df32(z, 0.f);
+      B[i * N + j] = a2;
     }
   }
 }
@@ -500,8 +546,10 @@ struct WarmState {
   const float* params = nullptr;   // caller-owned model (enkf_set_warm_model)
   int K = 0;                       // sketch size of the model (in_dim - N)
   int nparts = 0;
-  double* part = nullptr;          // [nparts][N][N]
-  double* gsum = nullptr;          // [N][N] = HA^T R^-1 D
+  double* part = nullptr;          // [nparts][2][N][N]
+  double* gsum = nullptr;          // [2][N][N]: HA^T R^-1 D, HA^T R^-1 HA
+  float* C = nullptr;              // [N][N] predicted coefficients (column j = c_j)
+  float* E = nullptr;              // [N][N] residual coefficients of the start
   float* F = nullptr;              // [N][K + N] features of the current analysis
   float* s = nullptr;              // [N] column scales
   float* Y = nullptr;              // [N][N] raw predictions
@@ -516,8 +564,10 @@ static cudaError_t warm_alloc(enkf_handle_s* h, int K) {
   cudaError_t e = cudaSuccess;
   if (!w.part) {
     w.nparts = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)h->sms, (h->cfg.m + 255) / 256));
-    e = cudaMalloc((void**)&w.part, sizeof(double) * (size_t)w.nparts * N * N);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&w.gsum, sizeof(double) * N * N);
+    e = cudaMalloc((void**)&w.part, sizeof(double) * (size_t)w.nparts * 2 * N * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.gsum, sizeof(double) * 2 * N * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.C, sizeof(float) * N * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.E, sizeof(float) * N * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.s, sizeof(float) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.Y, sizeof(float) * N * N);
   }
@@ -534,10 +584,15 @@ static cudaError_t warm_features_into(enkf_handle_s* h, int K, float* F) {
   WarmState& w = *h->warm;
   const auto& c = h->cfg;
   const int64_t rows_per = (c.m + w.nparts - 1) / w.nparts;
-  warm_gram_kernel<<<w.nparts, kThreads, 0, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r, c.m, c.N, rows_per, w.part);
+  if (c.N <= 32)
+    warm_gram_kernel<2><<<w.nparts, kThreads, 0, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, rows_per, w.part);
+  else if (c.N <= 64)
+    warm_gram_kernel<4><<<w.nparts, kThreads, 0, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, rows_per, w.part);
+  else
+    warm_gram_kernel<8><<<w.nparts, kThreads, 0, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, rows_per, w.part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  warm_reduce_kernel<<<(c.N * c.N + 255) / 256, 256, 0, h->stream>>>(w.part, w.nparts, c.N * c.N, w.gsum);
+  warm_reduce_kernel<<<(2 * c.N * c.N + 255) / 256, 256, 0, h->stream>>>(w.part, w.nparts, 2 * c.N * c.N, w.gsum);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   warm_features_kernel<<<c.N, kThreads, 0, h->stream>>>(h->ws.D, c.m, c.N, K, w.gsum, F, w.s);
@@ -566,7 +621,7 @@ cudaError_t warm_set_model(enkf_handle_s* h, const enkf_mlp_shape* shape, const 
   w.work = nullptr;
   e = cudaMalloc((void**)&w.work, sizeof(float) * mlp_work_floats(L, N));
   if (e != cudaSuccess) { err = "allocation"; return e; }
-  const int smem = (int)(sizeof(float) * (size_t)(N + 16) * (N + 1));   // up to 74 KB at N = 128
+  const int smem = (int)(sizeof(float) * (size_t)(2 * N + 16) * (N + 1));   // up to 140 KB at N = 128
   e = cudaFuncSetAttribute(warm_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) { err = "decoder shared memory"; return e; }
   w.L = L;
@@ -586,17 +641,21 @@ cudaError_t warm_prepare(enkf_handle_s* h) {
   const MlpWork W = carve(w.L, c.N, w.work);
   e = mlp_forward_impl(w.L, w.params, w.F, nullptr, c.N, W, w.Y, h->stream);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(float) * (size_t)(c.N + 16) * (c.N + 1);
+  warm_coef_kernel<<<c.N, 128, 0, h->stream>>>(w.Y, w.s, w.gsum, c.N, w.C, w.E);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(float) * (size_t)(2 * c.N + 16) * (c.N + 1);
   const int grid = (int)std::min<int64_t>(2 * (int64_t)h->sms, (c.m + 15) / 16);
-  warm_decode_kernel<<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r, c.m, c.N, w.Y, w.s,
-                                                          static_cast<df32*>(h->ws.Zdf));
+  warm_decode_kernel<<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, w.C, w.E,
+                                                          static_cast<df32*>(h->ws.Zdf),
+                                                          static_cast<float*>(h->ws.B));
   return cudaGetLastError();
 }
 
 void warm_free(enkf_handle_s* h) {
   WarmState* w = h->warm;
   if (!w) return;
-  void* ptrs[] = {w->part, w->gsum, w->F, w->s, w->Y, w->work};
+  void* ptrs[] = {w->part, w->gsum, w->C, w->E, w->F, w->s, w->Y, w->work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete w;

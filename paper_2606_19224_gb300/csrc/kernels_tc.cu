@@ -43,13 +43,44 @@ cudaError_t plan_solve_mixed(enkf_handle_s* h) {
   return cudaSuccess;
 }
 
+// Tile images of HA for the tensor-core pass: tiles of 128 rows within each CTA's row block.
+static int64_t mixed_rows_per(const enkf_handle_s* h) { return (h->cfg.m + h->launch.G - 1) / h->launch.G; }
+static int mixed_qmax(const enkf_handle_s* h) { return (int)((mixed_rows_per(h) + kTR - 1) / kTR); }
+
+size_t mixed_image_bytes(const enkf_handle_s* h) {
+  const int TM = mixed_split(h->cfg) ? 2 : 1;
+  return (size_t)h->launch.G * mixed_qmax(h) * 2 * TM * kTR * h->launch.NT * 2;
+}
+
+static cudaError_t launch_tc_images(enkf_handle_s* h) {
+  const auto& c = h->cfg;
+  const int blocks = (int)std::min<int64_t>((c.m * c.N + 255) / 256, (int64_t)h->sms * 32);
+  const df32* HAdf = static_cast<const df32*>(h->ws.HAdf);
+  const int64_t rp = mixed_rows_per(h);
+  const int qm = mixed_qmax(h), NT = h->launch.NT;
+  const bool split = mixed_split(c);
+  if (c.precision == ENKF_BF16_REFINE) {
+    auto* img = static_cast<__nv_bfloat16*>(h->ws.HA16);
+    if (split) tc_images_kernel<__nv_bfloat16, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+    else tc_images_kernel<__nv_bfloat16, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+  } else {
+    auto* img = static_cast<__half*>(h->ws.HA16);
+    if (split) tc_images_kernel<__half, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+    else tc_images_kernel<__half, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   const auto& c = h->cfg;
   auto& ws = h->ws;
+  cudaError_t ierr = launch_tc_images(h);
+  if (ierr != cudaSuccess) return ierr;
   MixedParams p{};
   p.m = c.m;
   p.N = c.N;
   p.HA16 = ws.HA16;
+  p.qmax = mixed_qmax(h);
   p.HA32 = ws.HA32;
   p.HAdf = static_cast<const df32*>(ws.HAdf);
   p.Ddf = static_cast<const df32*>(ws.Ddf);

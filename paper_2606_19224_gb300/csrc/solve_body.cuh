@@ -41,7 +41,7 @@ struct SolveParams {
   unsigned* bar;
   unsigned long long* prof;  // optional phase timers of CTA 0 (ns), nullptr when off
   int warm;                  // FP32 mode: Zdf holds a starting solution (learned warm start)
-  double* col_warm;          // [N] true relative residual of that start (-1 when not warm)
+  double* col_warm;          // [N] relative residual ||B_j|| / ||d_j|| of that start
 };
 
 // Phase timer slots (CTA 0, thread 0): accumulated ns per phase of the solve.
@@ -111,13 +111,13 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   int par = 0;
   bool ok = true;
 
-  // a warm start keeps the given Zdf and begins with a refresh (its true residual)
-  bool warm_pending = refine && p.warm != 0;
+  // a warm start keeps the given Zdf; B holds its residual (written by the decoder)
+  const bool warm = refine && p.warm != 0;
   // ---- ||d_j||^2 (and Z = 0 for the refinement accumulator)
   rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
     const double d = p.D[i * N + j];
     acc = fma(d, d, acc);
-    if (refine && !warm_pending) p.Zdf[i * N + j] = df32(0.f, 0.f);
+    if (refine && !warm) p.Zdf[i * N + j] = df32(0.f, 0.f);
   }, s_tmp, scratch);
   if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
   ok = bar.sync();
@@ -137,12 +137,50 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     }
     __syncthreads();
   }
+  if (ok && warm) {
+    // the start's residual norm judges it: a column whose start is non-finite or more than
+    // 1e3 times worse than the zero start (residual d_j) falls back to z_j = 0, B_j = d_j
+    VT* Bv = static_cast<VT*>(p.B);
+    rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
+      const double v = (double)Bv[i * N + j];
+      acc = fma(v, v, acc);
+    }, s_tmp, scratch);
+    if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
+    ok = bar.sync();
+    if (ok) {
+      reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
+      par ^= 1;
+      if (t < NT) {
+        const bool bad = t < N && !s_done[t] && !(s_tmp[t] <= 1e6 * s_dn2[t]);
+        if (b == 0 && t < N) p.col_warm[t] = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+        s_active[t] = bad ? 1 : 0;   // s_active is free until the first inner solve
+        if (t < N && !s_done[t] && !bad) {
+          const double tr = sqrt(s_tmp[t] / s_dn2[t]);
+          s_itol[t] = fmin(0.5, fmax(p.inner_tol, tr > 0.0 ? 0.1 * p.tol / tr : p.inner_tol));
+        }
+      }
+      __syncthreads();
+      int nbad = 0;
+      for (int j = 0; j < N; ++j) nbad += s_active[j];
+      if (nbad) {
+        for (int64_t e = (int64_t)t; e < (row1 - row0) * N; e += kThreads) {
+          const int64_t i = row0 + e / N;
+          const int j = (int)(e % N);
+          if (s_active[j]) {
+            p.Zdf[i * N + j] = df32(0.f, 0.f);
+            Bv[i * N + j] = (VT)p.D[i * N + j];
+          }
+        }
+        if (b == 0 && t == 0) p.status[2] = nbad;
+      }
+      __syncthreads();
+    }
+  }
   tick(PH_SETUP);
 
   int outer = 0, total_iter = 0, refinements = 0;
   while (ok) {
-   const bool warm_step = warm_pending;
-   if (!warm_step) {
+   {
     // ---- inner solve of S X = B from X = 0: first reduction of [HA^T r | sum r_i r^2 | (r, r)]
     {
       ProSetup<VT, PC> pro{B, X, Res, rv, N};
@@ -171,6 +209,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     int it = 0;
     for (;;) {
       // scalars of this step (identical in every CTA: same sums in the same order)
+      int my_active = 0;
       if (t < N) {
         int a = s_active[t];
         const double gm = s_gam[t];
@@ -197,15 +236,9 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
         s_beta[t] = be;
         s_alpha_v[t] = (VT)al;
         s_beta_v[t] = (VT)be;
+        my_active = a;
       }
-      __syncthreads();
-      if (t == 0) {
-        int any = 0;
-        for (int j = 0; j < N; ++j) any |= s_active[j];
-        s_flag[0] = any && it < limit;
-      }
-      __syncthreads();
-      if (!s_flag[0]) break;
+      if (!(__syncthreads_or(my_active) && it < limit)) break;
       tick(PH_SCAL);
       if constexpr (async_passF<VT, NT>()) {
         if ((N & 3) == 0)
@@ -248,7 +281,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       ProRefresh<VT> pro{p.Z, X, N, refine};
       passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
     } else {
-      ProRefreshDF<VT> pro{p.Zdf, X, N, !warm_pending};
+      ProRefreshDF<VT> pro{p.Zdf, X, N, true};
       passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
     }
     if (!(ok = bar.sync())) break;
@@ -278,33 +311,6 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
     par ^= 1;
     ++refinements;
-    if (warm_pending) {
-      // the start's true residual judges it: a column whose start is non-finite or more than
-      // 1e3 times worse than the zero start (residual d_j) falls back to z_j = 0
-      if (t < NT) {
-        const bool bad = t < N && !(s_tmp[t] <= 1e6 * s_dn2[t]);
-        if (b == 0 && t < N) p.col_warm[t] = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
-        s_active[t] = bad ? 1 : 0;   // s_active is free until the next inner solve
-        if (bad) s_tmp[t] = s_dn2[t];
-      }
-      __syncthreads();
-      int nbad = 0;
-      for (int j = 0; j < N; ++j) nbad += s_active[j];
-      if (nbad) {
-        VT* Bv = static_cast<VT*>(p.B);
-        for (int64_t e = (int64_t)t; e < (row1 - row0) * N; e += kThreads) {
-          const int64_t i = row0 + e / N;
-          const int j = (int)(e % N);
-          if (s_active[j]) {
-            p.Zdf[i * N + j] = df32(0.f, 0.f);
-            Bv[i * N + j] = (VT)p.D[i * N + j];
-          }
-        }
-        if (b == 0 && t == 0) p.status[2] = nbad;
-      }
-      __syncthreads();
-      warm_pending = false;
-    }
     if (t < N) {
       const double tr = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
       s_true[t] = tr;
@@ -315,19 +321,9 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
         if (s_itol[t] > 0.5) s_itol[t] = 0.5;
       }
     }
-    __syncthreads();
-    if (t == 0) {
-      int all = 1;
-      for (int j = 0; j < N; ++j) all &= s_done[j];
-      s_flag[1] = all;
-    }
-    __syncthreads();
+    const int all_done = __syncthreads_and(t >= N || s_done[t]);
     tick(PH_REFRESH);
-    if (warm_step) {
-      if (s_flag[1]) break;
-      continue;
-    }
-    if (!refine || fixed || s_flag[1] || outer >= p.max_refine || total_iter >= p.max_iter) break;
+    if (!refine || fixed || all_done || outer >= p.max_refine || total_iter >= p.max_iter) break;
     ++outer;
   }
 

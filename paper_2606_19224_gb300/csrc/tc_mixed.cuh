@@ -100,65 +100,121 @@ __device__ __forceinline__ int core_idx(int r, int k, int Kd) {
 constexpr int kTR = 128;  // rows per tile = M of the u MMA = K of the Gram MMA
 
 template <int NT> __host__ __device__ constexpr int tc_tmem_cols() { return (2 * NT) < 32 ? 32 : 2 * NT; }
-template <int NT, int TERMS> __host__ __device__ constexpr int tc_bytes() {
-  // sAu [128][NT] (reused as sBg [NT][128] once the u MMA has consumed it), sBu [NT][NT],
-  // sAg [128][128] (2-byte; hi and lo copies when the operands are split), sacc [8][2][NT] f32,
-  // scales zs, ts [NT] f32
-  return (TERMS == 3 ? 2 : 1) * 2 * (kTR * NT + NT * NT + kTR * kTR) + 4 * (8 * 2 * NT) + 4 * 2 * NT;
-}
 
 // ------------------------------------------------------------------ fused tensor-core CG step
 // Same recurrences as passF (Chronopoulos-Gear arrangement, optionally preconditioned by R);
-// the contractions run on the tensor cores. sBu holds (T/(N-1)) scaled per column by ts_j,
-// the Gram operand holds z scaled per column by zs_j (so FP16 neither overflows nor flushes);
+// the contractions run on the tensor cores. Bu holds (T/(N-1)) scaled per column by ts_j and
+// the z operand holds z scaled per column by zs_j (so FP16 neither overflows nor flushes);
 // the scales are undone on the FP32 values read from TMEM.
-//
 // TERMS == 3: every operand is split into x_hi = round(x) and x_lo = round(x - x_hi) and each
 // product is formed as hi*hi + hi*lo + lo*hi (three MMAs into the same accumulator), about 16
-// significant bits instead of 8 (BF16) or 11 (FP16). Tiles: [hi | lo] pairs of each operand.
+// significant bits instead of 8 (BF16) or 11 (FP16).
+//
+// HA reaches the CTA as precomputed tile images (tc_images_kernel): for every 128-row tile of
+// the CTA's row block, [Au hi | Au lo | Ag hi | Ag lo] with Au the K-major core layout of the
+// tile's rows (A operand of u = HA T) and Ag that of its transpose (B operand of the Gram
+// zT HA), so staging a tile is a plain 16-byte cp.async copy. The Gram is formed as
+// D_g[j][k] = sum_i z_ij HA_ik with z^T (scaled per column) as the A operand (M = 128, rows
+// j >= N zero) and Ag as the B operand (N = NT), so HA needs no padding rows.
+// NT <= 64: the next tile's Ag copy overlaps the whole current tile (two Ag buffers), the next
+// Au copy overlaps the epilogue, the z operand has its own buffer with a padded K-direction
+// core stride (144 B, conflict-free stores), and the column sums of (r, z) and (r, r) stay in
+// registers until the end of the pass. NT = 128: one buffer of each, z aliases Au.
+template <int NT, int TERMS> struct TcLayout {
+  static constexpr int TM = TERMS == 3 ? 2 : 1;
+  static constexpr bool DB = NT <= 64;
+  static constexpr int AU = kTR * NT, AG = NT * kTR, BU = NT * NT;   // elements per part
+  static constexpr uint32_t LBOG = DB ? 144 : 128;                   // z operand: K core stride
+  static constexpr uint32_t SBOG = 16 * LBOG;                        // 16 cores along K = 128
+  static constexpr int BGP = (int)(16 * SBOG);                       // bytes per z part (M = 128)
+  static constexpr int off_au = 0;
+  static constexpr int off_bu = off_au + TM * AU * 2;
+  static constexpr int off_ag = off_bu + TM * BU * 2;
+  static constexpr int n_ag = DB ? 2 : 1;
+  static constexpr int off_bg = DB ? off_ag + n_ag * TM * AG * 2 : off_au;
+  static constexpr int end_bg = DB ? off_bg + TM * BGP : off_ag + n_ag * TM * AG * 2;
+  static constexpr int off_sacc = end_bg;
+  static constexpr int off_zs = off_sacc + 4 * (8 * 2 * NT);
+  static constexpr int off_ts = off_zs + 4 * NT;
+  static constexpr int bytes = off_ts + 4 * NT;
+  static_assert(DB || TM * BGP <= TM * AU * 2, "z operand must fit in the Au region");
+};
+
+__device__ __forceinline__ void tc_cp16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// copy `bytes` (a multiple of 16) from global to shared with all threads of the CTA
+__device__ __forceinline__ void tc_copy(unsigned char* sdst, const unsigned char* gsrc, int bytes) {
+  for (int o = threadIdx.x * 16; o < bytes; o += kThreads * 16) tc_cp16(sdst + o, gsrc + o);
+}
+
 template <typename T16, int NT, bool PC, int TERMS>
-__device__ void passF_tc(const T16* __restrict__ HAhi, const T16* __restrict__ HAlo, int64_t row0,
-                         int64_t row1, int N, float* X, float* Res, float* P, float* Sv,
-                         const float* __restrict__ rv, const float* alpha, const float* beta,
-                         const float* zs, const float* ts, T16* sAu, const T16* sBu, T16* sAg,
-                         T16* sBg, float* sacc, uint32_t tmem, uint64_t* mbar_u, uint64_t* mbar_g,
-                         uint32_t& ph_u, uint32_t& ph_g, int* status, bool& ok,
-                         double* __restrict__ out) {
-  constexpr bool SPLIT = TERMS == 3;
+__device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, int64_t row1, int N,
+                          float* X, float* Res, float* P, float* Sv, const float* __restrict__ rv,
+                          const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
+                          uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g, int* status,
+                          bool& ok, double* __restrict__ out) {
+  using L = TcLayout<NT, TERMS>;
+  constexpr bool SPLIT = TERMS == 3, DB = L::DB;
+  constexpr int TM = L::TM;
   constexpr uint32_t idesc = umma_idesc(H16<T16>::fmt, NT);
-  constexpr int HALF = NT / 2, CH = HALF / 16;  // columns per warpgroup, 16-column chunks
-  constexpr int AU = kTR * NT, BU = NT * NT, AG = kTR * kTR, BG = NT * kTR;  // tile sizes
+  constexpr int HALF = NT / 2, CH = HALF / 16;   // columns per warp half, 16-column chunks
+  constexpr int TILE = 2 * TM * kTR * NT;        // elements per tile image
+  T16* sAu = reinterpret_cast<T16*>(tcs + L::off_au);
+  const T16* sBu = reinterpret_cast<const T16*>(tcs + L::off_bu);
+  unsigned char* sAg0 = tcs + L::off_ag;
+  unsigned char* sBg = tcs + L::off_bg;
+  float* sacc = reinterpret_cast<float*>(tcs + L::off_sacc);
+  const float* zs = reinterpret_cast<const float*>(tcs + L::off_zs);
+  const float* ts = reinterpret_cast<const float*>(tcs + L::off_ts);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int q = warp & 3, half = warp >> 2;
-  const int rt = 32 * q + lane;                 // the thread's row within the tile (TMEM lane)
+  const int qd = warp & 3, half = warp >> 2;
+  const int rt = 32 * qd + lane;                 // the thread's row within the tile (TMEM lane)
   const bool vec = (N & 3) == 0;
   const uint32_t d_u = tmem, d_g = tmem + NT;
+  const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
+  const unsigned char* gimg = reinterpret_cast<const unsigned char*>(img);
+  constexpr int AUB = TM * kTR * NT * 2, AGB = TM * NT * kTR * 2;   // bytes of Au / Ag per tile
+  auto au_src = [&](int q) { return gimg + (size_t)q * TILE * 2; };
+  auto ag_src = [&](int q) { return gimg + (size_t)q * TILE * 2 + AUB; };
+  auto sAg = [&](int q) { return sAg0 + (DB ? (q & 1) * AGB : 0); };
+  // z operand element (row j, col i) of part `part`
+  auto bg_ptr = [&](int part, int j, int i) {
+    return reinterpret_cast<T16*>(sBg + part * L::BGP + (j >> 3) * L::SBOG + (i >> 3) * L::LBOG +
+                                  (((j & 7) * 8 + (i & 7)) * 2));
+  };
+  (void)qmax;
   for (int e = t; e < 8 * 2 * NT; e += kThreads) sacc[e] = 0.f;
-  __syncthreads();
-  bool first_tile = true;
-  for (int64_t i0 = row0; i0 < row1 && ok; i0 += kTR) {
-    // stage HA rows [i0, i0+128): sAu (rows x k, K-major over k) and sAg (k x rows, K-major
-    // over rows); zero beyond row1 and beyond N
-    for (int c = t; c < kTR * (NT / 8); c += kThreads) {
-      const int r = c / (NT / 8), k0 = (c % (NT / 8)) * 8;
-      const int64_t i = i0 + r;
-#pragma unroll
-      for (int part = 0; part < (SPLIT ? 2 : 1); ++part) {
-        const T16* src = part ? HAlo : HAhi;
-        alignas(16) T16 v[8];
-        if (i < row1 && k0 + 8 <= N && ((N & 7) == 0)) {
-          *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(src + i * N + k0);
-        } else {
-#pragma unroll
-          for (int y = 0; y < 8; ++y) v[y] = (i < row1 && k0 + y < N) ? src[i * N + k0 + y] : H16<T16>::from(0.f);
-        }
-        *reinterpret_cast<uint4*>(sAu + part * AU + core_idx(r, k0, NT)) = *reinterpret_cast<const uint4*>(v);
-#pragma unroll
-        for (int y = 0; y < 8; ++y) sAg[part * AG + core_idx(k0 + y, r, kTR)] = v[y];
-      }
+  if constexpr (DB) {
+    // rows j in [NT, 128) of the z operand stay zero for the whole pass
+    for (int e = t; e < TM * (kTR - NT) * kTR; e += kThreads) {
+      const int part = e / ((kTR - NT) * kTR), rem = e % ((kTR - NT) * kTR);
+      *bg_ptr(part, NT + rem / kTR, rem % kTR) = H16<T16>::from(0.f);
     }
+  }
+  float gA[DB ? CH : 1][16], gB[DB ? CH : 1][16];
+#pragma unroll
+  for (int c = 0; c < (DB ? CH : 1); ++c)
+#pragma unroll
+    for (int y = 0; y < 16; ++y) { gA[c][y] = 0.f; gB[c][y] = 0.f; }
+  if (Qb > 0) {
+    tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), AUB);
+    tc_copy(sAg(0), ag_src(0), AGB);
+    tc_cp_commit();
+  }
+  for (int q = 0; q < Qb && ok; ++q) {
+    const int64_t i0 = row0 + (int64_t)q * kTR;
+    tc_cp_wait_all();
     fence_async_smem();
     __syncthreads();
+    if (DB && q + 1 < Qb) {   // next tile's Ag into the other buffer, behind this whole tile
+      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
+      tc_cp_commit();
+    }
     if (t == 0) {
       tc_fence_after();
       constexpr uint32_t sbo_u = (NT / 8) * 128;
@@ -167,8 +223,8 @@ __device__ void passF_tc(const T16* __restrict__ HAhi, const T16* __restrict__ H
       for (int kb = 0; kb < NT / 16; ++kb) {
         umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
         if (SPLIT) {
-          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * BU + kb * 256, 128, sbo_u), idesc, 1u);
-          umma_f16(d_u, umma_desc(au + 2 * AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
+          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
+          umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
         }
       }
       umma_commit(mbar_u);
@@ -177,126 +233,210 @@ __device__ void passF_tc(const T16* __restrict__ HAhi, const T16* __restrict__ H
     const bool valid = i < row1;
     const float ri = valid ? rv[i] : 1.f;
     const float rinv = 1.f / ri;
-    if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
-    ph_u ^= 1u;
-    tc_fence_after();
-    float gA[CH][16], gB[CH][16];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int j0 = half * HALF + 16 * c;
-      float u[16];
-      tmem_ld16(d_u + ((uint32_t)(32 * q) << 16) + j0, u);
+    // operands of the first chunk are loaded while the MMA runs
+    float rr[16], pp[16], ss[16], xx[16];
+    auto load_chunk = [&](int j0) {
 #pragma unroll
       for (int y4 = 0; y4 < 4; ++y4) {
         const int jj = j0 + 4 * y4;
-        float rr[4] = {0.f, 0.f, 0.f, 0.f}, pp[4] = {0.f, 0.f, 0.f, 0.f};
-        float ss[4] = {0.f, 0.f, 0.f, 0.f}, xx[4] = {0.f, 0.f, 0.f, 0.f};
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, bq[4] = {0.f, 0.f, 0.f, 0.f};
+        float cq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid && jj < N) {
-          ld4<float>(rr, Res + i * N, jj, N, vec);
-          ld4<float>(pp, P + i * N, jj, N, vec);
-          ld4<float>(ss, Sv + i * N, jj, N, vec);
-          ld4<float>(xx, X + i * N, jj, N, vec);
+          ld4<float>(a, Res + i * N, jj, N, vec);
+          ld4<float>(bq, P + i * N, jj, N, vec);
+          ld4<float>(cq, Sv + i * N, jj, N, vec);
+          ld4<float>(dq, X + i * N, jj, N, vec);
         }
-        float pn[4], sn[4], xn[4], rn[4];
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          const int j = jj + y;
-          const float uu = u[4 * y4 + y] / ts[j];
-          const float zz = PC ? rr[y] * rinv : rr[y];
-          const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
-          const float be = beta[j], al = alpha[j];
-          pn[y] = be == 0.f ? zz : fmaf(be, pp[y], zz);
-          sn[y] = be == 0.f ? ww : fmaf(be, ss[y], ww);
-          xn[y] = fmaf(al, pn[y], xx[y]);
-          rn[y] = fmaf(-al, sn[y], rr[y]);
-          const float zn = PC ? rn[y] * rinv : rn[y];
-          const bool live = valid && j < N;
-          gA[c][4 * y4 + y] = live ? (PC ? rn[y] * zn : ri * rn[y] * rn[y]) : 0.f;
-          gB[c][4 * y4 + y] = live ? rn[y] * rn[y] : 0.f;
-          const float zsc = live ? zn * zs[j] : 0.f;
-          const T16 zh = H16<T16>::from(zsc);
-          sBg[core_idx(j, rt, kTR)] = zh;
-          if (SPLIT) sBg[BG + core_idx(j, rt, kTR)] = H16<T16>::from(zsc - (float)zh);
+          rr[4 * y4 + y] = a[y];
+          pp[4 * y4 + y] = bq[y];
+          ss[4 * y4 + y] = cq[y];
+          xx[4 * y4 + y] = dq[y];
         }
-        if (valid && jj < N) {
-          st4<float>(P + i * N, jj, N, vec, pn);
-          st4<float>(Sv + i * N, jj, N, vec, sn);
-          st4<float>(X + i * N, jj, N, vec, xn);
-          st4<float>(Res + i * N, jj, N, vec, rn);
+      }
+    };
+    load_chunk(half * HALF);
+    if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
+    ph_u ^= 1u;
+    tc_fence_after();
+    if (DB && q + 1 < Qb) {   // the u MMA has consumed Au: the next tile's Au behind the epilogue
+      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
+      tc_cp_commit();
+    }
+    float tA[16], tB[16];   // NT = 128: this chunk's column terms, reduced over the warp per chunk
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j0 = half * HALF + 16 * c;
+      if (c > 0) load_chunk(j0);
+      float u[16];
+      tmem_ld16(d_u + ((uint32_t)(32 * qd) << 16) + j0, u);
+      float pn[16], sn[16], xn[16], rn[16];
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        const int j = j0 + y;
+        const float uu = u[y] / ts[j];
+        const float zz = PC ? rr[y] * rinv : rr[y];
+        const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
+        const float be = beta[j], al = alpha[j];
+        pn[y] = be == 0.f ? zz : fmaf(be, pp[y], zz);
+        sn[y] = be == 0.f ? ww : fmaf(be, ss[y], ww);
+        xn[y] = fmaf(al, pn[y], xx[y]);
+        rn[y] = fmaf(-al, sn[y], rr[y]);
+        const float zn = PC ? rn[y] * rinv : rn[y];
+        const bool live = valid && j < N;
+        const float a = live ? (PC ? rn[y] * zn : ri * rn[y] * rn[y]) : 0.f;
+        const float bb = live ? rn[y] * rn[y] : 0.f;
+        if (DB) { gA[DB ? c : 0][y] += a; gB[DB ? c : 0][y] += bb; }
+        else { tA[y] = a; tB[y] = bb; }
+        const float zsc = live ? zn * zs[j] : 0.f;
+        const T16 zh = H16<T16>::from(zsc);
+        *bg_ptr(0, j, rt) = zh;
+        if (SPLIT) *bg_ptr(1, j, rt) = H16<T16>::from(zsc - (float)zh);
+      }
+      if (valid) {
+#pragma unroll
+        for (int y4 = 0; y4 < 4; ++y4) {
+          const int jj = j0 + 4 * y4;
+          if (jj < N) {
+            const float o1[4] = {pn[4 * y4], pn[4 * y4 + 1], pn[4 * y4 + 2], pn[4 * y4 + 3]};
+            const float o2[4] = {sn[4 * y4], sn[4 * y4 + 1], sn[4 * y4 + 2], sn[4 * y4 + 3]};
+            const float o3[4] = {xn[4 * y4], xn[4 * y4 + 1], xn[4 * y4 + 2], xn[4 * y4 + 3]};
+            const float o4[4] = {rn[4 * y4], rn[4 * y4 + 1], rn[4 * y4 + 2], rn[4 * y4 + 3]};
+            st4<float>(P + i * N, jj, N, vec, o1);
+            st4<float>(Sv + i * N, jj, N, vec, o2);
+            st4<float>(X + i * N, jj, N, vec, o3);
+            st4<float>(Res + i * N, jj, N, vec, o4);
+          }
+        }
+      }
+      if constexpr (!DB) {
+        // this chunk's per-column sums over the warp's 32 rows, into the warp's shared slot
+#pragma unroll
+        for (int y = 0; y < 16; ++y) {
+          float a = tA[y], bb = tB[y];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          }
+          if (lane == 0) {
+            sacc[(warp * 2 + 0) * NT + j0 + y] += a;
+            sacc[(warp * 2 + 1) * NT + j0 + y] += bb;
+          }
         }
       }
     }
-    // per-column sums over the warp's 32 rows, accumulated in this warp's shared slot
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int y = 0; y < 16; ++y) {
-        float a = gA[c][y], b = gB[c][y];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) {
-          const int j = half * HALF + 16 * c + y;
-          sacc[(warp * 2 + 0) * NT + j] += a;
-          sacc[(warp * 2 + 1) * NT + j] += b;
-        }
-      }
     tc_fence_before();
     fence_async_smem();
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      constexpr uint32_t sbo_g = (kTR / 8) * 128;
-      const uint32_t ag = smem_addr(sAg), bg = smem_addr(sBg);
+      const uint32_t ag = smem_addr(sAg(q)), bg = smem_addr(sBg);
+      constexpr uint32_t sbo_a = 16 * 128;   // Ag: 16 cores of 128 B along K = 128
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
-        umma_f16(d_g, umma_desc(ag + kb * 256, 128, sbo_g), umma_desc(bg + kb * 256, 128, sbo_g), idesc,
-                 (first_tile && kb == 0) ? 0u : 1u);
+        const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+        const uint64_t B0 = umma_desc(ag + kb * 256, 128, sbo_a);
+        umma_f16(d_g, A0, B0, idesc, (q == 0 && kb == 0) ? 0u : 1u);
         if (SPLIT) {
-          umma_f16(d_g, umma_desc(ag + kb * 256, 128, sbo_g), umma_desc(bg + 2 * BG + kb * 256, 128, sbo_g), idesc, 1u);
-          umma_f16(d_g, umma_desc(ag + 2 * AG + kb * 256, 128, sbo_g), umma_desc(bg + kb * 256, 128, sbo_g), idesc, 1u);
+          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B1 = umma_desc(ag + L::AG * 2 + kb * 256, 128, sbo_a);
+          umma_f16(d_g, A0, B1, idesc, 1u);
+          umma_f16(d_g, A1, B0, idesc, 1u);
         }
       }
       umma_commit(mbar_g);
     }
-    // the Gram MMA reads sAg / sBg: wait before the next tile restages them
+    // the Gram MMA reads the z operand (and, NT = 128, the Au region): wait before reuse
     if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
     ph_g ^= 1u;
     tc_fence_after();
-    first_tile = false;
+    if (!DB && q + 1 < Qb) {
+      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
+      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
+      tc_cp_commit();
+    }
   }
-  // partial Gram from TMEM: thread (lane row k = rt, warpgroup half) -> out[k*N + j] / zs_j
-  // (tcgen05.ld is warp-collective: the condition below is uniform within a warp)
-  if (!first_tile && 32 * q < N) {
+  tc_cp_wait_all();
+  if constexpr (DB) {
+    // column sums of the pass: one warp reduction per column, this warp's shared slot
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        float a = gA[DB ? c : 0][y], bb = gB[DB ? c : 0][y];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+        }
+        if (lane == 0) {
+          const int j = half * HALF + 16 * c + y;
+          sacc[(warp * 2 + 0) * NT + j] = a;
+          sacc[(warp * 2 + 1) * NT + j] = bb;
+        }
+      }
+  }
+  // partial Gram from TMEM: D_g lane j, column k -> out[k*N + j] / zs_j (the condition is
+  // uniform within a warp: tcgen05.ld is warp-collective)
+  if (Qb > 0 && 32 * qd < N) {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-      const int j0 = half * HALF + 16 * c;
+      const int k0 = half * HALF + 16 * c;
       float v[16];
-      tmem_ld16(d_g + ((uint32_t)(32 * q) << 16) + j0, v);
+      tmem_ld16(d_g + ((uint32_t)(32 * qd) << 16) + k0, v);
       if (rt < N) {
+        const float inv = 1.f / zs[rt];
 #pragma unroll
         for (int y = 0; y < 16; ++y)
-          if (j0 + y < N) out[rt * N + j0 + y] = (double)(v[y] / zs[j0 + y]);
+          if (k0 + y < N) out[(k0 + y) * N + rt] = (double)(v[y] * inv);
       }
     }
-  } else if (first_tile) {
+  } else if (Qb == 0) {
     for (int e = t; e < N * N; e += kThreads) out[e] = 0.0;
   }
   tc_fence_before();
   __syncthreads();
   if (t < N) {
     const int h = t / HALF;
-    double a = 0.0, b = 0.0;
+    double a = 0.0, bb = 0.0;
     for (int w = 4 * h; w < 4 * h + 4; ++w) {
       a += (double)sacc[(w * 2 + 0) * NT + t];
-      b += (double)sacc[(w * 2 + 1) * NT + t];
+      bb += (double)sacc[(w * 2 + 1) * NT + t];
     }
     out[N * N + t] = a;
-    out[N * N + N + t] = b;
+    out[N * N + N + t] = bb;
   }
   __syncthreads();
+}
+
+// The tile images of the tensor-core pass, from the double-float HA: for CTA b (rows
+// [b rows_per, ...)) and its tile q (128 rows), at ((b qmax + q) 2 TM) 128 NT elements:
+// [Au hi | Au lo | Ag hi | Ag lo]; Au(r, k) = core_idx(r, k, NT), Ag(k, r) = core_idx(k, r, 128).
+// hi = round(HA), lo = round(HA - hi) in T16. Entries outside [0, m) x [0, N) are never
+// written (the buffer is zeroed once when the handle is created).
+template <typename T16, int TERMS>
+__global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N, int NT, int64_t rows_per,
+                                 int qmax, T16* __restrict__ img) {
+  constexpr int TM = TERMS == 3 ? 2 : 1;
+  const int64_t tile = (int64_t)2 * TM * kTR * NT;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    const int k = (int)(e % N);
+    const int64_t b = i / rows_per, l = i - b * rows_per;
+    const int q = (int)(l / kTR), r = (int)(l % kTR);
+    T16* base = img + (b * qmax + q) * tile;
+    const df32 h = HAdf[e];
+    const T16 hi = H16<T16>::from(h.hi);
+    base[core_idx(r, k, NT)] = hi;
+    base[(int64_t)TM * kTR * NT + core_idx(k, r, kTR)] = hi;
+    if (TM == 2) {
+      const T16 lo = H16<T16>::from((h.hi - (float)hi) + h.lo);
+      base[(int64_t)kTR * NT + core_idx(r, k, NT)] = lo;
+      base[(int64_t)3 * kTR * NT + core_idx(k, r, kTR)] = lo;
+    }
+  }
 }
 
 // Stage T^T/(N-1) scaled per column (ts_j = 1/rms_k(T_kj/(N-1))) into the B operand of the
@@ -335,7 +475,8 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
 struct MixedParams {
   int64_t m;
   int N;
-  const void* HA16;
+  const void* HA16;   // tile images of HA (tc_images_kernel)
+  int qmax;           // tiles per CTA row block in the images
   const float* HA32;
   const df32* HAdf;
   const df32* Ddf;
@@ -387,15 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   float* s_itol = s_beta_v + NT;   // per-column inner-solve reduction factor
   double* scratch = reinterpret_cast<double*>(smem + scalar_bytes<NT>());
   unsigned char* uni = smem + scalar_bytes<NT>() + kThreads * 8;
-  // tensor-core operands (inside the union; the FP32 refresh passes reuse the same bytes)
-  constexpr int TM = TERMS == 3 ? 2 : 1;   // hi (+ lo) copies of every operand tile
-  T16* sAu = reinterpret_cast<T16*>(uni);
-  T16* sBu = sAu + TM * kTR * NT;
-  T16* sAg = sBu + TM * NT * NT;
-  T16* sBg = sAu;   // the z operand of the Gram MMA is written after the u MMA has read sAu
-  float* sacc = reinterpret_cast<float*>(sAg + TM * kTR * kTR);
-  float* s_zs = sacc + 8 * 2 * NT;
-  float* s_ts = s_zs + NT;
+  // tensor-core operands (inside the union; the refresh passes reuse the same bytes)
+  using TL = TcLayout<NT, TERMS>;
+  T16* sBu = reinterpret_cast<T16*>(uni + TL::off_bu);
+  float* s_zs = reinterpret_cast<float*>(uni + TL::off_zs);
+  float* s_ts = reinterpret_cast<float*>(uni + TL::off_ts);
 
   const int N = p.N, G = gridDim.x, b = blockIdx.x, t = threadIdx.x, warp = t >> 5;
   const int64_t rows_per = (p.m + G - 1) / G;
@@ -405,8 +542,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   GridBarrier bar{p.bar, reinterpret_cast<int*>(p.bar + 1), p.status, (unsigned)G, 0u};
   const double inv_nm1 = 1.0 / (double)(N - 1);
   double* Tp = p.Tpart + (int64_t)b * NE;
-  const T16* HAhi = static_cast<const T16*>(p.HA16);
-  const T16* HAlo = HAhi + p.m * (int64_t)N;
+  // this CTA's tile images (tc_images_kernel uses the same row blocks)
+  const T16* img = static_cast<const T16*>(p.HA16) + (size_t)b * p.qmax * (2 * TL::TM * kTR * NT);
   constexpr int TMC = tc_tmem_cols<NT>();
 
   if (t == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); }
@@ -469,6 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     __syncthreads();
     int it = 0;
     for (;;) {
+      int my_active = 0;
       if (t < NT) {
         int a = s_active[t];
         const double gm = s_gam[t];
@@ -496,18 +634,12 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
         s_alpha_v[t] = (float)al;
         s_beta_v[t] = (float)be;
         s_zs[t] = (t < N && gm > 0.0) ? (float)(1.0 / sqrt(gm)) : 1.f;
+        my_active = a;
       }
-      __syncthreads();
-      if (t == 0) {
-        int any = 0;
-        for (int j = 0; j < N; ++j) any |= s_active[j];
-        s_flag[0] = any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter;
-      }
-      __syncthreads();
-      if (!s_flag[0]) break;
-      passF_tc<T16, NT, PC, TERMS>(HAhi, HAlo, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
-                                   s_beta_v, s_zs, s_ts, sAu, sBu, sAg, sBg, sacc, tmem, &mbar[0],
-                                   &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+      const int any = __syncthreads_or(my_active);
+      if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
+      passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+                                    s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       if (!(ok = bar.sync() && ok)) break;
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
       if (!(ok = bar.sync())) break;
@@ -560,14 +692,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       it_next = fmax(it_next, fmax(p.inner_tol, p.itol_floor));
       s_itol[t] = (float)fmin(it_next, 0.5);
     }
-    __syncthreads();
-    if (t == 0) {
-      int all = 1;
-      for (int j = 0; j < N; ++j) all &= s_done[j];
-      s_flag[1] = all || total >= p.max_iter;
-    }
-    __syncthreads();
-    if (s_flag[1]) break;
+    const int all_done = __syncthreads_and(t >= N || s_done[t]);
+    if (all_done || total >= p.max_iter) break;
   }
 
   if (b == 0 && t < N) {
@@ -584,7 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
 }
 
 template <int NT, int TERMS> __host__ __device__ constexpr int mixed_smem_bytes() {
-  constexpr int u = refresh_union_bytes<NT>() > tc_bytes<NT, TERMS>() ? refresh_union_bytes<NT>() : tc_bytes<NT, TERMS>();
+  constexpr int tcb = TcLayout<NT, TERMS>::bytes;
+  constexpr int u = refresh_union_bytes<NT>() > tcb ? refresh_union_bytes<NT>() : tcb;
   return scalar_bytes<NT>() + kThreads * 8 + u;
 }
 

@@ -152,3 +152,9 @@ def test_decoded_residual_lies_in_span_of_HA():
     res = D - (HA @ (HA.T @ Z0) / (N - 1) + r[:, None] * Z0)
     coef, *_ = np.linalg.lstsq(HA, res, rcond=None)
     assert np.max(np.abs(HA @ coef - res)) < 1e-10 * np.max(np.abs(res))
+    # and it equals the N x N form the decoder uses
+    assert np.max(np.abs(ows_start_residual(HA, D, r, C) - res)) < 1e-10 * np.max(np.abs(res))
+
+
+def ows_start_residual(HA, D, r, C):
+    return ws.start_residual(HA, D, r, C)
