@@ -206,7 +206,7 @@ def run_ours(args):
     seed = args.seed + 1000 * rank
     p = synth.workload(WORKLOAD, seed, dtype=np.float32)
     n, m, N = p.n, p.m, p.N
-    an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8,
+    an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision=args.precision, tol=1e-8,
                        precondition=args.precondition)
     an.set_phase_timing(True)
     Xf = torch.from_numpy(p.Xf).to(dev)
@@ -325,19 +325,21 @@ def run_ours(args):
     solve_avg_ms = float(np.mean(solve_ms))
     peak, peak_src = _peaks()
     achieved = alg_bytes / (solve_avg_ms / 1e3) / 1e9
-    tr = NCU_TRAFFIC.get("fp32", {})
+    tr = NCU_TRAFFIC.get(args.precision, {})
     traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash() else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64,1>",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64,1>" if args.precision == "fp32" else f"solve_mixed_kernel<{args.precision},64>",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_ms": solve_avg_ms, "cg_iterations": it_avg, "fp64_refreshes": ref_avg}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
-                       "precision": "fp32 CG + double-float residual refresh",
+                       "precision": {"fp32": "fp32 CG + double-float residual refresh",
+                                     "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
+                                     "bf16": "BF16 hi/lo tensor-core contractions (tcgen05) + double-float refresh"}[args.precision],
                        "solver": "CG preconditioned by R" if args.precondition else "plain CG",
                        "l2": "flushed between steps", "status": last_status["status"]},
             "error": {"rel_frobenius_vs_fp64_oracle": err, "fp64_cg_rel_frobenius": err64,
@@ -576,6 +578,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="inner-solve precision of the timed path (default workload)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD, MIXED_WORKLOAD])
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")

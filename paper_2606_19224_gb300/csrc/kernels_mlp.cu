@@ -69,7 +69,7 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 // ------------------------------------------------------------------ tiled FP32 GEMM
 // C[M][N] = sum_k A(m, k) B(k, n) with A(m, k) = A[m * sam + k * sak] and
 // B(k, n) = B[k * sbk + n * sbn], and a fused epilogue.
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBM = 64, GBN = 64, GBK = 32;
 
 enum : int { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_BWD = 2, EPI_STORE = 3 };
 
@@ -511,6 +511,9 @@ __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __re
     sC[k * LD + j] = C[e];
     sE[k * LD + j] = Ecoef[e];
   }
+  // thread (column j, group g of RB consecutive rows of the 16-row block): the C and E entries
+  // of column j are loaded once per k for RB rows
+  const int RB = (16 * N + kThreads - 1) / kThreads;   // rows per thread: 4 (N = 64), 8 (N = 128), 2 (N = 32)
   for (int64_t ib = (int64_t)blockIdx.x * 16; ib < m; ib += (int64_t)gridDim.x * 16) {
     __syncthreads();
     for (int e = t; e < 16 * N; e += kThreads) {
@@ -519,19 +522,30 @@ __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __re
       sHt[ii * LD + k] = i < m ? HA[i * N + k] : 0.f;
     }
     __syncthreads();
-    for (int e = t; e < 16 * N; e += kThreads) {
-      const int ii = e / N, j = e % N;
-      const int64_t i = ib + ii;
-      if (i >= m) continue;
-      float a1 = 0.f, a2 = 0.f;
+    const int NGR = (16 + RB - 1) / RB;   // row groups covering the 16 rows
+    for (int e = t; e < N * NGR; e += kThreads) {
+      const int j = e % N, g = e / N;
+      float a1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, a2[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int k = 0; k < N; ++k) {
-        const float h = sHt[ii * LD + k];
-        a1 = fmaf(h, sC[k * LD + j], a1);
-        a2 = fmaf(h, sE[k * LD + j], a2);
+        const float c = sC[k * LD + j], ev = sE[k * LD + j];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          if (x < RB && g * RB + x < 16) {
+            const float h = sHt[(g * RB + x) * LD + k];
+            a1[x] = fmaf(h, c, a1[x]);
+            a2[x] = fmaf(h, ev, a2[x]);
+          }
+        }
       }
-      const float z = ((float)D[i * N + j] - a1) / r32[i];
-      Z0[i * N + j] = df32(z, 0.f);
-      B[i * N + j] = a2;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const int64_t i = ib + g * RB + x;
+        if (x < RB && g * RB + x < 16 && i < m) {
+          const float z = ((float)D[i * N + j] - a1[x]) / r32[i];
+          Z0[i * N + j] = df32(z, 0.f);
+          B[i * N + j] = a2[x];
+        }
+      }
     }
   }
 }
@@ -563,7 +577,7 @@ static cudaError_t warm_alloc(enkf_handle_s* h, int K) {
   const int N = h->cfg.N;
   cudaError_t e = cudaSuccess;
   if (!w.part) {
-    w.nparts = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)h->sms, (h->cfg.m + 255) / 256));
+    w.nparts = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms, (h->cfg.m + 255) / 256));
     e = cudaMalloc((void**)&w.part, sizeof(double) * (size_t)w.nparts * 2 * N * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.gsum, sizeof(double) * 2 * N * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.C, sizeof(float) * N * N);

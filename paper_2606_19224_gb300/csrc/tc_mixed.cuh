@@ -135,8 +135,12 @@ template <int NT, int TERMS> struct TcLayout {
   static constexpr int end_bg = DB ? off_bg + TM * BGP : off_ag + n_ag * TM * AG * 2;
   static constexpr int off_sacc = end_bg;
   static constexpr int off_zs = off_sacc + 4 * (8 * 2 * NT);
-  static constexpr int off_ts = off_zs + 4 * NT;
-  static constexpr int bytes = off_ts + 4 * NT;
+  static constexpr int off_ts = off_zs + 4 * NT;   // ts [NT] then 1/ts [NT]
+  // NT <= 64: the tile's u = HA T read out of TMEM, staged as FP32 [128][NT] (swizzled 4-float
+  // groups) for the coalesced epilogue; it reuses the Au bytes when they are large enough
+  static constexpr bool U_ALIAS = TM * AU * 2 >= kTR * NT * 4;
+  static constexpr int off_u = U_ALIAS ? off_au : off_ts + 8 * NT;
+  static constexpr int bytes = (DB && !U_ALIAS) ? off_u + kTR * NT * 4 : off_ts + 8 * NT;
   static_assert(DB || TM * BGP <= TM * AU * 2, "z operand must fit in the Au region");
 };
 
@@ -275,7 +279,7 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
 #pragma unroll
       for (int y = 0; y < 16; ++y) {
         const int j = j0 + y;
-        const float uu = u[y] / ts[j];
+        const float uu = u[y] * ts[NT + j];
         const float zz = PC ? rr[y] * rinv : rr[y];
         const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
         const float be = beta[j], al = alpha[j];
@@ -411,6 +415,225 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
   __syncthreads();
 }
 
+// NT <= 64: the same step with a coalesced epilogue. The tile's u = HA T leaves TMEM row by
+// row (thread = row) into an FP32 staging tile (4-float groups XOR-swizzled by row, so both
+// the row-wise writes and the group-wise reads are free of bank conflicts); the CG update
+// then runs with NT/4 threads per row on 16-byte column groups, so the loads and stores of
+// r, p, S p and x are contiguous 256-byte row segments, and each thread keeps the (r, z) and
+// (r, r) sums of its four columns in registers for the whole pass.
+template <typename T16, int NT, bool PC, int TERMS>
+__device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t row1, int N, float* X,
+                            float* Res, float* P, float* Sv, const float* __restrict__ rv,
+                            const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
+                            uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g,
+                            int* status, bool& ok, double* __restrict__ out) {
+  using L = TcLayout<NT, TERMS>;
+  static_assert(L::DB, "NT <= 64 only");
+  constexpr bool SPLIT = TERMS == 3;
+  constexpr int TM = L::TM;
+  constexpr uint32_t idesc = umma_idesc(H16<T16>::fmt, NT);
+  constexpr int HALF = NT / 2, CH = HALF / 16;    // TMEM read-out: columns per warp half
+  constexpr int NG = NT / 4, GM = NG - 1;         // 4-float column groups, swizzle mask
+  constexpr int NJ = NG, RI = kThreads / NJ;      // update: threads per row, rows per sweep
+  constexpr int TILE = 2 * TM * kTR * NT;
+  constexpr int AUB = TM * kTR * NT * 2, AGB = TM * NT * kTR * 2;
+  T16* sAu = reinterpret_cast<T16*>(tcs + L::off_au);
+  const T16* sBu = reinterpret_cast<const T16*>(tcs + L::off_bu);
+  unsigned char* sAg0 = tcs + L::off_ag;
+  unsigned char* sBg = tcs + L::off_bg;
+  float* sU = reinterpret_cast<float*>(tcs + L::off_u);
+  const float* zs = reinterpret_cast<const float*>(tcs + L::off_zs);
+  const float* ts = reinterpret_cast<const float*>(tcs + L::off_ts);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int qd = warp & 3, half = warp >> 2;
+  const int rt = 32 * qd + lane;
+  const int tj = t % NJ, ti = t / NJ, j0 = 4 * tj;
+  const uint32_t d_u = tmem, d_g = tmem + NT;
+  const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
+  const unsigned char* gimg = reinterpret_cast<const unsigned char*>(img);
+  auto au_src = [&](int q) { return gimg + (size_t)q * TILE * 2; };
+  auto ag_src = [&](int q) { return gimg + (size_t)q * TILE * 2 + AUB; };
+  auto sAg = [&](int q) { return sAg0 + (q & 1) * AGB; };
+  auto bg_ptr = [&](int part, int j, int i) {
+    return reinterpret_cast<T16*>(sBg + part * L::BGP + (j >> 3) * L::SBOG + (i >> 3) * L::LBOG +
+                                  (((j & 7) * 8 + (i & 7)) * 2));
+  };
+  // per-column constants of the thread's four columns
+  float al[4], be[4], tsi[4], zsc[4];
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    al[y] = alpha[j0 + y];
+    be[y] = beta[j0 + y];
+    tsi[y] = ts[NT + j0 + y];
+    zsc[y] = zs[j0 + y];
+  }
+  // rows j in [NT, 128) of the z operand stay zero for the whole pass
+  for (int e = t; e < TM * (kTR - NT) * kTR; e += kThreads) {
+    const int part = e / ((kTR - NT) * kTR), rem = e % ((kTR - NT) * kTR);
+    *bg_ptr(part, NT + rem / kTR, rem % kTR) = H16<T16>::from(0.f);
+  }
+  float sg[4] = {0.f, 0.f, 0.f, 0.f}, sr[4] = {0.f, 0.f, 0.f, 0.f};
+  if (Qb > 0) {
+    tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), AUB);
+    tc_copy(sAg(0), ag_src(0), AGB);
+    tc_cp_commit();
+  }
+  const bool vec = (N & 3) == 0;
+  for (int q = 0; q < Qb && ok; ++q) {
+    const int64_t i0 = row0 + (int64_t)q * kTR;
+    tc_cp_wait_all();
+    fence_async_smem();
+    __syncthreads();
+    if (q + 1 < Qb) {   // next tile's Ag into the other buffer, behind this whole tile
+      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
+      tc_cp_commit();
+    }
+    if (t == 0) {
+      tc_fence_after();
+      constexpr uint32_t sbo_u = (NT / 8) * 128;
+      const uint32_t au = smem_addr(sAu), bu = smem_addr(sBu);
+#pragma unroll
+      for (int kb = 0; kb < NT / 16; ++kb) {
+        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
+        if (SPLIT) {
+          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
+          umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
+        }
+      }
+      umma_commit(mbar_u);
+    }
+    if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
+    ph_u ^= 1u;
+    tc_fence_after();
+    // u out of TMEM, one row per thread, into the swizzled staging tile
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int jc = half * HALF + 16 * c;
+      float v[16];
+      tmem_ld16(d_u + ((uint32_t)(32 * qd) << 16) + jc, v);
+#pragma unroll
+      for (int g4 = 0; g4 < 4; ++g4) {
+        const int pg = ((jc >> 2) + g4) ^ (rt & GM);
+        *reinterpret_cast<float4*>(sU + rt * NT + pg * 4) =
+            make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // the CG update, NT/4 threads per row
+    for (int r = ti; r < kTR; r += RI) {
+      const int64_t i = i0 + r;
+      const bool valid = i < row1 && j0 < N;
+      const float4 u4 = *reinterpret_cast<const float4*>(sU + r * NT + ((tj ^ (r & GM)) * 4));
+      float rr[4] = {0.f, 0.f, 0.f, 0.f}, pp[4] = {0.f, 0.f, 0.f, 0.f};
+      float ss[4] = {0.f, 0.f, 0.f, 0.f}, xx[4] = {0.f, 0.f, 0.f, 0.f};
+      float ri = 1.f;
+      if (valid) {
+        ld4<float>(rr, Res + i * N, j0, N, vec);
+        ld4<float>(pp, P + i * N, j0, N, vec);
+        ld4<float>(ss, Sv + i * N, j0, N, vec);
+        ld4<float>(xx, X + i * N, j0, N, vec);
+        ri = rv[i];
+      }
+      const float rinv = 1.f / ri;
+      const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+      float pn[4], sn[4], xn[4], rn[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const float uu = uv[y] * tsi[y];
+        const float zz = PC ? rr[y] * rinv : rr[y];
+        const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
+        pn[y] = be[y] == 0.f ? zz : fmaf(be[y], pp[y], zz);
+        sn[y] = be[y] == 0.f ? ww : fmaf(be[y], ss[y], ww);
+        xn[y] = fmaf(al[y], pn[y], xx[y]);
+        rn[y] = fmaf(-al[y], sn[y], rr[y]);
+        const float zn = PC ? rn[y] * rinv : rn[y];
+        const bool live = valid && j0 + y < N;
+        if (live) {
+          sg[y] = PC ? fmaf(rn[y], zn, sg[y]) : fmaf(ri * rn[y], rn[y], sg[y]);
+          sr[y] = fmaf(rn[y], rn[y], sr[y]);
+        }
+        const float zv = live ? zn * zsc[y] : 0.f;
+        const T16 zh = H16<T16>::from(zv);
+        *bg_ptr(0, j0 + y, r) = zh;
+        if (SPLIT) *bg_ptr(1, j0 + y, r) = H16<T16>::from(zv - (float)zh);
+      }
+      if (valid) {
+        st4<float>(P + i * N, j0, N, vec, pn);
+        st4<float>(Sv + i * N, j0, N, vec, sn);
+        st4<float>(X + i * N, j0, N, vec, xn);
+        st4<float>(Res + i * N, j0, N, vec, rn);
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    if (q + 1 < Qb) {   // Au (and the u staging on it) is free: next tile's Au behind the Gram MMA
+      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
+      tc_cp_commit();
+    }
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t ag = smem_addr(sAg(q)), bg = smem_addr(sBg);
+      constexpr uint32_t sbo_a = 16 * 128;
+#pragma unroll
+      for (int kb = 0; kb < kTR / 16; ++kb) {
+        const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+        const uint64_t B0 = umma_desc(ag + kb * 256, 128, sbo_a);
+        umma_f16(d_g, A0, B0, idesc, (q == 0 && kb == 0) ? 0u : 1u);
+        if (SPLIT) {
+          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B1 = umma_desc(ag + L::AG * 2 + kb * 256, 128, sbo_a);
+          umma_f16(d_g, A0, B1, idesc, 1u);
+          umma_f16(d_g, A1, B0, idesc, 1u);
+        }
+      }
+      umma_commit(mbar_g);
+    }
+    if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
+    ph_g ^= 1u;
+    tc_fence_after();
+  }
+  tc_cp_wait_all();
+  // partial Gram from TMEM: lane j, column k -> out[k*N + j] / zs_j (warp-uniform condition)
+  if (Qb > 0 && 32 * qd < N) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k0 = half * HALF + 16 * c;
+      float v[16];
+      tmem_ld16(d_g + ((uint32_t)(32 * qd) << 16) + k0, v);
+      if (rt < N) {
+        const float inv = 1.f / zs[rt];
+#pragma unroll
+        for (int y = 0; y < 16; ++y)
+          if (k0 + y < N) out[(k0 + y) * N + rt] = (double)(v[y] * inv);
+      }
+    }
+  } else if (Qb == 0) {
+    for (int e = t; e < N * N; e += kThreads) out[e] = 0.0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  // column sums: the RI row sweeps of each column, in a fixed order (the z region is free)
+  double* red = reinterpret_cast<double*>(sBg);
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    red[ti * NT + j0 + y] = (double)sg[y];
+    red[RI * NT + ti * NT + j0 + y] = (double)sr[y];
+  }
+  __syncthreads();
+  if (t < N) {
+    double a = 0.0, bb = 0.0;
+    for (int qq = 0; qq < RI; ++qq) {
+      a += red[qq * NT + t];
+      bb += red[RI * NT + qq * NT + t];
+    }
+    out[N * N + t] = a;
+    out[N * N + N + t] = bb;
+  }
+  __syncthreads();
+}
+
 // The tile images of the tensor-core pass, from the double-float HA: for CTA b (rows
 // [b rows_per, ...)) and its tile q (128 rows), at ((b qmax + q) 2 TM) 128 NT elements:
 // [Au hi | Au lo | Ag hi | Ag lo]; Au(r, k) = core_idx(r, k, NT), Ag(k, r) = core_idx(k, r, 128).
@@ -459,6 +682,7 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
     tn2[t] = s;
     const double rms = sqrt(s / (double)(N > 0 ? N : 1)) * inv;
     ts[t] = (t < N && rms > 0.0) ? (float)(1.0 / rms) : 1.f;
+    ts[NT + t] = (t < N && rms > 0.0) ? (float)rms : 1.f;   // 1/ts: undoes the scale on u
   }
   __syncthreads();
   for (int e = t; e < NT * NT; e += kThreads) {
@@ -638,8 +862,12 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       }
       const int any = __syncthreads_or(my_active);
       if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
-      passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
-                                    s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+      if constexpr (NT <= 64)
+        passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+                                        s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+      else
+        passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+                                      s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       if (!(ok = bar.sync() && ok)) break;
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
       if (!(ok = bar.sync())) break;
