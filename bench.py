@@ -351,7 +351,8 @@ def run_ours(args):
                               "iters": s_plain["iters_max"], "refinements": s_plain["refinements"]},
             "roofline": roofline,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            # innovations, (tile images of HA for the tensor-core path,) solve, update
+            "gpu_launches": (3 if args.precision == "fp32" else 4) * args.steps,
             "clocks": clk}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, E)
@@ -376,7 +377,7 @@ def run_batched(args):
     import synth
     ws, rank, local = _dist()
     seed = args.seed + 1000 * rank
-    specs = synth.problems.batched_problem_specs(256, seed)
+    specs = synth.problems.batched_problem_specs(args.batch_count, seed)
     t0 = time.time()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any GPU call
         probs = pool.map(_gen_problem, [(sp, seed, i) for i, sp in enumerate(specs)])
@@ -565,7 +566,7 @@ def run_mixed(args):
             "config": {"workload": MIXED_WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
                        "precision": "BF16 hi/lo split operands on tcgen05, FP32 accumulation, double-float refresh",
                        "l2": "flushed between steps"},
-            "variants": res, "gpu_launches": 3 * args.steps, "clocks": clk}
+            "variants": res, "gpu_launches": 4 * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -580,6 +581,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="inner-solve precision of the timed path (default workload)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="problems of the batched workload (256 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD, MIXED_WORKLOAD])
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")

@@ -41,10 +41,12 @@ template <typename CT, int NT> __host__ __device__ constexpr int passF_bytes() {
   constexpr int LD = NT + 16 / (int)sizeof(CT), TR = FTile<CT, NT>::TR;
   return NT * LD * (int)sizeof(CT) + 5 * TR * LD * (int)sizeof(CT) + TR * (int)sizeof(CT);
 }
-// FP32 solves with NT <= 64 use the double-buffered fused pass (passF_async)
+// FP32 solves use the double-buffered fused pass (passF_async)
 template <typename VT, int NT> __host__ __device__ constexpr bool async_passF() {
-  return sizeof(VT) == 4 && NT <= 64;
+  return sizeof(VT) == 4;
 }
+// NT = 128: x is read into registers instead of staged, so that two tiles fit in shared memory
+template <int NT> __host__ __device__ constexpr bool async_xreg() { return NT == 128; }
 template <int NT> __host__ __device__ constexpr int passF_async_bytes();
 template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
   constexpr int f = async_passF<VT, NT>() ? passF_async_bytes<NT>() : passF_bytes<VT, NT>();
@@ -679,8 +681,8 @@ template <int K> __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <int NT> __host__ __device__ constexpr int passF_async_bytes() {
-  constexpr int LD = NT + 4, TR = FTile<float, NT>::TR;
-  return NT * LD * 4 + 2 * (5 * TR * LD + TR) * 4;
+  constexpr int LD = NT + 4, TR = FTile<float, NT>::TR, NS = async_xreg<NT>() ? 4 : 5;
+  return NT * LD * 4 + 2 * (NS * TR * LD + TR) * 4;
 }
 
 template <int NT, bool PC>
@@ -694,7 +696,9 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
   constexpr int NJ = NT / 4, NI = kThreads / NJ;
   static_assert(NI * MR == TR, "fused tile");
   constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
-  constexpr int BUF = 5 * TR * LD + TR;   // floats per buffer
+  constexpr bool XREG = async_xreg<NT>();
+  constexpr int NS = XREG ? 4 : 5;          // staged arrays: HA, r, p, S p (, x)
+  constexpr int BUF = NS * TR * LD + TR;   // floats per buffer
   float* const buf0 = reinterpret_cast<float*>(tiles);
   const int t = threadIdx.x;
   const int tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * MR;
@@ -722,11 +726,11 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
       cp_async16(sb + 1 * TR * LD + ii * LD + c0, Res + off, ok);
       cp_async16(sb + 2 * TR * LD + ii * LD + c0, P + off, ok);
       cp_async16(sb + 3 * TR * LD + ii * LD + c0, Sv + off, ok);
-      cp_async16(sb + 4 * TR * LD + ii * LD + c0, X + off, ok);
+      if (!XREG) cp_async16(sb + 4 * TR * LD + ii * LD + c0, X + off, ok);
     }
     if (t < TR) {
       const int64_t i = i0 + t;
-      cp_async4(sb + 5 * TR * LD + t, rv + (i < row1 ? i : row0), i < row1);
+      cp_async4(sb + NS * TR * LD + t, rv + (i < row1 ? i : row0), i < row1);
     }
     cp_async_commit();
   };
@@ -746,8 +750,22 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
     float* sR = buf0 + b * BUF + TR * LD;
     const float* sP = sR + TR * LD;
     const float* sS = sP + TR * LD;
-    const float* sX = sS + TR * LD;
-    const float* sRv = sX + TR * LD;
+    const float* sX = sS + TR * LD;                      // (NS == 5 only)
+    const float* sRv = sS + (NS - 3) * TR * LD;
+    // NT = 128: the thread's x fragment straight from global, in flight during the contraction
+    float xg[MR][4];
+    if (XREG) {
+#pragma unroll
+      for (int x = 0; x < MR; ++x) {
+        const int64_t i = i0 + r0 + x;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) xg[x][y] = 0.f;
+        if (i < row1 && j0 < N) {
+          const float4 v = *reinterpret_cast<const float4*>(X + i * N + j0);
+          xg[x][0] = v.x; xg[x][1] = v.y; xg[x][2] = v.z; xg[x][3] = v.w;
+        }
+      }
+    }
     // u = HA T (the 1/(N-1) is applied below); four k per step from float4 rows of HA
     float acc[MR][4];
 #pragma unroll
@@ -782,7 +800,8 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
         const float4 rv4 = *reinterpret_cast<const float4*>(sR + row * LD + j0);
         const float4 pv4 = *reinterpret_cast<const float4*>(sP + row * LD + j0);
         const float4 sv4 = *reinterpret_cast<const float4*>(sS + row * LD + j0);
-        const float4 xv4 = *reinterpret_cast<const float4*>(sX + row * LD + j0);
+        const float4 xv4 = XREG ? make_float4(xg[x][0], xg[x][1], xg[x][2], xg[x][3])
+                                : *reinterpret_cast<const float4*>(sX + row * LD + j0);
         const float rvv[4] = {rv4.x, rv4.y, rv4.z, rv4.w}, pvv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
         const float svv[4] = {sv4.x, sv4.y, sv4.z, sv4.w}, xvv[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
         const float rinv = PC ? 1.f / ri : 0.f;
