@@ -97,18 +97,37 @@ __global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs g) {
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   float acc[TM][TM] = {};
-  for (int k0 = 0; k0 < g.K; k0 += GBK) {
-    for (int e = t; e < BM * GBK; e += 256) {
-      const int mm = e / GBK, kk = e % GBK;
+  // the next k-step's operands are loaded into registers while the current one is computed
+  constexpr int LA = BM * GBK / 256, LB = GBK * BN / 256;
+  float ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = t + q * 256, mm = e / GBK, kk = e % GBK;
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : 0.f;
+      ra[q] = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : 0.f;
     }
-    for (int e = t; e < GBK * BN; e += 256) {
-      const int kk = e / BN, nn = e % BN;
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = t + q * 256, kk = e / BN, nn = e % BN;
       const int k = k0 + kk, n = n0 + nn;
-      Bs[kk][nn] = (k < g.K && n < g.N) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.f;
+      rb[q] = (k < g.K && n < g.N) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.f;
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = t + q * 256;
+      As[e % GBK][e / GBK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = t + q * 256;
+      Bs[e / BN][e % BN] = rb[q];
     }
     __syncthreads();
+    if (k0 + GBK < g.K) fetch(k0 + GBK);
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
       float a[TM], b[TM];
@@ -367,35 +386,48 @@ __global__ void __launch_bounds__(kThreads) warm_gram_kernel(const float* __rest
                                                              const double* __restrict__ D,
                                                              const float* __restrict__ r32, int64_t m, int N,
                                                              int64_t rows_per, double* __restrict__ part) {
-  constexpr int NT = 16 * AM, RW = AM == 8 ? kWarmRows / 2 : kWarmRows;   // static smem < 48 KB
-  __shared__ float sH[RW][NT + 1];
-  __shared__ float sD[RW][NT + 1];
-  __shared__ float sHr[RW][NT + 1];
+  constexpr int NT = 16 * AM, LD = NT + 4, RW = AM == 8 ? kWarmRows / 2 : kWarmRows;   // static smem < 48 KB
+  __shared__ __align__(16) float sH[RW][LD];
+  __shared__ __align__(16) float sD[RW][LD];
+  __shared__ __align__(16) float sHr[RW][LD];
+  __shared__ float sRi[RW];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per, i1 = imin64(m, i0 + rows_per);
-  const int tk = t / 16, tj = t % 16;
+  // thread (tk, tj) owns the AM x AM block k in [AM tk, AM tk + AM), j in [AM tj, AM tj + AM)
+  const int tk = t / 16, tj = t % 16, k0 = AM * tk, c0 = AM * tj;
   float acc[AM][AM] = {}, accG[AM][AM] = {};
   for (int64_t ib = i0; ib < i1; ib += RW) {
+    __syncthreads();
+    if (t < RW) {
+      const int64_t i = ib + t;
+      sRi[t] = i < i1 ? 1.f / r32[i] : 0.f;
+    }
     __syncthreads();
     for (int e = t; e < RW * NT; e += kThreads) {
       const int ii = e / NT, k = e % NT;
       const int64_t i = ib + ii;
       const bool in = i < i1 && k < N;
-      const float rinv = in ? 1.f / r32[i] : 0.f;
+      const float rinv = sRi[ii];
       const float h = in ? HA[i * N + k] : 0.f;
       sH[ii][k] = h;
       sHr[ii][k] = h * rinv;
       sD[ii][k] = in ? (float)D[i * N + k] * rinv : 0.f;
     }
     __syncthreads();
+#pragma unroll 4
     for (int ii = 0; ii < RW; ++ii) {
       float h[AM], d[AM], hr[AM];
 #pragma unroll
-      for (int a = 0; a < AM; ++a) h[a] = sH[ii][tk + 16 * a];
-#pragma unroll
-      for (int c = 0; c < AM; ++c) {
-        d[c] = sD[ii][tj + 16 * c];
-        hr[c] = sHr[ii][tj + 16 * c];
+      for (int a = 0; a < AM; a += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(&sH[ii][k0 + a]);
+        h[a] = v.x;
+        h[a + 1] = v.y;
+        const float2 w = *reinterpret_cast<const float2*>(&sD[ii][c0 + a]);
+        d[a] = w.x;
+        d[a + 1] = w.y;
+        const float2 q = *reinterpret_cast<const float2*>(&sHr[ii][c0 + a]);
+        hr[a] = q.x;
+        hr[a + 1] = q.y;
       }
 #pragma unroll
       for (int a = 0; a < AM; ++a)
@@ -411,7 +443,7 @@ __global__ void __launch_bounds__(kThreads) warm_gram_kernel(const float* __rest
   for (int a = 0; a < AM; ++a)
 #pragma unroll
     for (int c = 0; c < AM; ++c) {
-      const int k = tk + 16 * a, j = tj + 16 * c;
+      const int k = k0 + a, j = c0 + c;
       if (k < N && j < N) {
         out[k * N + j] = acc[a][c];
         out[N * N + k * N + j] = accG[a][c];
@@ -494,6 +526,7 @@ __global__ void __launch_bounds__(128) warm_coef_kernel(const float* __restrict_
 // Decoder: z0[i][j] = (d_ij - sum_k HA[i][k] C[k][j]) / r_i as the double-float starting solution
 // of the FP32 solve, and its residual B[i][j] = sum_k HA[i][k] E[k][j] as the first inner
 // right-hand side (FP32; the refreshes recompute the true residual in double-float).
+template <int RB>
 __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __restrict__ HA,
                                                                const double* __restrict__ D,
                                                                const float* __restrict__ r32, int64_t m, int N,
@@ -512,8 +545,7 @@ __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __re
     sE[k * LD + j] = Ecoef[e];
   }
   // thread (column j, group g of RB consecutive rows of the 16-row block): the C and E entries
-  // of column j are loaded once per k for RB rows
-  const int RB = (16 * N + kThreads - 1) / kThreads;   // rows per thread: 4 (N = 64), 8 (N = 128), 2 (N = 32)
+  // of column j are loaded once per k for RB rows (RB = 2, 4, 8 for N <= 32, 64, 128)
   for (int64_t ib = (int64_t)blockIdx.x * 16; ib < m; ib += (int64_t)gridDim.x * 16) {
     __syncthreads();
     for (int e = t; e < 16 * N; e += kThreads) {
@@ -522,25 +554,26 @@ __global__ void __launch_bounds__(kThreads) warm_decode_kernel(const float* __re
       sHt[ii * LD + k] = i < m ? HA[i * N + k] : 0.f;
     }
     __syncthreads();
-    const int NGR = (16 + RB - 1) / RB;   // row groups covering the 16 rows
+    constexpr int NGR = 16 / RB;   // row groups covering the 16 rows
     for (int e = t; e < N * NGR; e += kThreads) {
       const int j = e % N, g = e / N;
-      float a1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, a2[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float a1[RB], a2[RB];
+#pragma unroll
+      for (int x = 0; x < RB; ++x) { a1[x] = 0.f; a2[x] = 0.f; }
+#pragma unroll 4
       for (int k = 0; k < N; ++k) {
         const float c = sC[k * LD + j], ev = sE[k * LD + j];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          if (x < RB && g * RB + x < 16) {
-            const float h = sHt[(g * RB + x) * LD + k];
-            a1[x] = fmaf(h, c, a1[x]);
-            a2[x] = fmaf(h, ev, a2[x]);
-          }
+        for (int x = 0; x < RB; ++x) {
+          const float h = sHt[(g * RB + x) * LD + k];
+          a1[x] = fmaf(h, c, a1[x]);
+          a2[x] = fmaf(h, ev, a2[x]);
         }
       }
 #pragma unroll
-      for (int x = 0; x < 8; ++x) {
+      for (int x = 0; x < RB; ++x) {
         const int64_t i = ib + g * RB + x;
-        if (x < RB && g * RB + x < 16 && i < m) {
+        if (i < m) {
           const float z = ((float)D[i * N + j] - a1[x]) / r32[i];
           Z0[i * N + j] = df32(z, 0.f);
           B[i * N + j] = a2[x];
@@ -636,7 +669,9 @@ cudaError_t warm_set_model(enkf_handle_s* h, const enkf_mlp_shape* shape, const 
   e = cudaMalloc((void**)&w.work, sizeof(float) * mlp_work_floats(L, N));
   if (e != cudaSuccess) { err = "allocation"; return e; }
   const int smem = (int)(sizeof(float) * (size_t)(2 * N + 16) * (N + 1));   // up to 140 KB at N = 128
-  e = cudaFuncSetAttribute(warm_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(warm_decode_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(warm_decode_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(warm_decode_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) { err = "decoder shared memory"; return e; }
   w.L = L;
   w.params = params;
@@ -660,9 +695,14 @@ cudaError_t warm_prepare(enkf_handle_s* h) {
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(float) * (size_t)(2 * c.N + 16) * (c.N + 1);
   const int grid = (int)std::min<int64_t>(2 * (int64_t)h->sms, (c.m + 15) / 16);
-  warm_decode_kernel<<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, w.C, w.E,
-                                                          static_cast<df32*>(h->ws.Zdf),
-                                                          static_cast<float*>(h->ws.B));
+  df32* Z0 = static_cast<df32*>(h->ws.Zdf);
+  float* B0 = static_cast<float*>(h->ws.B);
+  if (c.N <= 32)
+    warm_decode_kernel<2><<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, w.C, w.E, Z0, B0);
+  else if (c.N <= 64)
+    warm_decode_kernel<4><<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, w.C, w.E, Z0, B0);
+  else
+    warm_decode_kernel<8><<<grid, kThreads, smem, h->stream>>>(h->ws.HA32, h->ws.D, h->ws.r32, c.m, c.N, w.C, w.E, Z0, B0);
   return cudaGetLastError();
 }
 
