@@ -48,9 +48,12 @@ template <typename VT, int NT> __host__ __device__ constexpr bool async_passF() 
 // NT = 128: x is read into registers instead of staged, so that two tiles fit in shared memory
 template <int NT> __host__ __device__ constexpr bool async_xreg() { return NT == 128; }
 template <int NT> __host__ __device__ constexpr int passF_async_bytes();
+template <int NT> struct DFTile;
 template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
   constexpr int f = async_passF<VT, NT>() ? passF_async_bytes<NT>() : passF_bytes<VT, NT>();
-  return refresh_union_bytes<NT>() > f ? refresh_union_bytes<NT>() : f;
+  constexpr int d = sizeof(VT) == 4 ? DFTile<NT>::bytes : 0;   // pipelined double-float refresh
+  constexpr int m1 = refresh_union_bytes<NT>() > f ? refresh_union_bytes<NT>() : f;
+  return m1 > d ? m1 : d;
 }
 template <typename VT, int NT> __host__ __device__ constexpr int solve_smem_bytes() {
   return scalar_bytes<NT>() + kThreads * 8 + union_bytes<VT, NT>();
@@ -881,6 +884,219 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
     }
     out[N * N + t] = a;
     out[N * N + N + t] = bb;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ double-float refresh, pipelined
+// The two passes of the double-float refresh (FP32 mode, N % 4 == 0) with the row tiles
+// double-buffered through cp.async, as in passF_async. Same arithmetic and partial sums as
+// passA / passB with ProRefreshDF / EpiRefreshDF.
+template <int NT> struct DFTile {
+  static constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
+  static constexpr int TRA = NT == 128 ? 16 : 32;                  // pass A rows per tile
+  static constexpr int BUFA = TRA * NT * 20;                        // bytes: HA, Z (8 B), X (4 B)
+  static constexpr int NJ = NT / 4, NI = kThreads / NJ, MR = 2, TRB = NI * MR;   // pass B
+  static constexpr int LDT = NT + 2;                                // df32 row stride of T
+  static constexpr int BUFB = TRB * NT * 24;                        // HA, Z, D (8 B each)
+  static constexpr bool B_ASYNC = NT <= 64;                         // NT = 128 keeps passA/passB
+  static constexpr int RED = RG > 1 ? RG * NT * NT * 8 : 0;        // cross-group reduction
+  static constexpr int bytes_a = 2 * BUFA > RED ? 2 * BUFA : RED;
+  static constexpr int bytes_b = NT * LDT * 8 + 2 * BUFB;
+  static constexpr int bytes = B_ASYNC ? (bytes_a > bytes_b ? bytes_a : bytes_b) : bytes_a;
+};
+
+template <int NT>
+__device__ void refreshA_async(const df32* __restrict__ HAdf, df32* Zdf, const float* __restrict__ X,
+                               int64_t row0, int64_t row1, int N, unsigned char* tiles, double* __restrict__ out) {
+  using TL = DFTile<NT>;
+  constexpr int MA = TL::MA, NG = TL::NG, TPG = TL::TPG, RG = TL::RG, TR = TL::TRA;
+  const int t = threadIdx.x, g = t / TPG, u = t % TPG, tj = u % NG, tk = u / NG;
+  const int k0 = tk * MA, j0 = tj * MA;
+  df32 acc[MA][MA];
+#pragma unroll
+  for (int x = 0; x < MA; ++x)
+#pragma unroll
+    for (int y = 0; y < MA; ++y) acc[x][y] = df32(0.f, 0.f);
+  auto issue = [&](int64_t i0, int b) {
+    unsigned char* sb = tiles + b * TL::BUFA;
+    df32* sH = reinterpret_cast<df32*>(sb);
+    df32* sZ = sH + TR * NT;
+    float* sX = reinterpret_cast<float*>(sZ + TR * NT);
+    // HA and Z rows: 2 df32 per 16 bytes; X rows: 4 floats per 16 bytes
+    for (int c = t; c < TR * (NT / 2); c += kThreads) {
+      const int ii = c / (NT / 2), c0 = (c % (NT / 2)) * 2;
+      const int64_t i = i0 + ii;
+      const bool ok = i < row1 && c0 < N;
+      const int64_t off = ok ? i * N + c0 : row0 * N;
+      cp_async16(sH + ii * NT + c0, HAdf + off, ok);
+      cp_async16(sZ + ii * NT + c0, Zdf + off, ok);
+    }
+    for (int c = t; c < TR * (NT / 4); c += kThreads) {
+      const int ii = c / (NT / 4), c0 = (c % (NT / 4)) * 4;
+      const int64_t i = i0 + ii;
+      const bool ok = i < row1 && c0 < N;
+      cp_async16(sX + ii * NT + c0, X + (ok ? i * N + c0 : row0 * N), ok);
+    }
+    cp_async_commit();
+  };
+  int b = 0;
+  if (row0 < row1) issue(row0, 0);
+  for (int64_t i0 = row0; i0 < row1; i0 += TR, b ^= 1) {
+    if (i0 + TR < row1) {
+      issue(i0 + TR, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    unsigned char* sb = tiles + b * TL::BUFA;
+    const df32* sH = reinterpret_cast<const df32*>(sb);
+    df32* sZ = reinterpret_cast<df32*>(sb) + TR * NT;
+    const float* sX = reinterpret_cast<const float*>(sZ + TR * NT);
+    // Z += X in the tile (and back to global)
+    const int nrows = (int)imin64(TR, row1 - i0);
+    for (int e = t; e < nrows * (N / 2); e += kThreads) {
+      const int ii = e / (N / 2), c0 = (e % (N / 2)) * 2;
+      const df32 z0 = sZ[ii * NT + c0] + df32(sX[ii * NT + c0], 0.f);
+      const df32 z1 = sZ[ii * NT + c0 + 1] + df32(sX[ii * NT + c0 + 1], 0.f);
+      sZ[ii * NT + c0] = z0;
+      sZ[ii * NT + c0 + 1] = z1;
+      *reinterpret_cast<float4*>(Zdf + (i0 + ii) * N + c0) = make_float4(z0.hi, z0.lo, z1.hi, z1.lo);
+    }
+    __syncthreads();
+    for (int ii = g; ii < nrows; ii += RG) {
+      df32 a[MA], v[MA];
+      load_vec<df32>(a, sH + ii * NT + k0, MA);
+      load_vec<df32>(v, sZ + ii * NT + j0, MA);
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) acc[x][y] = fma(a[x], v[y], acc[x][y]);
+    }
+    __syncthreads();   // the buffer is refilled by the copy issued in the next iteration
+  }
+  double* red = reinterpret_cast<double*>(tiles);
+  if (RG > 1) {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + j0 + y] = (double)acc[x][y];
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) {
+          const int k = k0 + x, j = j0 + y;
+          double s = 0.0;
+          for (int gg = 0; gg < RG; ++gg) s += red[(gg * NT + k) * NT + j];
+          if (k < N && j < N) out[k * N + j] = s;
+        }
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) {
+        const int k = k0 + x, j = j0 + y;
+        if (k < N && j < N) out[k * N + j] = (double)acc[x][y];
+      }
+  }
+  if (t < N) {
+    out[N * N + t] = 0.0;
+    out[N * N + N + t] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Pass B: B = hi(D - (r Z + HA T')) with T' = T/(N-1) staged in double-float (sT, stride
+// LDT), rr_out[j] = block sum of the squared new residual (the float hi parts, as
+// EpiRefreshDF). MR = 2 rows x 4 columns per thread.
+template <int NT, typename VT>
+__device__ void refreshB_async(const df32* __restrict__ HAdf, const df32* __restrict__ Zdf,
+                               const df32* __restrict__ Ddf, const double* __restrict__ r, VT* B,
+                               int64_t row0, int64_t row1, int N, const df32* sT, df32 inv,
+                               unsigned char* tiles, double* rr_out) {
+  using TL = DFTile<NT>;
+  constexpr int NJ = TL::NJ, MR = TL::MR, TR = TL::TRB, LDT = TL::LDT;
+  const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = 4 * tj, r0 = ti * MR;
+  float rr[4] = {0.f, 0.f, 0.f, 0.f};
+  auto issue = [&](int64_t i0, int b) {
+    unsigned char* sb = tiles + b * TL::BUFB;
+    df32* sH = reinterpret_cast<df32*>(sb);
+    df32* sZ = sH + TR * NT;
+    df32* sD = sZ + TR * NT;
+    for (int c = t; c < TR * (NT / 2); c += kThreads) {
+      const int ii = c / (NT / 2), c0 = (c % (NT / 2)) * 2;
+      const int64_t i = i0 + ii;
+      const bool ok = i < row1 && c0 < N;
+      const int64_t off = ok ? i * N + c0 : row0 * N;
+      cp_async16(sH + ii * NT + c0, HAdf + off, ok);
+      cp_async16(sZ + ii * NT + c0, Zdf + off, ok);
+      cp_async16(sD + ii * NT + c0, Ddf + off, ok);
+    }
+    cp_async_commit();
+  };
+  int b = 0;
+  if (row0 < row1) issue(row0, 0);
+  for (int64_t i0 = row0; i0 < row1; i0 += TR, b ^= 1) {
+    if (i0 + TR < row1) {
+      issue(i0 + TR, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    unsigned char* sb = tiles + b * TL::BUFB;
+    const df32* sH = reinterpret_cast<const df32*>(sb);
+    const df32* sZ = sH + TR * NT;
+    const df32* sD = sZ + TR * NT;
+    df32 acc[MR][4];
+#pragma unroll
+    for (int x = 0; x < MR; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = df32(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < NT; ++k) {
+      df32 a[MR], bv[4];
+#pragma unroll
+      for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * NT + k];
+      load_vec<df32>(bv, sT + k * LDT + j0, 4);
+#pragma unroll
+      for (int x = 0; x < MR; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < MR; ++x) {
+      const int64_t i = i0 + r0 + x;
+      if (i < row1 && j0 < N) {
+        const df32 ri(r[i]);
+        df32 z[4], d[4];
+        load_vec<df32>(z, sZ + (r0 + x) * NT + j0, 4);
+        load_vec<df32>(d, sD + (r0 + x) * NT + j0, 4);
+        VT o[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const df32 q = fma(ri, z[y], acc[x][y] * inv);
+          const df32 rt = d[y] - q;
+          rr[y] = __fmaf_rn(rt.hi, rt.hi, rr[y]);
+          o[y] = (VT)rt.hi;
+        }
+        st4<VT>(B + i * N, j0, N, true, o);
+      }
+    }
+    __syncthreads();
+  }
+  double* red = reinterpret_cast<double*>(tiles);
+#pragma unroll
+  for (int y = 0; y < 4; ++y) red[ti * NT + j0 + y] = (double)rr[y];
+  __syncthreads();
+  if (t < NT) {
+    double s = 0.0;
+    for (int q = 0; q < TL::NI; ++q) s += red[q * NT + t];
+    rr_out[t] = s;
   }
   __syncthreads();
 }

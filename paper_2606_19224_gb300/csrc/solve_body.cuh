@@ -281,8 +281,12 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       ProRefresh<VT> pro{p.Z, X, N, refine};
       passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
     } else {
-      ProRefreshDF<VT> pro{p.Zdf, X, N, true};
-      passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
+      if (DFTile<NT>::B_ASYNC && (N & 3) == 0) {
+        refreshA_async<(NT <= 64 ? NT : 64)>(p.HAdf, p.Zdf, reinterpret_cast<const float*>(X), row0, row1, N, uni, Tp);
+      } else {
+        ProRefreshDF<VT> pro{p.Zdf, X, N, true};
+        passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
+      }
     }
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
@@ -303,8 +307,18 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       df32* sTd = reinterpret_cast<df32*>(uni);
       stage_T<df32, NT>(p.Tred, N, sTd);
       constexpr int LDD = NT + 2;
-      EpiRefreshDF<VT> epi{p.Zdf, p.Ddf, p.r, static_cast<VT*>(p.B), N, df32(inv_nm1)};
-      passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+      bool done_b = false;
+      if constexpr (DFTile<NT>::B_ASYNC) {
+        if ((N & 3) == 0) {
+          refreshB_async<NT, VT>(p.HAdf, p.Zdf, p.Ddf, p.r, static_cast<VT*>(p.B), row0, row1, N, sTd,
+                                 df32(inv_nm1), uni + NT * LDD * sizeof(df32), s_tmp);
+          done_b = true;
+        }
+      }
+      if (!done_b) {
+        EpiRefreshDF<VT> epi{p.Zdf, p.Ddf, p.r, static_cast<VT*>(p.B), N, df32(inv_nm1)};
+        passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+      }
     }
     if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
     if (!(ok = bar.sync())) break;

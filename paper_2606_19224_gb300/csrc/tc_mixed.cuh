@@ -885,7 +885,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     total += it;
     ++cycles;
     // ---- double-float refresh: Z += X; T = HA^T Z; W; true residual D - S Z -> next B
-    {
+    if (DFTile<NT>::B_ASYNC && (N & 3) == 0) {
+      refreshA_async<(NT <= 64 ? NT : 64)>(p.HAdf, p.Zdf, p.X, row0, row1, N, uni, Tp);
+    } else {
       ProRefreshDF<float> pro{p.Zdf, p.X, N, true};
       passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
     }
@@ -898,8 +900,18 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       df32* sTd = reinterpret_cast<df32*>(uni);
       stage_T<df32, NT>(p.Tred, N, sTd);
       constexpr int LDD = NT + 2;
-      EpiRefreshDF<float> epi{p.Zdf, p.Ddf, p.r, p.B, N, df32(inv_nm1)};
-      passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+      bool done_b = false;
+      if constexpr (DFTile<NT>::B_ASYNC) {
+        if ((N & 3) == 0) {
+          refreshB_async<NT, float>(p.HAdf, p.Zdf, p.Ddf, p.r, p.B, row0, row1, N, sTd, df32(inv_nm1),
+                                    uni + NT * LDD * sizeof(df32), s_tmp);
+          done_b = true;
+        }
+      }
+      if (!done_b) {
+        EpiRefreshDF<float> epi{p.Zdf, p.Ddf, p.r, p.B, N, df32(inv_nm1)};
+        passB<df32, NT>(p.HAdf, row0, row1, N, sTd, uni + NT * LDD * sizeof(df32), epi, s_tmp);
+      }
     }
     if (t < NT) p.rrpart[((int64_t)par * G + b) * NT + t] = s_tmp[t];
     if (!(ok = bar.sync())) break;
@@ -938,7 +950,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
 }
 
 template <int NT, int TERMS> __host__ __device__ constexpr int mixed_smem_bytes() {
-  constexpr int tcb = TcLayout<NT, TERMS>::bytes;
+  constexpr int tcb0 = TcLayout<NT, TERMS>::bytes;
+  constexpr int tcb = tcb0 > DFTile<NT>::bytes ? tcb0 : DFTile<NT>::bytes;
   constexpr int u = refresh_union_bytes<NT>() > tcb ? refresh_union_bytes<NT>() : tcb;
   return scalar_bytes<NT>() + kThreads * 8 + u;
 }
