@@ -241,8 +241,8 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
    as by enkf_create; h_rowptr, h_col, h_w and r_diag are HOST arrays of `count` HOST
    pointers to each problem's CSR operator and R diagonal (copied to the device). cfgs[0]
    .grid_blocks > 0 caps the persistent grid. Allocates one device arena (about 56 m N bytes
-   per problem, plus O(grid N_max^2)) and plans the launch: problems worth at least 1.5 CTAs
-   of the grid get their own team of CTAs, the rest are packed onto single-CTA teams. If the
+   per problem, plus O(grid N_max^2)) and plans the launch as enkf_batch_plan does with
+   alpha = 1 (large problems get teams of CTAs, the rest share single-CTA teams). If the
    environment variable ENKF_TUNE_CACHE names a file holding a tuning result for this batch
    (written by enkf_batch_tune), that plan is used. Errors as enkf_create, with the index of
    the failing problem in enkf_last_error(NULL). */
@@ -261,11 +261,14 @@ enkf_status enkf_batch_create(int32_t count, const enkf_config* cfgs,
 enkf_status enkf_batch_analyze(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
                                const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa);
 
-/* Autotune the plan on real inputs (arguments as enkf_batch_analyze): times a few team
-   sizings (alpha in {1, 0.85, 0.7, 0.55, 1.2}: a big problem's team is alpha times its
-   cost share of the grid), keeps the fastest, and appends it to the ENKF_TUNE_CACHE file if
-   that variable is set. Runs several analyses (X_a holds the last one's result);
-   synchronises the stream. *best_ms (HOST, may be NULL) receives the best mean time. */
+/* Autotune the plan on real inputs (arguments as enkf_batch_analyze). First it times the
+   plans of enkf_batch_plan for the team-scaling exponents alpha in {1, 0.9, 0.8}; then it
+   twice re-plans from measured costs (each problem's duration in the best plan so far, as
+   reported by enkf_batch_get_times, times k^alpha for a team of k CTAs, averaged over the
+   rounds) and times those plans too. It keeps the fastest plan and appends it (alpha, and
+   the measured costs when a measured plan won) to the ENKF_TUNE_CACHE file if that variable
+   is set. Runs about 20 analyses (X_a holds the last one's result); synchronises the
+   stream. *best_ms (HOST, may be NULL) receives the best mean time. */
 enkf_status enkf_batch_tune(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
                             const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa,
                             double* best_ms);
@@ -283,17 +286,35 @@ enkf_status enkf_batch_get_stats(enkf_handle h, int32_t* status, int32_t* iters_
 enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, double* alpha,
                                 int32_t* graphed);
 
-/* The planner alone, on the host (no GPU needed). A problem costs m N^2 (N + 8) + 2 n N^2;
-   one whose share of the total cost times max_grid is at least 1.5 gets a team of
-   min(floor(alpha * that), ceil(m / 64)) CTAs when that is >= 2 and fits (largest first,
-   leaving at least one CTA); the others go longest-first to the least-loaded of the
-   remaining single-CTA teams. For `count` problem shapes (only n, m, N of cfgs are read), a
-   grid of at most max_grid CTAs and team sizing alpha > 0, fill HOST
-   arrays cta_team[grid], cta_rank[grid] (team of each CTA and its rank in it; a team's CTAs
-   are contiguous), team_size[teams], team_first[teams + 1] (offsets into order) and
-   order[count] (problems in team order; every problem exactly once). Arrays of max_grid,
-   max_grid, max_grid, max_grid + 1 and count entries are always large enough; any may be
-   NULL. *grid and *teams receive the sizes. */
+/* Per-problem phase timers in later batched analyses (enable != 0) or not (0, the default):
+   the first CTA of each team reads the global nanosecond timer around the phases of the CG
+   solve, as enkf_get_solve_phases does for one analysis. Re-uploads the problem table and
+   re-captures the graph at the next analysis; synchronises the stream. */
+enkf_status enkf_batch_set_phase_timing(enkf_handle h, int32_t enable);
+
+/* Synchronise and report when each problem of the last batched analysis ran, into HOST
+   arrays of `count` entries (any may be NULL): start_us / end_us, microseconds from the
+   earliest start to the moment the first CTA of the problem's team began it (before the
+   innovations) and finished it (after its share of the update; -1 if it never finished);
+   phase_us [count][8] the solve phase timers in the order of enkf_get_solve_phases (only
+   while enkf_batch_set_phase_timing is on, else ENKF_ERR_INVALID_ARG); team_size the number
+   of CTAs in the team that ran each problem. The start and end stamps are always taken
+   (two timer reads per problem). ENKF_ERR_INVALID_ARG before the first analysis. */
+enkf_status enkf_batch_get_times(enkf_handle h, double* start_us, double* end_us, double* phase_us,
+                                 int32_t* team_size);
+
+/* The planner alone, on the host (no GPU needed). A problem costs c = m N^2 (N + 8) + 2 n N^2;
+   a team of k CTAs is estimated to take c / k^alpha (0 < alpha <= 1). For a target makespan
+   T every problem with c > T gets the smallest team (2 <= k <= ceil(m / 64)) that meets T and
+   the others go longest-first to the least-loaded of the remaining single-CTA teams, which
+   must stay within T; the plan is the one for the smallest feasible T (bisection), and CTAs
+   left over join the slowest multi-CTA teams. For `count` problem shapes (only n, m, N of
+   cfgs are read) and a grid of at most max_grid CTAs, fill HOST arrays cta_team[grid],
+   cta_rank[grid] (team of each CTA and its rank in it; a team's CTAs are contiguous),
+   team_size[teams], team_first[teams + 1] (offsets into order) and order[count] (problems in
+   team order; every problem exactly once). Arrays of max_grid, max_grid, max_grid,
+   max_grid + 1 and count entries are always large enough; any may be NULL. *grid and *teams
+   receive the sizes. ENKF_ERR_INVALID_ARG for alpha outside (0, 1] or bad shapes. */
 enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
                             int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
                             int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams);

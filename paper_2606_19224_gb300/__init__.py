@@ -25,7 +25,8 @@ EXPORTS = (
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
     "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
     "enkf_get_solve_phases", "enkf_batch_create", "enkf_batch_analyze", "enkf_batch_tune",
-    "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan",
+    "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan", "enkf_batch_set_phase_timing",
+    "enkf_batch_get_times",
     "enkf_mlp_param_count", "enkf_mlp_work_bytes", "enkf_mlp_forward", "enkf_mlp_loss_grad",
     "enkf_mlp_adam", "enkf_mlp_train_epoch", "enkf_mlp_standardize", "enkf_warm_features",
     "enkf_set_warm_model",
@@ -104,6 +105,8 @@ def load(path: str = None):
         "enkf_batch_tune": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "enkf_batch_get_stats": (i32, [vp, vp, vp, vp, vp]),
         "enkf_batch_get_plan": (i32, [vp, vp, vp, vp, vp]),
+        "enkf_batch_set_phase_timing": (i32, [vp, i32]),
+        "enkf_batch_get_times": (i32, [vp, vp, vp, vp, vp]),
         "enkf_mlp_param_count": (i64, [ctypes.POINTER(MlpShape)]),
         "enkf_mlp_work_bytes": (i64, [ctypes.POINTER(MlpShape), i32]),
         "enkf_mlp_forward": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, i32, vp, vp, vp]),
@@ -318,8 +321,9 @@ def _ptr_array(items, ctype=ctypes.c_void_p):
 
 
 def batch_plan(shapes, max_grid, alpha=1.0):
-    """The batched launch planner alone (host only): shapes is a list of (n, m, N). Returns
-    dict(grid, teams, cta_team, cta_rank, team_size, team_first, order) as numpy arrays."""
+    """The batched launch planner alone (host only): shapes is a list of (n, m, N), alpha the
+    team-scaling exponent in (0, 1]. Returns dict(grid, teams, cta_team, cta_rank, team_size,
+    team_first, order) as numpy arrays."""
     import numpy as np
     cfgs = (Config * len(shapes))()
     for i, (n, m, N) in enumerate(shapes):
@@ -407,6 +411,24 @@ class BatchAnalysis:
         _check(load().enkf_batch_get_plan(self.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(a),
                                           ctypes.byref(gr)), self.h)
         return dict(grid=g.value, teams=t.value, alpha=a.value, graphed=gr.value)
+
+    def set_phase_timing(self, enable=True):
+        _check(load().enkf_batch_set_phase_timing(self.h, 1 if enable else 0), self.h)
+
+    def times(self, phases=False):
+        """When each problem of the last analysis ran: dict(start_us, end_us, team_size[, phase_us
+        [count][8] when phases=True, which needs set_phase_timing(True) before the analysis])."""
+        import numpy as np
+        t0 = np.zeros(self.count)
+        t1 = np.zeros(self.count)
+        ts = np.zeros(self.count, dtype=np.int32)
+        ph = np.zeros((self.count, 8)) if phases else None
+        _check(load().enkf_batch_get_times(self.h, t0.ctypes.data, t1.ctypes.data,
+                                           ph.ctypes.data if phases else None, ts.ctypes.data), self.h)
+        out = dict(start_us=t0, end_us=t1, team_size=ts)
+        if phases:
+            out["phase_us"] = ph
+        return out
 
     def close(self):
         if getattr(self, "h", None):

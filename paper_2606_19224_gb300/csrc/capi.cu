@@ -539,10 +539,28 @@ enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, do
   return ENKF_OK;
 }
 
+enkf_status enkf_batch_set_phase_timing(enkf_handle h, int32_t enable) {
+  if (!h || !h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_set_phase_timing: not a batched handle");
+  cudaError_t e = enkf::batch_set_phase_timing(h, enable != 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_batch_set_phase_timing");
+  return ENKF_OK;
+}
+
+enkf_status enkf_batch_get_times(enkf_handle h, double* start_us, double* end_us, double* phase_us,
+                                 int32_t* team_size) {
+  if (!h || !h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_times: not a batched handle");
+  if (!h->has_result) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_times: no analysis yet");
+  if (phase_us && !enkf::batch_phase_timing(h))
+    return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_times: phase timers off (enkf_batch_set_phase_timing)");
+  cudaError_t e = enkf::batch_times(h, start_us, end_us, phase_us, team_size);
+  if (e != cudaSuccess) return cuda_fail(h, e, "enkf_batch_get_times");
+  return ENKF_OK;
+}
+
 enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
                             int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
                             int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams) {
-  if (count < 1 || !cfgs || max_grid < 1 || !(alpha > 0.0))
+  if (count < 1 || !cfgs || max_grid < 1 || !(alpha > 0.0 && alpha <= 1.0))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: bad argument");
   for (int32_t i = 0; i < count; ++i)
     if (cfgs[i].m < 1 || cfgs[i].n < 1 || cfgs[i].N < 2 || cfgs[i].N > 128)

@@ -216,6 +216,9 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
 cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, double* relres_max,
                         int32_t* refinements);
 BatchPlanOut batch_info(const enkf_handle_s* h);
+cudaError_t batch_set_phase_timing(enkf_handle_s* h, bool on);
+bool batch_phase_timing(const enkf_handle_s* h);
+cudaError_t batch_times(enkf_handle_s* h, double* start_us, double* end_us, double* phase_us, int32_t* team);
 int batch_count(const enkf_handle_s* h);
 size_t batch_state_bytes(const enkf_handle_s* h, int i);   // bytes of X_f of problem i
 void batch_free(enkf_handle_s* h);

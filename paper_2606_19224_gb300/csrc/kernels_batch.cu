@@ -4,19 +4,22 @@
 // matvec decomposition, X_a = X_f + A HA^T Z / (N - 1)), in the FP32-with-refresh mode.
 //
 // Planning (host): a problem is costed at m N^2 (N + 8) + 2 n N^2 (about N preconditioned
-// steps of 4 m N^2 flops each, plus the update). Problems worth at least 1.5 CTAs of the
-// grid get a team of CTAs of their own, sized by alpha times their cost share; the rest are
-// packed onto single-CTA teams longest-processing-time first. Every team walks its list of
-// problems; for each it runs the innovations over its rows, the persistent CG solve with a
-// bounded barrier over the team's CTAs only, and the ensemble update. The tuner times a few
-// alpha values on the caller's inputs and keeps the fastest; the choice can be cached in the
-// text file named by the ENKF_TUNE_CACHE environment variable.
+// steps of 4 m N^2 flops each, plus the update). The planner minimises the estimated
+// makespan: problems costlier than the target get a team of CTAs of their own, the rest are
+// packed onto single-CTA teams longest-processing-time first (make_plan). Every team walks
+// its list of problems; for each it runs the innovations over its rows, the persistent CG
+// solve with a bounded barrier over the team's CTAs only, and the ensemble update, and the
+// team's first CTA stamps the problem's start and end. The tuner times a few values of the
+// team-scaling exponent alpha on the caller's inputs, then re-plans from the measured
+// per-problem durations, and keeps the fastest plan; the choice can be cached in the text
+// file named by the ENKF_TUNE_CACHE variable.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <sstream>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
     const BatchProblem* __restrict__ probs, const BatchIO* __restrict__ io,
     const int* __restrict__ cta_team, const int* __restrict__ cta_rank,
     const int* __restrict__ team_size, const int* __restrict__ team_first,
-    const int* __restrict__ order, int perturb) {
+    const int* __restrict__ order, int perturb, unsigned long long* __restrict__ times) {
   constexpr int NT2 = NTMAX >= 64 ? 64 : 32;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SolveParams s_sp;
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
       s_io = io[pi];
       s_n = probs[pi].n;
       s_nt = probs[pi].NT;
+      if (rank == 0) times[2 * pi] = global_ns();
     }
     __syncthreads();
     const SolveParams& sp = s_sp;
@@ -109,12 +113,16 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
     if (NT == 32) batch_update<32>(s_io, sp.W, s_n, sp.N, rank, G, smem);
     else if (NT == 64) batch_update<NT2>(s_io, sp.W, s_n, sp.N, rank, G, smem);
     else batch_update<NTMAX>(s_io, sp.W, s_n, sp.N, rank, G, smem);
+    __syncthreads();
+    if (rank == 0 && threadIdx.x == 0) times[2 * pi + 1] = global_ns();
   }
 }
 
 // ------------------------------------------------------------------ host side
 struct BatchPlan {
   double alpha = 1.0;
+  std::vector<double> cost;   // per-problem one-CTA cost the plan was made from
+  bool measured = false;      // cost holds measured times (ns) instead of the model's
   int grid = 0;
   std::vector<int> cta_team, cta_rank, team_size, team_first, order, team_cta0;
 };
@@ -139,6 +147,8 @@ struct BatchState {
   int* d_status = nullptr;             // [count][4]: status bits, refinements
   unsigned* d_bar = nullptr;           // [count][4]: barrier counter, abort flag
   double* d_team = nullptr;            // Tpart [max_grid][NE], Tred [max_grid][NE], rrpart [max_grid][256]
+  unsigned long long* d_time = nullptr;   // [count][2]: start, end (global ns, by each team's rank 0)
+  unsigned long long* d_phase = nullptr;  // [count][PH_COUNT] solve phase timers, or nullptr when off
   BatchPlan plan;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -152,44 +162,103 @@ static double problem_cost(const enkf_config& c) {
   return m * N * N * (N + 8.0) + 2.0 * n * N * N;
 }
 
-static BatchPlan make_plan(const std::vector<enkf_config>& cfg, int G, double alpha) {
-  BatchPlan P;
-  P.alpha = alpha;
-  const int count = (int)cfg.size();
-  std::vector<double> cost(count);
-  for (int i = 0; i < count; ++i) cost[i] = problem_cost(cfg[i]);
-  const double C = std::accumulate(cost.begin(), cost.end(), 0.0);
-  std::vector<int> idx(count);
-  std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  struct Team { int size; double load; std::vector<int> probs; };
-  std::vector<Team> teams;
-  int used = 0;
+// Makespan planning. A team of k CTAs is assumed to finish a problem of cost c in c / k^alpha
+// (alpha <= 1 charges large teams for their barriers and reductions). For a target time T,
+// every problem with c > T gets the smallest team that meets T (at most ceil(m/64) CTAs, so
+// each CTA keeps >= 64 rows); the others are packed longest first onto the least-loaded of
+// the remaining single-CTA teams, which must stay within T. The plan is the one for the
+// smallest feasible T (bisection); CTAs left over then join the slowest teams.
+struct PlanTeam {
+  int size;
+  double load;   // estimated time
+  std::vector<int> probs;
+};
+
+static bool try_plan(const std::vector<double>& cost, const std::vector<int>& cap, const std::vector<int>& idx,
+                     int G, double alpha, double T, std::vector<PlanTeam>* out) {
+  std::vector<PlanTeam> teams;
   std::vector<int> small;
+  int used = 0;
   for (int pi : idx) {
-    const double share = G * cost[pi] / C;
-    const int cap = (int)std::max<int64_t>(1, (cfg[pi].m + 63) / 64);   // >= 64 rows per CTA
-    const int k = std::min((int)std::floor(alpha * share), cap);
-    if (share >= 1.5 && k >= 2 && used + k <= G - 1) {
-      teams.push_back({k, cost[pi] / k, {pi}});
+    if (cost[pi] > T) {
+      int k = (int)std::ceil(std::pow(cost[pi] / T, 1.0 / alpha) - 1e-9);
+      k = std::max(k, 2);
+      if (k > cap[pi]) return false;
       used += k;
+      if (used > G) return false;
+      teams.push_back({k, cost[pi] / std::pow((double)k, alpha), {pi}});
     } else {
       small.push_back(pi);
     }
   }
-  const size_t first_single = teams.size();
-  const int singles = std::min<int>(G - used, std::max<int>(1, (int)small.size()));
-  for (int s = 0; s < singles; ++s) teams.push_back({1, 0.0, {}});
-  for (int pi : small) {   // LPT onto the single-CTA teams (costs already descending)
-    size_t best = first_single;
-    for (size_t t = first_single + 1; t < teams.size(); ++t)
-      if (teams[t].load < teams[best].load) best = t;
-    teams[best].load += cost[pi];
-    teams[best].probs.push_back(pi);
+  const int R = G - used;
+  if (!small.empty()) {
+    if (R < 1) return false;
+    const size_t first = teams.size();
+    const int nb = std::min<int>(R, (int)small.size());
+    for (int q = 0; q < nb; ++q) teams.push_back({1, 0.0, {}});
+    for (int pi : small) {   // costs descending: LPT
+      size_t best = first;
+      for (size_t t = first + 1; t < teams.size(); ++t)
+        if (teams[t].load < teams[best].load) best = t;
+      teams[best].load += cost[pi];
+      teams[best].probs.push_back(pi);
+      if (teams[best].load > T * (1.0 + 1e-12)) return false;
+    }
+  }
+  if (out) *out = teams;
+  return true;
+}
+
+// cost[i]: the estimated time of problem i on one CTA (problem_cost, or a measurement).
+static BatchPlan make_plan(const std::vector<enkf_config>& cfg, const std::vector<double>& cost, int G,
+                           double alpha) {
+  BatchPlan P;
+  P.alpha = alpha;
+  P.cost = cost;
+  const int count = (int)cfg.size();
+  std::vector<int> cap(count);
+  for (int i = 0; i < count; ++i)
+    cap[i] = (int)std::max<int64_t>(1, std::min<int64_t>(G, (cfg[i].m + 63) / 64));   // >= 64 rows per CTA
+  std::vector<int> idx(count);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // bisection on the makespan T between a lower bound and a target that always fits
+  const double total = std::accumulate(cost.begin(), cost.end(), 0.0);
+  double lo = total / G;
+  for (int i = 0; i < count; ++i) lo = std::max(lo, cost[i] / std::pow((double)cap[i], alpha));
+  double hi = total + 1.0;   // one CTA does everything
+  std::vector<PlanTeam> teams;
+  if (!try_plan(cost, cap, idx, G, alpha, hi, &teams)) teams.assign(1, PlanTeam{1, hi, idx});
+  for (int it = 0; it < 60 && hi > lo * (1.0 + 1e-6); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    std::vector<PlanTeam> trial;
+    if (try_plan(cost, cap, idx, G, alpha, mid, &trial)) {
+      hi = mid;
+      teams.swap(trial);
+    } else {
+      lo = mid;
+    }
+  }
+  // spare CTAs join the slowest multi-CTA teams
+  int used = 0;
+  for (const PlanTeam& t : teams) used += t.size;
+  for (int spare = G - used; spare > 0; --spare) {
+    int best = -1;
+    double worst = -1.0;
+    for (int q = 0; q < (int)teams.size(); ++q) {
+      const PlanTeam& t = teams[q];
+      if (t.size < 2 || t.probs.size() != 1 || t.size >= cap[t.probs[0]]) continue;
+      if (t.load > worst) { worst = t.load; best = q; }
+    }
+    if (best < 0) break;
+    PlanTeam& t = teams[best];
+    t.size += 1;
+    t.load = cost[t.probs[0]] / std::pow((double)t.size, alpha);
   }
   int cta = 0;
   P.team_first.push_back(0);
-  for (const Team& t : teams) {
+  for (const PlanTeam& t : teams) {
     if (t.probs.empty()) continue;
     const int tid = (int)P.team_size.size();
     P.team_size.push_back(t.size);
@@ -206,11 +275,18 @@ static BatchPlan make_plan(const std::vector<enkf_config>& cfg, int G, double al
   return P;
 }
 
+static std::vector<double> model_costs(const std::vector<enkf_config>& cfg) {
+  std::vector<double> cost(cfg.size());
+  for (size_t i = 0; i < cfg.size(); ++i) cost[i] = problem_cost(cfg[i]);
+  return cost;
+}
+
 bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha,
                      int* cta_team, int* cta_rank, int* team_size, int* team_first, int* order,
                      BatchPlanOut* out) {
   if (count < 1 || !cfgs || max_grid < 1) return false;
-  const BatchPlan P = make_plan(std::vector<enkf_config>(cfgs, cfgs + count), max_grid, alpha);
+  const std::vector<enkf_config> cfg(cfgs, cfgs + count);
+  const BatchPlan P = make_plan(cfg, model_costs(cfg), max_grid, alpha);
   auto put = [](const std::vector<int>& v, int* dst) { if (dst) std::copy(v.begin(), v.end(), dst); };
   put(P.cta_team, cta_team);
   put(P.cta_rank, cta_rank);
@@ -286,7 +362,8 @@ static cudaError_t enqueue_batch(BatchState& B, cudaStream_t s) {
   const BatchProblem* probs = B.d_probs;
   const BatchIO* io = B.d_io;
   int perturb = B.perturb;
-  void* args[] = {&probs, &io, &cta_team, &cta_rank, &team_size, &team_first, &order, &perturb};
+  unsigned long long* times = B.d_time;
+  void* args[] = {&probs, &io, &cta_team, &cta_rank, &team_size, &team_first, &order, &perturb, &times};
   return cudaLaunchCooperativeKernel(batch_fn(B.ntmax), dim3(P.grid), dim3(kThreads), args,
                                      B.smem, s);
 }
@@ -388,6 +465,8 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_plan, sizeof(int) * (4 * (size_t)B.max_grid + 1 + count));
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_status, sizeof(int) * 4 * count);
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_bar, sizeof(unsigned) * 4 * count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_time, sizeof(unsigned long long) * 2 * count);
+  if (e == cudaSuccess) e = cudaMemset(B.d_time, 0, sizeof(unsigned long long) * 2 * count);
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&B.d_team, sizeof(double) * (2 * (size_t)B.max_grid * NE + (size_t)B.max_grid * 256));
   if (e != cudaSuccess) { err = "enkf_batch_create: device allocation"; return e; }
@@ -447,18 +526,33 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
     B.probs.push_back(bp);
   }
   if (e != cudaSuccess) { err = "enkf_batch_create: upload of the observation operators"; return e; }
+  // a tuning result for this batch: "key alpha [cost_0 .. cost_{count-1}]"; the last one wins
   double alpha = 1.0;
+  std::vector<double> cost = model_costs(B.cfg);
+  bool measured = false;
   if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
     std::ifstream f(path);
     const std::string key = cache_key(B);
     std::string line;
     while (std::getline(f, line)) {
-      const size_t sp = line.rfind(' ');
-      if (sp != std::string::npos && line.compare(0, sp, key) == 0) alpha = std::atof(line.c_str() + sp + 1);
+      std::istringstream ls(line);
+      std::string k;
+      double a = 0.0;
+      if (!(ls >> k >> a) || k != key || !(a > 0.0 && a <= 1.0)) continue;
+      std::vector<double> c;
+      double v;
+      while (ls >> v) c.push_back(v);
+      const bool ok_c = (int)c.size() == count &&
+                        std::all_of(c.begin(), c.end(), [](double x) { return x > 0.0 && std::isfinite(x); });
+      if (!c.empty() && !ok_c) continue;
+      alpha = a;
+      measured = !c.empty();
+      cost = measured ? c : model_costs(B.cfg);
     }
-    if (!(alpha > 0.0 && alpha <= 4.0)) alpha = 1.0;
   }
-  e = apply_plan(B, make_plan(B.cfg, B.max_grid, alpha), h->stream);
+  BatchPlan P = make_plan(B.cfg, cost, B.max_grid, alpha);
+  P.measured = measured;
+  e = apply_plan(B, P, h->stream);
   if (e != cudaSuccess) err = "enkf_batch_create: plan upload";
   return e;
 }
@@ -477,41 +571,108 @@ cudaError_t batch_analyze(enkf_handle_s* h, const void* const* Xf, const double*
   return run_batch(h, make_io(*h->batch, Xf, y, seeds, counters, Xa));
 }
 
+// Per-problem durations (ns) of the last analysis, from the start/end stamps of each team's
+// rank 0; team size of every problem under plan P.
+static cudaError_t problem_ns(const BatchState& B, cudaStream_t s, std::vector<double>& ns) {
+  std::vector<unsigned long long> t(2 * (size_t)B.count);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t.data(), B.d_time, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost);
+  ns.assign(B.count, 0.0);
+  for (int i = 0; i < B.count && e == cudaSuccess; ++i)
+    ns[i] = t[2 * i + 1] > t[2 * i] ? (double)(t[2 * i + 1] - t[2 * i]) : 0.0;
+  return e;
+}
+
+static std::vector<int> problem_team(const BatchPlan& P, int count) {
+  std::vector<int> k(count, 1);
+  for (size_t t = 0; t < P.team_size.size(); ++t)
+    for (int q = P.team_first[t]; q < P.team_first[t + 1]; ++q) k[P.order[q]] = P.team_size[t];
+  return k;
+}
+
+// The tuner. Stage 1 times the model-cost plans for alpha in {1, 0.9, 0.8}. Stage 2 replaces
+// the model by measurement: each problem's one-CTA cost is estimated from its duration in the
+// best plan so far (times k^alpha for a team of k), the batch is re-planned from those costs
+// and timed, and the estimate is averaged with the new plan's durations for a second round.
+// The fastest plan is kept.
 cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
                        const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
                        double* best_alpha, double* best_ms) {
   BatchState& B = *h->batch;
   const std::vector<BatchIO> io = make_io(B, Xf, y, seeds, counters, Xa);
-  const double cand[] = {1.0, 0.85, 0.7, 0.55, 1.2};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  double best = 1e300, ba = B.plan.alpha;
-  for (double a : cand) {
-    if (e != cudaSuccess) break;
-    e = apply_plan(B, make_plan(B.cfg, B.max_grid, a), h->stream);
-    if (e == cudaSuccess) e = run_batch(h, io);   // warm-up, captures the graph
+  // install P, one warm-up analysis (captures the graph), three timed; mean ms and the
+  // per-problem durations of the last one
+  auto time_plan = [&](const BatchPlan& P, double& ms_mean, std::vector<double>& ns) {
+    cudaError_t r = apply_plan(B, P, h->stream);
+    if (r == cudaSuccess) r = run_batch(h, io);
     float tot = 0.f;
-    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 3 && r == cudaSuccess; ++rep) {
       float ms = 0.f;
-      e = cudaEventRecord(e0, h->stream);
-      if (e == cudaSuccess) e = run_batch(h, io);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      r = cudaEventRecord(e0, h->stream);
+      if (r == cudaSuccess) r = run_batch(h, io);
+      if (r == cudaSuccess) r = cudaEventRecord(e1, h->stream);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
       tot += ms;
     }
-    if (e == cudaSuccess && tot / 3 < best) { best = tot / 3; ba = a; }
+    if (r == cudaSuccess) r = problem_ns(B, h->stream, ns);
+    ms_mean = tot / 3.0;
+    return r;
+  };
+  BatchPlan best_plan = B.plan;
+  std::vector<double> best_ns;
+  double best = 1e300;
+  const std::vector<double> model = model_costs(B.cfg);
+  for (double a : {1.0, 0.9, 0.8}) {
+    if (e != cudaSuccess) break;
+    const BatchPlan P = make_plan(B.cfg, model, B.max_grid, a);
+    double ms = 0.0;
+    std::vector<double> ns;
+    e = time_plan(P, ms, ns);
+    if (e == cudaSuccess && ms < best) { best = ms; best_plan = P; best_ns = ns; }
+  }
+  if (e == cudaSuccess) {
+    const double a = best_plan.alpha;
+    auto one_cta = [&](const BatchPlan& P, const std::vector<double>& ns) {
+      const std::vector<int> k = problem_team(P, B.count);
+      std::vector<double> c(B.count);
+      for (int i = 0; i < B.count; ++i) c[i] = std::max(1.0, ns[i]) * std::pow((double)k[i], a);
+      return c;
+    };
+    std::vector<double> est = one_cta(best_plan, best_ns);
+    for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+      BatchPlan P = make_plan(B.cfg, est, B.max_grid, a);
+      P.measured = true;
+      double ms = 0.0;
+      std::vector<double> ns;
+      e = time_plan(P, ms, ns);
+      if (e != cudaSuccess) break;
+      if (ms < best) { best = ms; best_plan = P; }
+      const std::vector<double> now = one_cta(P, ns);
+      for (int i = 0; i < B.count; ++i) est[i] = 0.5 * (est[i] + now[i]);
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
-  e = apply_plan(B, make_plan(B.cfg, B.max_grid, ba), h->stream);
-  if (best_alpha) *best_alpha = ba;
+  e = apply_plan(B, best_plan, h->stream);
+  if (best_alpha) *best_alpha = best_plan.alpha;
   if (best_ms) *best_ms = best;
   if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
     std::ofstream f(path, std::ios::app);
-    f << cache_key(B) << " " << ba << "\n";
+    f << cache_key(B) << " " << best_plan.alpha;
+    if (best_plan.measured) {
+      char buf[32];
+      for (double c : best_plan.cost) {
+        std::snprintf(buf, sizeof(buf), " %.6g", c);
+        f << buf;
+      }
+    }
+    f << "\n";
   }
   return e;
 }
@@ -544,6 +705,47 @@ cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, d
   return e;
 }
 
+cudaError_t batch_set_phase_timing(enkf_handle_s* h, bool on) {
+  BatchState& B = *h->batch;
+  cudaError_t e = cudaSuccess;
+  if (on && !B.d_phase) {
+    const size_t bytes = sizeof(unsigned long long) * PH_COUNT * (size_t)B.count;
+    e = cudaMalloc((void**)&B.d_phase, bytes);
+    if (e == cudaSuccess) e = cudaMemset(B.d_phase, 0, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < B.count; ++i) B.probs[i].sp.prof = on ? B.d_phase + (size_t)PH_COUNT * i : nullptr;
+  const BatchPlan P = B.plan;
+  return apply_plan(B, P, h->stream);   // uploads the problem table, recaptures the graph
+}
+
+bool batch_phase_timing(const enkf_handle_s* h) { return h->batch->count > 0 && h->batch->probs[0].sp.prof; }
+
+cudaError_t batch_times(enkf_handle_s* h, double* start_us, double* end_us, double* phase_us, int32_t* team) {
+  BatchState& B = *h->batch;
+  std::vector<unsigned long long> t(2 * (size_t)B.count);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t.data(), B.d_time, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && phase_us) {
+    std::vector<unsigned long long> ph((size_t)PH_COUNT * B.count);
+    e = cudaMemcpy(ph.data(), B.d_phase, sizeof(unsigned long long) * ph.size(), cudaMemcpyDeviceToHost);
+    for (size_t q = 0; q < ph.size() && e == cudaSuccess; ++q) phase_us[q] = 1e-3 * (double)ph[q];
+  }
+  if (e != cudaSuccess) return e;
+  unsigned long long t0 = ~0ull;
+  for (int i = 0; i < B.count; ++i) t0 = std::min(t0, t[2 * i]);
+  for (int i = 0; i < B.count; ++i) {
+    if (start_us) start_us[i] = 1e-3 * (double)(t[2 * i] - t0);
+    if (end_us) end_us[i] = t[2 * i + 1] >= t[2 * i] ? 1e-3 * (double)(t[2 * i + 1] - t0) : -1.0;
+  }
+  if (team) {
+    const std::vector<int> k = problem_team(B.plan, B.count);
+    std::copy(k.begin(), k.end(), team);
+  }
+  return e;
+}
+
 BatchPlanOut batch_info(const enkf_handle_s* h) {
   if (!h->batch) return BatchPlanOut{};
   const BatchPlan& P = h->batch->plan;
@@ -563,7 +765,8 @@ void batch_free(enkf_handle_s* h) {
   drop_graph(*B);
   if (B->io_copied) cudaEventDestroy(B->io_copied);
   if (B->h_io) cudaFreeHost(B->h_io);
-  void* ptrs[] = {B->arena, B->d_probs, B->d_io, B->d_plan, B->d_status, B->d_bar, B->d_team};
+  void* ptrs[] = {B->arena, B->d_probs, B->d_io, B->d_plan, B->d_status, B->d_bar, B->d_team, B->d_time,
+                  B->d_phase};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete B;
