@@ -242,7 +242,7 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
    pointers to each problem's CSR operator and R diagonal (copied to the device). cfgs[0]
    .grid_blocks > 0 caps the persistent grid. Allocates one device arena (about 56 m N bytes
    per problem, plus O(grid N_max^2)) and plans the launch as enkf_batch_plan does with
-   alpha = 1 (large problems get teams of CTAs, the rest share single-CTA teams). If the
+   alpha = 1 (large problems get teams of CTAs, the rest are queued for single CTAs). If the
    environment variable ENKF_TUNE_CACHE names a file holding a tuning result for this batch
    (written by enkf_batch_tune), that plan is used. Errors as enkf_create, with the index of
    the failing problem in enkf_last_error(NULL). */
@@ -305,14 +305,17 @@ enkf_status enkf_batch_get_times(enkf_handle h, double* start_us, double* end_us
 
 /* The planner alone, on the host (no GPU needed). A problem costs c = m N^2 (N + 8) + 2 n N^2;
    a team of k CTAs is estimated to take c / k^alpha (0 < alpha <= 1). For a target makespan
-   T every problem with c > T gets the smallest team (2 <= k <= ceil(m / 64)) that meets T and
-   the others go longest-first to the least-loaded of the remaining single-CTA teams, which
-   must stay within T; the plan is the one for the smallest feasible T (bisection), and CTAs
-   left over join the slowest multi-CTA teams. For `count` problem shapes (only n, m, N of
-   cfgs are read) and a grid of at most max_grid CTAs, fill HOST arrays cta_team[grid],
-   cta_rank[grid] (team of each CTA and its rank in it; a team's CTAs are contiguous),
-   team_size[teams], team_first[teams + 1] (offsets into order) and order[count] (problems in
-   team order; every problem exactly once). Arrays of max_grid, max_grid, max_grid,
+   T every problem with c > T gets the smallest team (2 <= k <= ceil(m / 64)) that meets T;
+   the others form a shared queue, longest first, from which the launch hands the next
+   problem to whichever CTA is free (the CTAs outside teams from the start, a team's CTAs
+   once its problem is done), each solving it alone; T must hold for that schedule too. The
+   plan is the one for the smallest feasible T (bisection); CTAs the queue cannot keep busy
+   join the slowest teams. For `count` problem shapes (only n, m, N of cfgs are read) and a
+   grid of at most max_grid CTAs, fill HOST arrays cta_team[grid], cta_rank[grid] (team of
+   each CTA and its rank in it; a team's CTAs are contiguous), team_size[teams],
+   team_first[teams + 1] (offsets into order; a team of one CTA has an empty list) and
+   order[count] (every problem exactly once: the teams' problems, then from
+   order[team_first[teams]] on the queue). Arrays of max_grid, max_grid, max_grid,
    max_grid + 1 and count entries are always large enough; any may be NULL. *grid and *teams
    receive the sizes. ENKF_ERR_INVALID_ARG for alpha outside (0, 1] or bad shapes. */
 enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,

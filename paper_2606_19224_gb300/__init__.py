@@ -323,7 +323,7 @@ def _ptr_array(items, ctype=ctypes.c_void_p):
 def batch_plan(shapes, max_grid, alpha=1.0):
     """The batched launch planner alone (host only): shapes is a list of (n, m, N), alpha the
     team-scaling exponent in (0, 1]. Returns dict(grid, teams, cta_team, cta_rank, team_size,
-    team_first, order) as numpy arrays."""
+    team_first, order) as numpy arrays; order[team_first[teams]:] is the shared queue."""
     import numpy as np
     cfgs = (Config * len(shapes))()
     for i, (n, m, N) in enumerate(shapes):

@@ -5,14 +5,15 @@
 //
 // Planning (host): a problem is costed at m N^2 (N + 8) + 2 n N^2 (about N preconditioned
 // steps of 4 m N^2 flops each, plus the update). The planner minimises the estimated
-// makespan: problems costlier than the target get a team of CTAs of their own, the rest are
-// packed onto single-CTA teams longest-processing-time first (make_plan). Every team walks
-// its list of problems; for each it runs the innovations over its rows, the persistent CG
-// solve with a bounded barrier over the team's CTAs only, and the ensemble update, and the
-// team's first CTA stamps the problem's start and end. The tuner times a few values of the
-// team-scaling exponent alpha on the caller's inputs, then re-plans from the measured
-// per-problem durations, and keeps the fastest plan; the choice can be cached in the text
-// file named by the ENKF_TUNE_CACHE variable.
+// makespan: problems costlier than the target get a team of CTAs of their own, the rest wait
+// in a queue, longest first (make_plan). Every team works through its problem; for each it
+// runs the innovations over its rows, the persistent CG solve with a bounded barrier over the
+// team's CTAs only, and the ensemble update, and the team's first CTA stamps the problem's
+// start and end. A CTA that is free (outside every team, or its team's problem done) takes
+// the next problem of the queue through an atomic counter and solves it alone. The tuner
+// times a few values of the team-scaling exponent alpha on the caller's inputs, then
+// re-plans from the measured per-problem durations, and keeps the fastest plan; the choice
+// can be cached in the text file named by the ENKF_TUNE_CACHE variable.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -21,6 +22,7 @@
 #include <fstream>
 #include <sstream>
 #include <numeric>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -58,27 +60,36 @@ __device__ __noinline__ void batch_update(const BatchIO& io, const double* W, in
 
 // NTMAX bounds the column tile of every problem in the batch. One CTA per SM (the
 // double-buffered fused pass takes most of the shared memory). The solve is the
-// Jacobi-preconditioned (M = R) form.
+// Jacobi-preconditioned (M = R) form. A CTA first works through its team's list of problems
+// (order[team_first[team] .. team_first[team + 1])), then takes problems one at a time from
+// the shared queue order[queue_first .. count) (longest first) and solves each alone.
 template <int NTMAX>
 __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
     const BatchProblem* __restrict__ probs, const BatchIO* __restrict__ io,
     const int* __restrict__ cta_team, const int* __restrict__ cta_rank,
     const int* __restrict__ team_size, const int* __restrict__ team_first,
-    const int* __restrict__ order, int perturb, unsigned long long* __restrict__ times) {
+    const int* __restrict__ order, int queue_first, int count, unsigned* __restrict__ queue_head,
+    double* __restrict__ team_buf, int max_grid, int ne_max, int perturb,
+    unsigned long long* __restrict__ times) {
   constexpr int NT2 = NTMAX >= 64 ? 64 : 32;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SolveParams s_sp;
   __shared__ BatchIO s_io;
   __shared__ int64_t s_n;
   __shared__ int s_nt;
-  const int team = cta_team[blockIdx.x], rank = cta_rank[blockIdx.x], G = team_size[team];
+  __shared__ int s_q;
   const int warp = threadIdx.x >> 5;
-  const int k_end = team_first[team + 1];
-  for (int k = team_first[team]; k < k_end; ++k) {
-    const int pi = order[k];
+  // problem pi on a team of G CTAs in which this CTA has `rank` (the team's CTAs are
+  // contiguous, so its reduction slices start at CTA blockIdx.x - rank); false if a barrier
+  // of the problem gave up
+  auto run = [&](int pi, int G, int rank) -> bool {
     __syncthreads();
     if (threadIdx.x == 0) {
       s_sp = probs[pi].sp;
+      const int64_t c0 = (int64_t)blockIdx.x - rank;
+      s_sp.Tpart = team_buf + c0 * ne_max;                                      // [G][NE]
+      s_sp.Tred = team_buf + (int64_t)max_grid * ne_max + c0 * ne_max;          // [NE]
+      s_sp.rrpart = team_buf + (int64_t)2 * max_grid * ne_max + c0 * 256;       // [2][G][NT]
       s_io = io[pi];
       s_n = probs[pi].n;
       s_nt = probs[pi].NT;
@@ -103,18 +114,32 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
       else batch_solve<NTMAX>(sp, G, rank, bar, smem);
       ok = bar.sync();   // W of this problem complete and visible to the team
     }
-    if (!ok) {
-      // a barrier of this problem gave up: the team is no longer in step, so it stops here
-      // and flags the problems it has not finished
-      if (rank == 0 && threadIdx.x == 0)
-        for (int q = k; q < k_end; ++q) atomicOr(probs[order[q]].sp.status, DS_TIMEOUT);
-      return;
-    }
+    if (!ok) return false;
     if (NT == 32) batch_update<32>(s_io, sp.W, s_n, sp.N, rank, G, smem);
     else if (NT == 64) batch_update<NT2>(s_io, sp.W, s_n, sp.N, rank, G, smem);
     else batch_update<NTMAX>(s_io, sp.W, s_n, sp.N, rank, G, smem);
     __syncthreads();
     if (rank == 0 && threadIdx.x == 0) times[2 * pi + 1] = global_ns();
+    return true;
+  };
+  const int team = cta_team[blockIdx.x], rank = cta_rank[blockIdx.x], G = team_size[team];
+  const int k_end = team_first[team + 1];
+  for (int k = team_first[team]; k < k_end; ++k) {
+    if (!run(order[k], G, rank)) {
+      // a barrier gave up: the team is no longer in step, so it leaves its list here and
+      // flags the problems it has not finished; its CTAs still serve the queue alone
+      if (rank == 0 && threadIdx.x == 0)
+        for (int q = k; q < k_end; ++q) atomicOr(probs[order[q]].sp.status, DS_TIMEOUT);
+      break;
+    }
+  }
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_q = queue_first + (int)atomicAdd(queue_head, 1u);
+    __syncthreads();
+    const int q = s_q;
+    if (q >= count) break;
+    run(order[q], 1, 0);   // one CTA: its barriers never wait
   }
 }
 
@@ -125,6 +150,7 @@ struct BatchPlan {
   bool measured = false;      // cost holds measured times (ns) instead of the model's
   int grid = 0;
   std::vector<int> cta_team, cta_rank, team_size, team_first, order, team_cta0;
+  int queue_first = 0;        // order[queue_first ..] is the shared queue
 };
 
 struct BatchState {
@@ -145,7 +171,7 @@ struct BatchState {
   int* d_plan = nullptr;               // cta_team | cta_rank | team_size | team_first | order
                                        // (grid, grid, teams, teams + 1, count entries)
   int* d_status = nullptr;             // [count][4]: status bits, refinements
-  unsigned* d_bar = nullptr;           // [count][4]: barrier counter, abort flag
+  unsigned* d_bar = nullptr;           // [count][4]: barrier counter, abort flag; then the queue head
   double* d_team = nullptr;            // Tpart [max_grid][NE], Tred [max_grid][NE], rrpart [max_grid][256]
   unsigned long long* d_time = nullptr;   // [count][2]: start, end (global ns, by each team's rank 0)
   unsigned long long* d_phase = nullptr;  // [count][PH_COUNT] solve phase timers, or nullptr when off
@@ -165,48 +191,52 @@ static double problem_cost(const enkf_config& c) {
 // Makespan planning. A team of k CTAs is assumed to finish a problem of cost c in c / k^alpha
 // (alpha <= 1 charges large teams for their barriers and reductions). For a target time T,
 // every problem with c > T gets the smallest team that meets T (at most ceil(m/64) CTAs, so
-// each CTA keeps >= 64 rows); the others are packed longest first onto the least-loaded of
-// the remaining single-CTA teams, which must stay within T. The plan is the one for the
-// smallest feasible T (bisection); CTAs left over then join the slowest teams.
+// each CTA keeps >= 64 rows); the others form the shared queue, longest first. The queue is
+// simulated as the kernel serves it: the next problem goes to the CTA that is free first
+// (the CTAs outside teams at time 0, each team's CTAs when its problem is done), and every
+// problem must end by T. The plan is the one for the smallest feasible T (bisection); CTAs
+// the queue cannot use then join the slowest teams.
 struct PlanTeam {
   int size;
   double load;   // estimated time
   std::vector<int> probs;
 };
+struct PlanTry {
+  std::vector<PlanTeam> teams;   // multi-CTA teams, one problem each
+  std::vector<int> queue;        // the other problems, costs descending
+  int free_ctas = 0;             // CTAs outside teams
+};
 
 static bool try_plan(const std::vector<double>& cost, const std::vector<int>& cap, const std::vector<int>& idx,
-                     int G, double alpha, double T, std::vector<PlanTeam>* out) {
-  std::vector<PlanTeam> teams;
-  std::vector<int> small;
+                     int G, double alpha, double T, PlanTry* out) {
+  PlanTry o;
   int used = 0;
-  for (int pi : idx) {
+  for (int pi : idx) {   // costs descending
     if (cost[pi] > T) {
       int k = (int)std::ceil(std::pow(cost[pi] / T, 1.0 / alpha) - 1e-9);
       k = std::max(k, 2);
       if (k > cap[pi]) return false;
       used += k;
       if (used > G) return false;
-      teams.push_back({k, cost[pi] / std::pow((double)k, alpha), {pi}});
+      o.teams.push_back({k, cost[pi] / std::pow((double)k, alpha), {pi}});
     } else {
-      small.push_back(pi);
+      o.queue.push_back(pi);
     }
   }
-  const int R = G - used;
-  if (!small.empty()) {
-    if (R < 1) return false;
-    const size_t first = teams.size();
-    const int nb = std::min<int>(R, (int)small.size());
-    for (int q = 0; q < nb; ++q) teams.push_back({1, 0.0, {}});
-    for (int pi : small) {   // costs descending: LPT
-      size_t best = first;
-      for (size_t t = first + 1; t < teams.size(); ++t)
-        if (teams[t].load < teams[best].load) best = t;
-      teams[best].load += cost[pi];
-      teams[best].probs.push_back(pi);
-      if (teams[best].load > T * (1.0 + 1e-12)) return false;
+  o.free_ctas = G - used;
+  if (!o.queue.empty()) {
+    std::priority_queue<double, std::vector<double>, std::greater<double>> avail;
+    for (int q = 0; q < o.free_ctas; ++q) avail.push(0.0);
+    for (const PlanTeam& t : o.teams)
+      for (int r = 0; r < t.size; ++r) avail.push(t.load);
+    for (int pi : o.queue) {
+      const double f = avail.top() + cost[pi];
+      if (f > T * (1.0 + 1e-12)) return false;
+      avail.pop();
+      avail.push(f);
     }
   }
-  if (out) *out = teams;
+  if (out) *out = std::move(o);
   return true;
 }
 
@@ -227,50 +257,56 @@ static BatchPlan make_plan(const std::vector<enkf_config>& cfg, const std::vecto
   const double total = std::accumulate(cost.begin(), cost.end(), 0.0);
   double lo = total / G;
   for (int i = 0; i < count; ++i) lo = std::max(lo, cost[i] / std::pow((double)cap[i], alpha));
-  double hi = total + 1.0;   // one CTA does everything
-  std::vector<PlanTeam> teams;
-  if (!try_plan(cost, cap, idx, G, alpha, hi, &teams)) teams.assign(1, PlanTeam{1, hi, idx});
+  double hi = total + 1.0;   // every problem in the queue: fits on one CTA
+  PlanTry best;
+  try_plan(cost, cap, idx, G, alpha, hi, &best);
   for (int it = 0; it < 60 && hi > lo * (1.0 + 1e-6); ++it) {
     const double mid = 0.5 * (lo + hi);
-    std::vector<PlanTeam> trial;
+    PlanTry trial;
     if (try_plan(cost, cap, idx, G, alpha, mid, &trial)) {
       hi = mid;
-      teams.swap(trial);
+      best = std::move(trial);
     } else {
       lo = mid;
     }
   }
-  // spare CTAs join the slowest multi-CTA teams
-  int used = 0;
-  for (const PlanTeam& t : teams) used += t.size;
-  for (int spare = G - used; spare > 0; --spare) {
-    int best = -1;
-    double worst = -1.0;
-    for (int q = 0; q < (int)teams.size(); ++q) {
-      const PlanTeam& t = teams[q];
-      if (t.size < 2 || t.probs.size() != 1 || t.size >= cap[t.probs[0]]) continue;
-      if (t.load > worst) { worst = t.load; best = q; }
+  // CTAs beyond what the queue can keep busy join the slowest teams
+  int spare = best.free_ctas - (int)best.queue.size();
+  for (; spare > 0; --spare) {
+    int w = -1;
+    for (int q = 0; q < (int)best.teams.size(); ++q) {
+      const PlanTeam& t = best.teams[q];
+      if (t.size >= cap[t.probs[0]]) continue;
+      if (w < 0 || t.load > best.teams[w].load) w = q;
     }
-    if (best < 0) break;
-    PlanTeam& t = teams[best];
+    if (w < 0) break;
+    PlanTeam& t = best.teams[w];
     t.size += 1;
     t.load = cost[t.probs[0]] / std::pow((double)t.size, alpha);
+    best.free_ctas -= 1;
   }
+  // multi-CTA teams with their problem, then the free CTAs as teams of one with empty lists;
+  // order ends with the queue
   int cta = 0;
   P.team_first.push_back(0);
-  for (const PlanTeam& t : teams) {
-    if (t.probs.empty()) continue;
+  auto add_team = [&](int size, const std::vector<int>& probs) {
     const int tid = (int)P.team_size.size();
-    P.team_size.push_back(t.size);
+    P.team_size.push_back(size);
     P.team_cta0.push_back(cta);
-    for (int r = 0; r < t.size; ++r) {
+    for (int r = 0; r < size; ++r) {
       P.cta_team.push_back(tid);
       P.cta_rank.push_back(r);
     }
-    cta += t.size;
-    for (int pi : t.probs) P.order.push_back(pi);
+    cta += size;
+    for (int pi : probs) P.order.push_back(pi);
     P.team_first.push_back((int)P.order.size());
-  }
+  };
+  for (const PlanTeam& t : best.teams) add_team(t.size, t.probs);
+  const int nfree = std::min(best.free_ctas, std::max(0, (int)best.queue.size()));
+  for (int q = 0; q < nfree; ++q) add_team(1, {});
+  if (cta == 0) add_team(1, {});   // a grid of at least one CTA
+  P.queue_first = (int)P.order.size();
+  for (int pi : best.queue) P.order.push_back(pi);
   P.grid = cta;
   return P;
 }
@@ -323,19 +359,9 @@ static void drop_graph(BatchState& B) {
   if (B.graph) { cudaGraphDestroy(B.graph); B.graph = nullptr; }
 }
 
-// Install a plan: per-team slices of the reduction buffers, plan arrays on the device.
+// Install a plan: plan arrays and the problem table on the device.
 static cudaError_t apply_plan(BatchState& B, const BatchPlan& P, cudaStream_t s) {
   B.plan = P;
-  const size_t NE = (size_t)B.ne_max;
-  for (size_t t = 0; t < P.team_size.size(); ++t) {
-    const size_t c0 = (size_t)P.team_cta0[t];
-    for (int k = P.team_first[t]; k < P.team_first[t + 1]; ++k) {
-      SolveParams& sp = B.probs[P.order[k]].sp;
-      sp.Tpart = B.d_team + c0 * NE;                                   // [team size][NE]
-      sp.Tred = B.d_team + (size_t)B.max_grid * NE + c0 * NE;          // [NE]
-      sp.rrpart = B.d_team + (size_t)2 * B.max_grid * NE + c0 * 256;   // [2][team size][NT]
-    }
-  }
   std::vector<int> flat;
   for (const auto* v : {&P.cta_team, &P.cta_rank, &P.team_size, &P.team_first, &P.order})
     flat.insert(flat.end(), v->begin(), v->end());
@@ -356,14 +382,18 @@ static cudaError_t enqueue_batch(BatchState& B, cudaStream_t s) {
   int* team_size = cta_rank + nC;
   int* team_first = team_size + nT;
   int* order = team_first + nT + 1;
-  cudaError_t e = cudaMemsetAsync(B.d_bar, 0, sizeof(unsigned) * 4 * B.count, s);
+  cudaError_t e = cudaMemsetAsync(B.d_bar, 0, sizeof(unsigned) * (4 * (size_t)B.count + 4), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.d_status, 0, sizeof(int) * 4 * B.count, s);
   if (e != cudaSuccess) return e;
   const BatchProblem* probs = B.d_probs;
   const BatchIO* io = B.d_io;
   int perturb = B.perturb;
   unsigned long long* times = B.d_time;
-  void* args[] = {&probs, &io, &cta_team, &cta_rank, &team_size, &team_first, &order, &perturb, &times};
+  int queue_first = P.queue_first, count = B.count, max_grid = B.max_grid, ne_max = B.ne_max;
+  unsigned* queue_head = B.d_bar + 4 * (size_t)B.count;
+  double* team_buf = B.d_team;
+  void* args[] = {&probs, &io, &cta_team, &cta_rank, &team_size, &team_first, &order, &queue_first, &count,
+                  &queue_head, &team_buf, &max_grid, &ne_max, &perturb, &times};
   return cudaLaunchCooperativeKernel(batch_fn(B.ntmax), dim3(P.grid), dim3(kThreads), args,
                                      B.smem, s);
 }
@@ -464,7 +494,7 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.io_copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_plan, sizeof(int) * (4 * (size_t)B.max_grid + 1 + count));
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_status, sizeof(int) * 4 * count);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_bar, sizeof(unsigned) * 4 * count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_bar, sizeof(unsigned) * (4 * (size_t)count + 4));
   if (e == cudaSuccess) e = cudaMalloc((void**)&B.d_time, sizeof(unsigned long long) * 2 * count);
   if (e == cudaSuccess) e = cudaMemset(B.d_time, 0, sizeof(unsigned long long) * 2 * count);
   if (e == cudaSuccess)

@@ -1,9 +1,13 @@
 """Host-side checks of the batched-launch planner (enkf_batch_plan): no GPU needed.
 
 Contract (include/enkf.h): cost c = m N^2 (N + 8) + 2 n N^2, a team of k CTAs takes
-c / k^alpha, problems costlier than the makespan target get 2 <= k <= ceil(m / 64) CTAs, the
-rest share single-CTA teams (longest first onto the least-loaded), the target is the smallest
-feasible one."""
+c / k^alpha, problems costlier than the makespan target get a team of 2 <= k <= ceil(m / 64)
+CTAs, the rest form a shared queue (longest first) served by whichever CTA is free first: the
+CTAs outside teams from the start, each team's CTAs once its problem is done. The target is
+the smallest feasible one. The makespan below is an independent event simulation of that
+queue."""
+import heapq
+
 import numpy as np
 import pytest
 
@@ -21,14 +25,18 @@ def cost(n, m, N):
     return m * N * N * (N + 8.0) + 2.0 * n * N * N
 
 
-def team_times(shapes, plan, alpha):
+def simulate(shapes, plan, alpha):
+    """Finish time of every CTA: team problems first, then the queue taken in order by the
+    CTA that is free first."""
     ts, tf, order = plan["team_size"], plan["team_first"], plan["order"]
-    out = []
+    free = []
     for t in range(plan["teams"]):
-        probs = order[tf[t]:tf[t + 1]]
-        c = sum(cost(*shapes[p]) for p in probs)
-        out.append(c / ts[t] ** alpha if ts[t] > 1 else c)
-    return np.array(out)
+        done = sum(cost(*shapes[p]) for p in order[tf[t]:tf[t + 1]]) / ts[t] ** alpha
+        free += [done] * int(ts[t])
+    heapq.heapify(free)
+    for p in order[tf[-1]:]:
+        heapq.heappush(free, heapq.heappop(free) + cost(*shapes[p]))
+    return np.array(sorted(free))
 
 
 def lower_bound(shapes, G, alpha):
@@ -42,19 +50,23 @@ def check_plan(shapes, G, alpha, plan):
     assert 1 <= g <= G and 1 <= t <= g
     ct, cr, ts, tf, order = (plan[k] for k in ("cta_team", "cta_rank", "team_size", "team_first", "order"))
     assert sorted(order.tolist()) == list(range(len(shapes)))          # every problem once
-    assert tf[0] == 0 and tf[-1] == len(shapes) and np.all(np.diff(tf) >= 1)
+    assert tf[0] == 0 and tf[-1] <= len(shapes) and np.all(np.diff(tf) >= 0)
     assert ts.sum() == g
     c = 0
     for team in range(t):                                               # contiguous, ranked
         assert np.all(ct[c:c + ts[team]] == team)
         assert cr[c:c + ts[team]].tolist() == list(range(ts[team]))
         c += ts[team]
-    for team in range(t):                                               # multi-CTA teams
+    for team in range(t):
         probs = order[tf[team]:tf[team + 1]]
-        if ts[team] > 1:
+        if ts[team] > 1:                                                # one problem, capped team
             assert len(probs) == 1
             assert ts[team] <= (shapes[probs[0]][1] + 63) // 64
-    return team_times(shapes, plan, alpha)
+        else:                                                           # a free CTA
+            assert len(probs) == 0
+    qc = [cost(*shapes[p]) for p in order[tf[-1]:]]
+    assert all(a >= b for a, b in zip(qc, qc[1:]))                      # queue: longest first
+    return simulate(shapes, plan, alpha)
 
 
 # with alpha < 1 the bound total/G (perfect scaling) is loose, hence the wider factor
@@ -68,12 +80,14 @@ def test_plan_uneven_batch_near_lower_bound(ext, count, alpha, factor):
     times = check_plan(shapes, G, alpha, plan)
     lb = lower_bound(shapes, G, alpha)
     assert times.max() <= factor * lb, (times.max() / lb)
+    assert plan["team_first"][-1] < count                               # the queue is used
 
 
 def test_plan_degenerate(ext):
-    # one problem, one CTA
+    # one problem, one CTA: a free CTA and the problem in the queue
     p = ext.batch_plan([(100, 25, 16)], 1, 1.0)
     assert p["grid"] == 1 and p["teams"] == 1 and p["order"].tolist() == [0]
+    assert p["team_first"].tolist() == [0, 0]
     # one large problem: as many CTAs as its rows allow (64 rows per CTA)
     p = ext.batch_plan([(4096, 1024, 64)], 152, 1.0)
     check_plan([(4096, 1024, 64)], 152, 1.0, p)
@@ -88,12 +102,18 @@ def test_plan_degenerate(ext):
     p = ext.batch_plan(shapes, 152, 1.0)
     check_plan(shapes, 152, 1.0, p)
     assert p["team_size"].tolist() == [4] * 10
-    # many tiny problems: single-CTA teams, loads within one problem of each other (LPT)
+    # many tiny problems: all in the queue on 152 free CTAs, which finish within one
+    # problem's time of each other
     shapes = [(256, 64, 16)] * 500
     p = ext.batch_plan(shapes, 152, 1.0)
+    done = check_plan(shapes, 152, 1.0, p)
+    assert p["team_size"].max() == 1 and p["teams"] == 152 and p["team_first"][-1] == 0
+    assert done.max() - done.min() <= cost(*shapes[0]) * (1 + 1e-12)
+    # fewer problems than CTAs: one free CTA per problem, no idle CTAs in the grid
+    shapes = [(256, 64, 16)] * 5
+    p = ext.batch_plan(shapes, 152, 1.0)
     check_plan(shapes, 152, 1.0, p)
-    assert p["team_size"].max() == 1 and p["teams"] == 152
-    assert np.diff(p["team_first"]).max() - np.diff(p["team_first"]).min() <= 1
+    assert p["grid"] == 5
 
 
 def test_plan_rejects_bad_args(ext):
