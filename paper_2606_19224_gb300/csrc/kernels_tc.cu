@@ -49,7 +49,7 @@ static int mixed_qmax(const enkf_handle_s* h) { return (int)((mixed_rows_per(h) 
 
 size_t mixed_image_bytes(const enkf_handle_s* h) {
   const int TM = mixed_split(h->cfg) ? 2 : 1;
-  return (size_t)h->launch.G * mixed_qmax(h) * 2 * TM * kTR * h->launch.NT * 2;
+  return (size_t)h->launch.G * mixed_qmax(h) * TM * kTR * h->launch.NT * 2;
 }
 
 static cudaError_t launch_tc_images(enkf_handle_s* h) {

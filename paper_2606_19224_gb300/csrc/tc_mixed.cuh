@@ -11,10 +11,12 @@
 // recomputed in double-float on CUDA cores as the next inner right-hand side (iterative
 // refinement of the low-precision solve, with an FP64-grade final residual check).
 //
-// Operands are staged by this kernel into shared memory in the canonical K-major,
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, K-direction core stride
-// 128 B = descriptor LBO, row-group stride = descriptor SBO). One thread issues the MMAs;
-// completion is signalled through an mbarrier by tcgen05.commit; every wait is bounded.
+// Operands sit in shared memory in the canonical no-swizzle core-matrix layout (8 rows x 16
+// bytes per core matrix). For a K-major operand the descriptor's LBO is the K-direction core
+// stride and SBO the row-group stride; for an MN-major one (16-bit elements contiguous along
+// M or N) LBO is again the K-direction core stride and SBO the MN-direction one. One thread
+// issues the MMAs; completion is signalled through an mbarrier by tcgen05.commit; every wait
+// is bounded.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -36,10 +38,11 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
   d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
   return d;
 }
-// kind::f16 instruction descriptor: D F32, A = B = F16 (fmt 0) or BF16 (fmt 1), both
-// K-major, dense, M = 128.
-__host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt, int N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// kind::f16 instruction descriptor: D F32, A = B = F16 (fmt 0) or BF16 (fmt 1), A K-major,
+// B K-major (b_mn = false) or MN-major (bit 16), dense, M = 128.
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt, int N, bool b_mn = false) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
 }
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -111,37 +114,38 @@ template <int NT> __host__ __device__ constexpr int tc_tmem_cols() { return (2 *
 // significant bits instead of 8 (BF16) or 11 (FP16).
 //
 // HA reaches the CTA as precomputed tile images (tc_images_kernel): for every 128-row tile of
-// the CTA's row block, [Au hi | Au lo | Ag hi | Ag lo] with Au the K-major core layout of the
-// tile's rows (A operand of u = HA T) and Ag that of its transpose (B operand of the Gram
-// zT HA), so staging a tile is a plain 16-byte cp.async copy. The Gram is formed as
-// D_g[j][k] = sum_i z_ij HA_ik with z^T (scaled per column) as the A operand (M = 128, rows
-// j >= N zero) and Ag as the B operand (N = NT), so HA needs no padding rows.
-// NT <= 64: the next tile's Ag copy overlaps the whole current tile (two Ag buffers), the next
-// Au copy overlaps the epilogue, the z operand has its own buffer with a padded K-direction
-// core stride (144 B, conflict-free stores), and the column sums of (r, z) and (r, r) stay in
-// registers until the end of the pass. NT = 128: one buffer of each, z aliases Au.
+// the CTA's row block, [hi | lo] in the K-major core layout of the tile's rows (128 x NT), so
+// staging a tile is a plain 16-byte cp.async copy. The same image serves both MMAs: as the
+// K-major A operand of u = HA T (M = 128 rows, K = NT) and as the MN-major B operand of the
+// Gram D_g[j][k] = sum_i z_ij HA_ik (N = NT along k, K = the tile's 128 rows), whose A operand
+// is z^T scaled per column (M = 128, rows j >= N zero). One image instead of one per MMA keeps
+// the working set (images and CG vectors) in L2.
+// NT <= 64: two image buffers (the next tile's copy overlaps the whole current tile), the u
+// read-out staged as FP32 in its own region, the z operand with a padded K-direction core
+// stride (144 B, conflict-free stores), and the column sums of (r, z) and (r, r) in registers
+// until the end of the pass. NT = 128: one image buffer, refilled once the Gram MMA is done.
 template <int NT, int TERMS> struct TcLayout {
   static constexpr int TM = TERMS == 3 ? 2 : 1;
   static constexpr bool DB = NT <= 64;
-  static constexpr int AU = kTR * NT, AG = NT * kTR, BU = NT * NT;   // elements per part
+  static constexpr int AU = kTR * NT, BU = NT * NT;                  // elements per part
+  static constexpr int TILE = TM * AU;                               // elements per tile image
+  static constexpr int AUB = TILE * 2;                               // bytes per tile image
   static constexpr uint32_t LBOG = DB ? 144 : 128;                   // z operand: K core stride
   static constexpr uint32_t SBOG = 16 * LBOG;                        // 16 cores along K = 128
   static constexpr int BGP = (int)(16 * SBOG);                       // bytes per z part (M = 128)
+  static constexpr int n_au = DB ? 2 : 1;
   static constexpr int off_au = 0;
-  static constexpr int off_bu = off_au + TM * AU * 2;
-  static constexpr int off_ag = off_bu + TM * BU * 2;
-  static constexpr int n_ag = DB ? 2 : 1;
-  static constexpr int off_bg = DB ? off_ag + n_ag * TM * AG * 2 : off_au;
-  static constexpr int end_bg = DB ? off_bg + TM * BGP : off_ag + n_ag * TM * AG * 2;
+  static constexpr int off_bu = off_au + n_au * AUB;
+  static constexpr int off_bg = off_bu + TM * BU * 2;
+  static constexpr int end_bg = off_bg + TM * BGP;
   static constexpr int off_sacc = end_bg;
   static constexpr int off_zs = off_sacc + 4 * (8 * 2 * NT);
   static constexpr int off_ts = off_zs + 4 * NT;   // ts [NT] then 1/ts [NT]
   // NT <= 64: the tile's u = HA T read out of TMEM, staged as FP32 [128][NT] (swizzled 4-float
-  // groups) for the coalesced epilogue; it reuses the Au bytes when they are large enough
-  static constexpr bool U_ALIAS = TM * AU * 2 >= kTR * NT * 4;
-  static constexpr int off_u = U_ALIAS ? off_au : off_ts + 8 * NT;
-  static constexpr int bytes = (DB && !U_ALIAS) ? off_u + kTR * NT * 4 : off_ts + 8 * NT;
-  static_assert(DB || TM * BGP <= TM * AU * 2, "z operand must fit in the Au region");
+  // groups) for the coalesced epilogue
+  static constexpr int off_u = off_ts + 8 * NT;
+  static constexpr int bytes = DB ? off_u + kTR * NT * 4 : off_ts + 8 * NT;
+  static_assert(off_bu % 1024 == 0 && off_bg % 1024 == 0 && off_u % 16 == 0, "operand alignment");
 };
 
 __device__ __forceinline__ void tc_cp16(void* sdst, const void* gsrc) {
@@ -164,13 +168,12 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
                           bool& ok, double* __restrict__ out) {
   using L = TcLayout<NT, TERMS>;
   constexpr bool SPLIT = TERMS == 3, DB = L::DB;
-  constexpr int TM = L::TM;
+  static_assert(!DB, "NT = 128 only");
   constexpr uint32_t idesc = umma_idesc(H16<T16>::fmt, NT);
+  constexpr uint32_t idesc_g = umma_idesc(H16<T16>::fmt, NT, true);
   constexpr int HALF = NT / 2, CH = HALF / 16;   // columns per warp half, 16-column chunks
-  constexpr int TILE = 2 * TM * kTR * NT;        // elements per tile image
   T16* sAu = reinterpret_cast<T16*>(tcs + L::off_au);
   const T16* sBu = reinterpret_cast<const T16*>(tcs + L::off_bu);
-  unsigned char* sAg0 = tcs + L::off_ag;
   unsigned char* sBg = tcs + L::off_bg;
   float* sacc = reinterpret_cast<float*>(tcs + L::off_sacc);
   const float* zs = reinterpret_cast<const float*>(tcs + L::off_zs);
@@ -182,10 +185,7 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
   const uint32_t d_u = tmem, d_g = tmem + NT;
   const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
   const unsigned char* gimg = reinterpret_cast<const unsigned char*>(img);
-  constexpr int AUB = TM * kTR * NT * 2, AGB = TM * NT * kTR * 2;   // bytes of Au / Ag per tile
-  auto au_src = [&](int q) { return gimg + (size_t)q * TILE * 2; };
-  auto ag_src = [&](int q) { return gimg + (size_t)q * TILE * 2 + AUB; };
-  auto sAg = [&](int q) { return sAg0 + (DB ? (q & 1) * AGB : 0); };
+  auto au_src = [&](int q) { return gimg + (size_t)q * L::AUB; };
   // z operand element (row j, col i) of part `part`
   auto bg_ptr = [&](int part, int j, int i) {
     return reinterpret_cast<T16*>(sBg + part * L::BGP + (j >> 3) * L::SBOG + (i >> 3) * L::LBOG +
@@ -193,21 +193,13 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
   };
   (void)qmax;
   for (int e = t; e < 8 * 2 * NT; e += kThreads) sacc[e] = 0.f;
-  if constexpr (DB) {
-    // rows j in [NT, 128) of the z operand stay zero for the whole pass
-    for (int e = t; e < TM * (kTR - NT) * kTR; e += kThreads) {
-      const int part = e / ((kTR - NT) * kTR), rem = e % ((kTR - NT) * kTR);
-      *bg_ptr(part, NT + rem / kTR, rem % kTR) = H16<T16>::from(0.f);
-    }
-  }
   float gA[DB ? CH : 1][16], gB[DB ? CH : 1][16];
 #pragma unroll
   for (int c = 0; c < (DB ? CH : 1); ++c)
 #pragma unroll
     for (int y = 0; y < 16; ++y) { gA[c][y] = 0.f; gB[c][y] = 0.f; }
   if (Qb > 0) {
-    tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), AUB);
-    tc_copy(sAg(0), ag_src(0), AGB);
+    tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), L::AUB);
     tc_cp_commit();
   }
   for (int q = 0; q < Qb && ok; ++q) {
@@ -215,10 +207,6 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     tc_cp_wait_all();
     fence_async_smem();
     __syncthreads();
-    if (DB && q + 1 < Qb) {   // next tile's Ag into the other buffer, behind this whole tile
-      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
-      tc_cp_commit();
-    }
     if (t == 0) {
       tc_fence_after();
       constexpr uint32_t sbo_u = (NT / 8) * 128;
@@ -264,10 +252,6 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
     ph_u ^= 1u;
     tc_fence_after();
-    if (DB && q + 1 < Qb) {   // the u MMA has consumed Au: the next tile's Au behind the epilogue
-      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
-      tc_cp_commit();
-    }
     float tA[16], tB[16];   // NT = 128: this chunk's column terms, reduced over the warp per chunk
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -336,29 +320,30 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      const uint32_t ag = smem_addr(sAg(q)), bg = smem_addr(sBg);
-      constexpr uint32_t sbo_a = 16 * 128;   // Ag: 16 cores of 128 B along K = 128
+      // B = the tile image read MN-major: K = rows (row-group stride (NT/8) 128 B, two per
+      // K block of 16), N = NT (core stride 128 B)
+      const uint32_t au = smem_addr(sAu), bg = smem_addr(sBg);
+      constexpr uint32_t kst = (NT / 8) * 128;
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-        const uint64_t B0 = umma_desc(ag + kb * 256, 128, sbo_a);
-        umma_f16(d_g, A0, B0, idesc, (q == 0 && kb == 0) ? 0u : 1u);
+        const uint64_t B0 = umma_desc(au + kb * 2 * kst, kst, 128);
+        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
         if (SPLIT) {
           const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-          const uint64_t B1 = umma_desc(ag + L::AG * 2 + kb * 256, 128, sbo_a);
-          umma_f16(d_g, A0, B1, idesc, 1u);
-          umma_f16(d_g, A1, B0, idesc, 1u);
+          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * kst, kst, 128);
+          umma_f16(d_g, A0, B1, idesc_g, 1u);
+          umma_f16(d_g, A1, B0, idesc_g, 1u);
         }
       }
       umma_commit(mbar_g);
     }
-    // the Gram MMA reads the z operand (and, NT = 128, the Au region): wait before reuse
+    // the Gram MMA reads the z operand and the image: wait before either is rewritten
     if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
     ph_g ^= 1u;
     tc_fence_after();
-    if (!DB && q + 1 < Qb) {
-      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
-      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
+    if (q + 1 < Qb) {
+      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), L::AUB);
       tc_cp_commit();
     }
   }
@@ -432,14 +417,12 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   constexpr bool SPLIT = TERMS == 3;
   constexpr int TM = L::TM;
   constexpr uint32_t idesc = umma_idesc(H16<T16>::fmt, NT);
+  constexpr uint32_t idesc_g = umma_idesc(H16<T16>::fmt, NT, true);
   constexpr int HALF = NT / 2, CH = HALF / 16;    // TMEM read-out: columns per warp half
   constexpr int NG = NT / 4, GM = NG - 1;         // 4-float column groups, swizzle mask
   constexpr int NJ = NG, RI = kThreads / NJ;      // update: threads per row, rows per sweep
-  constexpr int TILE = 2 * TM * kTR * NT;
-  constexpr int AUB = TM * kTR * NT * 2, AGB = TM * NT * kTR * 2;
-  T16* sAu = reinterpret_cast<T16*>(tcs + L::off_au);
+  unsigned char* sAu0 = tcs + L::off_au;
   const T16* sBu = reinterpret_cast<const T16*>(tcs + L::off_bu);
-  unsigned char* sAg0 = tcs + L::off_ag;
   unsigned char* sBg = tcs + L::off_bg;
   float* sU = reinterpret_cast<float*>(tcs + L::off_u);
   const float* zs = reinterpret_cast<const float*>(tcs + L::off_zs);
@@ -451,9 +434,8 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   const uint32_t d_u = tmem, d_g = tmem + NT;
   const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
   const unsigned char* gimg = reinterpret_cast<const unsigned char*>(img);
-  auto au_src = [&](int q) { return gimg + (size_t)q * TILE * 2; };
-  auto ag_src = [&](int q) { return gimg + (size_t)q * TILE * 2 + AUB; };
-  auto sAg = [&](int q) { return sAg0 + (q & 1) * AGB; };
+  auto au_src = [&](int q) { return gimg + (size_t)q * L::AUB; };
+  auto sAu = [&](int q) { return sAu0 + (q & 1) * L::AUB; };
   auto bg_ptr = [&](int part, int j, int i) {
     return reinterpret_cast<T16*>(sBg + part * L::BGP + (j >> 3) * L::SBOG + (i >> 3) * L::LBOG +
                                   (((j & 7) * 8 + (i & 7)) * 2));
@@ -474,8 +456,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   }
   float sg[4] = {0.f, 0.f, 0.f, 0.f}, sr[4] = {0.f, 0.f, 0.f, 0.f};
   if (Qb > 0) {
-    tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), AUB);
-    tc_copy(sAg(0), ag_src(0), AGB);
+    tc_copy(sAu(0), au_src(0), L::AUB);
     tc_cp_commit();
   }
   const bool vec = (N & 3) == 0;
@@ -484,14 +465,15 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     tc_cp_wait_all();
     fence_async_smem();
     __syncthreads();
-    if (q + 1 < Qb) {   // next tile's Ag into the other buffer, behind this whole tile
-      tc_copy(sAg(q + 1), ag_src(q + 1), AGB);
+    if (q + 1 < Qb) {   // next tile's image into the other buffer, behind this whole tile
+      tc_copy(sAu(q + 1), au_src(q + 1), L::AUB);
       tc_cp_commit();
     }
+    const uint32_t au = smem_addr(sAu(q));
+    constexpr uint32_t sbo_u = (NT / 8) * 128;
     if (t == 0) {
       tc_fence_after();
-      constexpr uint32_t sbo_u = (NT / 8) * 128;
-      const uint32_t au = smem_addr(sAu), bu = smem_addr(sBu);
+      const uint32_t bu = smem_addr(sBu);
 #pragma unroll
       for (int kb = 0; kb < NT / 16; ++kb) {
         umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
@@ -568,24 +550,21 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     tc_fence_before();
     fence_async_smem();
     __syncthreads();
-    if (q + 1 < Qb) {   // Au (and the u staging on it) is free: next tile's Au behind the Gram MMA
-      tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(q + 1), AUB);
-      tc_cp_commit();
-    }
     if (t == 0) {
       tc_fence_after();
-      const uint32_t ag = smem_addr(sAg(q)), bg = smem_addr(sBg);
-      constexpr uint32_t sbo_a = 16 * 128;
+      // B = the same tile image read MN-major: K = rows (row-group stride sbo_u, two per K
+      // block of 16), N = NT (core stride 128 B)
+      const uint32_t bg = smem_addr(sBg);
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-        const uint64_t B0 = umma_desc(ag + kb * 256, 128, sbo_a);
-        umma_f16(d_g, A0, B0, idesc, (q == 0 && kb == 0) ? 0u : 1u);
+        const uint64_t B0 = umma_desc(au + kb * 2 * sbo_u, sbo_u, 128);
+        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
         if (SPLIT) {
           const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-          const uint64_t B1 = umma_desc(ag + L::AG * 2 + kb * 256, 128, sbo_a);
-          umma_f16(d_g, A0, B1, idesc, 1u);
-          umma_f16(d_g, A1, B0, idesc, 1u);
+          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * sbo_u, sbo_u, 128);
+          umma_f16(d_g, A0, B1, idesc_g, 1u);
+          umma_f16(d_g, A1, B0, idesc_g, 1u);
         }
       }
       umma_commit(mbar_g);
@@ -635,15 +614,15 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
 }
 
 // The tile images of the tensor-core pass, from the double-float HA: for CTA b (rows
-// [b rows_per, ...)) and its tile q (128 rows), at ((b qmax + q) 2 TM) 128 NT elements:
-// [Au hi | Au lo | Ag hi | Ag lo]; Au(r, k) = core_idx(r, k, NT), Ag(k, r) = core_idx(k, r, 128).
-// hi = round(HA), lo = round(HA - hi) in T16. Entries outside [0, m) x [0, N) are never
-// written (the buffer is zeroed once when the handle is created).
+// [b rows_per, ...)) and its tile q (128 rows), at (b qmax + q) TM 128 NT elements: [hi | lo],
+// element (r, k) of each part at core_idx(r, k, NT); hi = round(HA), lo = round(HA - hi) in
+// T16. Entries outside [0, m) x [0, N) are never written (the buffer is zeroed once when the
+// handle is created).
 template <typename T16, int TERMS>
 __global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N, int NT, int64_t rows_per,
                                  int qmax, T16* __restrict__ img) {
   constexpr int TM = TERMS == 3 ? 2 : 1;
-  const int64_t tile = (int64_t)2 * TM * kTR * NT;
+  const int64_t tile = (int64_t)TM * kTR * NT;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * N; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / N;
     const int k = (int)(e % N);
@@ -653,12 +632,7 @@ __global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N
     const df32 h = HAdf[e];
     const T16 hi = H16<T16>::from(h.hi);
     base[core_idx(r, k, NT)] = hi;
-    base[(int64_t)TM * kTR * NT + core_idx(k, r, kTR)] = hi;
-    if (TM == 2) {
-      const T16 lo = H16<T16>::from((h.hi - (float)hi) + h.lo);
-      base[(int64_t)kTR * NT + core_idx(r, k, NT)] = lo;
-      base[(int64_t)3 * kTR * NT + core_idx(k, r, kTR)] = lo;
-    }
+    if (TM == 2) base[(int64_t)kTR * NT + core_idx(r, k, NT)] = H16<T16>::from((h.hi - (float)hi) + h.lo);
   }
 }
 
@@ -767,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   const double inv_nm1 = 1.0 / (double)(N - 1);
   double* Tp = p.Tpart + (int64_t)b * NE;
   // this CTA's tile images (tc_images_kernel uses the same row blocks)
-  const T16* img = static_cast<const T16*>(p.HA16) + (size_t)b * p.qmax * (2 * TL::TM * kTR * NT);
+  const T16* img = static_cast<const T16*>(p.HA16) + (size_t)b * p.qmax * TL::TILE;
   constexpr int TMC = tc_tmem_cols<NT>();
 
   if (t == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); }
