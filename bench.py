@@ -48,15 +48,22 @@ def B_REF(m, N):
     writes the next right-hand side (4 m N)."""
     return 56 * m * N
 
-# DRAM bytes (read + write) of one solve_kernel launch on this workload, from the ncu capture
-# summarised in profiles/solve_kernel_fp32_grf512_N64_m65536.md, and the hash of the kernel source
-# that capture measured; reported as null once the source has changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 4.646492e9, "src_sha": "013d8296b5c10161"}}
+# DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
+# captures summarised in profiles/solve_kernel_fp32_grf512_N64_m65536.md and
+# profiles/solve_mixed_kernel_fp16_grf512_N64_m65536.md, with the hash of the kernel sources
+# each capture measured; reported as null once those sources have changed.
+NCU_TRAFFIC = {"fp32": {"bytes": 4.641770e9, "src_sha": "05a9f335b2719b7a"},
+               "fp16": {"bytes": 6.278849e9, "src_sha": "6ff7635f911fe74f"}}
+_KERNEL_SOURCES = {
+    "fp32": ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"),
+    "fp16": ("kernels_tc.cu", "kernels_tc_fp16.cu", "tc_mixed.cuh", "common.cuh", "cg_device.cuh"),
+    "bf16": ("kernels_tc.cu", "kernels_tc_bf16.cu", "tc_mixed.cuh", "common.cuh", "cg_device.cuh"),
+}
 
 
-def _src_hash():
+def _src_hash(precision="fp32"):
     h = hashlib.sha256()
-    for f in ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"):
+    for f in _KERNEL_SOURCES[precision]:
         with open(os.path.join(ROOT, "paper_2606_19224_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -326,7 +333,7 @@ def run_ours(args):
     peak, peak_src = _peaks()
     achieved = alg_bytes / (solve_avg_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(args.precision, {})
-    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash() else None
+    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash(args.precision) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64,1>" if args.precision == "fp32" else f"solve_mixed_kernel<{args.precision},64>",
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
