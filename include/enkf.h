@@ -146,7 +146,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
    otherwise); d_y: device [m] FP64; (seed, counter) select the Philox4x32-10 stream of the
    perturbations E when cfg.perturb_obs = 1 (element (i, j) uses counter
    (i, j >> 1, counter_lo, counter_hi) and key (seed_lo, seed_hi); two 53-bit uniforms and
-   Box-Muller give the normal, E_ij = sqrt(r_i) * normal). d_Xa: device [n][N], same dtype
+   Box-Muller give the normal, E_ij = sqrt(r_i) * normal; ENKF_FP64 evaluates Box-Muller in
+   FP64, the FP32 and tensor-core modes in FP32 from the same uniforms, within about 1e-7 of
+   the FP64 normal). d_Xa: device [n][N], same dtype
    as d_Xf; d_Xa == d_Xf (in-place) is allowed, partial overlap is not. Never allocates. */
 enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uint64_t seed,
                          uint64_t counter, void* d_Xa);
@@ -181,8 +183,9 @@ enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
 enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z,
                                     double* d_W);
 
-/* Draw the observation perturbations exactly as enkf_analyze does: d_r device [m] FP64,
-   d_E device [m][N] FP64 output, on cuda_stream. */
+/* Draw the observation perturbations exactly as enkf_analyze does in ENKF_FP64 mode (the
+   FP32 and tensor-core modes draw the same normals in single precision): d_r device [m]
+   FP64, d_E device [m][N] FP64 output, on cuda_stream. */
 enkf_status enkf_draw_perturbations(uint64_t seed, uint64_t counter, const double* d_r,
                                     int64_t m, int32_t N, double* d_E, void* cuda_stream);
 

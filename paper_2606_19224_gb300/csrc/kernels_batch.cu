@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "innov_device.cuh"
 #include "solve_body.cuh"
 
 namespace enkf {

@@ -20,6 +20,7 @@
 // contraction so their latency overlaps it. In the FP32 mode the inner loops contain no
 // FP64 arithmetic (FP64 runs at 1/64 of the FP32 rate on this part): per-thread partial
 // sums are FP32 and only the cross-thread / cross-CTA reductions and the CG scalars are FP64.
+#include "innov_device.cuh"
 #include "solve_body.cuh"
 
 #include <algorithm>

@@ -1,6 +1,6 @@
 // The persistent CG solve of one problem by a set of co-resident CTAs, and the row-range
-// forms of the innovation and update steps: shared by the single-analysis kernels
-// (kernels_fp.cu) and the batched kernel (kernels_batch.cu).
+// form of the update step: shared by the single-analysis kernels (kernels_fp.cu) and the
+// batched kernel (kernels_batch.cu). The innovations are in innov_device.cuh.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -357,93 +357,6 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     if (prof) {
       ph[PH_REFRESH] += 0;
       for (int q = 0; q < PH_COUNT; ++q) p.prof[q] = ph[q];
-    }
-  }
-}
-
-// ------------------------------------------------------------------ K1: innovations
-// Standard normals of members (j, j + 1), j even, from one Philox block and one Box-Muller
-// pair (the definition of perturbation_normal for both members, computed once).
-__device__ __forceinline__ void perturbation_pair(int64_t i, int j, uint64_t seed, uint64_t counter,
-                                                  double& n_even, double& n_odd) {
-  uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(j >> 1), c2 = (uint32_t)counter, c3 = (uint32_t)(counter >> 32);
-  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-  const uint64_t x1 = ((uint64_t)c0 << 21) | (c1 >> 11);
-  const uint64_t x2 = ((uint64_t)c2 << 21) | (c3 >> 11);
-  const double u1 = ((double)x1 + 0.5) * 0x1p-53;
-  const double u2 = (double)x2 * 0x1p-53;
-  const double rho = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincos(6.283185307179586 * u2, &sn, &cs);
-  n_even = rho * cs;
-  n_odd = rho * sn;
-}
-
-// Rows [i_begin, i_end) of the observation operator, one warp per row: `warp` is this warp's
-// index among `nwarps` warps sharing the range. Lane l owns members 2l, 2l + 1, 2l + 64,
-// 2l + 65, so each perturbation pair is drawn once.
-template <typename VT>
-__device__ __forceinline__ void innov_rows(
-    const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-    const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
-    const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
-    double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
-    float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
-    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
-    int64_t warp, int64_t nwarps) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t i = i_begin + warp; i < i_end; i += nwarps) {
-    double z[4] = {0.0, 0.0, 0.0, 0.0};
-    const int k0 = rowptr[i], k1 = rowptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const double wk = w[k];
-      const VT* xr = Xf + (int64_t)col[k] * N;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 2 * lane + (q & 1) + 64 * (q >> 1);
-        if (j < N) z[q] = fma(wk, (double)xr[j], z[q]);
-      }
-    }
-    double s = z[0] + z[1] + z[2] + z[3];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double zbar = s / (double)N;
-    const double yi = y[i], sr = sqrt(r[i]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int jp = 2 * lane + 64 * h;   // even member of the pair
-      if (jp >= N) continue;
-      double nrm[2] = {0.0, 0.0};
-      if (emode == 2) perturbation_pair(i, jp, seed, counter, nrm[0], nrm[1]);
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int j = jp + b;
-        if (j >= N) continue;
-        const int q = 2 * h + b;
-        const int64_t e = i * N + j;
-        double pert = 0.0;
-        if (emode == 1) pert = E[e];
-        else if (emode == 2) pert = sr * nrm[b];
-        const double ha = z[q] - zbar;
-        const double d = (yi - z[q]) + pert;
-        if (HA64) HA64[e] = ha;
-        D[e] = d;
-        if (HA32) HA32[e] = (float)ha;
-        if (B32) B32[e] = (float)d;
-        if (HAdf) HAdf[e] = df32(ha);
-        if (Ddf) Ddf[e] = df32(d);
-        // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
-        if (HAb) {
-          const __nv_bfloat16 hi = __double2bfloat16(ha);
-          HAb[e] = hi;
-          if (split_lo) HAb[m * N + e] = __double2bfloat16(ha - (double)__bfloat162float(hi));
-        }
-        if (HAh) {
-          const __half hi = __double2half(ha);
-          HAh[e] = hi;
-          if (split_lo) HAh[m * N + e] = __double2half(ha - (double)__half2float(hi));
-        }
-      }
     }
   }
 }
