@@ -95,24 +95,52 @@ __device__ __forceinline__ void innov_rows(
         if constexpr (sizeof(VT) == 4) perturbation_pair_f32(i, jp, seed, counter, nrm[0], nrm[1]);
         else perturbation_pair(i, jp, seed, counter, nrm[0], nrm[1]);
       }
+      const int64_t e0 = i * N + jp;
+      double hv[2], dv[2];
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        const int j = jp + b;
-        if (j >= N) continue;
-        const int q = 2 * h + b;
-        const int64_t e = i * N + j;
         double pert = 0.0;
-        if (emode == 1) pert = E[e];
-        else if (emode == 2) pert = sr * nrm[b];
-        const double ha = z[q] - zbar;
-        const double d = (yi - z[q]) + pert;
-        if (HA64) HA64[e] = ha;
-        D[e] = d;
-        if (HA32) HA32[e] = (float)ha;
-        if (B32) B32[e] = (float)d;
-        if (HAdf) HAdf[e] = df32(ha);
-        if (Ddf) Ddf[e] = df32(d);
-        // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
+        if (jp + b < N) {
+          if (emode == 1) pert = E[e0 + b];
+          else if (emode == 2) pert = sr * nrm[b];
+        }
+        hv[b] = z[2 * h + b] - zbar;
+        dv[b] = (yi - z[2 * h + b]) + pert;
+      }
+      if ((N & 1) == 0) {
+        // both members present and e0 even: one 8- or 16-byte store per array per lane, so a
+        // warp writes contiguous row segments
+        if (HA64) *reinterpret_cast<double2*>(HA64 + e0) = make_double2(hv[0], hv[1]);
+        *reinterpret_cast<double2*>(D + e0) = make_double2(dv[0], dv[1]);
+        if (HA32) *reinterpret_cast<float2*>(HA32 + e0) = make_float2((float)hv[0], (float)hv[1]);
+        if (B32) *reinterpret_cast<float2*>(B32 + e0) = make_float2((float)dv[0], (float)dv[1]);
+        if (HAdf) {
+          const df32 a0(hv[0]), a1(hv[1]);
+          *reinterpret_cast<float4*>(HAdf + e0) = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
+        }
+        if (Ddf) {
+          const df32 d0(dv[0]), d1(dv[1]);
+          *reinterpret_cast<float4*>(Ddf + e0) = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          if (jp + b >= N) continue;
+          const int64_t e = e0 + b;
+          if (HA64) HA64[e] = hv[b];
+          D[e] = dv[b];
+          if (HA32) HA32[e] = (float)hv[b];
+          if (B32) B32[e] = (float)dv[b];
+          if (HAdf) HAdf[e] = df32(hv[b]);
+          if (Ddf) Ddf[e] = df32(dv[b]);
+        }
+      }
+      // low-precision copies: hi part at [0, m N), lo part (ha - hi) at [m N, 2 m N) when split
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        if (jp + b >= N) continue;
+        const int64_t e = e0 + b;
+        const double ha = hv[b];
         if (HAb) {
           const __nv_bfloat16 hi = __double2bfloat16(ha);
           HAb[e] = hi;
