@@ -54,10 +54,14 @@ def B_REF(m, N):
 # each capture measured; reported as null once those sources have changed.
 NCU_TRAFFIC = {"fp32": {"bytes": 4.641770e9, "src_sha": "7a1ece797b921175"},
                "fp16": {"bytes": 6.278849e9, "src_sha": "6ff7635f911fe74f"}}
+# The same for one batch_kernel launch on the 256-problem batch (seed 1), from the one-pass
+# DRAM capture summarised in profiles/batch_kernel_batched256_grf_dram.md.
+NCU_TRAFFIC_BATCH = {"bytes": 1.436830e12, "problems": 256, "seed": 1, "src_sha": "19d58d4932c5b47f"}
 _KERNEL_SOURCES = {
     "fp32": ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"),
     "fp16": ("kernels_tc.cu", "kernels_tc_fp16.cu", "tc_mixed.cuh", "common.cuh", "cg_device.cuh"),
     "bf16": ("kernels_tc.cu", "kernels_tc_bf16.cu", "tc_mixed.cuh", "common.cuh", "cg_device.cuh"),
+    "batch": ("kernels_batch.cu", "solve_body.cuh", "innov_device.cuh", "common.cuh", "cg_device.cuh"),
 }
 
 
@@ -479,6 +483,9 @@ def run_batched(args):
     launch_ms = ms / args.steps
     peak, peak_src = _peaks()
     achieved = alg / (launch_ms / 1e3) / 1e9
+    tb = NCU_TRAFFIC_BATCH
+    batch_traffic = (tb["bytes"] if (count == tb["problems"] and args.seed == tb["seed"]
+                                     and tb["src_sha"] == _src_hash("batch")) else None)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -492,7 +499,7 @@ def run_batched(args):
             "error": {"rel_frobenius_vs_fp64_oracle_max": max(errs), "sampled_problems": len(errs),
                       "status_ok": int(np.sum(st["status"] == 0))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel<128>",
+                         "frac": achieved / peak, "traffic": batch_traffic, "kernel": "batch_kernel<128>",
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms},
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -54,6 +54,26 @@ def test_perturbations_match_oracle_generator(lib):
         assert np.max(np.abs(E - ref)) <= 1e-14 * np.max(np.abs(ref))
 
 
+def test_single_precision_perturbations_in_fp32_mode(lib):
+    # The FP32 and tensor-core modes draw the Box-Muller normals in FP32 from the same Philox
+    # uniforms; the innovations D = y + E - H X_f they form must agree with the oracle's (E
+    # drawn in FP64) to about 1e-7 of the perturbation scale, tails included (m N / 2 = 640 k
+    # pairs reach uniforms within 1e-5 of 0 and of 1).
+    p = synth.workload("grf512_N64_m65536", 21, scale=2, dtype=np.float32)   # n = 65,536, m = 16,384, N = 64
+    for prec in ("fp32", "fp16"):
+        an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8,
+                          precondition=1)
+        Xf = torch.from_numpy(p.Xf).cuda()
+        an.analyze(Xf, torch.from_numpy(p.y).cuda(), seed=9, counter=4)
+        _, D, _, _ = (t.cpu().numpy() for t in an.intermediates())
+        E = oracle.obs_perturbations(9, 4, p.r, p.N)
+        Dref = oracle.innovations(p.y, oracle.apply_H(p.rowptr, p.col, p.w, p.Xf.astype(np.float64)), E)
+        err = np.abs(D - Dref) / np.sqrt(p.r)[:, None]
+        assert err.max() <= 2e-6, (prec, err.max())
+        assert np.sqrt(np.mean(err ** 2)) <= 2e-7, (prec, np.sqrt(np.mean(err ** 2)))
+        an.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("shape", [(4096, 64, 1024), (2500, 37, 999), (1600, 20, 400),
                                    (3000, 100, 700), (2048, 128, 1536), (500, 2, 130)])
