@@ -118,6 +118,32 @@ __device__ __forceinline__ df32 operator*(const df32& a, const df32& b) {
 }
 __device__ __forceinline__ df32& operator+=(df32& a, const df32& b) { a = a + b; return a; }
 
+// A running sum of double-float products kept as an unnormalised pair (s, c): each product's
+// high part enters s through TwoSum, and its rounding error, the cross terms of the operands'
+// low parts and the TwoSum error are added to c. renorm() folds c back into s and is called
+// every few terms, so c stays within a few ulp(s) (the compensated dot product of Ogita,
+// Rump and Oishi, renormalised in short blocks): 12 FP32 operations per term instead of the
+// 15 of a renormalising double-float multiply-add, with the same double-float accuracy.
+struct DFAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(const df32& a, const df32& b) {
+    const float ph = __fmul_rn(a.hi, b.hi);
+    float pl = __fmaf_rn(a.hi, b.hi, -ph);
+    pl = __fmaf_rn(a.hi, b.lo, pl);
+    pl = __fmaf_rn(a.lo, b.hi, pl);
+    float t, e;
+    df_two_sum(s, ph, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pl));
+  }
+  __device__ __forceinline__ void renorm() {
+    const df32 v = df_fast2sum(s, c);
+    s = v.hi;
+    c = v.lo;
+  }
+  __device__ __forceinline__ df32 value() const { return df_fast2sum(s, c); }
+};
+
 // ------------------------------------------------------------------ 4-wide fragments
 template <typename CT> __device__ __forceinline__ void load_vec(CT* d, const CT* s, int n);
 template <> __device__ __forceinline__ void load_vec<float>(float* d, const float* s, int n) {
@@ -913,11 +939,8 @@ __device__ void refreshA_async(const df32* __restrict__ HAdf, df32* Zdf, const f
   constexpr int MA = TL::MA, NG = TL::NG, TPG = TL::TPG, RG = TL::RG, TR = TL::TRA;
   const int t = threadIdx.x, g = t / TPG, u = t % TPG, tj = u % NG, tk = u / NG;
   const int k0 = tk * MA, j0 = tj * MA;
-  df32 acc[MA][MA];
-#pragma unroll
-  for (int x = 0; x < MA; ++x)
-#pragma unroll
-    for (int y = 0; y < MA; ++y) acc[x][y] = df32(0.f, 0.f);
+  DFAcc acc[MA][MA];
+  int since = 0;   // rows added since the last renormalisation
   auto issue = [&](int64_t i0, int b) {
     unsigned char* sb = tiles + b * TL::BUFA;
     df32* sH = reinterpret_cast<df32*>(sb);
@@ -972,7 +995,14 @@ __device__ void refreshA_async(const df32* __restrict__ HAdf, df32* Zdf, const f
 #pragma unroll
       for (int x = 0; x < MA; ++x)
 #pragma unroll
-        for (int y = 0; y < MA; ++y) acc[x][y] = fma(a[x], v[y], acc[x][y]);
+        for (int y = 0; y < MA; ++y) acc[x][y].add(a[x], v[y]);
+      if (++since == 4) {
+        since = 0;
+#pragma unroll
+        for (int x = 0; x < MA; ++x)
+#pragma unroll
+          for (int y = 0; y < MA; ++y) acc[x][y].renorm();
+      }
     }
     __syncthreads();   // the buffer is refilled by the copy issued in the next iteration
   }
@@ -981,7 +1011,7 @@ __device__ void refreshA_async(const df32* __restrict__ HAdf, df32* Zdf, const f
 #pragma unroll
     for (int x = 0; x < MA; ++x)
 #pragma unroll
-      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + j0 + y] = (double)acc[x][y];
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + j0 + y] = (double)acc[x][y].value();
     __syncthreads();
     if (g == 0) {
 #pragma unroll
@@ -1000,7 +1030,7 @@ __device__ void refreshA_async(const df32* __restrict__ HAdf, df32* Zdf, const f
 #pragma unroll
       for (int y = 0; y < MA; ++y) {
         const int k = k0 + x, j = j0 + y;
-        if (k < N && j < N) out[k * N + j] = (double)acc[x][y];
+        if (k < N && j < N) out[k * N + j] = (double)acc[x][y].value();
       }
   }
   if (t < N) {
@@ -1052,21 +1082,23 @@ __device__ void refreshB_async(const df32* __restrict__ HAdf, const df32* __rest
     const df32* sH = reinterpret_cast<const df32*>(sb);
     const df32* sZ = sH + TR * NT;
     const df32* sD = sZ + TR * NT;
-    df32 acc[MR][4];
+    DFAcc acc[MR][4];
+    for (int k = 0; k < NT; k += 4) {   // NT % 4 == 0; renormalised after every 4 terms
 #pragma unroll
-    for (int x = 0; x < MR; ++x)
+      for (int kk = 0; kk < 4; ++kk) {
+        df32 a[MR], bv[4];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = df32(0.f, 0.f);
-#pragma unroll 4
-    for (int k = 0; k < NT; ++k) {
-      df32 a[MR], bv[4];
+        for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * NT + k + kk];
+        load_vec<df32>(bv, sT + (k + kk) * LDT + j0, 4);
 #pragma unroll
-      for (int x = 0; x < MR; ++x) a[x] = sH[(r0 + x) * NT + k];
-      load_vec<df32>(bv, sT + k * LDT + j0, 4);
+        for (int x = 0; x < MR; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y].add(a[x], bv[y]);
+      }
 #pragma unroll
       for (int x = 0; x < MR; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
+        for (int y = 0; y < 4; ++y) acc[x][y].renorm();
     }
 #pragma unroll
     for (int x = 0; x < MR; ++x) {
@@ -1079,7 +1111,7 @@ __device__ void refreshB_async(const df32* __restrict__ HAdf, const df32* __rest
         VT o[4];
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          const df32 q = fma(ri, z[y], acc[x][y] * inv);
+          const df32 q = fma(ri, z[y], acc[x][y].value() * inv);
           const df32 rt = d[y] - q;
           rr[y] = __fmaf_rn(rt.hi, rt.hi, rr[y]);
           o[y] = (VT)rt.hi;
