@@ -141,6 +141,26 @@ def _dist():
     return ws, rank, local
 
 
+def _rank_seed(seed, rank):
+    """Each rank analyses its own seeded problems (weak scaling): seeds 1000 apart."""
+    return seed + 1000 * rank
+
+
+def _max_over_ranks(x, dev, ws):
+    """The slowest rank's figure (the job's time): all_reduce MAX of one float64 on `dev`."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, seconds, ws):
+    """Whole-job throughput: the units all ws ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def _cores():
     try:
         from threadpoolctl import threadpool_info
@@ -214,7 +234,7 @@ def run_ours(args):
     import paper_2606_19224_gb300 as enkf
     import synth
 
-    seed = args.seed + 1000 * rank
+    seed = _rank_seed(args.seed, rank)
     p = synth.workload(WORKLOAD, seed, dtype=np.float32)
     n, m, N = p.n, p.m, p.N
     an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision=args.precision, tol=1e-8,
@@ -256,12 +276,8 @@ def run_ours(args):
         refines.append(s["refinements"])
     barrier()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms = _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, ws)
+    value = _job_rate(args.steps, ms / 1e3, ws)
     last_status = an.stats()
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
@@ -275,12 +291,8 @@ def run_ours(args):
     e2e_steps = max(3, args.steps // 4)
     for k in range(e2e_steps):
         an.analyze_host(Xh, yh, seed, k, out=Xo)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT,
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, dev, ws)
+    e2e = {"value": _job_rate(e2e_steps, e2e_s, ws), "unit": UNIT,
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
            "d2h_bytes_per_step": int(Xo.numel() * 4)}
 
@@ -387,7 +399,7 @@ def run_batched(args):
     import numpy as np
     import synth
     ws, rank, local = _dist()
-    seed = args.seed + 1000 * rank
+    seed = _rank_seed(args.seed, rank)
     specs = synth.problems.batched_problem_specs(args.batch_count, seed)
     t0 = time.time()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any GPU call
@@ -435,13 +447,9 @@ def run_batched(args):
     barrier()
     clk = clocks.stop()
     st = ba.stats()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, ws)
     count = len(probs)
-    value = ws * count * args.steps / (ms / 1e3)
+    value = _job_rate(count * args.steps, ms / 1e3, ws)
     # end to end: pinned host inputs copied in, the batched call, results copied out
     Xh = [torch.from_numpy(p.Xf).pin_memory() for p in probs]
     yh = [torch.from_numpy(p.y).pin_memory() for p in probs]
@@ -458,8 +466,8 @@ def run_batched(args):
         for a, b in zip(Xo, out):
             a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": ws * count * e2e_steps / e2e_s, "unit": UNIT,
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, dev, ws)
+    e2e = {"value": _job_rate(count * e2e_steps, e2e_s, ws), "unit": UNIT,
            "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in Xh) + sum(v.numel() * 8 for v in yh)),
            "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in Xo))}
     if rank != 0:
@@ -522,7 +530,7 @@ def run_mixed(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    seed = args.seed + 1000 * rank
+    seed = _rank_seed(args.seed, rank)
     p = synth.workload(MIXED_WORKLOAD, seed, dtype=np.float32)
     n, m, N = p.n, p.m, p.N
     Xf = torch.from_numpy(p.Xf).to(dev)
@@ -566,14 +574,10 @@ def run_mixed(args):
         an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp64", tol=1e-8, precondition=pc)
         res[tag] = timed(an, X64, o64, args.fp64_steps, tag)
         an.close()
-    ms = res["bf16"]["ms_per_step"]
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(res["bf16"]["ms_per_step"], dev, ws)
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": ws * 1e3 / ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    line = {"metric": METRIC, "value": _job_rate(1, ms / 1e3, ws), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (seeded 1024x1024 GRF ensemble, random point observations)",
