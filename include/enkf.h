@@ -306,6 +306,16 @@ enkf_status enkf_batch_set_phase_timing(enkf_handle h, int32_t enable);
 enkf_status enkf_batch_get_times(enkf_handle h, double* start_us, double* end_us, double* phase_us,
                                  int32_t* team_size);
 
+/* Self-test of the failure detection (the paper has no counterpart): run one of the bounded
+   device waits on a condition that nothing ever satisfies, with a time limit of timeout_ms
+   (0 < timeout_ms <= 10,000) instead of the library's 4 s. which = 0: the grid barrier of
+   the persistent kernels, entered by one CTA of a two-CTA barrier; which = 1: the mbarrier
+   wait of the tensor-core kernels on a barrier nothing arrives on. Synchronises cuda_stream.
+   Returns ENKF_ERR_TIMEOUT when the wait ended at its limit and raised the timeout status, as
+   it must (the context stays usable); ENKF_ERR_CUDA if it was released or reported nothing;
+   ENKF_ERR_INVALID_ARG for bad arguments. Allocates 16 bytes of device memory per call. */
+enkf_status enkf_selftest_wait_timeout(int32_t which, double timeout_ms, void* cuda_stream);
+
 /* The planner alone, on the host (no GPU needed). A problem costs c = m N^2 (N + 8) + 2 n N^2;
    a team of k CTAs is estimated to take c / k^alpha (0 < alpha <= 1). For a target makespan
    T every problem with c > T gets the smallest team (2 <= k <= ceil(m / 64)) that meets T;

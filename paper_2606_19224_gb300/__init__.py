@@ -26,7 +26,7 @@ EXPORTS = (
     "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
     "enkf_get_solve_phases", "enkf_batch_create", "enkf_batch_analyze", "enkf_batch_tune",
     "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan", "enkf_batch_set_phase_timing",
-    "enkf_batch_get_times",
+    "enkf_batch_get_times", "enkf_selftest_wait_timeout",
     "enkf_mlp_param_count", "enkf_mlp_work_bytes", "enkf_mlp_forward", "enkf_mlp_loss_grad",
     "enkf_mlp_adam", "enkf_mlp_train_epoch", "enkf_mlp_standardize", "enkf_warm_features",
     "enkf_set_warm_model",
@@ -107,6 +107,7 @@ def load(path: str = None):
         "enkf_batch_get_plan": (i32, [vp, vp, vp, vp, vp]),
         "enkf_batch_set_phase_timing": (i32, [vp, i32]),
         "enkf_batch_get_times": (i32, [vp, vp, vp, vp, vp]),
+        "enkf_selftest_wait_timeout": (i32, [i32, ctypes.c_double, vp]),
         "enkf_mlp_param_count": (i64, [ctypes.POINTER(MlpShape)]),
         "enkf_mlp_work_bytes": (i64, [ctypes.POINTER(MlpShape), i32]),
         "enkf_mlp_forward": (i32, [ctypes.POINTER(MlpShape), vp, vp, vp, i32, vp, vp, vp]),
@@ -318,6 +319,13 @@ def _ptr_array(items, ctype=ctypes.c_void_p):
     for i, x in enumerate(items):
         arr[i] = x
     return arr
+
+
+def selftest_wait_timeout(which, timeout_ms=50.0, stream=None):
+    """Run a bounded device wait that nothing releases (0: grid barrier, 1: mbarrier) with the
+    given limit; returns the library status name ("timeout" is the expected outcome)."""
+    st = load().enkf_selftest_wait_timeout(int(which), float(timeout_ms), _stream_handle(stream))
+    return STATUS.get(st, st)
 
 
 def batch_plan(shapes, max_grid, alpha=1.0):

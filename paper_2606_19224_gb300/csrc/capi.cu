@@ -539,6 +539,16 @@ enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, do
   return ENKF_OK;
 }
 
+enkf_status enkf_selftest_wait_timeout(int32_t which, double timeout_ms, void* cuda_stream) {
+  if ((which != 0 && which != 1) || !(timeout_ms > 0.0 && timeout_ms <= 10000.0))
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_selftest_wait_timeout: which must be 0 or 1, timeout_ms in (0, 1e4]");
+  int bits = 0;
+  cudaError_t e = enkf::selftest_wait_timeout(which, timeout_ms, static_cast<cudaStream_t>(cuda_stream), &bits);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "enkf_selftest_wait_timeout");
+  if (bits & enkf::DS_TIMEOUT) return ENKF_ERR_TIMEOUT;
+  return fail(nullptr, ENKF_ERR_CUDA, "enkf_selftest_wait_timeout: the wait was not reported as timed out");
+}
+
 enkf_status enkf_batch_set_phase_timing(enkf_handle h, int32_t enable) {
   if (!h || !h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_set_phase_timing: not a batched handle");
   cudaError_t e = enkf::batch_set_phase_timing(h, enable != 0);

@@ -37,7 +37,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier for a cooperative (co-resident) launch. `count` is a monotonic arrival
 // counter zeroed before the launch; `epoch` is the block's local barrier number. Each wait
-// is bounded: after kBarrierTimeoutNs the waiting block raises `abort_flag` and the
+// is bounded: after timeout_ns (kBarrierTimeoutNs unless set) the waiting block raises `abort_flag` and the
 // DS_TIMEOUT status bit, and every block that sees the flag leaves the barrier with false.
 // Returns the same value to all threads of the block.
 struct GridBarrier {
@@ -46,6 +46,7 @@ struct GridBarrier {
   int* status;
   unsigned nblocks;
   unsigned epoch;
+  unsigned long long timeout_ns = kBarrierTimeoutNs;
 
   __device__ bool sync() {
     __shared__ int s_ok;
@@ -60,7 +61,7 @@ struct GridBarrier {
         const unsigned long long t0 = global_ns();
         while (ld_acquire_u32(count) < target) {
           if (*(volatile int*)abort_flag) { ok = 0; break; }
-          if (global_ns() - t0 > kBarrierTimeoutNs) {
+          if (global_ns() - t0 > timeout_ns) {
             atomicExch(abort_flag, 1);
             atomicOr(status, DS_TIMEOUT);
             ok = 0;
@@ -216,6 +217,8 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
 cudaError_t batch_stats(enkf_handle_s* h, int32_t* status, int32_t* iters_max, double* relres_max,
                         int32_t* refinements);
 BatchPlanOut batch_info(const enkf_handle_s* h);
+// selftest.cu: a bounded wait that nothing releases (failure-detection check)
+cudaError_t selftest_wait_timeout(int which, double timeout_ms, cudaStream_t s, int* status_bits);
 cudaError_t batch_set_phase_timing(enkf_handle_s* h, bool on);
 bool batch_phase_timing(const enkf_handle_s* h);
 cudaError_t batch_times(enkf_handle_s* h, double* start_us, double* end_us, double* phase_us, int32_t* team);

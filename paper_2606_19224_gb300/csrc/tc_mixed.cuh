@@ -60,13 +60,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
   asm volatile("fence.mbarrier_init.release.cluster;");
 }
 // bounded wait for the given phase; returns false (and raises DS_TIMEOUT) if it never completes
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, int* status,
+                                          unsigned long long timeout_ns = kBarrierTimeoutNs) {
   uint32_t done = 0;
   const unsigned long long t0 = global_ns();
   while (!done) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(smem_addr(mbar)), "r"(phase));
-    if (!done && global_ns() - t0 > kBarrierTimeoutNs) {
+    if (!done && global_ns() - t0 > timeout_ns) {
       atomicOr(status, DS_TIMEOUT);
       return false;
     }

@@ -85,3 +85,10 @@ def test_status_strings():
     for s in range(9):
         assert lib.enkf_status_str(s)
     assert enkf.load().enkf_destroy(None) == 0
+
+
+def test_selftest_rejects_bad_arguments_without_a_gpu():
+    # argument checks come before any CUDA call
+    lib = enkf.load()
+    for which, ms in ((2, 50.0), (0, 0.0), (1, 2e4)):
+        assert enkf.STATUS[lib.enkf_selftest_wait_timeout(which, ms, None)] == "invalid_arg"
