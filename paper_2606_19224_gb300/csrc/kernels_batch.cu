@@ -624,9 +624,9 @@ static std::vector<int> problem_team(const BatchPlan& P, int count) {
 
 // The tuner. Stage 1 times the model-cost plans for alpha in {1, 0.9, 0.8}. Stage 2 replaces
 // the model by measurement: each problem's one-CTA cost is estimated from its duration in the
-// best plan so far (times k^alpha for a team of k), the batch is re-planned from those costs
-// and timed, and the estimate is averaged with the new plan's durations for a second round.
-// The fastest plan is kept.
+// best plan so far (the mean over its three timed analyses, times k^alpha for a team of k),
+// the batch is re-planned from those costs and timed, and the estimate is averaged with the
+// new plan's durations for the next of four rounds. The fastest plan is kept.
 cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
                        const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
                        double* best_alpha, double* best_ms) {
@@ -635,12 +635,14 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  // install P, one warm-up analysis (captures the graph), three timed; mean ms and the
-  // per-problem durations of the last one
+  // install P, one warm-up analysis (captures the graph), three timed; mean ms and the mean
+  // per-problem durations over the three
   auto time_plan = [&](const BatchPlan& P, double& ms_mean, std::vector<double>& ns) {
     cudaError_t r = apply_plan(B, P, h->stream);
     if (r == cudaSuccess) r = run_batch(h, io);
     float tot = 0.f;
+    ns.assign(B.count, 0.0);
+    std::vector<double> one;
     for (int rep = 0; rep < 3 && r == cudaSuccess; ++rep) {
       float ms = 0.f;
       r = cudaEventRecord(e0, h->stream);
@@ -648,9 +650,10 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
       if (r == cudaSuccess) r = cudaEventRecord(e1, h->stream);
       if (r == cudaSuccess) r = cudaEventSynchronize(e1);
       if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+      if (r == cudaSuccess) r = problem_ns(B, h->stream, one);
+      for (int i = 0; i < B.count && r == cudaSuccess; ++i) ns[i] += one[i] / 3.0;
       tot += ms;
     }
-    if (r == cudaSuccess) r = problem_ns(B, h->stream, ns);
     ms_mean = tot / 3.0;
     return r;
   };
@@ -675,7 +678,7 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
       return c;
     };
     std::vector<double> est = one_cta(best_plan, best_ns);
-    for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+    for (int round = 0; round < 4 && e == cudaSuccess; ++round) {
       BatchPlan P = make_plan(B.cfg, est, B.max_grid, a);
       P.measured = true;
       double ms = 0.0;
