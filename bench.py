@@ -52,8 +52,8 @@ def B_REF(m, N):
 # captures summarised in profiles/solve_kernel_fp32_grf512_N64_m65536.md and
 # profiles/solve_mixed_kernel_fp16_grf512_N64_m65536.md, with the hash of the kernel sources
 # each capture measured; reported as null once those sources have changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 4.641770e9, "src_sha": "7a1ece797b921175"},
-               "fp16": {"bytes": 6.278849e9, "src_sha": "6ff7635f911fe74f"}}
+NCU_TRAFFIC = {"fp32": {"bytes": 4.647486e9, "src_sha": "e2e8acb674ec66d9"},
+               "fp16": {"bytes": 6.279850e9, "src_sha": "6c1bbd465509db28"}}
 # The same for one batch_kernel launch on the 256-problem batch (seed 1), from the one-pass
 # DRAM capture summarised in profiles/batch_kernel_batched256_grf_dram.md.
 NCU_TRAFFIC_BATCH = {"bytes": 1.436830e12, "problems": 256, "seed": 1, "src_sha": "19d58d4932c5b47f"}
