@@ -418,7 +418,10 @@ def run_batched(args):
     y = [torch.from_numpy(p.y).to(dev) for p in probs]
     out = [torch.empty_like(x) for x in Xf]
     seeds = [seed + i for i in range(len(probs))]
-    tune_ms = ba.tune(Xf, y, seeds, None, out=out)
+    if args.reuse_tuned_plan and os.environ.get("ENKF_TUNE_CACHE"):
+        tune_ms = None                     # the plan enkf_batch_create read from the cache file
+    else:
+        tune_ms = ba.tune(Xf, y, seeds, None, out=out)
     plan = ba.plan()
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -602,6 +605,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256,
                     help="problems of the batched workload (256 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCH_WORKLOAD, MIXED_WORKLOAD])
+    ap.add_argument("--reuse-tuned-plan", action="store_true",
+                    help="batched workload: keep the plan enkf_batch_create read from the ENKF_TUNE_CACHE "
+                         "file (written by an earlier run's tuner) instead of tuning again")
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")
     args = ap.parse_args()

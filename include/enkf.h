@@ -265,14 +265,15 @@ enkf_status enkf_batch_analyze(enkf_handle h, const void* const* d_Xf, const dou
                                const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa);
 
 /* Autotune the plan on real inputs (arguments as enkf_batch_analyze). First it times the
-   plans of enkf_batch_plan for the team-scaling exponents alpha in {1, 0.9, 0.8}; then, four
-   times, it re-plans from measured costs (each problem's duration in the best plan so far,
-   as reported by enkf_batch_get_times and averaged over that plan's three timed analyses,
-   times k^alpha for a team of k CTAs, averaged with the previous round's estimate) and times
-   that plan too. It keeps the fastest plan and appends it (alpha, and the measured costs
-   when a measured plan won) to the ENKF_TUNE_CACHE file if that variable is set. Runs about
-   30 analyses (X_a holds the last one's result); synchronises the stream. *best_ms (HOST,
-   may be NULL) receives the best mean time. */
+   plans of enkf_batch_plan for the team-scaling exponents alpha in {1, 0.9, 0.8}; then,
+   starting from the alpha = 1 plan and, if another alpha was faster, from that plan too, it
+   four times re-plans from measured costs (each problem's duration in the last plan, as
+   reported by enkf_batch_get_times and averaged over that plan's three timed analyses, times
+   k^alpha for a team of k CTAs, averaged with the previous round's estimate) and times that
+   plan. It keeps the fastest plan and appends it (alpha, and the measured costs when a
+   measured plan won) to the ENKF_TUNE_CACHE file if that variable is set. Runs 28 to 44
+   analyses (X_a holds the last one's result); synchronises the stream. *best_ms (HOST, may
+   be NULL) receives the best mean time. */
 enkf_status enkf_batch_tune(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
                             const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa,
                             double* best_ms);

@@ -623,10 +623,11 @@ static std::vector<int> problem_team(const BatchPlan& P, int count) {
 }
 
 // The tuner. Stage 1 times the model-cost plans for alpha in {1, 0.9, 0.8}. Stage 2 replaces
-// the model by measurement: each problem's one-CTA cost is estimated from its duration in the
-// best plan so far (the mean over its three timed analyses, times k^alpha for a team of k),
-// the batch is re-planned from those costs and timed, and the estimate is averaged with the
-// new plan's durations for the next of four rounds. The fastest plan is kept.
+// the model by measurement, starting from the alpha = 1 plan and from the stage-1 winner if
+// that is another: each problem's one-CTA cost is estimated from its duration in the start
+// plan (the mean over its three timed analyses, times k^alpha for a team of k), the batch is
+// re-planned from those costs and timed, and the estimate is averaged with the new plan's
+// durations for the next of four rounds. The fastest plan of all is kept.
 cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
                        const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
                        double* best_alpha, double* best_ms) {
@@ -658,26 +659,38 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
     return r;
   };
   BatchPlan best_plan = B.plan;
-  std::vector<double> best_ns;
   double best = 1e300;
   const std::vector<double> model = model_costs(B.cfg);
+  struct Start { BatchPlan plan; std::vector<double> ns; double ms; };
+  std::vector<Start> stage1;
   for (double a : {1.0, 0.9, 0.8}) {
     if (e != cudaSuccess) break;
-    const BatchPlan P = make_plan(B.cfg, model, B.max_grid, a);
-    double ms = 0.0;
-    std::vector<double> ns;
-    e = time_plan(P, ms, ns);
-    if (e == cudaSuccess && ms < best) { best = ms; best_plan = P; best_ns = ns; }
+    Start st{make_plan(B.cfg, model, B.max_grid, a), {}, 0.0};
+    e = time_plan(st.plan, st.ms, st.ns);
+    if (e != cudaSuccess) break;
+    if (st.ms < best) { best = st.ms; best_plan = st.plan; }
+    stage1.push_back(std::move(st));
   }
+  // measured-cost rounds from the alpha = 1 plan and, if another alpha won stage 1, from that
+  // plan too (which model plan wins is itself noisy, and each start converges differently)
+  std::vector<size_t> starts;
   if (e == cudaSuccess) {
-    const double a = best_plan.alpha;
+    size_t win = 0;
+    for (size_t q = 1; q < stage1.size(); ++q)
+      if (stage1[q].ms < stage1[win].ms) win = q;
+    starts.push_back(0);
+    if (win != 0) starts.push_back(win);
+  }
+  for (size_t sidx : starts) {
+    if (e != cudaSuccess) break;
+    const double a = stage1[sidx].plan.alpha;
     auto one_cta = [&](const BatchPlan& P, const std::vector<double>& ns) {
       const std::vector<int> k = problem_team(P, B.count);
       std::vector<double> c(B.count);
       for (int i = 0; i < B.count; ++i) c[i] = std::max(1.0, ns[i]) * std::pow((double)k[i], a);
       return c;
     };
-    std::vector<double> est = one_cta(best_plan, best_ns);
+    std::vector<double> est = one_cta(stage1[sidx].plan, stage1[sidx].ns);
     for (int round = 0; round < 4 && e == cudaSuccess; ++round) {
       BatchPlan P = make_plan(B.cfg, est, B.max_grid, a);
       P.measured = true;
