@@ -56,7 +56,7 @@ NCU_TRAFFIC = {"fp32": {"bytes": 4.647486e9, "src_sha": "e2e8acb674ec66d9"},
                "fp16": {"bytes": 6.279850e9, "src_sha": "6c1bbd465509db28"}}
 # The same for one batch_kernel launch on the 256-problem batch (seed 1), from the one-pass
 # DRAM capture summarised in profiles/batch_kernel_batched256_grf_dram.md.
-NCU_TRAFFIC_BATCH = {"bytes": 1.436830e12, "problems": 256, "seed": 1, "src_sha": "19d58d4932c5b47f"}
+NCU_TRAFFIC_BATCH = {"bytes": 1.435980e12, "problems": 256, "seed": 1, "src_sha": "a66cc2ee8c818606"}
 _KERNEL_SOURCES = {
     "fp32": ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"),
     "fp16": ("kernels_tc.cu", "kernels_tc_fp16.cu", "tc_mixed.cuh", "common.cuh", "cg_device.cuh"),
