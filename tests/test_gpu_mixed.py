@@ -20,7 +20,8 @@ def _run(lib, p, prec, seed=7, counter=3, **cfg):
     return an, Xa.double().cpu().numpy(), an.stats()
 
 
-SHAPES = [(4096, 64, 1024), (2500, 37, 999), (1600, 20, 400), (3000, 100, 700), (20000, 128, 5000)]
+SHAPES = [(4096, 64, 1024), (2500, 37, 999), (1600, 20, 400), (3000, 100, 700), (2000, 97, 900),
+          (20000, 128, 5000)]
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
