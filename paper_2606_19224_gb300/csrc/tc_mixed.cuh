@@ -461,11 +461,29 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     tc_cp_commit();
   }
   const bool vec = (N & 3) == 0;
+  // the operands of one row sweep of the update: r, p, S p, x of the thread's four columns
+  // and r_i; loaded one sweep ahead so that their latency overlaps the previous sweep
+  struct Ops { float rr[4], pp[4], ss[4], xx[4], ri; };
+  auto load_ops = [&](int64_t i0, int r, Ops& o) {
+    const int64_t i = i0 + r;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) { o.rr[y] = 0.f; o.pp[y] = 0.f; o.ss[y] = 0.f; o.xx[y] = 0.f; }
+    o.ri = 1.f;
+    if (i < row1 && j0 < N) {
+      ld4<float>(o.rr, Res + i * N, j0, N, vec);
+      ld4<float>(o.pp, P + i * N, j0, N, vec);
+      ld4<float>(o.ss, Sv + i * N, j0, N, vec);
+      ld4<float>(o.xx, X + i * N, j0, N, vec);
+      o.ri = rv[i];
+    }
+  };
   for (int q = 0; q < Qb && ok; ++q) {
     const int64_t i0 = row0 + (int64_t)q * kTR;
     tc_cp_wait_all();
     fence_async_smem();
     __syncthreads();
+    Ops cur;
+    load_ops(i0, ti, cur);   // the first sweep's operands, in flight during the u MMA
     if (q + 1 < Qb) {   // next tile's image into the other buffer, behind this whole tile
       tc_copy(sAu(q + 1), au_src(q + 1), L::AUB);
       tc_cp_commit();
@@ -507,29 +525,22 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     for (int r = ti; r < kTR; r += RI) {
       const int64_t i = i0 + r;
       const bool valid = i < row1 && j0 < N;
+      Ops nxt;
+      if (r + RI < kTR) load_ops(i0, r + RI, nxt);
       const float4 u4 = *reinterpret_cast<const float4*>(sU + r * NT + ((tj ^ (r & GM)) * 4));
-      float rr[4] = {0.f, 0.f, 0.f, 0.f}, pp[4] = {0.f, 0.f, 0.f, 0.f};
-      float ss[4] = {0.f, 0.f, 0.f, 0.f}, xx[4] = {0.f, 0.f, 0.f, 0.f};
-      float ri = 1.f;
-      if (valid) {
-        ld4<float>(rr, Res + i * N, j0, N, vec);
-        ld4<float>(pp, P + i * N, j0, N, vec);
-        ld4<float>(ss, Sv + i * N, j0, N, vec);
-        ld4<float>(xx, X + i * N, j0, N, vec);
-        ri = rv[i];
-      }
+      const float ri = cur.ri;
       const float rinv = 1.f / ri;
       const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
       float pn[4], sn[4], xn[4], rn[4];
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const float uu = uv[y] * tsi[y];
-        const float zz = PC ? rr[y] * rinv : rr[y];
-        const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
-        pn[y] = be[y] == 0.f ? zz : fmaf(be[y], pp[y], zz);
-        sn[y] = be[y] == 0.f ? ww : fmaf(be[y], ss[y], ww);
-        xn[y] = fmaf(al[y], pn[y], xx[y]);
-        rn[y] = fmaf(-al[y], sn[y], rr[y]);
+        const float zz = PC ? cur.rr[y] * rinv : cur.rr[y];
+        const float ww = PC ? uu + cur.rr[y] : fmaf(ri, cur.rr[y], uu);
+        pn[y] = be[y] == 0.f ? zz : fmaf(be[y], cur.pp[y], zz);
+        sn[y] = be[y] == 0.f ? ww : fmaf(be[y], cur.ss[y], ww);
+        xn[y] = fmaf(al[y], pn[y], cur.xx[y]);
+        rn[y] = fmaf(-al[y], sn[y], cur.rr[y]);
         const float zn = PC ? rn[y] * rinv : rn[y];
         const bool live = valid && j0 + y < N;
         if (live) {
@@ -547,6 +558,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
         st4<float>(X + i * N, j0, N, vec, xn);
         st4<float>(Res + i * N, j0, N, vec, rn);
       }
+      if (r + RI < kTR) cur = nxt;
     }
     tc_fence_before();
     fence_async_smem();
