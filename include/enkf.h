@@ -134,8 +134,8 @@ enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t 
    observation operator, nnz = h_rowptr[m]) and r_diag[m] (> 0, finite) are HOST arrays
    and are copied to the device. cuda_stream is a cudaStream_t (NULL: the legacy default
    stream); every later call on the handle is ordered on it. Allocates all workspace
-   (about 48 m N bytes in ENKF_FP32 mode at N <= 128, 48 m N in ENKF_FP64 mode, plus
-   O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad shape, column index outside [0, n),
+   (about 56 m N + 4 n N bytes in ENKF_FP32 mode, 4 m N more in the tensor-core modes,
+   48 m N + 8 n N in ENKF_FP64 mode, plus O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad shape, column index outside [0, n),
    decreasing rowptr, r <= 0), ENKF_ERR_UNSUPPORTED (N > 128, unknown precision or
    variant), ENKF_ERR_OOM, ENKF_ERR_CUDA. *out is NULL on error. */
 enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
@@ -177,9 +177,11 @@ enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
 
 /* Copy the last analysis's intermediate results to DEVICE buffers (any may be NULL):
    d_HA [m][N] and d_D [m][N] (FP64), d_Z [m][N] (FP64 solution of S Z = D), d_W [N][N]
-   (FP64, W = HA^T Z/(N-1)). For ENKF_CGD_REDUCED, d_HA and d_D must be NULL (that variant
-   never stores them), d_Z receives the N x N CG solution V and d_W the N x N matrix
-   G = I + P^T P. Enqueued on the handle's stream. */
+   (FP64, W = HA^T Z/(N-1)). In the FP32 and tensor-core modes HA and Z are the solve's
+   double-float arrays (FP32 pairs, about 48 significant bits) widened to FP64. For
+   ENKF_CGD_REDUCED, d_HA and d_D must be NULL (that variant never stores them), d_Z receives
+   the N x N CG solution V and d_W the N x N matrix G = I + P^T P. Enqueued on the handle's
+   stream. */
 enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z,
                                     double* d_W);
 

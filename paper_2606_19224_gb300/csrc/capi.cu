@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "intermediates.cuh"
 
 using enkf::Workspace;
 
@@ -192,11 +193,13 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   };
   if (!reduced) {
     allocs.push_back({(void**)&ws.Sv, vs * mN});
-    allocs.push_back({(void**)&ws.HA64, sizeof(double) * mN});
     allocs.push_back({(void**)&ws.D, sizeof(double) * mN});
-    allocs.push_back({(void**)&ws.Z, sizeof(double) * mN});
     allocs.push_back({(void**)&ws.Res, vs * mN});
     allocs.push_back({(void**)&ws.P, vs * mN});
+    if (c.precision == ENKF_FP64) {   // the other modes keep HA and Z in double-float only
+      allocs.push_back({(void**)&ws.HA64, sizeof(double) * mN});
+      allocs.push_back({(void**)&ws.Z, sizeof(double) * mN});
+    }
   }
   if (!reduced && c.precision != ENKF_FP64) {
     allocs.push_back({(void**)&ws.HA32, sizeof(float) * mN});
@@ -379,9 +382,15 @@ enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, do
     if (e != cudaSuccess) return cuda_fail(h, e, "copy_intermediates");
     return ENKF_OK;
   }
-  if (d_HA) e = cudaMemcpyAsync(d_HA, h->ws.HA64, mN, cudaMemcpyDeviceToDevice, h->stream);
+  if (c.precision == ENKF_FP64) {
+    if (d_HA) e = cudaMemcpyAsync(d_HA, h->ws.HA64, mN, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && d_Z) e = cudaMemcpyAsync(d_Z, h->ws.Z, mN, cudaMemcpyDeviceToDevice, h->stream);
+  } else {   // HA and the solution Z live in double-float (FP32 pairs) in these modes
+    const int64_t cnt = c.m * c.N;
+    if (d_HA) e = enkf::launch_df32_to_f64(h->ws.HAdf, d_HA, cnt, h->stream);
+    if (e == cudaSuccess && d_Z) e = enkf::launch_df32_to_f64(h->ws.Zdf, d_Z, cnt, h->stream);
+  }
   if (e == cudaSuccess && d_D) e = cudaMemcpyAsync(d_D, h->ws.D, mN, cudaMemcpyDeviceToDevice, h->stream);
-  if (e == cudaSuccess && d_Z) e = cudaMemcpyAsync(d_Z, h->ws.Z, mN, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess && d_W)
     e = cudaMemcpyAsync(d_W, h->ws.W, sizeof(double) * c.N * c.N, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy_intermediates");

@@ -244,3 +244,23 @@ def test_preconditioned_full_size_grf512_N64_m65536_fp32(lib):
     E = oracle.obs_perturbations(1, 0, p.r, p.N)
     err = oracle.rel_frobenius(Xa, _oracle_exact(p, E))
     assert st["status"] == "ok" and err <= 1e-6, (err, st)
+
+
+def test_fp32_intermediates_are_the_double_float_arrays(lib):
+    # In the FP32 mode HA and Z exist only as FP32 pairs; the intermediates widen them: HA to
+    # about 48 bits of the oracle's, Z to the solution within the analysis tolerance, and
+    # W = HA^T Z / (N - 1) consistent with both.
+    p = synth.workload("grf512_N64_m65536", 5, scale=4, dtype=np.float32)   # m = 4,096, N = 64
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-9,
+                      precondition=1)
+    E = oracle.obs_perturbations(8, 1, p.r, p.N)
+    an.analyze_with_E(torch.from_numpy(p.Xf).cuda(), torch.from_numpy(p.y).cuda(), torch.from_numpy(E).cuda())
+    assert an.stats()["status"] == "ok"
+    HA, D, Z, W = (t.cpu().numpy() for t in an.intermediates())
+    Xf = p.Xf.astype(np.float64)
+    _, _, _, _, HAref = oracle.ensemble_stats(Xf, p.rowptr, p.col, p.w)
+    assert np.max(np.abs(HA - HAref)) <= 1e-13 * np.max(np.abs(HAref))
+    S_Z = oracle.S_matvec(HAref, p.r, Z)
+    assert np.linalg.norm(S_Z - D) <= 1e-9 * np.linalg.norm(D)         # the stopping rule, tol 1e-9
+    assert np.max(np.abs(W - HA.T @ Z / (p.N - 1))) <= 1e-10 * np.max(np.abs(W))
+    an.close()
