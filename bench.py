@@ -190,6 +190,28 @@ def cpu_baseline(problem, E, budget_s=20.0):
                       f"in {el:.1f} s"}
 
 
+def cpu_baseline_one_core(seed, reps=3):
+    """The same oracle on one thread (BLAS and OpenMP limited to 1), in a child process so that
+    the limit holds from its first import; the analyses are the benchmark's full-size problem."""
+    import subprocess
+    import sys
+    code = ("import time\nimport numpy as np\nimport oracle, synth\n"
+            f"p = synth.workload({WORKLOAD!r}, {int(seed)}, dtype=np.float32)\n"
+            f"E = oracle.obs_perturbations({int(seed)}, 0, p.r, p.N)\n"
+            "X = p.Xf.astype('float64')\n"
+            "t0 = time.perf_counter()\n"
+            f"for _ in range({int(reps)}):\n"
+            "    oracle.enkf_exact(X, p.rowptr, p.col, p.w, p.r, p.y, E)\n"
+            "print(time.perf_counter() - t0)\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=900, check=True)
+    el = float(out.stdout.strip().splitlines()[-1])
+    return {"value": reps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, FP64 numpy) "
+                      f"on one thread in {el:.1f} s"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -422,6 +444,7 @@ def run_ours(args):
             "clocks": clk}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, E)
+        line["cpu_baseline_1core"] = cpu_baseline_one_core(seed)
     print(json.dumps(line), flush=True)
 
 
