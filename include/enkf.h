@@ -16,6 +16,11 @@
  * (Sec. 5.2): X_a = X_f (I + P^T P)^{-1} [I + P^T L^{-1}((y - zbar) 1^T + E)],
  * P = L^{-1} HA, L L^T = (N-1) R.
  *
+ * The variant ENKF_SENKF is the paper's serial-EnKF comparator (Algorithm 3, Appendix A):
+ * S^{-1} replaced by the inverse of its diagonal, with no solve,
+ *   X_a = X_f + A HA^T diag(HA HA^T + R_N)^{-1} D,  R_N = (N-1) R.
+ * It is an approximation of the EnKF analysis, not the same result.
+ *
  * Letters: n = state dimension, m = observation count, N = ensemble size (the paper writes
  * m, p, N).
  *
@@ -73,7 +78,9 @@ typedef enum {
 
 typedef enum {
   ENKF_CGD = 0,         /* CGD-EnKF: CG on S Z = D (m x m operator, N columns)           */
-  ENKF_CGD_REDUCED = 1  /* CGD-EnKF-Reduced: CG on I + P^T P (N x N, N columns)          */
+  ENKF_CGD_REDUCED = 1, /* CGD-EnKF-Reduced: CG on I + P^T P (N x N, N columns)          */
+  ENKF_SENKF = 2        /* sEnKF comparator (Algorithm 3): diagonal inverse, no solve;
+                           ENKF_FP64 or ENKF_FP32, no warm start                         */
 } enkf_variant;
 
 typedef struct enkf_config {
@@ -135,9 +142,11 @@ enkf_status enkf_config_default(enkf_config* cfg, int64_t n, int64_t m, int32_t 
    and are copied to the device. cuda_stream is a cudaStream_t (NULL: the legacy default
    stream); every later call on the handle is ordered on it. Allocates all workspace
    (about 56 m N + 4 n N bytes in ENKF_FP32 mode, 4 m N more in the tensor-core modes,
-   48 m N + 8 n N in ENKF_FP64 mode, plus O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad shape, column index outside [0, n),
-   decreasing rowptr, r <= 0), ENKF_ERR_UNSUPPORTED (N > 128, unknown precision or
-   variant), ENKF_ERR_OOM, ENKF_ERR_CUDA. *out is NULL on error. */
+   48 m N + 8 n N in ENKF_FP64 mode, plus O(grid N^2); ENKF_CGD_REDUCED and ENKF_SENKF keep
+   no m x N arrays: 4 or 8 n N bytes plus O(grid N^2)). Errors: ENKF_ERR_INVALID_ARG (bad
+   shape, column index outside [0, n), decreasing rowptr, r <= 0), ENKF_ERR_UNSUPPORTED
+   (N > 128, unknown precision or variant, a variant other than ENKF_CGD in the BF16/FP16
+   modes), ENKF_ERR_OOM, ENKF_ERR_CUDA. *out is NULL on error. */
 enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
                         const double* h_w, const double* r_diag, void* cuda_stream,
                         enkf_handle* out);
@@ -146,9 +155,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
    otherwise); d_y: device [m] FP64; (seed, counter) select the Philox4x32-10 stream of the
    perturbations E when cfg.perturb_obs = 1 (element (i, j) uses counter
    (i, j >> 1, counter_lo, counter_hi) and key (seed_lo, seed_hi); two 53-bit uniforms and
-   Box-Muller give the normal, E_ij = sqrt(r_i) * normal; ENKF_FP64 evaluates Box-Muller in
-   FP64, the FP32 and tensor-core modes in FP32 from the same uniforms, within about 1e-7 of
-   the FP64 normal). d_Xa: device [n][N], same dtype
+   Box-Muller give the normal, E_ij = sqrt(r_i) * normal; ENKF_CGD in the FP32 and
+   tensor-core modes evaluates Box-Muller in FP32 from the same uniforms, within about 1e-7
+   of the FP64 normal, every other mode and variant in FP64). d_Xa: device [n][N], same dtype
    as d_Xf; d_Xa == d_Xf (in-place) is allowed, partial overlap is not. Never allocates. */
 enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uint64_t seed,
                          uint64_t counter, void* d_Xa);
@@ -180,8 +189,9 @@ enkf_status enkf_get_column_stats(enkf_handle h, int32_t* iters, double* relres,
    (FP64, W = HA^T Z/(N-1)). In the FP32 and tensor-core modes HA and Z are the solve's
    double-float arrays (FP32 pairs, about 48 significant bits) widened to FP64. For
    ENKF_CGD_REDUCED, d_HA and d_D must be NULL (that variant never stores them), d_Z receives
-   the N x N CG solution V and d_W the N x N matrix G = I + P^T P. Enqueued on the handle's
-   stream. */
+   the N x N CG solution V and d_W the N x N matrix G = I + P^T P. For ENKF_SENKF only d_W
+   may be non-NULL: it receives W = HA^T diag(HA HA^T + R_N)^{-1} D (X_a = X_f + A W).
+   Enqueued on the handle's stream. */
 enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, double* d_Z,
                                     double* d_W);
 

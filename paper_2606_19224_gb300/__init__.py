@@ -11,9 +11,9 @@ import os
 from .build import LIB, build, up_to_date
 
 FP64, FP32, BF16_REFINE, FP16_REFINE = 0, 1, 2, 3
-CGD, CGD_REDUCED = 0, 1
+CGD, CGD_REDUCED, SENKF = 0, 1, 2
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16_REFINE, "fp16": FP16_REFINE}
-_VARIANT = {"cgd": CGD, "reduced": CGD_REDUCED}
+_VARIANT = {"cgd": CGD, "reduced": CGD_REDUCED, "senkf": SENKF}
 
 STATUS = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "oom", 4: "not_converged", 5: "nonfinite",
           6: "breakdown", 7: "timeout", 8: "unsupported"}
@@ -261,6 +261,16 @@ class Analysis:
         _check(load().enkf_copy_intermediates(self.h, None, None, _ptr(V), _ptr(G)), self.h)
         self.stream.synchronize()
         return V, G
+
+    def intermediates_senkf(self):
+        """W = HA^T diag(HA HA^T + R_N)^{-1} D (N x N, FP64 device tensor) of the last sEnKF
+        analysis (X_a = X_f + A W)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        W = torch.empty((self.N, self.N), dtype=torch.float64, device=dev)
+        _check(load().enkf_copy_intermediates(self.h, None, None, None, _ptr(W)), self.h)
+        self.stream.synchronize()
+        return W
 
     def set_phase_timing(self, enable=True, phases=False):
         _check(load().enkf_set_phase_timing(self.h, (2 if phases else 1) if enable else 0), self.h)

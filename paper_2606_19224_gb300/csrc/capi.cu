@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "intermediates.cuh"
+#include "senkf.cuh"
 
 using enkf::Workspace;
 
@@ -53,7 +54,7 @@ enkf_status check_problem(const enkf_config& c, const int32_t* h_rowptr, const i
     return bad(ENKF_ERR_UNSUPPORTED, "the BF16/FP16 modes are built for ENKF_CGD");
   if (mixed && c.fixed_iters > 0)
     return bad(ENKF_ERR_UNSUPPORTED, "fixed_iters is not offered in the BF16/FP16 modes");
-  if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED)
+  if (c.variant != ENKF_CGD && c.variant != ENKF_CGD_REDUCED && c.variant != ENKF_SENKF)
     return bad(ENKF_ERR_UNSUPPORTED, "unknown variant");
   if (c.fixed_iters < 0 || c.max_iter < 1 || c.max_refine < 0)
     return bad(ENKF_ERR_INVALID_ARG, "bad iteration limits");
@@ -169,7 +170,8 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   const size_t vs = elem_size(c);
   Workspace& ws = h->ws;
   struct Alloc { void** p; size_t bytes; };
-  const bool reduced = c.variant == ENKF_CGD_REDUCED;
+  // the Reduced variant and the sEnKF comparator work from one Gram pass and keep no m x N arrays
+  const bool reduced = c.variant != ENKF_CGD;
   const int64_t tpart = reduced ? (int64_t)enkf::reduced_grid(h) * 2 * c.N * c.N : (int64_t)G * NE;
   std::vector<Alloc> allocs = {
       {(void**)&ws.rowptr, sizeof(int32_t) * (c.m + 1)},
@@ -251,10 +253,11 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: X_a partially overlaps X_f");
   cudaError_t e = cudaSuccess;
   const bool reduced = c.variant == ENKF_CGD_REDUCED;
+  const bool senkf = c.variant == ENKF_SENKF;
   if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
   if (c.warm_start && !enkf::warm_ready(h))
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: warm_start = 1 but no model attached (enkf_set_warm_model)");
-  if (e == cudaSuccess && !reduced) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
+  if (e == cudaSuccess && !reduced && !senkf) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
   if (c.warm_start) {
     e = enkf::warm_prepare(h);
@@ -262,8 +265,9 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   }
   if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
   if (e == cudaSuccess)
-    e = reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter)
-                : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
+    e = senkf ? enkf::launch_senkf(h, d_Xf, d_y, d_E, emode, seed, counter)
+        : reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter)
+                  : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
   if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
   if (e == cudaSuccess)
@@ -374,6 +378,13 @@ enkf_status enkf_copy_intermediates(enkf_handle h, double* d_HA, double* d_D, do
   const auto& c = h->cfg;
   const size_t mN = sizeof(double) * c.m * c.N;
   cudaError_t e = cudaSuccess;
+  if (c.variant == ENKF_SENKF) {
+    if (d_HA || d_D || d_Z)
+      return fail(h, ENKF_ERR_INVALID_ARG, "copy_intermediates: the sEnKF variant keeps no HA, D or Z");
+    if (d_W) e = cudaMemcpyAsync(d_W, h->ws.W, sizeof(double) * c.N * c.N, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy_intermediates");
+    return ENKF_OK;
+  }
   if (c.variant == ENKF_CGD_REDUCED) {
     if (d_HA || d_D) return fail(h, ENKF_ERR_INVALID_ARG, "copy_intermediates: the reduced variant keeps no HA or D");
     const size_t nn = sizeof(double) * c.N * c.N;

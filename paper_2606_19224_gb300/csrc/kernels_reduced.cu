@@ -13,7 +13,15 @@
 //   reduced_sum_kernel     fixed-order sum of the CTA partials -> G, M (FP64)
 //   reduced_cg_kernel      one CTA per group of columns; G staged in shared memory; FP64 CG
 //   update (kernels_fp.cu) X_a = X_f V (plain product mode)
+//
+// The same pass serves the paper's sEnKF comparator (Algorithm 3, the diagonal-inverse
+// approximation): with the weights 1/s_i, s_i = |HA_i|^2 + (N-1) r_i (the diagonal of
+// HA HA^T + R_N) instead of 1/r_i, and the innovation row D_i = Y~_i - HA_i as the only right
+// factor (an N x N product per row instead of N x 2N), it forms
+// W = sum_i HA_i^T D_i / s_i = HA^T diag(HA HA^T + R_N)^{-1} D, and X_a = X_f + A W (the
+// CGD-EnKF update) with no solve at all.
 #include "common.cuh"
+#include "senkf.cuh"
 
 #include <algorithm>
 
@@ -26,8 +34,9 @@ template <typename VT, int NT> __host__ __device__ constexpr int red_tr() {
 }
 
 // Gram pass. CTA (bx, ks) accumulates, over its block of observation rows, the rows
-// k in [ks*KR, (ks+1)*KR) of HA^T R^{-1} [HA | Y~] (an N x 2N product) with a 4x4 register
-// tile per thread; gridDim.y = NT/KR splits k so that a thread keeps at most 32 accumulators.
+// k in [ks*KR, (ks+1)*KR) of HA^T R^{-1} [HA | Y~] (an N x 2N product; sEnKF:
+// HA^T diag^{-1} D, N x N) with a 4x4 register tile per thread; gridDim.y = NT/KR splits k so
+// that a thread keeps at most 32 accumulators.
 template <int NT> struct GramCfg;
 template <> struct GramCfg<32> { static constexpr int KR = 32; };
 template <> struct GramCfg<64> { static constexpr int KR = 64; };
@@ -35,20 +44,21 @@ template <> struct GramCfg<128> { static constexpr int KR = 32; };
 
 // VT: type of X_f; AT: type of the staged tiles and the accumulators (FP64 in both modes:
 // FP32 products of FP32-rounded anomalies lose ~sqrt(m) in the cancelling off-diagonals).
-template <typename VT, typename AT, int NT>
+template <typename VT, typename AT, int NT, bool SENKF = false>
 __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
     const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
     const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
-    double* __restrict__ part /* [gridDim.x][2][N][N] */) {
+    double* __restrict__ part /* [gridDim.x][2][N][N]; sEnKF writes only [b][0] */) {
   constexpr int KR = GramCfg<NT>::KR;
-  constexpr int KG = KR / 4, JG = 2 * NT / 4, TILES = KG * JG;
+  constexpr int JW = SENKF ? NT : 2 * NT;                          // columns of the right factor
+  constexpr int KG = KR / 4, JG = JW / 4, TILES = KG * JG;
   constexpr int TPT = TILES >= kThreads ? TILES / kThreads : 1;   // tiles per thread
   constexpr int RG = TILES >= kThreads ? 1 : kThreads / TILES;    // row groups
   static_assert(TILES % kThreads == 0 || kThreads % TILES == 0, "mapping");
   constexpr int TR = red_tr<AT, NT>();
-  __shared__ __align__(16) AT sK[TR][NT];            // HA_i / r_i
-  __shared__ __align__(16) AT sJ[TR][2 * NT];        // [HA_i | Y~_i]
+  __shared__ __align__(16) AT sK[TR][NT];            // HA_i / r_i (sEnKF: HA_i / s_i)
+  __shared__ __align__(16) AT sJ[TR][JW];            // [HA_i | Y~_i] (sEnKF: D_i)
   __shared__ double sred[RG > 1 ? TILES * 16 : 1];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int g = t / (kThreads / RG);                 // row group of this thread
@@ -89,21 +99,38 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
       const double ri = i < row1 ? r[i] : 1.0;
       const double yi = i < row1 ? y[i] : 0.0;
       const double sr = sqrt(ri);
+      double ha[4], yt[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        ha[q] = 0.0;
+        yt[q] = 0.0;
+        if (i < row1 && j < N) {
+          double pert = 0.0;
+          if (emode == 1) pert = E[i * N + j];
+          else if (emode == 2) pert = sr * perturbation_normal(i, j, seed, counter);
+          ha[q] = z[q] - zbar;
+          yt[q] = (yi - zbar) + pert;
+        }
+      }
+      double wgt = ri;   // the row's weight divisor: r_i, or s_i = |HA_i|^2 + (N-1) r_i
+      if (SENKF) {
+        double hn = ha[0] * ha[0] + ha[1] * ha[1] + ha[2] * ha[2] + ha[3] * ha[3];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hn += __shfl_xor_sync(0xffffffffu, hn, o);
+        wgt = hn + (double)(N - 1) * ri;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int j = lane + 32 * q;
         if (j < NT) {
-          double ha = 0.0, yt = 0.0;
-          if (i < row1 && j < N) {
-            double pert = 0.0;
-            if (emode == 1) pert = E[i * N + j];
-            else if (emode == 2) pert = sr * perturbation_normal(i, j, seed, counter);
-            ha = z[q] - zbar;
-            yt = (yi - zbar) + pert;
+          sK[ii][j] = (AT)(ha[q] / wgt);
+          if (SENKF) {
+            sJ[ii][j] = (AT)(yt[q] - ha[q]);
+          } else {
+            sJ[ii][j] = (AT)ha[q];
+            sJ[ii][NT + j] = (AT)yt[q];
           }
-          sK[ii][j] = (AT)(ha / ri);
-          sJ[ii][j] = (AT)ha;
-          sJ[ii][NT + j] = (AT)yt;
         }
       }
     }
@@ -175,6 +202,16 @@ __global__ void reduced_sum_kernel(const double* __restrict__ part, int nparts, 
     const int half = e / NN, ee = e % NN;
     const double v = s * inv + ((ee / N) == (ee % N) ? 1.0 : 0.0);
     (half == 0 ? Gm : Mm)[ee] = v;
+  }
+}
+
+// sEnKF: W = sum_b part_b[0] (= HA^T diag^{-1} D), fixed order over b.
+__global__ void senkf_sum_kernel(const double* __restrict__ part, int nparts, int N, double* __restrict__ W) {
+  const int NN = N * N;
+  for (int e = blockIdx.x * kThreads + threadIdx.x; e < NN; e += gridDim.x * kThreads) {
+    double a = 0.0;
+    for (int q = 0; q < nparts; ++q) a += part[(int64_t)q * 2 * NN + e];
+    W[e] = a;
   }
 }
 
@@ -272,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) reduced_cg_kernel(
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename VT>
+template <typename VT, bool SENKF>
 static cudaError_t gram_launch(enkf_handle_s* h, const void* Xf, const double* y, const double* E,
                                int emode, uint64_t seed, uint64_t counter, int grid) {
   const auto& c = h->cfg;
@@ -280,11 +317,11 @@ static cudaError_t gram_launch(enkf_handle_s* h, const void* Xf, const double* y
   const int NT = c.N <= 32 ? 32 : (c.N <= 64 ? 64 : 128);
   const VT* X = static_cast<const VT*>(Xf);
   if (NT == 32)
-    reduced_gram_kernel<VT, double, 32><<<dim3(grid, 32 / GramCfg<32>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, double, 32, SENKF><<<dim3(grid, 32 / GramCfg<32>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   else if (NT == 64)
-    reduced_gram_kernel<VT, double, 64><<<dim3(grid, 64 / GramCfg<64>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, double, 64, SENKF><<<dim3(grid, 64 / GramCfg<64>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   else
-    reduced_gram_kernel<VT, double, 128><<<dim3(grid, 128 / GramCfg<128>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, double, 128, SENKF><<<dim3(grid, 128 / GramCfg<128>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   return cudaGetLastError();
 }
 
@@ -300,8 +337,8 @@ cudaError_t launch_reduced(enkf_handle_s* h, const void* Xf, const double* y, co
   const int grid = reduced_grid(h);
   cudaError_t e = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);
   if (e != cudaSuccess) return e;
-  e = c.precision == ENKF_FP64 ? gram_launch<double>(h, Xf, y, E, emode, seed, counter, grid)
-                               : gram_launch<float>(h, Xf, y, E, emode, seed, counter, grid);
+  e = c.precision == ENKF_FP64 ? gram_launch<double, false>(h, Xf, y, E, emode, seed, counter, grid)
+                               : gram_launch<float, false>(h, Xf, y, E, emode, seed, counter, grid);
   if (e != cudaSuccess) return e;
   double* Gm = ws.Tred;            // N x N
   double* Mm = ws.Wacc;            // N x N
@@ -315,6 +352,24 @@ cudaError_t launch_reduced(enkf_handle_s* h, const void* Xf, const double* y, co
   reduced_cg_kernel<<<c.N, kThreads, smem, h->stream>>>(Gm, Mm, c.N, c.tol, c.max_iter, c.fixed_iters,
                                                        ws.W, ws.col_iters, ws.col_relres, ws.col_true,
                                                        ws.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_senkf(enkf_handle_s* h, const void* Xf, const double* y, const double* E,
+                         int emode, uint64_t seed, uint64_t counter) {
+  const auto& c = h->cfg;
+  auto& ws = h->ws;
+  const int grid = reduced_grid(h);
+  cudaError_t e = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.col_iters, 0, sizeof(int32_t) * c.N, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.col_relres, 0, sizeof(double) * c.N, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.col_true, 0, sizeof(double) * c.N, h->stream);
+  if (e != cudaSuccess) return e;
+  e = c.precision == ENKF_FP64 ? gram_launch<double, true>(h, Xf, y, E, emode, seed, counter, grid)
+                               : gram_launch<float, true>(h, Xf, y, E, emode, seed, counter, grid);
+  if (e != cudaSuccess) return e;
+  const int NN = c.N * c.N;
+  senkf_sum_kernel<<<(NN + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(ws.Tpart, grid, c.N, ws.W);
   return cudaGetLastError();
 }
 

@@ -51,7 +51,8 @@ def _create(cfg, rowptr, col, w, r):
     return st, h, lib.enkf_last_error(None).decode()
 
 
-@pytest.mark.parametrize("case", ["N1", "bad_col", "neg_r", "rowptr", "N_big", "tol", "reserved"])
+@pytest.mark.parametrize("case", ["N1", "bad_col", "neg_r", "rowptr", "N_big", "tol", "reserved",
+                                  "variant", "senkf_bf16", "senkf_warm"])
 def test_create_rejects_bad_arguments_before_touching_the_gpu(case):
     n, m, N = 10, 4, 5
     rowptr = np.arange(m + 1, dtype=np.int32)
@@ -76,6 +77,15 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(case):
         cfg.tol = 0.0
     elif case == "reserved":
         cfg.reserved[1] = 1
+    elif case == "variant":
+        cfg.variant = 3
+        expect = 8
+    elif case == "senkf_bf16":   # the sEnKF comparator is built for FP64 and FP32 only
+        cfg.variant, cfg.precision = enkf.SENKF, enkf.BF16_REFINE
+        expect = 8
+    elif case == "senkf_warm":
+        cfg.variant, cfg.precision, cfg.warm_start = enkf.SENKF, enkf.FP32, 1
+        expect = 8
     st, h, msg = _create(cfg, rowptr, col, w, r)
     assert st == expect and not h.value and msg
 

@@ -336,6 +336,34 @@ def test_senkf_differs_from_enkf_but_equals_it_for_uncorrelated_single_rows():
     assert oracle.rel_frobenius(s, a) > 1e-6
 
 
+def test_senkf_equals_enkf_when_observed_anomalies_are_orthogonal():
+    # Algorithm 3 replaces S by its diagonal; when the rows of Z-hat are mutually orthogonal
+    # (Hadamard rows 1..7 are zero-mean and orthogonal), HA HA^T is diagonal, S equals its
+    # diagonal and the sEnKF analysis is the exact EnKF analysis (Sec. 2.2 / Appendix A).
+    Hd = np.array([[1.0]])
+    for _ in range(3):
+        Hd = np.block([[Hd, Hd], [Hd, -Hd]])
+    rng = np.random.default_rng(17)
+    n, N = 12, 8
+    Xf = rng.standard_normal((n, 1)) + 0.2 * rng.standard_normal((n, N))
+    obs = [2, 5, 7, 10]
+    for q, a in enumerate(obs):   # observed states: mean + scaled Hadamard row (distinct rows)
+        Xf[a] = 1.5 + (0.3 + 0.1 * q) * Hd[q + 1]
+    rowptr = np.arange(len(obs) + 1, dtype=np.int32)
+    col = np.array(obs, np.int32)
+    w = np.ones(len(obs))
+    r = np.array([0.04, 0.5, 0.2, 1.3])
+    y = rng.standard_normal(len(obs))
+    E = 0.1 * rng.standard_normal((len(obs), N))
+    _, _, _, _, Zhat = oracle.ensemble_stats(Xf, rowptr, col, w)
+    G = Zhat @ Zhat.T
+    assert np.max(np.abs(G - np.diag(np.diag(G)))) < 1e-12
+    a = oracle.enkf_alg1(Xf, rowptr, col, w, r, y, E)
+    s = oracle.senkf_alg3(Xf, rowptr, col, w, r, y, E)
+    assert np.max(np.abs(s - a)) < 1e-12
+    assert oracle.rel_frobenius(a, Xf) > 1e-2     # the analysis does move the ensemble
+
+
 # ---------------------------------------------------------------- generator pins
 def test_philox_known_answer_vectors():
     with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
