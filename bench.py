@@ -73,6 +73,19 @@ def _src_hash(precision="fp32"):
     return h.hexdigest()[:16]
 
 
+# FP64 FMA rate of a GB300 (nominal, 2 flops per FMA); a register-resident FMA loop measured
+# 1.20 TF/s on this part at 2.07 GHz
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _gram_roofline(flops, ms):
+    """The Gram pass of the Reduced and sEnKF variants accumulates in FP64: ALU-bound."""
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_launch": flops, "launch_ms": ms,
+            "peak_source": "nominal FP64 FMA rate"}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -353,20 +366,30 @@ def run_ours(args):
     fp64_solve_ms = float(an64.phase_times()[1])
     an64.set_phase_timing(False)
 
-    # the paper's sEnKF comparator (Algorithm 3: S^{-1} replaced by its diagonal's inverse, no
-    # solve) on the same FP32 ensemble, L2 flushed before each timed analysis
+    # the two variants built on one Gram pass over the observation rows, on the same FP32
+    # ensemble, L2 flushed before each timed analysis: CGD-EnKF-Reduced (Algorithm 2 with CG on
+    # the N x N system) and the paper's sEnKF comparator (Algorithm 3: S^{-1} replaced by its
+    # diagonal's inverse, no solve); phases = (Gram pass, N x N stage, update)
+    def time_variant(an_v):
+        an_v.set_phase_timing(True)
+        an_v.analyze(Xf, y, seed, 0, out=out)
+        tot, ph = [], []
+        for k in range(max(3, args.fp64_steps)):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            an_v.analyze(Xf, y, seed, k, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot.append(e0.elapsed_time(e1))
+            ph.append(an_v.phase_times())
+        return float(np.mean(tot)), [float(v) for v in np.mean(np.array(ph), axis=0)]
+
+    an_r = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", variant="reduced", tol=1e-8)
+    reduced_ms, reduced_ph = time_variant(an_r)
+    reduced_st = an_r.stats()
     an_s = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", variant="senkf")
-    an_s.analyze(Xf, y, seed, 0, out=out)
-    senkf_ms = []
-    for k in range(max(3, args.fp64_steps)):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        an_s.analyze(Xf, y, seed, k, out=out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        senkf_ms.append(e0.elapsed_time(e1))
-    senkf_ms = float(np.mean(senkf_ms))
+    senkf_ms, senkf_ph = time_variant(an_s)
 
     if rank != 0:
         return
@@ -414,6 +437,9 @@ def run_ours(args):
     err = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
     an64.analyze(X64, y, seed, 0, out=o64)
     err64 = oracle.rel_frobenius(o64.cpu().numpy(), ref)
+    an_r.analyze(Xf, y, seed, 0, out=out)
+    err_reduced = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
+    an_r.close()
     an_s.analyze(Xf, y, seed, 0, out=out)
     err_senkf = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
     err_senkf_oracle = oracle.rel_frobenius(
@@ -456,9 +482,17 @@ def run_ours(args):
             "fp64_cg": {"ms_per_step": fp64_ms, "solve_ms": fp64_solve_ms, "value": 1e3 / fp64_ms, "unit": UNIT,
                         "iters": s64["iters_max"], "speedup_of_value": value / (ws * 1e3 / fp64_ms),
                         "solver": "plain CG, FP64 throughout"},
+            "reduced_variant": {"ms_per_step": reduced_ms, "value": 1e3 / reduced_ms, "unit": UNIT,
+                                "phases_ms": dict(zip(("gram", "nxn_cg", "update"), reduced_ph)),
+                                "cg_iterations": reduced_st["iters_max"], "status": reduced_st["status"],
+                                "rel_frobenius_vs_fp64_oracle": err_reduced,
+                                "roofline_gram": _gram_roofline(4.0 * m * N * N, reduced_ph[0]),
+                                "method": "Algorithm 2 with CG on I + P^T P (N x N), FP32 ensemble, FP64 Gram"},
             "senkf_comparator": {"ms_per_step": senkf_ms, "value": 1e3 / senkf_ms, "unit": UNIT,
+                                 "phases_ms": dict(zip(("gram", "sum", "update"), senkf_ph)),
                                  "rel_frobenius_vs_exact_enkf": err_senkf,
                                  "rel_frobenius_vs_oracle_senkf": err_senkf_oracle,
+                                 "roofline_gram": _gram_roofline(2.0 * m * N * N, senkf_ph[0]),
                                  "method": "Algorithm 3 (diagonal inverse of S, no solve), FP32 ensemble, "
                                            "FP64 Gram accumulation; an approximation of the EnKF analysis"},
             "fp32_plain_cg": {"ms_per_step": plain32_ms, "value": 1e3 / plain32_ms, "unit": UNIT,

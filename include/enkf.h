@@ -155,9 +155,9 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
    otherwise); d_y: device [m] FP64; (seed, counter) select the Philox4x32-10 stream of the
    perturbations E when cfg.perturb_obs = 1 (element (i, j) uses counter
    (i, j >> 1, counter_lo, counter_hi) and key (seed_lo, seed_hi); two 53-bit uniforms and
-   Box-Muller give the normal, E_ij = sqrt(r_i) * normal; ENKF_CGD in the FP32 and
-   tensor-core modes evaluates Box-Muller in FP32 from the same uniforms, within about 1e-7
-   of the FP64 normal, every other mode and variant in FP64). d_Xa: device [n][N], same dtype
+   Box-Muller give the normal, E_ij = sqrt(r_i) * normal; ENKF_FP64 evaluates Box-Muller in
+   FP64, the FP32 and tensor-core modes (every variant) in FP32 from the same uniforms,
+   within about 1e-7 of the FP64 normal). d_Xa: device [n][N], same dtype
    as d_Xf; d_Xa == d_Xf (in-place) is allowed, partial overlap is not. Never allocates. */
 enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uint64_t seed,
                          uint64_t counter, void* d_Xa);
@@ -209,7 +209,10 @@ enkf_status enkf_set_phase_timing(enkf_handle h, int32_t enable);
 
 /* Synchronise and return the last timed analysis's kernel durations in milliseconds:
    ms[0] innovations (gather, anomalies, perturbations), ms[1] the persistent CG solve,
-   ms[2] the ensemble update. ENKF_ERR_INVALID_ARG if timing is off or nothing was timed. */
+   ms[2] the ensemble update. For ENKF_CGD_REDUCED and ENKF_SENKF, ms[0] is the Gram pass
+   over the observation rows (gather, anomalies and perturbations included) and ms[1] the
+   N x N stage (Reduced: the sums and the N x N CG; sEnKF: the sum of the partials).
+   ENKF_ERR_INVALID_ARG if timing is off or nothing was timed. */
 enkf_status enkf_get_phase_times(enkf_handle h, float* ms);
 
 /* Synchronise and return the in-kernel phase timers of the last timed solve, measured by

@@ -283,7 +283,8 @@ class Analysis:
         return dict(zip(("setup", "pass", "barrier1", "reduce", "barrier2", "scalars", "refresh"), us[:7]))
 
     def phase_times(self):
-        """(innovations, solve, update) kernel milliseconds of the last timed analysis."""
+        """(innovations, solve, update) kernel milliseconds of the last timed analysis; for the
+        Reduced and sEnKF variants (Gram pass, N x N stage, update)."""
         ms = (ctypes.c_float * 3)()
         _check(load().enkf_get_phase_times(self.h, ms), self.h)
         return tuple(ms)

@@ -8,7 +8,7 @@
 
 #include "common.cuh"
 #include "intermediates.cuh"
-#include "senkf.cuh"
+#include "gram_stages.cuh"
 
 using enkf::Workspace;
 
@@ -171,8 +171,8 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   Workspace& ws = h->ws;
   struct Alloc { void** p; size_t bytes; };
   // the Reduced variant and the sEnKF comparator work from one Gram pass and keep no m x N arrays
-  const bool reduced = c.variant != ENKF_CGD;
-  const int64_t tpart = reduced ? (int64_t)enkf::reduced_grid(h) * 2 * c.N * c.N : (int64_t)G * NE;
+  const bool gram = c.variant != ENKF_CGD;
+  const int64_t tpart = gram ? (int64_t)enkf::reduced_grid(h) * 2 * c.N * c.N : (int64_t)G * NE;
   std::vector<Alloc> allocs = {
       {(void**)&ws.rowptr, sizeof(int32_t) * (c.m + 1)},
       {(void**)&ws.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)},
@@ -193,7 +193,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       {(void**)&ws.stage_y, sizeof(double) * c.m},
       {(void**)&ws.prof, sizeof(unsigned long long) * 8},
   };
-  if (!reduced) {
+  if (!gram) {
     allocs.push_back({(void**)&ws.Sv, vs * mN});
     allocs.push_back({(void**)&ws.D, sizeof(double) * mN});
     allocs.push_back({(void**)&ws.Res, vs * mN});
@@ -203,7 +203,7 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       allocs.push_back({(void**)&ws.Z, sizeof(double) * mN});
     }
   }
-  if (!reduced && c.precision != ENKF_FP64) {
+  if (!gram && c.precision != ENKF_FP64) {
     allocs.push_back({(void**)&ws.HA32, sizeof(float) * mN});
     allocs.push_back({(void**)&ws.r32, sizeof(float) * c.m});
     allocs.push_back({(void**)&ws.B, vs * mN});
@@ -252,26 +252,28 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   if (a != b && a < b + xb && b < a + xb)
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: X_a partially overlaps X_f");
   cudaError_t e = cudaSuccess;
-  const bool reduced = c.variant == ENKF_CGD_REDUCED;
-  const bool senkf = c.variant == ENKF_SENKF;
+  // Reduced and sEnKF: a Gram pass over the observation rows, then an N x N stage (both
+  // variants form HA and D inside the Gram pass instead of the innovations kernel)
+  const bool gram = c.variant != ENKF_CGD;
   if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
   if (c.warm_start && !enkf::warm_ready(h))
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: warm_start = 1 but no model attached (enkf_set_warm_model)");
-  if (e == cudaSuccess && !reduced && !senkf) e = enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
-  if (e != cudaSuccess) return cuda_fail(h, e, "analyze: innovations launch");
+  if (e == cudaSuccess)
+    e = gram ? enkf::launch_gram_stage(h, d_Xf, d_y, d_E, emode, seed, counter)
+             : enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
+  if (e != cudaSuccess) return cuda_fail(h, e, gram ? "analyze: Gram pass launch" : "analyze: innovations launch");
   if (c.warm_start) {
     e = enkf::warm_prepare(h);
     if (e != cudaSuccess) return cuda_fail(h, e, "analyze: learned warm start");
   }
   if (h->timing) e = cudaEventRecord(h->ev[1], h->stream);
   if (e == cudaSuccess)
-    e = senkf ? enkf::launch_senkf(h, d_Xf, d_y, d_E, emode, seed, counter)
-        : reduced ? enkf::launch_reduced(h, d_Xf, d_y, d_E, emode, seed, counter)
-                  : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
+    e = gram ? enkf::launch_nxn_stage(h)
+             : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
   if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
   if (e == cudaSuccess)
-    e = reduced ? enkf::launch_update_product(h, d_Xf, d_Xa) : enkf::launch_update(h, d_Xf, d_Xa);
+    e = c.variant == ENKF_CGD_REDUCED ? enkf::launch_update_product(h, d_Xf, d_Xa) : enkf::launch_update(h, d_Xf, d_Xa);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: update launch");
   if (h->timing) {
     e = cudaEventRecord(h->ev[3], h->stream);
