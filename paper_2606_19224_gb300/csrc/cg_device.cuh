@@ -237,10 +237,18 @@ __device__ __forceinline__ void reduce_all(const double* __restrict__ part, int 
 }
 
 // CTA b (of G) sums its slice of the NE-long partial vectors part[g*NE + e] over g < G (fixed
-// order) and writes red[e].
+// order) and writes red[e]. Entries e < n_f32 are written in FP32 instead, at
+// reinterpret_cast<float*>(red)[e] (bytes [0, 4 n_f32), so they never overlap an FP64 entry
+// e >= n_f32): the CG steps of the FP32 and tensor-core modes read T only as FP32, and one
+// conversion per entry here replaces N^2 FP64 conversions in every CTA.
+__device__ __forceinline__ void store_reduced(double* __restrict__ red, int e, int n_f32, double v) {
+  if (e < n_f32) reinterpret_cast<float*>(red)[e] = (float)v;
+  else red[e] = v;
+}
+
 __device__ __forceinline__ void reduce_slice(const double* __restrict__ part, int G, int NE,
                                              double* __restrict__ red, double* scratch,
-                                             int b) {
+                                             int b, int n_f32 = 0) {
   const int t = threadIdx.x;
   const int chunk = (NE + G - 1) / G;
   const int e0 = b * chunk;
@@ -251,7 +259,7 @@ __device__ __forceinline__ void reduce_slice(const double* __restrict__ part, in
       double s = 0.0;
 #pragma unroll 8
       for (int g = 0; g < G; ++g) s += __ldcg(part + (int64_t)g * NE + e);
-      red[e] = s;
+      store_reduced(red, e, n_f32, s);
     }
     return;
   }
@@ -268,7 +276,7 @@ __device__ __forceinline__ void reduce_slice(const double* __restrict__ part, in
   if (t < cnt) {
     double v = 0.0;
     for (int qq = 0; qq < parts; ++qq) v += scratch[qq * cnt + t];
-    red[e0 + t] = v;
+    store_reduced(red, e0 + t, n_f32, v);
   }
   __syncthreads();
 }
@@ -1133,19 +1141,47 @@ __device__ void refreshB_async(const df32* __restrict__ HAdf, const df32* __rest
   __syncthreads();
 }
 
-// Stage the reduced N x N matrix T (FP64 in global, first N*N entries of Tred) into shared
-// memory as CT with stride NT + 16/sizeof(CT), zero-padded, and return the FP64 column norms
-// ||T_:j||^2 in tn2[j] (thread j owns column j's sum over its rows; fixed order).
+// Compensated sum of squares of FP32 values (exact products by FMA, two-sum accumulation):
+// the FP64 column norms of the FP32 T without FP64 arithmetic per term.
+struct SqAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float ph = __fmul_rn(v, v);
+    const float pl = __fmaf_rn(v, v, -ph);
+    float t, e;
+    df_two_sum(s, ph, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pl));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Stage the reduced N x N matrix T (first N*N entries of Tred: FP64, or FP32 when CT is float,
+// see reduce_slice) into shared memory as CT with stride NT + 16/sizeof(CT), zero-padded, and
+// return the column norms ||T_:j||^2 of the staged T in tn2[j] (FP64 products for FP64, an
+// exact-product compensated sum for FP32; thread j owns column j's sum over its rows; fixed
+// order).
 template <typename CT, int NT>
 __device__ __forceinline__ void stage_T_norms(const double* __restrict__ Tred, int N, CT* sT,
                                               double* tn2, double* scratch) {
   constexpr int LD = NT + 16 / (int)sizeof(CT), L = kThreads / NT;
   const int t = threadIdx.x, j = t % NT, k0 = t / NT;
   double nrm = 0.0;
-  for (int k = k0; k < NT; k += L) {
-    const double v = (k < N && j < N) ? __ldcg(Tred + k * N + j) : 0.0;
-    sT[k * LD + j] = (CT)v;
-    nrm = fma(v, v, nrm);
+  if constexpr (sizeof(CT) == 4) {
+    const float* T32 = reinterpret_cast<const float*>(Tred);
+    SqAcc acc;
+    for (int k = k0; k < NT; k += L) {
+      const float v = (k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f;
+      sT[k * LD + j] = v;
+      acc.add(v);
+    }
+    nrm = acc.value();
+  } else {
+    for (int k = k0; k < NT; k += L) {
+      const double v = (k < N && j < N) ? __ldcg(Tred + k * N + j) : 0.0;
+      sT[k * LD + j] = (CT)v;
+      nrm = fma(v, v, nrm);
+    }
   }
   for (int k = t; k < NT * (LD - NT); k += kThreads) sT[(k / (LD - NT)) * LD + NT + k % (LD - NT)] = CT(0);
   scratch[t] = nrm;

@@ -64,8 +64,8 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   double* s_itol = s_beta + NT;
   double* s_tmp = s_itol + NT;
   double* s_true = s_tmp + NT;
-  double* s_spare = s_true + NT;
-  int* s_active = reinterpret_cast<int*>(s_spare + NT);
+  double* s_den = s_true + NT;
+  int* s_active = reinterpret_cast<int*>(s_den + NT);
   int* s_done = s_active + NT;
   int* s_iters = s_done + NT;
   int* s_flag = s_iters + NT;
@@ -178,6 +178,8 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   }
   tick(PH_SETUP);
 
+  // the CG steps read T only as the staged CT copy: FP32 modes take it from an FP32 T
+  const int t_f32 = sizeof(VT) == 4 ? N * N : 0;
   int outer = 0, total_iter = 0, refinements = 0;
   while (ok) {
    {
@@ -187,7 +189,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       passA<VT, NT, ProSetup<VT, PC>, PC>(HA, row0, row1, N, rv, true, pro, uni, Tp);
     }
     if (!(ok = bar.sync())) break;
-    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
     if (!(ok = bar.sync())) break;
     stage_T_norms<VT, NT>(p.Tred, N, sT, s_tn2, scratch);
     // slots: plain CG: s_sig = sum r r_i^2, s_gam = (r, r); preconditioned: s_sig = (r, z)
@@ -201,7 +203,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
       s_alpha[t] = 0.0;
       s_beta[t] = 0.0;
-      s_spare[t] = 0.0;
+      s_den[t] = 0.0;
     }
     __syncthreads();
     tick(PH_SETUP);
@@ -214,22 +216,29 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
         int a = s_active[t];
         const double gm = s_gam[t];
         if (a && it > 0) {
+          // |r| <= itol |b| in squares (itol shrunk by 4 ulps: a stop implies the square-root
+          // form); FP64 square roots and divisions are costly on this part's FP64 pipe
+          const double itm = s_itol[t] * (1.0 - 4.0 * 2.220446049250313e-16);
           if (!isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
-          else if (fixed ? gm == 0.0 : sqrt(gm) <= s_itol[t] * sqrt(s_bn2[t])) a = 0;
+          else if (fixed ? gm == 0.0 : gm <= itm * itm * s_bn2[t]) a = 0;
         }
         double al = 0.0, be = 0.0;
         if (a) {
-          // CG gamma: (r, r) plain, (r, R^-1 r) preconditioned; delta = (z, S z)
+          // CG gamma: (r, r) plain, (r, R^-1 r) preconditioned; delta = (z, S z). With
+          // beta = gamma / gamma_prev and alpha_prev = gamma_prev / den_prev, the
+          // Chronopoulos-Gear denominator delta - beta gamma / alpha_prev is
+          // delta - beta^2 den_prev: one division fewer per step.
           const double cg = PC ? s_sig[t] : gm;
           const double delta = s_tn2[t] * inv_nm1 + s_sig[t];
           double den = delta;
           if (it > 0) {
             be = cg / s_gold[t];
-            den = delta - be * cg / s_alpha[t];
+            den = delta - be * be * s_den[t];
           }
           if (!isfinite(den)) { atomicOr(p.status, DS_NONFINITE); a = 0; be = 0.0; }
           else if (den <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); a = 0; be = 0.0; }
           else al = cg / den;
+          s_den[t] = den;   // den_prev of the next step
         }
         s_active[t] = a;
         s_alpha[t] = al;
@@ -254,7 +263,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       tick(PH_PASS);
       if (!(ok = bar.sync())) break;
       tick(PH_BAR1);
-      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
       tick(PH_RED);
       if (!(ok = bar.sync())) break;
       tick(PH_BAR2);

@@ -89,10 +89,12 @@ template <typename T16> struct H16;
 template <> struct H16<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   __device__ static __nv_bfloat16 from(float x) { return __float2bfloat16_rn(x); }
+  __device__ static float to(__nv_bfloat16 x) { return __bfloat162float(x); }
 };
 template <> struct H16<__half> {
   static constexpr uint32_t fmt = 0;
   __device__ static __half from(float x) { return __float2half_rn(x); }
+  __device__ static float to(__half x) { return __half2float(x); }
 };
 
 // element (r, k) of a K-major operand with Kd K-elements per row, in elements of 2 bytes:
@@ -650,18 +652,19 @@ __global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N
 }
 
 // Stage T^T/(N-1) scaled per column (ts_j = 1/rms_k(T_kj/(N-1))) into the B operand of the
-// u MMA (rows j, K-major over k); also the FP64 column norms ||T_:j||^2.
+// u MMA (rows j, K-major over k); also the column norms ||T_:j||^2 in FP64. T arrives in FP32
+// (reduce_slice's FP32 output): the norms are exact-product compensated sums of the FP32
+// values, and the scaling and the hi/lo split are FP32 (lo = v - hi is exact in FP32), so no
+// per-entry FP64 arithmetic runs in any CTA.
 template <typename T16, int NT, int TERMS>
 __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int N, double inv,
                                            T16* sBu, float* ts, double* tn2, double* scratch) {
   constexpr int L = kThreads / NT;
   const int t = threadIdx.x, j = t % NT, k0 = t / NT;
-  double nrm = 0.0;
-  for (int k = k0; k < NT; k += L) {
-    const double v = (k < N && j < N) ? __ldcg(Tred + k * N + j) : 0.0;
-    nrm = fma(v, v, nrm);
-  }
-  scratch[t] = nrm;
+  const float* T32 = reinterpret_cast<const float*>(Tred);
+  SqAcc acc;
+  for (int k = k0; k < NT; k += L) acc.add((k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f);
+  scratch[t] = acc.value();
   __syncthreads();
   if (t < NT) {
     double s = 0.0;
@@ -672,12 +675,13 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
     ts[NT + t] = (t < N && rms > 0.0) ? (float)rms : 1.f;   // 1/ts: undoes the scale on u
   }
   __syncthreads();
+  const float inv_f = (float)inv;
   for (int e = t; e < NT * NT; e += kThreads) {
     const int jj = e / NT, k = e % NT;
-    const double v = (k < N && jj < N) ? __ldcg(Tred + k * N + jj) * inv * (double)ts[jj] : 0.0;
-    const T16 hi = H16<T16>::from((float)v);
+    const float v = (k < N && jj < N) ? __ldcg(T32 + k * N + jj) * inv_f * ts[jj] : 0.f;
+    const T16 hi = H16<T16>::from(v);
     sBu[core_idx(jj, k, NT)] = hi;
-    if (TERMS == 3) sBu[NT * NT + core_idx(jj, k, NT)] = H16<T16>::from((float)(v - (double)(float)hi));
+    if (TERMS == 3) sBu[NT * NT + core_idx(jj, k, NT)] = H16<T16>::from(v - H16<T16>::to(hi));
   }
   fence_async_smem();
   __syncthreads();
@@ -725,8 +729,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   double* s_bn2 = s_tn2 + NT;
   double* s_dn2 = s_bn2 + NT;
   double* s_alpha = s_dn2 + NT;
-  double* s_beta = s_alpha + NT;
-  double* s_prev = s_beta + NT;
+  double* s_den = s_alpha + NT;   // the previous step's Chronopoulos-Gear denominator
+  double* s_prev = s_den + NT;
   double* s_tmp = s_prev + NT;
   double* s_true = s_tmp + NT;
   double* s_rel = s_true + NT;
@@ -801,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       passA<float, NT, ProSetup<float, PC>, PC>(p.HA32, row0, row1, N, p.r32, true, pro, uni, Tp);
     }
     if (!(ok = bar.sync())) break;
-    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
     if (!(ok = bar.sync())) break;
     stage_Tt16<T16, NT, TERMS>(p.Tred, N, inv_nm1, sBu, s_ts, s_tn2, scratch);
     if (t < NT) {
@@ -812,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       s_bn2[t] = gm;   // residual norm^2 at the start of this inner solve
       s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
       s_alpha[t] = 0.0;
-      s_beta[t] = 0.0;
+      s_den[t] = 0.0;
     }
     __syncthreads();
     int it = 0;
@@ -824,24 +828,29 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
         double al = 0.0, be = 0.0;
         if (a && !isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
         // the inner solve of this column ends once its residual fell by the factor s_itol
-        if (a && it > 0 && sqrt(gm) <= s_itol[t] * sqrt(s_bn2[t])) a = 0;
+        // (compared in squares: FP64 square roots are costly on this part's FP64 pipe)
+        if (a && it > 0) {
+          const double itf = (double)s_itol[t];
+          if (gm <= itf * itf * s_bn2[t]) a = 0;
+        }
         if (a) {
+          // beta gamma / alpha_old = beta^2 den_old (alpha_old = gamma_old / den_old)
           const double cg = PC ? s_sig[t] : gm;
           const double delta = s_tn2[t] * inv_nm1 + s_sig[t];
           double den = delta;
           if (it > 0) {
             be = cg / s_gold[t];
-            den = delta - be * cg / s_alpha[t];
+            den = delta - be * be * s_den[t];
           }
           // p^T S p = delta - beta gamma/alpha_old cancels; with BF16/FP16 contractions a
           // small or non-positive value means the low-precision recurrences have drifted:
           // this column's inner solve ends here and the refresh restarts it
           if (!isfinite(den) || !(den > 0.05 * delta)) { a = 0; be = 0.0; }
           else al = cg / den;
+          s_den[t] = den;
         }
         s_active[t] = a;
         s_alpha[t] = al;
-        s_beta[t] = be;
         s_alpha_v[t] = (float)al;
         s_beta_v[t] = (float)be;
         s_zs[t] = (t < N && gm > 0.0) ? (float)(1.0 / sqrt(gm)) : 1.f;
@@ -856,7 +865,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
         passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
                                       s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       if (!(ok = bar.sync() && ok)) break;
-      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b);
+      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
       if (!(ok = bar.sync())) break;
       stage_Tt16<T16, NT, TERMS>(p.Tred, N, inv_nm1, sBu, s_ts, s_tn2, scratch);
       if (t < N && s_active[t]) {
