@@ -37,7 +37,7 @@ __device__ __forceinline__ void perturbation_pair(int64_t i, int j, uint64_t see
 // FP64 log and sincos, which dominate the innovations on a GPU whose FP64 rate is a small
 // fraction of its FP32 rate, are avoided.
 __device__ __forceinline__ void perturbation_pair_f32(int64_t i, int j, uint64_t seed, uint64_t counter,
-                                                      double& n_even, double& n_odd) {
+                                                      float& n_even, float& n_odd) {
   uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(j >> 1), c2 = (uint32_t)counter, c3 = (uint32_t)(counter >> 32);
   philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
   const uint64_t x1 = ((uint64_t)c0 << 21) | (c1 >> 11);
@@ -52,15 +52,22 @@ __device__ __forceinline__ void perturbation_pair_f32(int64_t i, int j, uint64_t
   const float rho = sqrtf(-2.f * lg);
   float sn, cs;
   sincospif(__ull2float_rn(x2) * 0x1p-52f, &sn, &cs);
-  n_even = (double)(rho * cs);
-  n_odd = (double)(rho * sn);
+  n_even = rho * cs;
+  n_odd = rho * sn;
+}
+__device__ __forceinline__ void perturbation_pair_f32(int64_t i, int j, uint64_t seed, uint64_t counter,
+                                                      double& n_even, double& n_odd) {
+  float a, b;
+  perturbation_pair_f32(i, j, seed, counter, a, b);
+  n_even = (double)a;
+  n_odd = (double)b;
 }
 
 // Rows [i_begin, i_end) of the observation operator, one warp per row: `warp` is this warp's
 // index among `nwarps` warps sharing the range. Lane l owns members 2l, 2l + 1, 2l + 64,
 // 2l + 65, so each perturbation pair is drawn once.
 template <typename VT>
-__device__ __forceinline__ void innov_rows(
+__device__ __forceinline__ void innov_rows_f64(
     const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
     const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
@@ -68,7 +75,11 @@ __device__ __forceinline__ void innov_rows(
     float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
     int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
     int64_t warp, int64_t nwarps) {
+  // FP64 instructions are scarce on this part (2 per clock per SM): 1/N is applied as a
+  // product and members 64..127 are skipped when N <= 64
   const int lane = threadIdx.x & 31;
+  const double inv_n = 1.0 / (double)N;
+  const bool wide = N > 64;   // members 64..127 present (warp-uniform)
   for (int64_t i = i_begin + warp; i < i_end; i += nwarps) {
     double z[4] = {0.0, 0.0, 0.0, 0.0};
     const int k0 = rowptr[i], k1 = rowptr[i + 1];
@@ -81,20 +92,19 @@ __device__ __forceinline__ void innov_rows(
         if (j < N) z[q] = fma(wk, (double)xr[j], z[q]);
       }
     }
-    double s = z[0] + z[1] + z[2] + z[3];
+    double s = z[0] + z[1];
+    if (wide) s += z[2] + z[3];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double zbar = s / (double)N;
-    const double yi = y[i], sr = sqrt(r[i]);
+    const double zbar = s * inv_n;
+    const double yi = y[i], ri = r[i];
+    const double sr = emode == 2 ? sqrt(ri) : 0.0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int jp = 2 * lane + 64 * h;   // even member of the pair
       if (jp >= N) continue;
       double nrm[2] = {0.0, 0.0};
-      if (emode == 2) {
-        if constexpr (sizeof(VT) == 4) perturbation_pair_f32(i, jp, seed, counter, nrm[0], nrm[1]);
-        else perturbation_pair(i, jp, seed, counter, nrm[0], nrm[1]);
-      }
+      if (emode == 2) perturbation_pair(i, jp, seed, counter, nrm[0], nrm[1]);
       const int64_t e0 = i * N + jp;
       double hv[2], dv[2];
 #pragma unroll
@@ -154,6 +164,125 @@ __device__ __forceinline__ void innov_rows(
       }
     }
   }
+}
+
+// The same rows for FP32 ensembles (the FP32 and tensor-core modes), in double-float (FP32
+// pair) arithmetic: this part issues FP32 at 64x its FP64 rate, and the FP64 version spends
+// its time in FP64 adds and FP32<->FP64 conversions. z = sum w_k x_k accumulates exact
+// products of the double-float weight and the FP32 member value, z-bar is a double-float warp
+// sum (each lane adds the same operands in the same order: the double-float sum is
+// commutative), HA = z - z-bar and D = (y - z) + E are double-float (about 48 significant
+// bits, the precision of the HAdf and Ddf arrays they fill), E = sqrt(r_i) times the FP32
+// normal as an exact double-float product; HA32 and B32 are the high parts, and only the
+// FP64 copy of D is widened per element.
+template <typename VT>
+__device__ __forceinline__ void innov_rows_df(
+    const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
+    const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
+    double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
+    float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
+    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
+    int64_t warp, int64_t nwarps) {
+  static_assert(sizeof(VT) == 4, "double-float innovations take an FP32 ensemble");
+  const int lane = threadIdx.x & 31;
+  const df32 inv_n(1.0 / (double)N);
+  const bool wide = N > 64;   // members 64..127 present (warp-uniform)
+  for (int64_t i = i_begin + warp; i < i_end; i += nwarps) {
+    df32 z[4];
+    const int k0 = rowptr[i], k1 = rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const df32 wk(w[k]);
+      const VT* xr = Xf + (int64_t)col[k] * N;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = 2 * lane + (q & 1) + 64 * (q >> 1);
+        if (j < N) z[q] = fma(wk, df32((float)xr[j], 0.f), z[q]);
+      }
+    }
+    df32 s = z[0] + z[1];
+    if (wide) s = s + (z[2] + z[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      s = s + df32(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
+    const df32 zbar = s * inv_n;
+    const df32 yd(y[i]);
+    const df32 sr = emode == 2 ? df32(sqrt(r[i])) : df32();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jp = 2 * lane + 64 * h;   // even member of the pair
+      if (jp >= N) continue;
+      float nrm[2] = {0.f, 0.f};
+      if (emode == 2) perturbation_pair_f32(i, jp, seed, counter, nrm[0], nrm[1]);
+      const int64_t e0 = i * N + jp;
+      df32 hv[2], dv[2];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        df32 pert;
+        if (jp + b < N) {
+          if (emode == 1) pert = df32(E[e0 + b]);
+          else if (emode == 2) pert = sr * df32(nrm[b], 0.f);
+        }
+        hv[b] = z[2 * h + b] - zbar;
+        dv[b] = (yd - z[2 * h + b]) + pert;
+      }
+      if ((N & 1) == 0) {
+        // both members present and e0 even: one 8- or 16-byte store per array per lane
+        *reinterpret_cast<double2*>(D + e0) = make_double2((double)dv[0], (double)dv[1]);
+        if (HA32) *reinterpret_cast<float2*>(HA32 + e0) = make_float2(hv[0].hi, hv[1].hi);
+        if (B32) *reinterpret_cast<float2*>(B32 + e0) = make_float2(dv[0].hi, dv[1].hi);
+        if (HAdf) *reinterpret_cast<float4*>(HAdf + e0) = make_float4(hv[0].hi, hv[0].lo, hv[1].hi, hv[1].lo);
+        if (Ddf) *reinterpret_cast<float4*>(Ddf + e0) = make_float4(dv[0].hi, dv[0].lo, dv[1].hi, dv[1].lo);
+      } else {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          if (jp + b >= N) continue;
+          const int64_t e = e0 + b;
+          D[e] = (double)dv[b];
+          if (HA32) HA32[e] = hv[b].hi;
+          if (B32) B32[e] = dv[b].hi;
+          if (HAdf) HAdf[e] = hv[b];
+          if (Ddf) Ddf[e] = dv[b];
+        }
+      }
+      // optional copies (not requested by the current callers): FP64 HA and 16-bit images
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        if (jp + b >= N) continue;
+        const int64_t e = e0 + b;
+        if (HA64) HA64[e] = (double)hv[b];
+        if (HAb) {
+          const __nv_bfloat16 hi = __float2bfloat16(hv[b].hi);
+          HAb[e] = hi;
+          if (split_lo) HAb[m * N + e] = __float2bfloat16((hv[b] - df32(__bfloat162float(hi), 0.f)).hi);
+        }
+        if (HAh) {
+          const __half hi = __float2half(hv[b].hi);
+          HAh[e] = hi;
+          if (split_lo) HAh[m * N + e] = __float2half((hv[b] - df32(__half2float(hi), 0.f)).hi);
+        }
+      }
+    }
+  }
+}
+
+// Rows [i_begin, i_end) of the innovation step: FP64 arithmetic for FP64 ensembles,
+// double-float for FP32 ones.
+template <typename VT>
+__device__ __forceinline__ void innov_rows(
+    const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double* __restrict__ w, const double* __restrict__ y, const double* __restrict__ r,
+    const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
+    double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
+    float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
+    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
+    int64_t warp, int64_t nwarps) {
+  if constexpr (sizeof(VT) == 4)
+    innov_rows_df<VT>(Xf, rowptr, col, w, y, r, E, emode, seed, counter, m, N, HA64, HA32, D, B32,
+                      HAb, HAh, split_lo, HAdf, Ddf, i_begin, i_end, warp, nwarps);
+  else
+    innov_rows_f64<VT>(Xf, rowptr, col, w, y, r, E, emode, seed, counter, m, N, HA64, HA32, D, B32,
+                       HAb, HAh, split_lo, HAdf, Ddf, i_begin, i_end, warp, nwarps);
 }
 
 }  // namespace enkf
