@@ -382,30 +382,57 @@ __device__ __forceinline__ void update_rows(const VT* Xf, VT* Xa, const double* 
   constexpr int LD = NT + 16 / (int)sizeof(VT), TRB = Tile<NT>::TRB, C4 = NT / 4;
   constexpr int NJ = NT / 4;
   VT* sW = reinterpret_cast<VT*>(smem);
-  VT* sX = sW + NT * LD;
-  VT* smean = sX + TRB * LD;
+  VT* sXb[2] = {sW + NT * LD, sW + NT * LD + TRB * LD};   // X_f row tiles, double-buffered
+  VT* smean = sW + NT * LD + 2 * TRB * LD;
   const int t = threadIdx.x, tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * 4;
   const bool vec = (N & 3) == 0;
   for (int e = t; e < NT * LD; e += kThreads) {
     const int k = e / LD, j = e % LD;
     sW[e] = (k < N && j < N) ? (VT)__ldcg(W + k * N + j) : VT(0);   // W may be written by this launch
   }
-  for (int64_t i0 = tile0 * TRB; i0 < n; i0 += tstride * TRB) {
-    __syncthreads();
+  // the tile of rows [i0, i0 + TRB) into dst: 16-byte cp.async pieces (zero-filled past n and
+  // N) when rows are 16-byte aligned (N % 4 == 0), else plain loads
+  auto load_tile = [&](int64_t i0, VT* dst) {
 #pragma unroll
     for (int c = t; c < TRB * C4; c += kThreads) {
       const int ii = c / C4, c0 = (c % C4) * 4;
       const int64_t i = i0 + ii;
-      VT a[4] = {VT(0), VT(0), VT(0), VT(0)};
-      if (i < n && c0 < N) ld4<VT>(a, Xf + i * N, c0, N, vec);
+      const bool ok = i < n && c0 < N;
+      if (vec) {
+        const VT* src = ok ? Xf + i * N + c0 : Xf;
 #pragma unroll
-      for (int y = 0; y < 4; ++y) sX[ii * LD + c0 + y] = a[y];
+        for (int q = 0; q < (int)sizeof(VT) / 4; ++q)
+          cp_async16(dst + ii * LD + c0 + q * (16 / (int)sizeof(VT)), src + q * (16 / (int)sizeof(VT)), ok);
+      } else {
+        VT a[4] = {VT(0), VT(0), VT(0), VT(0)};
+        if (ok) ld4<VT>(a, Xf + i * N, c0, N, false);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) dst[ii * LD + c0 + y] = a[y];
+      }
+    }
+  };
+  int cur = 0;
+  if (vec && tile0 * TRB < n) load_tile(tile0 * TRB, sXb[0]);
+  cp_async_commit();
+  for (int64_t i0 = tile0 * TRB; i0 < n; i0 += tstride * TRB) {
+    VT* sX = sXb[cur];
+    const int64_t inext = i0 + tstride * TRB;
+    if (vec) {
+      if (inext < n) load_tile(inext, sXb[cur ^ 1]);   // overlaps this tile's work
+      cp_async_commit();
+      cp_async_wait<1>();                               // this tile has landed
+    } else {
+      load_tile(i0, sX);
     }
     __syncthreads();
-    if (t < TRB) {
-      VT s = VT(0);
-      for (int k = 0; k < N; ++k) s += sX[t * LD + k];
-      smean[t] = s / (VT)N;
+    // row means: four threads per row (consecutive rows on consecutive lane groups read
+    // distinct banks), partial sums over k = g, g + 4, ..., added by two shuffle steps
+    for (int rr = t / 4; rr < TRB; rr += kThreads / 4) {
+      VT sm = VT(0);
+      for (int k = t % 4; k < N; k += 4) sm += sX[rr * LD + k];
+      sm += __shfl_xor_sync(0xffffffffu, sm, 1);
+      sm += __shfl_xor_sync(0xffffffffu, sm, 2);
+      if ((t & 3) == 0) smean[rr] = sm / (VT)N;
     }
     __syncthreads();
     // original X_f fragments for the output (same threads write X_a, so X_a may alias X_f)
@@ -448,12 +475,15 @@ __device__ __forceinline__ void update_rows(const VT* Xf, VT* Xa, const double* 
         st4<VT>(Xa + i * N, j0, N, vec, o);
       }
     }
+    __syncthreads();   // every read of sX ends before the next iteration refills it
+    cur ^= 1;
   }
+  cp_async_wait<0>();
 }
 
 template <typename VT, int NT> __host__ __device__ constexpr int update_smem_bytes() {
   constexpr int LD = NT + 16 / (int)sizeof(VT);
-  return (NT * LD + Tile<NT>::TRB * LD + Tile<NT>::TRB) * (int)sizeof(VT);
+  return (NT * LD + 2 * Tile<NT>::TRB * LD + Tile<NT>::TRB) * (int)sizeof(VT);
 }
 
 }  // namespace enkf
