@@ -114,3 +114,33 @@ def test_gram_variants_time_their_two_stages(lib, variant):
     ref = (oracle.senkf_alg3(X64, p.rowptr, p.col, p.w, p.r, p.y, E) if variant == "senkf"
            else oracle.enkf_exact(X64, p.rowptr, p.col, p.w, p.r, p.y, E))
     assert oracle.rel_frobenius(Xa.double().cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [2, 37, 128])
+def test_senkf_single_observation_is_the_enkf(lib, N):
+    # with one observation S is 1 x 1 and equals its diagonal: Algorithm 3 is then the exact
+    # EnKF analysis (Sec. 2.4's scalar gain), a property independent of the oracle's Algorithm 3
+    p = synth.grf_problem(12, 3.0, N, 1, 0.5, 1.5, seed=40 + N)
+    an = _analysis(lib, p, "fp64")
+    Xf, y = _dev(p, "fp64")
+    Xa = an.analyze(Xf, y, seed=3, counter=2).cpu().numpy()
+    E = oracle.obs_perturbations(3, 2, p.r, p.N)
+    exact = oracle.enkf_exact(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert oracle.rel_frobenius(Xa, exact) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", ["senkf", "reduced"])
+@pytest.mark.parametrize("m", [1, 3, 31, 33])
+@pytest.mark.parametrize("N", [2, 64, 128])
+def test_gram_variants_fewer_rows_than_a_tile(lib, variant, m, N):
+    # m below and around the Gram pass's 32-row tile: one CTA, ragged last tile
+    p = synth.grf_problem(10, 3.0, N, m, 0.5, 1.5, seed=7 * m + N)
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp64", variant=variant,
+                      tol=1e-12)
+    Xf, y = _dev(p, "fp64")
+    Xa = an.analyze(Xf, y, seed=5, counter=1).cpu().numpy()
+    assert an.stats()["status"] == "ok"
+    E = oracle.obs_perturbations(5, 1, p.r, p.N)
+    ref = (oracle.senkf_alg3(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E) if variant == "senkf"
+           else oracle.enkf_exact(p.Xf, p.rowptr, p.col, p.w, p.r, p.y, E))
+    assert oracle.rel_frobenius(Xa, ref) <= 1e-10
