@@ -25,6 +25,7 @@
 #include "gram_stages.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace enkf {
 
@@ -43,8 +44,33 @@ template <> struct GramCfg<32> { static constexpr int KR = 32; };
 template <> struct GramCfg<64> { static constexpr int KR = 64; };
 template <> struct GramCfg<128> { static constexpr int KR = 32; };
 
-// VT: type of X_f; AT: type of the staged tiles and the accumulators (FP64 in both modes:
-// FP32 products of FP32-rounded anomalies lose ~sqrt(m) in the cancelling off-diagonals).
+// A running product sum of the Gram pass: FP64 FMAs, or for double-float operands the
+// compensated pair of DFAcc (exact FP32 products, TwoSum, errors gathered in c), renormalised
+// every few terms. FP32 products of FP32-rounded anomalies would lose ~sqrt(m) in G's
+// cancelling off-diagonals; double-float keeps about 44 bits at 12 FP32 operations per term,
+// and FP32 issues at 64x the FP64 rate on this part.
+template <typename AT> struct GramAcc;
+template <> struct GramAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void renorm() {}
+  __device__ __forceinline__ double value() const { return v; }
+  __device__ __forceinline__ void set(double x) { v = x; }
+};
+template <> struct GramAcc<df32> {
+  DFAcc d;
+  __device__ __forceinline__ void add(const df32& a, const df32& b) { d.add(a, b); }
+  __device__ __forceinline__ void renorm() { d.renorm(); }
+  __device__ __forceinline__ double value() const { return (double)d.value(); }
+  __device__ __forceinline__ void set(double x) {
+    const df32 v(x);
+    d.s = v.hi;
+    d.c = v.lo;
+  }
+};
+
+// VT: type of X_f; AT: type of the staged tiles and the accumulators: FP64 for FP64
+// ensembles, double-float for FP32 ensembles (see GramAcc).
 template <typename VT, typename AT, int NT, bool SENKF = false>
 __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
     const VT* __restrict__ Xf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -66,13 +92,7 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int g = t / (kThreads / RG);                 // row group of this thread
   const int kbase = blockIdx.y * KR;
-  AT acc[TPT][4][4];
-#pragma unroll
-  for (int q = 0; q < TPT; ++q)
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int yy = 0; yy < 4; ++yy) acc[q][x][yy] = AT(0);
+  GramAcc<AT> acc[TPT][4][4];   // zero-initialised
 
   const double inv_n = 1.0 / (double)N;   // FP64 divisions run on the same pipe as the Gram's
                                            // FMAs: one per thread here, one per row below
@@ -170,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
     for (int q = 0; q < TPT; ++q) {
       const int u = (RG > 1) ? t % TILES : t + q * kThreads;
       const int tj = u % JG, tk = u / JG;
+      int terms = 0;
       for (int ii = g; ii < nrows; ii += RG) {
         AT a[4], b[4];
 #pragma unroll
@@ -179,8 +200,18 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int yy = 0; yy < 4; ++yy) acc[q][x][yy] = fma(a[x], b[yy], acc[q][x][yy]);
+          for (int yy = 0; yy < 4; ++yy) acc[q][x][yy].add(a[x], b[yy]);
+        if ((++terms & 3) == 0) {
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int yy = 0; yy < 4; ++yy) acc[q][x][yy].renorm();
+        }
       }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int yy = 0; yy < 4; ++yy) acc[q][x][yy].renorm();
     }
   }
   // fold the row groups (fixed order) and write this CTA's partial rows (FP64)
@@ -192,14 +223,14 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int yy = 0; yy < 4; ++yy) sred[u * 16 + x * 4 + yy] = (double)acc[0][x][yy];
+          for (int yy = 0; yy < 4; ++yy) sred[u * 16 + x * 4 + yy] = acc[0][x][yy].value();
       }
       __syncthreads();
       if (g == 0) {
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int yy = 0; yy < 4; ++yy) acc[0][x][yy] = (AT)((double)acc[0][x][yy] + sred[t * 16 + x * 4 + yy]);
+          for (int yy = 0; yy < 4; ++yy) acc[0][x][yy].set(acc[0][x][yy].value() + sred[t * 16 + x * 4 + yy]);
       }
       __syncthreads();
     }
@@ -216,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) reduced_gram_kernel(
       for (int yy = 0; yy < 4; ++yy) {
         const int k = kbase + tk * 4 + x, jj = tj * 4 + yy;
         const int half = jj / NT, j = jj % NT;
-        if (k < N && j < N) out[(int64_t)half * N * N + k * N + j] = (double)acc[q][x][yy];
+        if (k < N && j < N) out[(int64_t)half * N * N + k * N + j] = acc[q][x][yy].value();
       }
   }
 }
@@ -388,12 +419,13 @@ static cudaError_t gram_launch(enkf_handle_s* h, const void* Xf, const double* y
   auto& ws = h->ws;
   const int NT = c.N <= 32 ? 32 : (c.N <= 64 ? 64 : 128);
   const VT* X = static_cast<const VT*>(Xf);
+  using AT = typename std::conditional<sizeof(VT) == 8, double, df32>::type;
   if (NT == 32)
-    reduced_gram_kernel<VT, double, 32, SENKF><<<dim3(grid, 32 / GramCfg<32>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, AT, 32, SENKF><<<dim3(grid, 32 / GramCfg<32>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   else if (NT == 64)
-    reduced_gram_kernel<VT, double, 64, SENKF><<<dim3(grid, 64 / GramCfg<64>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, AT, 64, SENKF><<<dim3(grid, 64 / GramCfg<64>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   else
-    reduced_gram_kernel<VT, double, 128, SENKF><<<dim3(grid, 128 / GramCfg<128>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
+    reduced_gram_kernel<VT, AT, 128, SENKF><<<dim3(grid, 128 / GramCfg<128>::KR), kThreads, 0, h->stream>>>(X, ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter, c.m, c.N, ws.Tpart);
   return cudaGetLastError();
 }
 
