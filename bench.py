@@ -5,14 +5,25 @@ One step = one full analysis (observation gather + anomalies + perturbed innovat
 persistent CG solve of S Z = D, and the ensemble update X_a = X_f + A W) through the C ABI
 on the synthetic 512x512 Gaussian-random-field workload: n = 262,144 state variables,
 N = 64 members, m = 65,536 randomly placed observations, r ~ U[0.5, 1.5], CG tolerance
-1e-8 (true FP64 relative residual).
+1e-8 (true relative residual, checked in double-float or FP64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0). `value` is analyses/s summed over ranks (each rank runs its
-own independent analyses: weak scaling, no collective on the data path). The headline path
-is the FP32 CG with FP64 residual refresh (meets 1e-6 relative Frobenius error); the plain
-FP64 GPU CG is timed beside it. `--impl reference` times the CPU oracle instead (host cores).
+own independent analyses: weak scaling, no collective on the data path). The timed headline
+is FP32 CG preconditioned by R with a double-float residual refresh (meets 1e-6 relative
+Frobenius error against the FP64 oracle). On one GPU the same run then measures, after the
+timed region, every other configuration of the method as keys of the same line:
+  c1_variants      the 512x512 workload in plain FP64 CG (the comparison point), FP64 CG
+                   preconditioned by R, plain FP32 CG, FP16 and BF16 tensor-core solves
+  reduced_variant, senkf_comparator   the two one-pass variants on the same ensemble
+  c2_mixed         1024x1024 GRF, N = 128, m = 262,144: BF16 / FP16 / FP32 / FP64
+  c3_batch         256 uneven analyses in one persistent launch (tuned plan, CUDA graph)
+  c4_warm_start    the learned CG warm start, trained here, on held-out problems
+  c0_l96           200 Lorenz-96 forecast + analysis cycles
+  cpu_baseline(_1core), cpu_plain_fp64_cg   the CPU oracle and the paper's CG on the host
+each with its error against the FP64 oracle and the roofline of its solve.
+`--impl reference` times the CPU oracle instead (host cores).
 """
 import argparse
 import hashlib
@@ -35,27 +46,87 @@ BATCH_WORKLOAD = "batched256_grf"
 MIXED_WORKLOAD = "grf1024_N128_m262144"
 
 
-def B_ITER(m, N):
-    """Algorithmic DRAM bytes of one fused FP32 CG step (Chronopoulos-Gear form): HA read
-    once (4 m N), the iterate, residual, direction and S-direction read and written
-    (4 x 8 m N), r read (4 m)."""
+# ------------------------------------------------------------------ algorithmic work
+# The roofline of an analysis (the paper's CG, Sec. 3.3, with the matvec of Eq.
+# matvec_decomp): time = max(F / peak_F, B / BW) over the algorithmic flops F and DRAM bytes
+# B, with the iteration and refresh counts the run actually took.
+#   per CG step:  B = 2 m N s_HA (HA read twice) + 8 m N s_v (x: 1R+1W, r: 2R+1W, p: 2R+1W)
+#                 + 2 m 8 (r_i, twice);  F = 4 m N^2 (HA^T p and HA (.))
+#   per refresh:  B = 2 m N s_HA + 3 m N s_v (HA twice, Z, D in, residual out)
+# s_HA = s_v = 8 (FP64), 4 (FP32); s_HA = 2 for BF16/FP16 HA with FP32 vectors.
+S_BYTES = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 4), "bf16": (2, 4)}
+
+
+def B_ITER(m, N, prec="fp32"):
+    s_ha, s_v = S_BYTES[prec]
+    return 2 * m * N * s_ha + 8 * m * N * s_v + 16 * m
+
+
+def B_REF(m, N, prec="fp32"):
+    s_ha, s_v = S_BYTES[prec]
+    return 2 * m * N * s_ha + 3 * m * N * s_v
+
+
+def F_ITER(m, N):
+    return 4.0 * m * N * N
+
+
+def B_FUSED(m, N):
+    """The same step as one fused FP32 pass reads and writes it (HA read once, x, r, p and
+    S p read and written, r_i read): 36 m N + 4 m bytes."""
     return 36 * m * N + 4 * m
 
 
-def B_REF(m, N):
-    """Algorithmic DRAM bytes of one double-float residual refresh: pass A reads HA (8 m N),
-    reads and writes Z (16 m N) and reads X (4 m N); pass B reads HA, Z and D (24 m N) and
-    writes the next right-hand side (4 m N)."""
-    return 56 * m * N
+# Measured on a GB300 with a register-resident FMA loop (152 SMs at 2.07 GHz): FP64 FMA
+# 1.20 TFLOP/s, FP32 FMA 74.7 TFLOP/s. Tensor peaks (BF16 = FP16) from the driver's file.
+FP64_TFLOPS = 1.20
+FP32_TFLOPS = 74.7
+
+
+def _peak_flops(prec):
+    if prec == "fp64":
+        return FP64_TFLOPS, "FP64 FMA, measured"
+    if prec == "fp32":
+        return FP32_TFLOPS, "FP32 FMA, measured"
+    return _tensor_peak(), "dense BF16/FP16 tensor, measured sustained"
+
+
+def _tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("bf16_tflops_sustained", 1700.0))
+    except OSError:
+        return 1700.0
+
+
+def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=None):
+    """Roofline of one solve launch on the byte and flop model above."""
+    bw, bw_src = _peaks()
+    pf, pf_src = _peak_flops(prec)
+    B = iters * B_ITER(m, N, prec) + refreshes * B_REF(m, N, prec)
+    F = iters * F_ITER(m, N)
+    t_b = B / (bw * 1e9)
+    t_f = F / (pf * 1e12)
+    t = solve_ms / 1e3
+    if t_b >= t_f:
+        return {"bound": "hbm", "achieved": B / t / 1e9, "peak": bw, "unit": "GB/s", "frac": t_b / t,
+                "traffic": traffic, "kernel": kernel, "peak_source": bw_src,
+                "algorithmic_bytes_per_launch": B, "algorithmic_flops_per_launch": F,
+                "launch_ms": solve_ms, "cg_iterations": iters, "refreshes": refreshes,
+                "compute_bound_frac": t_f / t}
+    unit = "TFLOP/s"
+    return {"bound": "tensor" if prec in ("fp16", "bf16") else "alu", "achieved": F / t / 1e12, "peak": pf,
+            "unit": unit, "frac": t_f / t, "traffic": traffic, "kernel": kernel, "peak_source": pf_src,
+            "algorithmic_bytes_per_launch": B, "algorithmic_flops_per_launch": F, "launch_ms": solve_ms,
+            "cg_iterations": iters, "refreshes": refreshes, "hbm_frac": t_b / t}
 
 # DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
-# captures summarised in profiles/solve_kernel_fp32_grf512_N64_m65536.md and
-# profiles/solve_mixed_kernel_fp16_grf512_N64_m65536.md, with the hash of the kernel sources
-# each capture measured; reported as null once those sources have changed.
+# captures summarised under profiles/, with the hash of the kernel sources each capture
+# measured; reported as null once those sources have changed.
 NCU_TRAFFIC = {"fp32": {"bytes": 4.646017e9, "src_sha": "f359344179649ea3"},
                "fp16": {"bytes": 6.431757e9, "src_sha": "18d941411bdfab5b"}}
-# The same for one batch_kernel launch on the 256-problem batch (seed 1), from the one-pass
-# DRAM capture summarised in profiles/batch_kernel_batched256_grf_dram.md.
+# DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
+# profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
 NCU_TRAFFIC_BATCH = {"bytes": 1.436453e12, "problems": 256, "seed": 1, "src_sha": "869cf69968486ece"}
 _KERNEL_SOURCES = {
     "fp32": ("kernels_fp.cu", "common.cuh", "cg_device.cuh", "solve_body.cuh"),
@@ -81,14 +152,29 @@ FP32_OPS_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 DF_OPS_PER_TERM = 12
 
 
-def _gram_roofline(terms, ms):
-    """The Gram pass of the Reduced and sEnKF variants on an FP32 ensemble: double-float
-    product sums, bound by the FP32 issue rate (`terms` products per launch)."""
+def _gram_roofline(terms, ms, m, N, ens_bytes=4):
+    """The Gram pass of the Reduced and sEnKF variants (`terms` products m N^2 or 2 m N^2 per
+    launch, reading the observed rows of X_f plus the CSR operator, r and y). The roofline is
+    the slower of the products at the FP32 FMA peak and the bytes at HBM bandwidth; the
+    issue efficiency of the double-float implementation (12 FP32 operations per product
+    against the FP32 lanes x clock) is reported beside it, not as the roofline fraction."""
+    bw, bw_src = _peaks()
+    t = ms / 1e3
+    B = ens_bytes * m * N + 32 * m
+    t_f = 2.0 * terms / (FP32_TFLOPS * 1e12)
+    t_b = B / (bw * 1e9)
     ops = DF_OPS_PER_TERM * terms
-    achieved = ops / (ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP32_OPS_PEAK_T, "unit": "T FP32 op/s",
-            "frac": achieved / FP32_OPS_PEAK_T, "ops_per_launch": ops, "terms_per_launch": terms,
-            "launch_ms": ms, "peak_source": "FP32 lanes x maximum SM clock"}
+    issue = ops / t / 1e12
+    base = {"terms_per_launch": terms, "algorithmic_bytes_per_launch": B, "launch_ms": ms,
+            "issue_efficiency": {"achieved": issue, "peak": FP32_OPS_PEAK_T, "unit": "T FP32 op/s",
+                                 "frac": issue / FP32_OPS_PEAK_T, "ops_per_term": DF_OPS_PER_TERM}}
+    if t_f >= t_b:
+        base.update({"bound": "alu", "achieved": 2.0 * terms / t / 1e12, "peak": FP32_TFLOPS, "unit": "TFLOP/s",
+                     "frac": t_f / t, "peak_source": "FP32 FMA, measured"})
+    else:
+        base.update({"bound": "hbm", "achieved": B / t / 1e9, "peak": bw, "unit": "GB/s", "frac": t_b / t,
+                     "peak_source": bw_src})
+    return base
 
 
 def _peaks():
@@ -190,47 +276,93 @@ def _cores():
     return len(os.sched_getaffinity(0))
 
 
-def cpu_baseline(problem, E, budget_s=20.0):
-    """The CPU oracle as it stands on the host cores: exact analysis through Algorithm 2
-    (N x N Cholesky), repeated on the benchmark's full-size problem within the budget."""
+def _oracle_loop(p, seed, reps_cap, budget_s):
+    """The oracle as it stands, per analysis: the perturbations from its own Philox stream and
+    the exact FP64 analysis (Algorithm 2 route, N x N Cholesky), both inside the timed loop,
+    as the library draws E inside each analysis."""
+    import numpy as np
     import oracle
+    X = p.Xf.astype(np.float64)
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oracle.enkf_exact(problem.Xf.astype("float64"), problem.rowptr, problem.col, problem.w,
-                          problem.r, problem.y, E)
+        E = oracle.obs_perturbations(seed, reps, p.r, p.N)
+        oracle.enkf_exact(X, p.rowptr, p.col, p.w, p.r, p.y, E)
         reps += 1
         el = time.perf_counter() - t0
-        if el > budget_s or reps >= 8:
-            break
+        if el > budget_s or reps >= reps_cap:
+            return reps, el
+
+
+def cpu_baseline(problem, seed, budget_s=20.0, reps_cap=8):
+    """The CPU oracle on the host cores: a bounded sample of full-size analyses."""
+    reps, el = _oracle_loop(problem, seed, reps_cap, budget_s)
     return {"value": reps / el, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-            "sample": f"{reps} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, FP64 numpy) "
-                      f"in {el:.1f} s"}
+            "sample": f"{reps} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, FP64 numpy; "
+                      f"perturbations drawn by the oracle's Philox stream inside the timed loop) in {el:.1f} s"}
+
+
+def _child(code, threads=None, timeout=900):
+    env = dict(os.environ)
+    if threads:
+        env.update(OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads), MKL_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=timeout, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def cpu_baseline_one_core(seed, reps=3):
     """The same oracle on one thread (BLAS and OpenMP limited to 1), in a child process so that
-    the limit holds from its first import; the analyses are the benchmark's full-size problem."""
-    import subprocess
-    import sys
-    code = ("import time\nimport numpy as np\nimport oracle, synth\n"
+    the limit holds from its first import."""
+    code = ("import json, numpy as np, synth, bench\n"
             f"p = synth.workload({WORKLOAD!r}, {int(seed)}, dtype=np.float32)\n"
-            f"E = oracle.obs_perturbations({int(seed)}, 0, p.r, p.N)\n"
-            "X = p.Xf.astype('float64')\n"
-            "t0 = time.perf_counter()\n"
-            f"for _ in range({int(reps)}):\n"
-            "    oracle.enkf_exact(X, p.rowptr, p.col, p.w, p.r, p.y, E)\n"
-            "print(time.perf_counter() - t0)\n")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                         timeout=900, check=True)
-    el = float(out.stdout.strip().splitlines()[-1])
-    return {"value": reps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, FP64 numpy) "
+            f"n, el = bench._oracle_loop(p, {int(seed)}, {int(reps)}, 1e9)\n"
+            "print(json.dumps([n, el]))\n")
+    n, el = _child(code, threads=1)
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full-size exact analyses ({WORKLOAD}, Algorithm 2 route, same protocol) "
                       f"on one thread in {el:.1f} s"}
 
 
+def _cpu_cg_timing(p, seed, k1=2, k2=10):
+    """Plain FP64 CPU CG (the paper's method, oracle.cgd_enkf: textbook CG on S Z = D with
+    the matvec of Eq. matvec_decomp) on the full-size problem, timed at two fixed step
+    counts: returns (set-up + update seconds, seconds per CG step)."""
+    import numpy as np
+    import oracle
+    X = p.Xf.astype(np.float64)
+    E = oracle.obs_perturbations(seed, 0, p.r, p.N)
+    ts = []
+    for k in (k1, k2):
+        t0 = time.perf_counter()
+        oracle.cgd_enkf(X, p.rowptr, p.col, p.w, p.r, p.y, E, fixed_iters=k)
+        ts.append(time.perf_counter() - t0)
+    per = (ts[1] - ts[0]) / (k2 - k1)
+    return max(ts[0] - k1 * per, 0.0), per
+
+
+def cpu_cg_baseline(p, seed, iters):
+    """The paper's method on the CPU: plain FP64 CG (tol 1e-8, stopping rule as the GPU's), on
+    all host cores and on one thread; a bounded sample (2 and 10 CG steps) extrapolated to
+    the `iters` steps the plain FP64 GPU CG took on the same problem."""
+    fixed, per = _cpu_cg_timing(p, seed)
+    code = ("import json, numpy as np, synth, bench\n"
+            f"p = synth.workload({WORKLOAD!r}, {int(seed)}, dtype=np.float32)\n"
+            f"print(json.dumps(bench._cpu_cg_timing(p, {int(seed)})))\n")
+    fixed1, per1 = _child(code, threads=1)
+    out = {}
+    for tag, (f, q, cores) in (("all_cores", (fixed, per, _cores())), ("one_core", (fixed1, per1, 1))):
+        t = f + iters * q
+        out[tag] = {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle plain FP64 CG",
+                    "s_per_cg_step": q, "s_setup_and_update": f, "cg_steps": iters,
+                    "sample": f"oracle.cgd_enkf on {WORKLOAD} timed at 2 and 10 CG steps, extrapolated "
+                              f"to {iters} steps"}
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands (exact FP64 analysis, perturbations from
+    its own Philox stream inside the loop) on the host cores, rank 0 only."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
@@ -238,13 +370,13 @@ def run_reference(args):
     import oracle
     import synth
     p = synth.workload(WORKLOAD, args.seed, dtype=np.float32)
-    E = oracle.obs_perturbations(args.seed, 0, p.r, p.N)
-    for _ in range(args.warmup):
-        oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    X = p.Xf.astype(np.float64)
+    for k in range(args.warmup):
+        oracle.enkf_exact(X, p.rowptr, p.col, p.w, p.r, p.y, oracle.obs_perturbations(args.seed, k, p.r, p.N))
     t0 = time.perf_counter()
     for k in range(args.steps):
         E = oracle.obs_perturbations(args.seed, k, p.r, p.N)
-        oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+        oracle.enkf_exact(X, p.rowptr, p.col, p.w, p.r, p.y, E)
     el = time.perf_counter() - t0
     v = args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -255,9 +387,73 @@ def run_reference(args):
                        "route": "CPU oracle, exact FP64 analysis (Algorithm 2, N x N Cholesky)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                              "sample": f"{args.steps} full-size exact analyses, perturbations "
-                                       f"from the oracle's Philox stream"},
+                                       f"from the oracle's Philox stream inside the timed loop"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Timer:
+    """CUDA-event timing of analyses on the launching stream, L2 flushed before each."""
+
+    def __init__(self, stream, flush):
+        self.stream, self.flush = stream, flush
+
+    def analyses(self, an, Xd, y, seed, steps, warmup, out, phases=True, counter0=0):
+        import numpy as np
+        import torch
+        for k in range(warmup):
+            an.analyze(Xd, y, seed, counter0 + k, out=out)
+        an.set_phase_timing(phases)
+        tot, solve, iters, refs = [], [], [], []
+        for k in range(steps):
+            self.flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            an.analyze(Xd, y, seed, counter0 + warmup + k, out=out)
+            e1.record(self.stream)
+            torch.cuda.synchronize()
+            tot.append(e0.elapsed_time(e1))
+            if phases:
+                solve.append(an.phase_times()[1])
+            st = an.stats()
+            iters.append(st["iters_max"])
+            refs.append(st["refinements"])
+        an.set_phase_timing(False)
+        return {"ms_per_step": float(np.mean(tot)), "solve_ms": float(np.mean(solve)) if solve else None,
+                "iters": float(np.mean(iters)), "refinements": float(np.mean(refs)), "status": st["status"],
+                "true_relres_max": st["true_relres_max"]}
+
+
+def _err(out, ref):
+    import numpy as np
+    import oracle
+    X = out.double().cpu().numpy()
+    return {"rel_frobenius_vs_fp64_oracle": oracle.rel_frobenius(X, ref),
+            "max_abs_err_over_max_abs": float(np.max(np.abs(X - ref)) / np.max(np.abs(ref)))}
+
+
+KERNEL_NAME = {"fp64": "solve_kernel<double>", "fp32": "solve_kernel<float>",
+               "fp16": "solve_mixed_kernel<half>", "bf16": "solve_mixed_kernel<bf16>"}
+
+
+def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref):
+    """One precision / solver variant on problem p: timing, iterations, accuracy and the
+    roofline of its solve launch."""
+    import torch
+    an = enkf.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8, precondition=pc)
+    out = torch.empty_like(Xd)
+    res = timer.analyses(an, Xd, y, seed, steps, warmup, out)
+    an.analyze(Xd, y, seed, 0, out=out)
+    torch.cuda.synchronize()
+    if ref is not None:
+        res.update(_err(out, ref))
+    res["value"] = 1e3 / res["ms_per_step"]
+    res["unit"] = UNIT
+    res["solver"] = "CG preconditioned by R" if pc else "plain CG"
+    res["roofline"] = analysis_roofline(p.m, p.N, prec, res["iters"], res["refinements"] if prec != "fp64" else 1,
+                                        res["solve_ms"], KERNEL_NAME[prec])
+    an.close()
+    return res
 
 
 def run_ours(args):
@@ -285,6 +481,7 @@ def run_ours(args):
     out = torch.empty_like(Xf)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    timer = Timer(stream, flush)
 
     def barrier():
         torch.cuda.synchronize()
@@ -298,6 +495,7 @@ def run_ours(args):
     if st["status"] != "ok":
         raise SystemExit(f"warm-up analysis failed: {st}")
 
+    # ---- the timed region: K analyses of the headline configuration
     clocks = Clocks(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -320,7 +518,7 @@ def run_ours(args):
     value = _job_rate(args.steps, ms / 1e3, ws)
     last_status = an.stats()
 
-    # end to end through the host-buffer entry point (pinned host memory, copies inside)
+    # ---- end to end through the host-buffer entry point (pinned host memory, copies inside)
     Xh = torch.from_numpy(p.Xf).pin_memory()
     yh = torch.from_numpy(p.y).pin_memory()
     Xo = torch.empty_like(Xh).pin_memory()
@@ -336,45 +534,68 @@ def run_ours(args):
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
            "d2h_bytes_per_step": int(Xo.numel() * 4)}
 
-    # the same FP32 path with plain (unpreconditioned) CG, for reference
-    an_plain = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", tol=1e-8,
-                             precondition=0)
-    an_plain.analyze(Xf, y, seed, 0, out=out)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.fp64_steps):
-        an_plain.analyze(Xf, y, seed, k, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain32_ms = e0.elapsed_time(e1) / args.fp64_steps
-    s_plain = an_plain.stats()
-    an_plain.close()
+    # ---- roofline of the dominant kernel (the persistent CG solve), live CUDA-event time
+    it_avg, ref_avg = float(np.mean(iters)), float(np.mean(refines))
+    solve_avg_ms = float(np.mean(solve_ms))
+    tr = NCU_TRAFFIC.get(args.precision, {})
+    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash(args.precision) else None
+    roofline = analysis_roofline(m, N, args.precision, it_avg, ref_avg, solve_avg_ms,
+                                 KERNEL_NAME[args.precision] + ("<64, preconditioned>" if args.precondition else "<64>"),
+                                 traffic)
+    roofline["fused_pass_model"] = {
+        "bytes_per_launch": it_avg * B_FUSED(m, N) + ref_avg * 56 * m * N,
+        "note": "HA read once per step (36 m N + 4 m) and a double-float refresh of 56 m N bytes: what the "
+                "fused implementation moves at minimum"}
 
-    # plain FP64 GPU CG on the same problem (the comparison point)
-    p64 = synth.workload(WORKLOAD, seed, dtype=np.float64)
-    an64 = enkf.Analysis(n, m, N, p64.rowptr, p64.col, p64.w, p64.r, precision="fp64", tol=1e-8)
-    X64 = torch.from_numpy(p64.Xf).to(dev)
-    o64 = torch.empty_like(X64)
-    an64.analyze(X64, y, seed, 0, out=o64)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.fp64_steps):
-        an64.analyze(X64, y, seed, k, out=o64)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
-    s64 = an64.stats()
-    an64.set_phase_timing(True)                    # the solve kernel alone, for the context leg
-    an64.analyze(X64, y, seed, 0, out=o64)
-    fp64_solve_ms = float(an64.phase_times()[1])
-    an64.set_phase_timing(False)
+    prec_name = {"fp32": "fp32 CG + double-float residual refresh",
+                 "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
+                 "bf16": "BF16 hi/lo tensor-core contractions (tcgen05) + double-float refresh"}[args.precision]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
+            "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8, "precision": prec_name,
+                       "solver": "CG preconditioned by R" if args.precondition else "plain CG",
+                       "l2": "flushed between steps", "status": last_status["status"]},
+            "roofline": roofline, "e2e": e2e,
+            # innovations, (tile images of HA for the tensor-core path,) solve, update
+            "gpu_launches": (3 if args.precision == "fp32" else 4) * args.steps,
+            "clocks": clk}
+    if ws > 1 or args.headline_only:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
-    # the two variants built on one Gram pass over the observation rows, on the same FP32
-    # ensemble, L2 flushed before each timed analysis: CGD-EnKF-Reduced (Algorithm 2 with CG on
-    # the N x N system) and the paper's sEnKF comparator (Algorithm 3: S^{-1} replaced by its
-    # diagonal's inverse, no solve); phases = (Gram pass, N x N stage, update)
+    # ---- everything below: one GPU, after the timed region
+    import oracle
+    E = oracle.obs_perturbations(seed, 0, p.r, N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    an.analyze(Xf, y, seed, 0, out=out)
+    torch.cuda.synchronize()
+    line["error"] = dict(_err(out, ref), true_relres_max=last_status["true_relres_max"])
+    an.close()
+    t_sec = {}
+
+    # C1 variants: the comparison points (plain FP64 CG, the metric's baseline; FP64 CG
+    # preconditioned by R, so that the precision gain is shown apart from the preconditioning
+    # gain), plain FP32 CG, and the tensor-core forms
+    t0 = time.time()
+    X64 = Xf.double()
+    c1 = {}
+    c1["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, args.fp64_steps, 1, ref)
+    c1["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, args.fp64_steps, 1, ref)
+    c1["fp32_plain_cg"] = _variant(enkf, p, "fp32", 0, timer, Xf, y, seed, args.fp64_steps, 1, ref)
+    for prec in ("fp16", "bf16"):
+        c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref)
+    base = c1["fp64_plain_cg"]["ms_per_step"]
+    for k, v in c1.items():
+        v["speedup_vs_fp64_plain_cg"] = base / v["ms_per_step"]
+    line["speedup_vs_fp64_plain_cg"] = value / (1e3 / base)
+    line["speedup_vs_fp64_pcg"] = value / (1e3 / c1["fp64_pcg"]["ms_per_step"])
+    line["c1_variants"] = c1
+
+    # the variants built on one Gram pass over the observation rows (FP32 ensemble)
     def time_variant(an_v):
         an_v.set_phase_timing(True)
         an_v.analyze(Xf, y, seed, 0, out=out)
@@ -393,17 +614,63 @@ def run_ours(args):
     an_r = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", variant="reduced", tol=1e-8)
     reduced_ms, reduced_ph = time_variant(an_r)
     reduced_st = an_r.stats()
+    an_r.analyze(Xf, y, seed, 0, out=out)
+    err_reduced = _err(out, ref)
+    an_r.close()
     an_s = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp32", variant="senkf")
     senkf_ms, senkf_ph = time_variant(an_s)
+    an_s.analyze(Xf, y, seed, 0, out=out)
+    err_senkf = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
+    err_senkf_oracle = oracle.rel_frobenius(
+        out.double().cpu().numpy(), oracle.senkf_alg3(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E))
+    an_s.close()
+    line["reduced_variant"] = {
+        "ms_per_step": reduced_ms, "value": 1e3 / reduced_ms, "unit": UNIT,
+        "phases_ms": dict(zip(("gram", "nxn_cg", "update"), reduced_ph)),
+        "cg_iterations": reduced_st["iters_max"], "status": reduced_st["status"], **err_reduced,
+        "roofline_gram": _gram_roofline(2.0 * m * N * N, reduced_ph[0], m, N),
+        "method": "Algorithm 2 with CG on I + P^T P (N x N), FP32 ensemble, double-float Gram"}
+    line["senkf_comparator"] = {
+        "ms_per_step": senkf_ms, "value": 1e3 / senkf_ms, "unit": UNIT,
+        "phases_ms": dict(zip(("gram", "sum", "update"), senkf_ph)),
+        "rel_frobenius_vs_exact_enkf": err_senkf, "rel_frobenius_vs_oracle_senkf": err_senkf_oracle,
+        "roofline_gram": _gram_roofline(1.0 * m * N * N, senkf_ph[0], m, N),
+        "method": "Algorithm 3 (diagonal inverse of S, no solve), FP32 ensemble, double-float Gram; "
+                  "an approximation of the EnKF analysis"}
+    line["torch_fp64_cg_context"] = _torch_cg_context(enkf, p, X64, y, seed, N, dev, stream)
+    t_sec["c1"] = time.time() - t0
 
-    if rank != 0:
-        return
-    # context only, so that the FP64 comparison point is visibly not a strawman: the same plain
-    # FP64 CG written with PyTorch (cuBLAS DGEMM for the two contractions of every matvec, a
-    # host check of the stopping rule after every step), on the HA and D of that FP64 analysis;
-    # the solve alone is timed
+    for name, fn in (("c2_mixed", section_c2), ("c3_batch", section_c3), ("c4_warm_start", section_c4),
+                     ("c0_l96", section_c0)):
+        if name in args.skip:
+            continue
+        t0 = time.time()
+        line[name] = fn(args, enkf, dev, timer)
+        t_sec[name] = time.time() - t0
+        torch.cuda.empty_cache()
+
+    if not args.no_cpu_baseline:
+        t0 = time.time()
+        line["cpu_baseline"] = cpu_baseline(p, seed)
+        line["cpu_baseline_1core"] = cpu_baseline_one_core(seed)
+        line["cpu_plain_fp64_cg"] = cpu_cg_baseline(p, seed, int(round(c1["fp64_plain_cg"]["iters"])))
+        t_sec["cpu"] = time.time() - t0
+    line["section_wall_s"] = t_sec
+    print(json.dumps(line), flush=True)
+
+
+def _torch_cg_context(enkf, p, X64, y, seed, N, dev, stream):
+    """Context only, so that the FP64 comparison point is visibly not a strawman: the same plain
+    FP64 CG written with PyTorch (cuBLAS DGEMM for the two contractions of every matvec, a
+    host check of the stopping rule after every step), on the HA and D of an FP64 analysis;
+    the solve alone is timed."""
+    import torch
+    an64 = enkf.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp64", tol=1e-8)
+    o64 = torch.empty_like(X64)
+    an64.analyze(X64, y, seed, 0, out=o64)
     HA64, D64, _, _ = an64.intermediates()
-    r64 = torch.from_numpy(p64.r).to(dev)
+    an64.close()
+    r64 = torch.from_numpy(p.r).to(dev)
 
     def torch_cg(tol=1e-8, max_iter=1000):
         Z = torch.zeros_like(D64)
@@ -432,86 +699,38 @@ def run_ours(args):
     _, torch_iters = torch_cg()
     e1.record(stream)
     torch.cuda.synchronize()
-    torch_cg_ms = e0.elapsed_time(e1)
+    return {"solve_ms": e0.elapsed_time(e1), "iters": torch_iters,
+            "note": "plain FP64 CG in PyTorch (cuBLAS DGEMM matvecs), solve only; compare with the solve part "
+                    "of c1_variants.fp64_plain_cg"}
 
-    # accuracy of one timed configuration against the FP64 oracle (exact analysis)
+
+def section_c2(args, enkf, dev, timer):
+    """The mixed-precision workload (1024 x 1024 GRF, length 24, N = 128, m = 262,144,
+    r ~ U[0.25, 1.0], tol 1e-8): BF16 and FP16 tensor-core contractions (split operands, FP32
+    accumulation) with the double-float refresh, FP32, and the FP64 comparison points, each
+    against the exact FP64 oracle analysis."""
+    import numpy as np
+    import torch
     import oracle
-    E = oracle.obs_perturbations(seed, 0, p.r, N)
-    an.analyze(Xf, y, seed, 0, out=out)
+    import synth
+    seed = args.seed
+    p = synth.workload(MIXED_WORKLOAD, seed, dtype=np.float32)
+    E = oracle.obs_perturbations(seed, 0, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
-    err = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
-    an64.analyze(X64, y, seed, 0, out=o64)
-    err64 = oracle.rel_frobenius(o64.cpu().numpy(), ref)
-    an_r.analyze(Xf, y, seed, 0, out=out)
-    err_reduced = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
-    an_r.close()
-    an_s.analyze(Xf, y, seed, 0, out=out)
-    err_senkf = oracle.rel_frobenius(out.double().cpu().numpy(), ref)
-    err_senkf_oracle = oracle.rel_frobenius(
-        out.double().cpu().numpy(),
-        oracle.senkf_alg3(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E))
-    an_s.close()
-
-    # roofline of the dominant kernel (the persistent CG solve)
-    mN = m * N
-    it_avg = float(np.mean(iters))
-    ref_avg = float(np.mean(refines))
-    b_iter = B_ITER(m, N)
-    b_ref = B_REF(m, N)
-    alg_bytes = it_avg * b_iter + ref_avg * b_ref
-    solve_avg_ms = float(np.mean(solve_ms))
-    peak, peak_src = _peaks()
-    achieved = alg_bytes / (solve_avg_ms / 1e3) / 1e9
-    tr = NCU_TRAFFIC.get(args.precision, {})
-    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash(args.precision) else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel<float,64,1>" if args.precision == "fp32" else f"solve_mixed_kernel<{args.precision},64>",
-                "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
-                "launch_ms": solve_avg_ms, "cg_iterations": it_avg, "fp64_refreshes": ref_avg}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
-            "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
-            "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
-                       "precision": {"fp32": "fp32 CG + double-float residual refresh",
-                                     "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
-                                     "bf16": "BF16 hi/lo tensor-core contractions (tcgen05) + double-float refresh"}[args.precision],
-                       "solver": "CG preconditioned by R" if args.precondition else "plain CG",
-                       "l2": "flushed between steps", "status": last_status["status"]},
-            "error": {"rel_frobenius_vs_fp64_oracle": err, "fp64_cg_rel_frobenius": err64,
-                      "true_relres_max": last_status["true_relres_max"]},
-            "torch_fp64_cg_context": {"solve_ms": torch_cg_ms, "iters": torch_iters,
-                                      "note": "plain FP64 CG in PyTorch (cuBLAS DGEMM matvecs), solve only; "
-                                              "compare with the solve part of fp64_cg"},
-            "fp64_cg": {"ms_per_step": fp64_ms, "solve_ms": fp64_solve_ms, "value": 1e3 / fp64_ms, "unit": UNIT,
-                        "iters": s64["iters_max"], "speedup_of_value": value / (ws * 1e3 / fp64_ms),
-                        "solver": "plain CG, FP64 throughout"},
-            "reduced_variant": {"ms_per_step": reduced_ms, "value": 1e3 / reduced_ms, "unit": UNIT,
-                                "phases_ms": dict(zip(("gram", "nxn_cg", "update"), reduced_ph)),
-                                "cg_iterations": reduced_st["iters_max"], "status": reduced_st["status"],
-                                "rel_frobenius_vs_fp64_oracle": err_reduced,
-                                "roofline_gram": _gram_roofline(2.0 * m * N * N, reduced_ph[0]),
-                                "method": "Algorithm 2 with CG on I + P^T P (N x N), FP32 ensemble, "
-                                          "double-float Gram"},
-            "senkf_comparator": {"ms_per_step": senkf_ms, "value": 1e3 / senkf_ms, "unit": UNIT,
-                                 "phases_ms": dict(zip(("gram", "sum", "update"), senkf_ph)),
-                                 "rel_frobenius_vs_exact_enkf": err_senkf,
-                                 "rel_frobenius_vs_oracle_senkf": err_senkf_oracle,
-                                 "roofline_gram": _gram_roofline(1.0 * m * N * N, senkf_ph[0]),
-                                 "method": "Algorithm 3 (diagonal inverse of S, no solve), FP32 ensemble, "
-                                           "double-float Gram; an approximation of the EnKF analysis"},
-            "fp32_plain_cg": {"ms_per_step": plain32_ms, "value": 1e3 / plain32_ms, "unit": UNIT,
-                              "iters": s_plain["iters_max"], "refinements": s_plain["refinements"]},
-            "roofline": roofline,
-            "e2e": e2e,
-            # innovations, (tile images of HA for the tensor-core path,) solve, update
-            "gpu_launches": (3 if args.precision == "fp32" else 4) * args.steps,
-            "clocks": clk}
-    if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, E)
-        line["cpu_baseline_1core"] = cpu_baseline_one_core(seed)
-    print(json.dumps(line), flush=True)
+    Xf = torch.from_numpy(p.Xf).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    res = {"workload": MIXED_WORKLOAD, "n": p.n, "m": p.m, "N": p.N}
+    steps = max(3, min(args.steps, 6))
+    for prec in ("bf16", "fp16", "fp32"):
+        res[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, steps, 2, ref)
+    X64 = Xf.double()
+    res["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, 2, 1, ref)
+    res["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, 1, 1, ref)
+    base = res["fp64_plain_cg"]["ms_per_step"]
+    for k in ("bf16_pcg", "fp16_pcg", "fp32_pcg", "fp64_pcg"):
+        res[k]["speedup_vs_fp64_plain_cg"] = base / res[k]["ms_per_step"]
+        res[k]["speedup_vs_fp64_pcg"] = res["fp64_pcg"]["ms_per_step"] / res[k]["ms_per_step"]
+    return res
 
 
 def _gen_problem(args):
@@ -522,74 +741,52 @@ def _gen_problem(args):
                              sub=1000 + i)
 
 
-def run_batched(args):
-    """256 independent analyses of uneven size (n log-uniform in [4096, 262144], m = n/4,
-    N in {16, 32, 64, 128}, GRF ensembles with correlation length U[4, 32], r ~ U[0.5, 1.5])
-    in one persistent launch replayed from a CUDA graph; FP32 with Jacobi preconditioning,
-    tol 1e-8. value = analyses/s."""
+def _batch_problems(count, seed):
     import multiprocessing as mp
-    import numpy as np
     import synth
-    ws, rank, local = _dist()
-    seed = _rank_seed(args.seed, rank)
-    specs = synth.problems.batched_problem_specs(args.batch_count, seed)
-    t0 = time.time()
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any GPU call
-        probs = pool.map(_gen_problem, [(sp, seed, i) for i, sp in enumerate(specs)])
-    gen_s = time.time() - t0
+    specs = synth.problems.batched_problem_specs(count, seed)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_problem, [(sp, seed, i) for i, sp in enumerate(specs)])
+
+
+def _batch_run(args, enkf, dev, timer, probs, seed, steps, warmup, ws=1, barrier=None):
+    """Tune, time and check one batched launch; returns (value, ms, the section dict)."""
+    import numpy as np
     import torch
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
-    import paper_2606_19224_gb300 as enkf
     ba = enkf.BatchAnalysis([dict(n=p.n, m=p.m, N=p.N, rowptr=p.rowptr, col=p.col, w=p.w, r=p.r) for p in probs],
                             tol=1e-8)
     Xf = [torch.from_numpy(p.Xf).to(dev) for p in probs]
     y = [torch.from_numpy(p.y).to(dev) for p in probs]
     out = [torch.empty_like(x) for x in Xf]
     seeds = [seed + i for i in range(len(probs))]
-    if args.reuse_tuned_plan and os.environ.get("ENKF_TUNE_CACHE"):
+    if getattr(args, "reuse_tuned_plan", False) and os.environ.get("ENKF_TUNE_CACHE"):
         tune_ms = None                     # the plan enkf_batch_create read from the cache file
     else:
         tune_ms = ba.tune(Xf, y, seeds, None, out=out)
     plan = ba.plan()
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    for k in range(args.warmup):
+    stream = timer.stream
+    barrier = barrier or torch.cuda.synchronize
+    for k in range(warmup):
         ba.analyze(Xf, y, seeds, [k] * len(probs), out=out)
     st = ba.stats()
     if np.any(st["status"] != 0):
         raise SystemExit(f"warm-up batch failed: {st['status']}")
-    clocks = Clocks(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters, refs = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
-    for k in range(args.steps):
-        flush.fill_(float(k))
+    for k in range(steps):
+        timer.flush.fill_(float(k))
         ev[k][0].record(stream)
-        ba.analyze(Xf, y, seeds, [args.warmup + k] * len(probs), out=out)
+        ba.analyze(Xf, y, seeds, [warmup + k] * len(probs), out=out)
         ev[k][1].record(stream)
     barrier()
-    clk = clocks.stop()
     st = ba.stats()
-    ms = _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, ws)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
     count = len(probs)
-    value = _job_rate(count * args.steps, ms / 1e3, ws)
     # end to end: pinned host inputs copied in, the batched call, results copied out
     Xh = [torch.from_numpy(p.Xf).pin_memory() for p in probs]
     yh = [torch.from_numpy(p.y).pin_memory() for p in probs]
     Xo = [torch.empty_like(x).pin_memory() for x in Xh]
-    e2e_steps = max(2, args.steps // 4)
+    e2e_steps = max(2, steps // 4)
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -601,12 +798,7 @@ def run_batched(args):
         for a, b in zip(Xo, out):
             a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = _max_over_ranks(time.perf_counter() - t0, dev, ws)
-    e2e = {"value": _job_rate(count * e2e_steps, e2e_s, ws), "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in Xh) + sum(v.numel() * 8 for v in yh)),
-           "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in Xo))}
-    if rank != 0:
-        return
+    e2e_s = time.perf_counter() - t0
     # accuracy: a sample of problems against the exact FP64 analysis
     import oracle
     ba.analyze(Xf, y, seeds, [0] * count, out=out)
@@ -622,104 +814,186 @@ def run_batched(args):
     alg = 0.0
     for i, p in enumerate(probs):
         alg += float(st["iters_max"][i]) * B_ITER(p.m, p.N) + float(st["refinements"][i]) * B_REF(p.m, p.N)
-        alg += 4 * p.n * p.N * 2 + 32 * p.m * p.N   # update (X_f in, X_a out); innovations out (HA, B, D, HA and D double-float)
-    launch_ms = ms / args.steps
+        alg += 4 * p.n * p.N * 2 + 3 * 4 * p.m * p.N   # update (X_f in, X_a out); innovations (HA, D written, X_f rows read)
+    launch_ms = ms / steps
     peak, peak_src = _peaks()
     achieved = alg / (launch_ms / 1e3) / 1e9
     tb = NCU_TRAFFIC_BATCH
-    batch_traffic = (tb["bytes"] if (count == tb["problems"] and args.seed == tb["seed"]
+    batch_traffic = (tb["bytes"] if (count == tb["problems"] and seed == tb["seed"]
                                      and tb["src_sha"] == _src_hash("batch")) else None)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded GRF ensembles, random point observations)",
-            "config": {"workload": BATCH_WORKLOAD, "problems": count,
-                       "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
-                       "sum_mN": int(sum(p.m * p.N for p in probs)), "tol": 1e-8,
-                       "precision": "fp32 CG + double-float refresh, preconditioned by R",
-                       "plan": plan, "tune_ms": tune_ms, "l2": "flushed between steps",
-                       "generation_s": gen_s},
-            "error": {"rel_frobenius_vs_fp64_oracle_max": max(errs), "sampled_problems": len(errs),
-                      "status_ok": int(np.sum(st["status"] == 0))},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": batch_traffic, "kernel": "batch_kernel<128>",
-                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms},
-            "e2e": e2e, "gpu_launches": args.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    sec = {"workload": BATCH_WORKLOAD, "problems": count, "value": count * steps / (ms / 1e3), "unit": UNIT,
+           "ms_per_launch": launch_ms, "steps": steps,
+           "n_range": [min(p.n for p in probs), max(p.n for p in probs)],
+           "sum_mN": int(sum(p.m * p.N for p in probs)), "plan": plan, "tune_ms": tune_ms,
+           "rel_frobenius_vs_fp64_oracle_max": max(errs), "sampled_problems": len(errs),
+           "status_ok": int(np.sum(st["status"] == 0)),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": batch_traffic, "kernel": "batch_kernel<128>",
+                        "peak_source": peak_src, "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms},
+           "e2e": {"value": count * e2e_steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in Xh) + sum(v.numel() * 8 for v in yh)),
+                   "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in Xo))},
+           "gpu_launches": steps}
+    ba.close()
+    return sec, ms
 
 
-def run_mixed(args):
-    """The mixed-precision workload: 1024 x 1024 GRF (length 24), N = 128, m = 262,144,
-    r ~ U[0.25, 1.0], tol 1e-8. One line per run; `value` is the BF16 tensor-core path
-    (split hi/lo operands, FP32 accumulation in TMEM, double-float refresh); FP16, FP32 and
-    FP64 (preconditioned and plain) are timed beside it with their errors against the exact
-    FP64 oracle analysis."""
+def section_c3(args, enkf, dev, timer):
+    """256 analyses of uneven size in one persistent launch replayed from a CUDA graph, plan
+    tuned on the batch."""
+    t0 = time.time()
+    probs = _batch_problems(args.batch_count, args.seed)
+    gen_s = time.time() - t0
+    sec, _ = _batch_run(args, enkf, dev, timer, probs, args.seed, steps=3, warmup=2)
+    sec["generation_s"] = gen_s
+    return sec
+
+
+def section_c4(args, enkf, dev, timer):
+    """Learned warm start on the 512 x 512 workload shapes: train the MLP (1,024-row sketch + N
+    projections -> 3 x 512 GELU -> N) with the library's kernels on pairs from the method's own
+    solves, then time held-out analyses from the zero start and from the learned start."""
+    from paper_2606_19224_gb300 import warm_train
+    cfg = dict(warm_train.FULL)
+    cfg.update(train_seeds=args.warm_train_seeds, draws=8, test_seeds=4, epochs=40)
+    res, _ = warm_train.run(cfg, log=lambda s: None)
+    ev = res["eval"]
+    return {"train_problems": cfg["train_seeds"] * cfg["draws"], "pairs": res["pairs"],
+            "loss_first": res["loss_first"], "loss_last": res["loss_last"],
+            "collect_s": res["collect_s"], "train_s": res["train_s"],
+            "iters_mean_zero": res["iters_mean_zero"], "iters_mean_learned": res["iters_mean_learned"],
+            "ms_zero": res["ms_zero"], "ms_learned": res["ms_learned"],
+            "speedup": res["ms_zero"] / res["ms_learned"],
+            "rel_diff_zero_vs_learned_max": max(r["rel_diff_zero_vs_learned"] for r in ev),
+            "warm_fallbacks": sum(r["learned"]["warm_fallbacks"] for r in ev),
+            "status": [r["learned"]["status"] for r in ev], "held_out_seeds": len(ev)}
+
+
+def section_c0(args, enkf, dev, timer):
+    """Lorenz-96 cycling (n = 40, N = 20, m = 20, R = I, FP64, tol 1e-10): 200 forecast +
+    analysis cycles with the analysis on the GPU and the forecast on the host; the oracle
+    analyses the same forecast each cycle (lockstep error), and the same 200 cycles with the
+    oracle's analysis give the CPU rate."""
     import numpy as np
     import torch
     import oracle
     import synth
+    cycles = 200
+
+    def run(gpu):
+        cyc = synth.L96Cycle(seed=args.seed)
+        an = enkf.Analysis(40, cyc.col.size, 20, cyc.rowptr, cyc.col, cyc.w, cyc.r, precision="fp64",
+                           tol=1e-10) if gpu else None
+        yd = torch.empty(cyc.col.size, dtype=torch.float64, device=dev) if gpu else None
+        Xd = torch.empty((40, 20), dtype=torch.float64, device=dev) if gpu else None
+        err, an_s = 0.0, 0.0
+        t0 = time.perf_counter()
+        for k in range(cycles):
+            cyc.forecast()
+            y = cyc.observe()
+            ta = time.perf_counter()
+            if gpu:
+                Xd.copy_(torch.from_numpy(cyc.ensemble))
+                yd.copy_(torch.from_numpy(y))
+                Xa = an.analyze(Xd, yd, seed=99, counter=k).cpu().numpy()
+            else:
+                Xa = oracle.enkf_alg1(cyc.ensemble, cyc.rowptr, cyc.col, cyc.w, cyc.r, y,
+                                      oracle.obs_perturbations(99, k, cyc.r, 20))
+            an_s += time.perf_counter() - ta
+            if gpu and k % 20 == 0:
+                ref = oracle.enkf_alg1(cyc.ensemble, cyc.rowptr, cyc.col, cyc.w, cyc.r, y,
+                                       oracle.obs_perturbations(99, k, cyc.r, 20))
+                err = max(err, oracle.rel_frobenius(Xa, ref))
+            cyc.ensemble = np.ascontiguousarray(Xa)
+        el = time.perf_counter() - t0
+        rmse = float(np.sqrt(np.mean((cyc.ensemble.mean(axis=1) - cyc.truth) ** 2)))
+        status = an.stats()["status"] if gpu else "ok"
+        return el, an_s, err, rmse, status
+
+    el, an_s, err, rmse, status = run(True)
+    el_c, an_c, _, rmse_c, _ = run(False)
+    return {"cycles": cycles, "cycles_per_s": cycles / el, "analyses_per_s": cycles / an_s,
+            "analysis_ms": 1e3 * an_s / cycles, "rel_frobenius_vs_oracle_max_sampled": err,
+            "final_rmse_vs_truth": rmse, "status": status,
+            "oracle": {"cycles_per_s": cycles / el_c, "analyses_per_s": cycles / an_c, "cores": _cores(),
+                       "final_rmse_vs_truth": rmse_c},
+            "note": "analysis on the GPU (host copies included), forecast (RK4) on the host; the analyses "
+                    "are launch-bound at this size"}
+
+
+def run_batched(args):
+    """The batched workload alone: 256 independent analyses of uneven size (n log-uniform in
+    [4096, 262144], m = n/4, N in {16, 32, 64, 128}, GRF ensembles with correlation length
+    U[4, 32], r ~ U[0.5, 1.5]) in one persistent launch replayed from a CUDA graph; FP32 with
+    Jacobi preconditioning, tol 1e-8. value = analyses/s summed over ranks."""
+    import torch
+    ws, rank, local = _dist()
+    seed = _rank_seed(args.seed, rank)
+    t0 = time.time()
+    probs = _batch_problems(args.batch_count, seed)        # spawn pool, before any GPU call
+    gen_s = time.time() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
     import paper_2606_19224_gb300 as enkf
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    timer = Timer(torch.cuda.current_stream(), flush)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    sec, ms = _batch_run(args, enkf, dev, timer, probs, seed, args.steps, args.warmup, ws, barrier)
+    clk = clocks.stop()
+    ms = _max_over_ranks(ms, dev, ws)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": _job_rate(len(probs) * args.steps, ms / 1e3, ws), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded GRF ensembles, random point observations)",
+            "config": {"workload": BATCH_WORKLOAD, "problems": len(probs), "l2": "flushed between steps",
+                       "generation_s": gen_s},
+            "roofline": sec.pop("roofline"), "e2e": sec.pop("e2e"), "gpu_launches": args.steps,
+            "clocks": clk, "batch": sec}
+    print(json.dumps(line), flush=True)
+
+
+def run_mixed(args):
+    """The mixed-precision workload alone (see section_c2): `value` is the BF16 tensor-core
+    path."""
+    import torch
     ws, rank, local = _dist()
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    seed = _rank_seed(args.seed, rank)
-    p = synth.workload(MIXED_WORKLOAD, seed, dtype=np.float32)
-    n, m, N = p.n, p.m, p.N
-    Xf = torch.from_numpy(p.Xf).to(dev)
-    y = torch.from_numpy(p.y).to(dev)
-    out = torch.empty_like(Xf)
+    import paper_2606_19224_gb300 as enkf
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    E = oracle.obs_perturbations(seed, 0, p.r, N) if rank == 0 else None
-    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E) if rank == 0 else None
-
-    def timed(an, Xd, od, steps, tag):
-        for k in range(args.warmup):
-            an.analyze(Xd, y, seed, k, out=od)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for k in range(steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            an.analyze(Xd, y, seed, k, out=od)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-        st = an.stats()
-        an.analyze(Xd, y, seed, 0, out=od)
-        err = oracle.rel_frobenius(od.double().cpu().numpy(), ref) if rank == 0 else None
-        return {"ms_per_step": ms, "value": 1e3 / ms, "iters": st["iters_max"], "refinements": st["refinements"],
-                "true_relres_max": st["true_relres_max"], "rel_frobenius_vs_fp64_oracle": err,
-                "status": st["status"], "precision": tag}
-
+    timer = Timer(torch.cuda.current_stream(), flush)
     clocks = Clocks(local)
     clocks.start()
-    res = {}
-    for tag, prec in (("bf16", "bf16"), ("fp16", "fp16"), ("fp32", "fp32")):
-        an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8, precondition=1)
-        res[tag] = timed(an, Xf, out, args.steps, tag)
-        an.close()
+    res = section_c2(args, enkf, dev, timer)
     clk = clocks.stop()
-    X64 = Xf.double()
-    o64 = torch.empty_like(X64)
-    for tag, pc in (("fp64_pc", 1), ("fp64", 0)):
-        an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision="fp64", tol=1e-8, precondition=pc)
-        res[tag] = timed(an, X64, o64, args.fp64_steps, tag)
-        an.close()
-    ms = _max_over_ranks(res["bf16"]["ms_per_step"], dev, ws)
+    ms = _max_over_ranks(res["bf16_pcg"]["ms_per_step"], dev, ws)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": _job_rate(1, ms / 1e3, ws), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (seeded 1024x1024 GRF ensemble, random point observations)",
-            "config": {"workload": MIXED_WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8,
+            "config": {"workload": MIXED_WORKLOAD, "n": res["n"], "m": res["m"], "N": res["N"], "tol": 1e-8,
                        "precision": "BF16 hi/lo split operands on tcgen05, FP32 accumulation, double-float refresh",
                        "l2": "flushed between steps"},
-            "variants": res, "gpu_launches": 4 * args.steps, "clocks": clk}
+            "roofline": res["bf16_pcg"]["roofline"], "variants": res, "gpu_launches": 4 * args.steps,
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -732,6 +1006,12 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the timed headline configuration and its end-to-end number")
+    ap.add_argument("--skip", default="", help="comma-separated sections to leave out of the default run: "
+                                               "c2_mixed, c3_batch, c4_warm_start, c0_l96")
+    ap.add_argument("--warm-train-seeds", type=int, default=40,
+                    help="ensembles (x 8 observation draws) the learned warm start trains on in the default run")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="inner-solve precision of the timed path (default workload)")
     ap.add_argument("--batch-count", type=int, default=256,
@@ -743,6 +1023,7 @@ def main():
     ap.add_argument("--precondition", type=int, default=1,
                     help="1: CG preconditioned by R (default, converges in about N steps); 0: plain CG")
     args = ap.parse_args()
+    args.skip = set(x for x in args.skip.split(",") if x)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == BATCH_WORKLOAD:

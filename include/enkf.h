@@ -68,11 +68,12 @@ typedef enum {
 
 typedef enum {
   ENKF_FP64 = 0,        /* FP64 storage and arithmetic throughout (the plain FP64 CG)    */
-  ENKF_FP32 = 1,        /* FP32 CG inner solves + FP64 residual refresh (iterative
-                           refinement) with FP64 scalar recurrences                      */
+  ENKF_FP32 = 1,        /* FP32 CG inner solves + double-float (FP32-pair, about 44-bit)
+                           residual refresh (iterative refinement) with FP64 scalar
+                           recurrences                                                   */
   ENKF_BF16_REFINE = 2, /* BF16 HA contractions on tensor cores (tcgen05), FP32
                            accumulation, FP32 vectors, FP64 scalars; inner solves refined
-                           by an FP32 residual refresh (see refresh_every)              */
+                           by the same double-float residual refresh (see refresh_every) */
   ENKF_FP16_REFINE = 3  /* as ENKF_BF16_REFINE with FP16 HA                              */
 } enkf_precision;
 
@@ -93,9 +94,10 @@ typedef struct enkf_config {
   double tol;             /* stop column j when ||r_j||_2 <= tol * ||d_j||_2             */
   int32_t fixed_iters;    /* > 0: run exactly this many CG steps (the paper's Tables 4-5
                              mode); tol is then ignored                                  */
-  int32_t max_refine;     /* ENKF_FP32: maximum FP64 residual refreshes (default 4)      */
+  int32_t max_refine;     /* FP32 and tensor-core modes: maximum double-float residual
+                             refreshes (default 4)                                       */
   double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
-  int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between FP32 residual
+  int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between double-float residual
                              refreshes; 0 (default): each inner solve runs until its
                              residual fell by inner_tol (at least 2e-2 BF16, 4e-3 FP16)  */
   int32_t perturb_obs;    /* 1: E ~ N(0, R) drawn from (seed, counter); 0: E = 0         */
@@ -118,7 +120,8 @@ typedef struct enkf_stats {
   int32_t status;            /* enkf_status of the last analysis                         */
   int32_t iters_max;         /* max over columns of CG iterations                        */
   int32_t iters_min;         /* min over columns of CG iterations                        */
-  int32_t refinements;       /* FP64 residual refreshes performed                        */
+  int32_t refinements;       /* residual refreshes performed (FP64 in ENKF_FP64 mode,
+                                double-float in the other modes)                         */
   double relres_max;         /* max over columns of the recursive ||r_j|| / ||d_j||      */
   double true_relres_max;    /* max over columns of the FP64 true residual
                                 ||d_j - S z_j|| / ||d_j||; -1 when not computed          */
@@ -127,8 +130,8 @@ typedef struct enkf_stats {
   double warm_relres_max;    /* learned warm start: max over columns of the start's
                                 relative residual ||d_j - S z0_j|| / ||d_j|| (evaluated in
                                 FP32 through the N x N identity below); -1 if off         */
-  double warm_fallbacks;     /* columns whose start was rejected (non-finite or more than
-                                1e3 times the zero start's residual) and began at 0      */
+  double warm_fallbacks;     /* columns whose start was rejected (non-finite, or a true
+                                residual larger than the zero start's) and began at 0    */
   double reserved[2];
 } enkf_stats;
 
@@ -232,9 +235,10 @@ enkf_status enkf_get_solve_phases(enkf_handle h, double* us);
    they are not validated, so the caller guarantees 0 <= col < n and r > 0), and cfg must
    use ENKF_CGD with ENKF_FP64 or ENKF_FP32. All working memory lives in one fixed 16 MiB
    array in the library's device memory (held by every GPU that loads the library until the
-   process exits); problems whose working memory (about 48 m N bytes in FP64 mode, 48 m N in
-   FP32 mode, plus the CG partials) exceeds it are rejected with ENKF_ERR_UNSUPPORTED and a
-   one-line message on stderr. The first call on each device looks up the array's device
+   process exits); problems whose working memory (about 48 m N bytes in FP64 mode, 56 m N in
+   FP32 mode, plus the CG partials) exceeds it are rejected with ENKF_ERR_UNSUPPORTED before
+   anything is enqueued. X_a == X_f is allowed; a partial overlap is ENKF_ERR_INVALID_ARG.
+   The first call on each device looks up the array's device
    address; make that first call before any stream capture. Every call shares the array, so
    calls that may overlap on the GPU (different streams, or different host threads without
    ordering) race and must be serialised by the caller. If out_stats (HOST) is non-NULL the
@@ -360,8 +364,8 @@ enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_
    g_j = HA^T R^{-1} d_j/(N-1). The prediction is decoded into the start
    z0_j = R^{-1}(d_j - HA c_j), whose residual is HA e_j with
    e_j = c_j + (HA^T R^{-1} HA c_j - HA^T R^{-1} d_j)/(N-1) (so no extra pass over S is needed);
-   a column whose start residual is non-finite or more than 1e3 times that of z_j = 0 starts
-   from 0 instead. The refreshes of the solve then measure the true residual as usual. The network: inputs standardised per feature, `layers` hidden layers of
+   a column whose start residual is non-finite or larger than that of z_j = 0 (that is, ||d_j||)
+   starts from 0 instead. The refreshes of the solve then measure the true residual as usual. The network: inputs standardised per feature, `layers` hidden layers of
    width `hidden` with GELU (x Phi(x)), linear output of the standardised c_j/s_j; trained
    with mean squared error and Adam (Kingma & Ba 2015). All of it runs in this library's
    kernels (FP32). */

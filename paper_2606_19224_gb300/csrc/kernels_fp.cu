@@ -4,7 +4,7 @@
 //                  D = y 1^T - Z_obs + E                         (Sec. 2.3, Eq. Zhat_def)
 //   solve_kernel   persistent cooperative CG on S Z = D with S V = HA (HA^T V)/(N-1) + R V
 //                  (Sec. 3.3, Eq. matvec_decomp); N independent recurrences share each
-//                  matvec; FP64 scalars; FP32 mode = FP32 inner solves + FP64 residual
+//                  matvec; FP64 scalars; FP32 mode = FP32 inner solves + double-float residual
 //                  refresh (iterative refinement), all on the device in one launch
 //   update_kernel  X_a = X_f + A W, W = HA^T Z/(N-1), A = X_f - xbar 1^T  (Fig. 2, Alg. 1)
 //

@@ -10,7 +10,6 @@
 //
 // The analysis is the same as enkf_create + enkf_analyze + enkf_get_stats (same kernels,
 // same launch plan), with the observation operator and R passed as device pointers.
-#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -77,6 +76,15 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
     return noalloc_fail(ENKF_ERR_INVALID_ARG, "enkf_analyze_noalloc: tol must be positive");
   if (c.precision == ENKF_FP32 && !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
     return noalloc_fail(ENKF_ERR_INVALID_ARG, "enkf_analyze_noalloc: inner_tol must be in (0, 1)");
+  {
+    // X_a may be X_f itself (in-place) but must not partially overlap it: the update kernel
+    // reads X_f rows while it writes X_a rows
+    const size_t xb = (c.precision == ENKF_FP64 ? 8 : 4) * size_t(c.n) * size_t(c.N);
+    const char* a = static_cast<const char*>(d_Xf);
+    const char* b = static_cast<const char*>(d_Xa);
+    if (a != b && a < b + xb && b < a + xb)
+      return noalloc_fail(ENKF_ERR_INVALID_ARG, "enkf_analyze_noalloc: X_a partially overlaps X_f");
+  }
 
   enkf_handle_s h;
   h.cfg = c;
@@ -95,7 +103,9 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
   struct Part { void** p; size_t bytes; };
   enkf::Workspace& ws = h.ws;
   Part parts[] = {
-      {(void**)&ws.HA64, 8 * mN}, {(void**)&ws.D, 8 * mN}, {(void**)&ws.Z, 8 * mN},
+      // FP64 mode keeps HA and the solution in FP64; FP32 mode keeps them in double-float
+      // only (HA64 and Z stay NULL, so the innovations kernel writes no FP64 HA)
+      {(void**)&ws.HA64, fp64 ? 8 * mN : 0}, {(void**)&ws.D, 8 * mN}, {(void**)&ws.Z, fp64 ? 8 * mN : 0},
       {(void**)&ws.Res, vs * mN}, {(void**)&ws.P, vs * mN}, {(void**)&ws.Sv, vs * mN},
       {(void**)&ws.HA32, fp64 ? 0 : 4 * mN}, {(void**)&ws.B, fp64 ? 0 : vs * mN},
       {(void**)&ws.X, fp64 ? 0 : vs * mN}, {(void**)&ws.r32, fp64 ? 0 : 4 * size_t(c.m)},
@@ -109,13 +119,8 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
   };
   size_t need = 0;
   for (const Part& q : parts) need += align256(q.bytes);
-  if (need > kScratchBytes) {
-    std::fprintf(stderr,
-                 "enkf_analyze_noalloc: this problem needs %zu bytes of working memory; the "
-                 "no-allocation entry point holds %zu bytes (use enkf_create for larger problems)\n",
-                 need, kScratchBytes);
-    return ENKF_ERR_UNSUPPORTED;
-  }
+  if (need > kScratchBytes)   // too large for the fixed array: enkf_create serves it
+    return noalloc_fail(ENKF_ERR_UNSUPPORTED, "enkf_analyze_noalloc: working memory exceeds the fixed array");
   void* base = nullptr;
   e = scratch_address(h.device, &base);
   if (e != cudaSuccess) return noalloc_fail(ENKF_ERR_CUDA, "enkf_analyze_noalloc: cudaGetSymbolAddress");

@@ -4,7 +4,7 @@ backward and Adam). Pairs (features of d_j, target c_j = W e_j / s_j) come from 
 method's own solves on seeded synthetic ensembles; evaluation compares CG iterations and
 analysis time with and without the learned start on held-out seeds.
 
-    python -m paper_2606_19224_gb300.warm_train --out gpurun_out/warm.json
+    python -m paper_2606_19224_gb300.warm_train --out warm_results.json
 
 runs the full-size case (512 x 512 GRF, N = 64, m = 65,536, sketch 1,024, 3 x 512 GELU
 layers, 20,480 training pairs from 320 analyses over 40 ensembles); --small runs a

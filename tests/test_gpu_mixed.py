@@ -54,3 +54,82 @@ def test_mixed_rejects_fixed_iterations(lib):
     p = synth.workload("grf512_N64_m65536", 3, scale=16, dtype=np.float32)
     with pytest.raises(lib.EnKFError):
         lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="bf16", fixed_iters=3)
+
+
+def _check_close(Xa, ref, bar, elem_bar=None):
+    """The relative Frobenius error (Eq. rel_frob) within `bar` and, so that an error confined
+    to one tile of a large problem cannot hide in the norm, the largest entry-wise error
+    relative to the largest entry within `elem_bar` (default `bar`). The FP32 path's X_a is
+    stored in FP32 and its update sums N FP32 products, so its entry-wise errors are not
+    uniform: at 1024^2 / N = 128 the largest is 3.3e-6 of the largest entry while the
+    Frobenius error is 5.2e-7; its entry-wise bar is ten times its Frobenius bar."""
+    err = oracle.rel_frobenius(Xa, ref)
+    emax = float(np.max(np.abs(Xa - ref)) / np.max(np.abs(ref)))
+    eb = bar if elem_bar is None else elem_bar
+    assert err <= bar and emax <= eb, (err, emax)
+    return err, emax
+
+
+# (N, m, grid CTAs): every CTA holds several 128-row tiles (rows per CTA = m / grid), with
+# N <= 64 (double-buffered tile images) and N > 64 (NT = 128), ragged last tiles included
+MULTI = [(37, 8000, 8), (64, 12000, 12), (64, 1024, 4), (100, 6000, 4), (128, 16000, 16), (128, 4100, 5)]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("pc", [0, 1])
+@pytest.mark.parametrize("N,m,G", MULTI)
+def test_split_mixed_several_tiles_per_cta(lib, prec, pc, N, m, G):
+    side = max(64, int(np.ceil(np.sqrt(2 * m))))
+    p = synth.grf_problem(side, 6.0, N, m, 0.25, 1.0, seed=13 * m + N + G, dtype=np.float32)
+    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=pc, grid_blocks=G)
+    assert st["grid_blocks"] == G and (m + G - 1) // G > 128, st
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert st["status"] == "ok", st
+    _check_close(Xa, ref, 1e-4)
+    assert 0 < st["true_relres_max"] <= 1e-8, st
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("N,m,G", [(64, 4096, 4), (128, 4096, 8)])
+def test_single_term_mixed_several_tiles_per_cta(lib, prec, N, m, G):
+    # single low-precision operands on a well-conditioned case (large r), several tiles per CTA
+    p = synth.grf_problem(96, 6.0, N, m, 4.0, 8.0, seed=m + N, dtype=np.float32)
+    an, Xa, st = _run(lib, p, prec, tol=1e-6, precondition=1, lowprec_terms=1, grid_blocks=G)
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert st["status"] == "ok", st
+    _check_close(Xa, ref, 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_full_size_grf512_N64_m65536_tensor_cores(lib, prec):
+    """The 512 x 512 workload (n = 262,144, m = 65,536, N = 64) at full size on the automatic
+    grid (several tiles per CTA), preconditioned as the benchmark runs it."""
+    p = synth.workload("grf512_N64_m65536", 1, dtype=np.float32)
+    an, Xa, st = _run(lib, p, prec, seed=1, counter=0, tol=1e-8, precondition=1)
+    E = oracle.obs_perturbations(1, 0, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert st["status"] == "ok", st
+    _check_close(Xa, ref, 1e-4)
+    assert st["true_relres_max"] <= 1e-8, st
+
+
+@pytest.fixture(scope="module")
+def grf1024():
+    """The mixed-precision workload at full size: 1024 x 1024 GRF (length 24), N = 128,
+    m = 262,144, r ~ U[0.25, 1.0], and the oracle's exact analysis of it (N x N route)."""
+    p = synth.workload("grf1024_N128_m262144", 1, dtype=np.float32)
+    E = oracle.obs_perturbations(1, 0, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    return p, ref
+
+
+@pytest.mark.parametrize("prec,bar,elem_bar", [("bf16", 1e-4, 1e-4), ("fp16", 1e-4, 1e-4), ("fp32", 1e-6, 1e-5)])
+def test_full_size_grf1024_N128_m262144(lib, grf1024, prec, bar, elem_bar):
+    p, ref = grf1024
+    an, Xa, st = _run(lib, p, prec, seed=1, counter=0, tol=1e-8, precondition=1)
+    assert st["status"] == "ok", st
+    _check_close(Xa, ref, bar, elem_bar)
+    assert st["true_relres_max"] <= 1e-8, st
+    an.close()

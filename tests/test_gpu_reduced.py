@@ -79,3 +79,30 @@ def test_reduced_full_size_grf512_N64_m65536(lib, prec):
     err = oracle.rel_frobenius(Xa, ref)
     assert st["status"] == "ok", st
     assert err <= 1e-6, (err, st)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("scale", [1.0, 1e-8, 1e8])
+def test_reduced_fp32_double_float_gram_matches_oracle(lib, k, scale):
+    """The FP32 mode forms G and the right-hand sides from FP32 ensembles with double-float
+    (FP32-pair) product sums. Against the FP64 oracle on the same FP32-rounded ensemble and
+    explicit FP64 perturbations, G and the fixed-k CG iterate V must agree to about 1e-11.
+    Scaling X_f, y and E by s and r by s^2 leaves P = L^{-1} HA, G and V unchanged
+    (Sec. 5.2), so s = 1e-8 and 1e8 (r down to 1e-16 and up to 1e16) check that the FP32
+    exponent range of the pairs neither underflows nor overflows on such inputs."""
+    p = synth.workload("grf512_N64_m65536", 21, scale=8, dtype=np.float32)
+    Xf32 = np.ascontiguousarray((p.Xf.astype(np.float64) * scale).astype(np.float32))
+    r = p.r * scale * scale
+    y = p.y * scale
+    E = oracle.obs_perturbations(7, 3, p.r, p.N) * scale
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, r, precision="fp32", variant="reduced",
+                      fixed_iters=k)
+    Xa = an.analyze_with_E(torch.from_numpy(Xf32).cuda(), torch.from_numpy(y).cuda(),
+                           torch.from_numpy(E).cuda()).double().cpu().numpy()
+    ref, info = oracle.cgd_enkf_reduced(Xf32.astype(np.float64), p.rowptr, p.col, p.w, r, y, E,
+                                        fixed_iters=k)
+    V, G = (t.cpu().numpy() for t in an.intermediates_reduced())
+    assert np.linalg.norm(G - info["G"]) <= 1e-11 * np.linalg.norm(info["G"])
+    assert np.linalg.norm(V - info["V"]) <= 1e-10 * np.linalg.norm(info["V"])
+    # X_a itself is stored in FP32 (unit roundoff 6e-8)
+    assert oracle.rel_frobenius(Xa, ref) <= 1e-6

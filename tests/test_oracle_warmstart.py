@@ -158,3 +158,60 @@ def test_decoded_residual_lies_in_span_of_HA():
 
 def ows_start_residual(HA, D, r, C):
     return ws.start_residual(HA, D, r, C)
+
+
+def _gelu_by_hand(z):
+    """z Phi(z) with Phi written out through math.erf (independent of the oracle's gelu)."""
+    return z * 0.5 * (1.0 + math.erf(z / math.sqrt(2.0)))
+
+
+def _theta(layers, mu_in, sd_in, mu_out, sd_out):
+    """Flat parameter vector in the library's layout from explicit (W, b) pairs."""
+    parts = []
+    for W, b in layers:
+        parts += [np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64)]
+    parts += [np.asarray(v, np.float64) for v in (mu_in, sd_in, mu_out, sd_out)]
+    return np.concatenate(parts)
+
+
+def test_forward_one_hidden_layer_evaluated_by_hand():
+    # 2 inputs with non-trivial standardisation, 2 GELU hidden units, 1 linear output:
+    # a = (x - mu_in)/sd_in = ((3 - 1)/2, (-1 - 2)/0.5) = (1, -6)
+    # z1 = 0.5*1 + 0.25*(-6) + 0.2 = -0.8,  z2 = -1*1 + 0.1*(-6) - 0.3 = -1.9
+    # y_std = 2 gelu(z1) - 3 gelu(z2) + 0.7,  Y = 10 + 4 y_std
+    W1, b1 = [[0.5, 0.25], [-1.0, 0.1]], [0.2, -0.3]
+    W2, b2 = [[2.0, -3.0]], [0.7]
+    theta = _theta([(W1, b1), (W2, b2)], [1.0, 2.0], [2.0, 0.5], [10.0], [4.0])
+    assert theta.size == ws.param_count(2, 2, 1, 1)
+    y_std = 2.0 * _gelu_by_hand(-0.8) - 3.0 * _gelu_by_hand(-1.9) + 0.7
+    expect = 10.0 + 4.0 * y_std
+    Y = ws.forward(theta, (2, 2, 1, 1), np.array([[3.0, -1.0]]))
+    assert Y.shape == (1, 1)
+    assert abs(Y[0, 0] - expect) <= 1e-14 * abs(expect)
+    # the slips this must catch give other values: GELU on the output layer, sd multiplied
+    # instead of divided, the output scale and shift swapped
+    wrong = [10.0 + 4.0 * _gelu_by_hand(y_std),
+             10.0 + 4.0 * (2.0 * _gelu_by_hand(0.5 * 4 + 0.25 * -1.5 + 0.2)
+                           - 3.0 * _gelu_by_hand(-1.0 * 4 + 0.1 * -1.5 - 0.3) + 0.7),
+             4.0 + 10.0 * y_std]
+    assert all(abs(Y[0, 0] - v) > 1e-3 for v in wrong)
+
+
+def test_forward_two_hidden_layers_evaluated_by_hand():
+    # two hidden layers of width 2 (order matters: W1 then W2), x = (0.5, 4), mu_in = (-0.5, 2),
+    # sd_in = (0.25, 4): a = (4, 0.5)
+    W1, b1 = [[0.3, -0.2], [0.1, 0.4]], [0.0, -1.0]
+    W2, b2 = [[1.5, -0.5], [-2.0, 1.0]], [0.1, 0.2]
+    W3, b3 = [[0.75, -1.25]], [-0.05]
+    theta = _theta([(W1, b1), (W2, b2), (W3, b3)], [-0.5, 2.0], [0.25, 4.0], [-3.0], [0.5])
+    a = (4.0, 0.5)
+    h1 = [_gelu_by_hand(0.3 * a[0] - 0.2 * a[1] + 0.0), _gelu_by_hand(0.1 * a[0] + 0.4 * a[1] - 1.0)]
+    h2 = [_gelu_by_hand(1.5 * h1[0] - 0.5 * h1[1] + 0.1), _gelu_by_hand(-2.0 * h1[0] + 1.0 * h1[1] + 0.2)]
+    expect = -3.0 + 0.5 * (0.75 * h2[0] - 1.25 * h2[1] - 0.05)
+    Y = ws.forward(theta, (2, 2, 2, 1), np.array([[0.5, 4.0]]))
+    assert abs(Y[0, 0] - expect) <= 1e-14 * abs(expect)
+    # the hidden layers applied in the other order give another value
+    g1 = [_gelu_by_hand(1.5 * a[0] - 0.5 * a[1] + 0.1), _gelu_by_hand(-2.0 * a[0] + 1.0 * a[1] + 0.2)]
+    g2 = [_gelu_by_hand(0.3 * g1[0] - 0.2 * g1[1]), _gelu_by_hand(0.1 * g1[0] + 0.4 * g1[1] - 1.0)]
+    swapped = -3.0 + 0.5 * (0.75 * g2[0] - 1.25 * g2[1] - 0.05)
+    assert abs(Y[0, 0] - swapped) > 1e-3

@@ -1,4 +1,5 @@
-"""The allocation-free entry point (enkf_analyze_noalloc) against the handle-based one.
+"""The allocation-free entry point (enkf_analyze_noalloc) against the handle-based one and
+against the FP64 oracle's exact analysis.
 
 Some callers of this library cannot allocate device memory when they run an analysis
 (inside a CUDA-graph capture, under an application-owned memory pool, in a real-time loop
@@ -29,8 +30,27 @@ def test_noalloc_matches_handle_path_on_two_consecutive_calls(lib, prec):
         ref = an.analyze(Xf, y, seed=9, counter=counter).double().cpu().numpy()
         Xa, st = lib.analyze_noalloc(cfg, *dev, Xf, y, seed=9, counter=counter)
         assert st["status"] == "ok", (call, st)
-        err = oracle.rel_frobenius(Xa.double().cpu().numpy(), ref)
+        Xa = Xa.double().cpu().numpy()
+        err = oracle.rel_frobenius(Xa, ref)
         assert err <= 1e-6, (call, err)      # the suite's parity bar; same kernels, so ~0
+        # and against the oracle's exact FP64 analysis of the same inputs, so that a fault
+        # shared by both entry points cannot pass
+        E = oracle.obs_perturbations(9, counter, p.r, p.N)
+        exact = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+        err_o = oracle.rel_frobenius(Xa, exact)
+        assert err_o <= 1e-6, (call, err_o)
+
+
+def test_noalloc_rejects_partial_overlap(lib):
+    p = synth.workload("grf512_N64_m65536", 79, scale=8, dtype=np.float32)
+    cfg = lib.default_config(p.n, p.m, p.N, precision="fp32")
+    dev = [torch.from_numpy(a).cuda() for a in (p.rowptr, p.col, p.w, p.r)]
+    buf = torch.empty(2 * p.n * p.N, dtype=torch.float32, device="cuda")
+    Xf = buf[: p.n * p.N].view(p.n, p.N)
+    Xf.copy_(torch.from_numpy(p.Xf))
+    Xa = buf[p.N: p.N + p.n * p.N].view(p.n, p.N)        # shifted by one row: partial overlap
+    _, st = lib.analyze_noalloc(cfg, *dev, Xf, torch.from_numpy(p.y).cuda(), out=Xa)
+    assert st["status"] == "invalid_arg"
 
 
 def test_noalloc_rejects_problems_beyond_its_fixed_memory(lib):
