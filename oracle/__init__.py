@@ -15,11 +15,13 @@ Prop. 1, the single-observation scalar case, brute force, and Philox known-answe
 from .philox import philox4x32_10, uniform53_pair, obs_perturbations
 from .enkf import (
     apply_H, ensemble_stats, innovations, enkf_alg1, enkf_alg2, enkf_exact, cgd_enkf,
-    cgd_enkf_reduced, senkf_alg3, kalman_analysis, rel_frobenius, S_matvec,
+    cgd_enkf_reduced, senkf_alg3, kalman_analysis, rel_frobenius, S_matvec, R_apply, R_dense,
+    tridiag_cholesky, L_solve, L_apply,
 )
 
 __all__ = [
     "philox4x32_10", "uniform53_pair", "obs_perturbations", "apply_H", "ensemble_stats",
     "innovations", "enkf_alg1", "enkf_alg2", "enkf_exact", "cgd_enkf", "cgd_enkf_reduced",
-    "senkf_alg3", "kalman_analysis", "rel_frobenius", "S_matvec",
+    "senkf_alg3", "kalman_analysis", "rel_frobenius", "S_matvec", "R_apply", "R_dense",
+    "tridiag_cholesky", "L_solve", "L_apply",
 ]

@@ -47,8 +47,10 @@ def uniform53_pair(w0, w1, w2, w3):
     return u1, u2
 
 
-def obs_perturbations(seed: int, counter: int, r: np.ndarray, N: int) -> np.ndarray:
-    """E (m, N) with column j ~ N(0, diag(r)), drawn as defined in the module docstring."""
+def obs_perturbations(seed: int, counter: int, r: np.ndarray, N: int, r_off=None) -> np.ndarray:
+    """E (m, N) with column j ~ N(0, R), drawn as defined in the module docstring: the
+    standard normals xi scaled by sqrt(r) (diagonal R), or E = L xi with L the bidiagonal
+    Cholesky factor of a tridiagonal R (diagonal r, off-diagonal r_off)."""
     m = r.shape[0]
     i = np.arange(m, dtype=np.uint64)[:, None]
     q = np.arange((N + 1) // 2, dtype=np.uint64)[None, :]
@@ -60,4 +62,7 @@ def obs_perturbations(seed: int, counter: int, r: np.ndarray, N: int) -> np.ndar
     xi = np.empty((m, 2 * q.shape[1]))
     xi[:, 0::2] = rho * np.cos(theta)
     xi[:, 1::2] = rho * np.sin(theta)
-    return np.sqrt(r)[:, None] * xi[:, :N]
+    if r_off is None:
+        return np.sqrt(r)[:, None] * xi[:, :N]
+    from .enkf import L_apply
+    return L_apply(r, r_off, xi[:, :N])

@@ -24,11 +24,12 @@ from .problems import (
     batched_problems,
     L96Cycle,
     WORKLOADS,
+    l96_tridiag_problem,
 )
 
 __all__ = [
     "grf_fields", "periodic_sqexp_eigenvalues", "l96_tendency", "l96_rk4", "Problem",
     "subsample_operator", "identity_operator", "every_kth_operator", "obs_variances",
     "grf_problem", "workload", "batched_problem_specs", "batched_problems", "L96Cycle",
-    "WORKLOADS",
+    "WORKLOADS", "l96_tridiag_problem",
 ]

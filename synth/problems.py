@@ -33,6 +33,7 @@ class Problem:
     y: np.ndarray             # (m,) float64
     truth: np.ndarray = None  # (n,) float64
     meta: dict = field(default_factory=dict)
+    r_off: np.ndarray = None  # (m-1,) float64: off-diagonal of a tridiagonal R, None = diagonal
 
     @property
     def n(self):
@@ -107,6 +108,47 @@ def workload(name: str, seed: int, scale: int = 1, dtype=np.float64, sub: int = 
     m = c["m"] // (scale * scale)
     return grf_problem(side, c["ell"] / scale, c["N"], m, c["r"][0], c["r"][1], seed,
                        dtype=dtype, sub=sub, meta=dict(name=name, scale=scale, tol=c["tol"]))
+
+
+def _tridiag_noise(sig2, off, rng, m):
+    """A draw of N(0, R) for the symmetric tridiagonal Toeplitz R (diagonal sig2, off-diagonal
+    off): v = C xi with C the lower bidiagonal factor of R (C C^T = R), from its recurrence."""
+    xi = rng.standard_normal(m)
+    v = np.empty(m)
+    c_prev = math.sqrt(sig2)
+    v[0] = c_prev * xi[0]
+    for i in range(1, m):
+        b = off / c_prev
+        c = math.sqrt(sig2 - b * b)
+        v[i] = c * xi[i] + b * xi[i - 1]
+        c_prev = c
+    return v
+
+
+def l96_tridiag_problem(p: int, N: int, seed: int, sigma: float = 0.3, rho: float = 0.2,
+                        dt: float = 0.01, spinup: int = 20, model_noise: float = 0.0,
+                        dtype=np.float64) -> Problem:
+    """The Lorenz-96 workload with correlated observation noise: state dimension p, H = I
+    (m = p), R tridiagonal Toeplitz with diagonal sigma^2 and off-diagonals sigma^2 rho.
+    Truth x0 ~ N(0, I) integrated `spinup` RK4 steps of dt; initial ensemble = truth + 0.1
+    N(0, I); one forecast step (RK4, dt) of every member plus model noise of standard
+    deviation `model_noise` (0 by default: the analysis errors the paper prints for this
+    workload are reproduced without it); the truth advanced by the same step; y = truth + v,
+    v ~ N(0, R)."""
+    truth = _rng(seed, STREAM_TRUTH).standard_normal(p)
+    truth = l96_rk4(truth, dt, spinup)
+    Xa0 = truth[:, None] + 0.1 * _rng(seed, STREAM_ENSEMBLE).standard_normal((p, N))
+    Xf = l96_rk4(Xa0, dt, 1)
+    if model_noise:
+        Xf = Xf + model_noise * _rng(seed, STREAM_ENSEMBLE, 1).standard_normal((p, N))
+    truth = l96_rk4(truth, dt, 1)
+    rowptr, col, w = identity_operator(p)
+    sig2 = sigma * sigma
+    r = np.full(p, sig2)
+    r_off = np.full(p - 1, sig2 * rho)
+    y = truth + _tridiag_noise(sig2, sig2 * rho, _rng(seed, STREAM_OBSNOISE), p)
+    return Problem(np.ascontiguousarray(Xf.astype(dtype)), rowptr, col, w, r, y, truth,
+                   dict(sigma=sigma, rho=rho, dt=dt, spinup=spinup, model_noise=model_noise), r_off)
 
 
 def batched_problem_specs(count: int, seed: int, n_lo: int = 4096, n_hi: int = 262144,
