@@ -154,6 +154,24 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
                         const double* h_w, const double* r_diag, void* cuda_stream,
                         enkf_handle* out);
 
+/* As enkf_create with a symmetric tridiagonal R (the observation-noise model of the paper's
+   Example 2, Sec. 6.2, whose factorisation costs are discussed in Sec. 5.3): R_ii = r_diag[i]
+   and R_{i,i+1} = R_{i+1,i} = r_off[i] (HOST, m - 1 entries, finite; NULL only when m = 1).
+   R must be positive definite (ENKF_ERR_INVALID_ARG otherwise, checked through its banded
+   Cholesky factor R = L L^T, L lower bidiagonal). ENKF_CGD_REDUCED and ENKF_CGD with
+   precondition = 1 (CG preconditioned by R) analyse the whitened problem X' = L^{-1} HA,
+   y' = L^{-1}(y - zbar), E' = L^{-1} E with H' = I and R' = I, which is exactly Algorithm 2
+   (P = L_N^{-1} HA) and CG on L^{-1} S L^{-T}; the update uses the caller's X_f, and the
+   perturbations drawn in an analysis are E = L xi (xi the same standard normals as with a
+   diagonal R). The stopping rule, the reported residuals and enkf_copy_intermediates
+   (HA, D, Z) are those of the whitened system (Z' = L^T Z; W is unchanged). ENKF_SENKF uses
+   only the diagonal of R (Algorithm 3). ENKF_CGD with precondition = 0 is
+   ENKF_ERR_UNSUPPORTED with a tridiagonal R. Allocates about 24 m N bytes more than
+   enkf_create (the whitened rows and their scan buffers). */
+enkf_status enkf_create_tridiag(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                                const double* h_w, const double* r_diag, const double* r_off,
+                                void* cuda_stream, enkf_handle* out);
+
 /* One analysis on the handle's stream. d_Xf: device [n][N] (FP64 in ENKF_FP64 mode, FP32
    otherwise); d_y: device [m] FP64; (seed, counter) select the Philox4x32-10 stream of the
    perturbations E when cfg.perturb_obs = 1 (element (i, j) uses counter

@@ -23,7 +23,7 @@ EXPORTS = (
     "enkf_config_default", "enkf_create", "enkf_analyze", "enkf_analyze_with_E",
     "enkf_analyze_host", "enkf_get_stats", "enkf_get_column_stats", "enkf_copy_intermediates",
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
-    "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc",
+    "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc", "enkf_create_tridiag",
     "enkf_get_solve_phases", "enkf_batch_create", "enkf_batch_analyze", "enkf_batch_tune",
     "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan", "enkf_batch_set_phase_timing",
     "enkf_batch_get_times", "enkf_selftest_wait_timeout",
@@ -85,6 +85,7 @@ def load(path: str = None):
     sig = {
         "enkf_config_default": (i32, [ctypes.POINTER(Config), i64, i64, i32]),
         "enkf_create": (i32, [ctypes.POINTER(Config), vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "enkf_create_tridiag": (i32, [ctypes.POINTER(Config), vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
         "enkf_analyze": (i32, [vp, vp, dp, u64, u64, vp]),
         "enkf_analyze_with_E": (i32, [vp, vp, dp, dp, vp]),
         "enkf_analyze_host": (i32, [vp, vp, dp, u64, u64, vp]),
@@ -162,7 +163,9 @@ class Analysis:
     """One problem shape (n, m, N, H, R) bound to a stream. Wraps enkf_create / enkf_destroy;
     analyze* enqueue one analysis step on the stream."""
 
-    def __init__(self, n, m, N, rowptr, col, w, r, stream=None, **config):
+    def __init__(self, n, m, N, rowptr, col, w, r, stream=None, r_off=None, **config):
+        """r: the diagonal of R; r_off (optional, m - 1 entries): the off-diagonal of a
+        symmetric tridiagonal R (enkf_create_tridiag)."""
         import numpy as np
         import torch
         if not torch.cuda.is_available():
@@ -175,9 +178,15 @@ class Analysis:
         self._r = np.ascontiguousarray(r, dtype=np.float64)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
-        st = lib.enkf_create(ctypes.byref(self.cfg), self._rowptr.ctypes.data, self._col.ctypes.data,
-                             self._w.ctypes.data, self._r.ctypes.data,
-                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if r_off is None:
+            st = lib.enkf_create(ctypes.byref(self.cfg), self._rowptr.ctypes.data, self._col.ctypes.data,
+                                 self._w.ctypes.data, self._r.ctypes.data,
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        else:
+            self._r_off = np.ascontiguousarray(r_off, dtype=np.float64)
+            st = lib.enkf_create_tridiag(ctypes.byref(self.cfg), self._rowptr.ctypes.data, self._col.ctypes.data,
+                                         self._w.ctypes.data, self._r.ctypes.data, self._r_off.ctypes.data,
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         _check(st, None)
         self.h = h
         self.n, self.m, self.N = n, m, N

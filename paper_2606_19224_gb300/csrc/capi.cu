@@ -30,7 +30,9 @@ enkf_status cuda_fail(enkf_handle_s* h, cudaError_t e, const char* what) {
 void free_workspace(Workspace& ws) {
   void* ptrs[] = {ws.rowptr, ws.col, ws.w, ws.r, ws.r32, ws.HA64, ws.HA32, ws.HA16, ws.HAdf, ws.Ddf, ws.Zdf, ws.D, ws.Z, ws.B, ws.X,
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
-                  ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y};
+                  ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y,
+                  ws.Hrowptr, ws.Hcol, ws.Hw, ws.wa, ws.wb, ws.wcp, ws.wmu, ws.wU, ws.wV, ws.wcarry,
+                  ws.wcarryV, ws.Xw, ws.yw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace{};
@@ -138,9 +140,9 @@ const char* enkf_last_error(enkf_handle h) {
   return h ? h->last_error.c_str() : g_create_error.c_str();
 }
 
-enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
-                        const double* h_w, const double* r_diag, void* cuda_stream,
-                        enkf_handle* out) {
+static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                               const double* h_w, const double* r_diag, const double* r_off,
+                               void* cuda_stream, enkf_handle* out) {
   if (out) *out = nullptr;
   if (!cfg || !out || !h_rowptr || !r_diag)
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: NULL argument");
@@ -150,12 +152,26 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
     const enkf_status cs = check_problem(c, h_rowptr, h_col, h_w, r_diag, msg);
     if (cs != ENKF_OK) return fail(nullptr, cs, "enkf_create: " + msg);
   }
+  // tridiagonal R: the sEnKF comparator uses only the diagonal of R (Algorithm 3); the other
+  // forms analyse the whitened problem (kernels_whiten.cu)
+  const bool tri = r_off != nullptr && c.variant != ENKF_SENKF && c.m > 1;
+  std::vector<double> wa, wb, wcp, wmu;
+  if (tri) {
+    for (int64_t i = 0; i + 1 < c.m; ++i)
+      if (!std::isfinite(r_off[i])) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: non-finite r_off");
+    if (c.variant == ENKF_CGD && c.precondition != 1)
+      return fail(nullptr, ENKF_ERR_UNSUPPORTED,
+                  "enkf_create: a tridiagonal R needs precondition = 1 in ENKF_CGD (CG preconditioned by R)");
+    if (!enkf::whiten_coefficients(c.m, r_diag, r_off, wa, wb, wcp, wmu))
+      return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create: R is not positive definite");
+  }
   const bool mixed = c.precision == ENKF_BF16_REFINE || c.precision == ENKF_FP16_REFINE;
-  const int64_t nnz = h_rowptr[c.m];
+  const int64_t nnz = tri ? c.m : h_rowptr[c.m];
   auto* h = new enkf_handle_s();
   h->cfg = c;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->nnz = nnz;
+  h->tri = tri;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = mixed ? enkf::plan_solve_mixed(h) : enkf::plan_solve(h);
@@ -213,6 +229,23 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
     allocs.push_back({(void**)&ws.Zdf, 8 * (size_t)mN});
   }
   if (mixed) allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
+  const int64_t hnnz = h_rowptr[c.m];
+  const int64_t nblk = enkf::whiten_blocks(c.m);
+  if (tri) {
+    allocs.push_back({(void**)&ws.Hrowptr, sizeof(int32_t) * (c.m + 1)});
+    allocs.push_back({(void**)&ws.Hcol, sizeof(int32_t) * (size_t)std::max<int64_t>(hnnz, 1)});
+    allocs.push_back({(void**)&ws.Hw, sizeof(double) * (size_t)std::max<int64_t>(hnnz, 1)});
+    allocs.push_back({(void**)&ws.wa, sizeof(double) * c.m});
+    allocs.push_back({(void**)&ws.wb, sizeof(double) * c.m});
+    allocs.push_back({(void**)&ws.wcp, sizeof(double) * c.m});
+    allocs.push_back({(void**)&ws.wmu, sizeof(double) * nblk});
+    allocs.push_back({(void**)&ws.wU, sizeof(double) * c.m * (c.N + 1)});
+    allocs.push_back({(void**)&ws.wV, sizeof(double) * mN});
+    allocs.push_back({(void**)&ws.wcarry, sizeof(double) * nblk * (c.N + 1)});
+    allocs.push_back({(void**)&ws.wcarryV, sizeof(double) * nblk * c.N});
+    allocs.push_back({(void**)&ws.Xw, vs * mN});
+    allocs.push_back({(void**)&ws.yw, sizeof(double) * c.m});
+  }
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -221,10 +254,28 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
       return cuda_fail(nullptr, e, "enkf_create: cudaMalloc");
     }
   }
-  e = cudaMemcpy(ws.rowptr, h_rowptr, sizeof(int32_t) * (c.m + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.col, h_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.w, h_w, sizeof(double) * nnz, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(ws.r, r_diag, sizeof(double) * c.m, cudaMemcpyHostToDevice);
+  if (!tri) {
+    e = cudaMemcpy(ws.rowptr, h_rowptr, sizeof(int32_t) * (c.m + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.col, h_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(ws.w, h_w, sizeof(double) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.r, r_diag, sizeof(double) * c.m, cudaMemcpyHostToDevice);
+  } else {
+    // the whitened problem: H' = I, r' = 1; the caller's H for the whitening pass
+    std::vector<int32_t> idx(c.m + 1);
+    for (int64_t i = 0; i <= c.m; ++i) idx[i] = (int32_t)i;
+    const std::vector<double> ones(c.m, 1.0);
+    e = cudaMemcpy(ws.rowptr, idx.data(), sizeof(int32_t) * (c.m + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.col, idx.data(), sizeof(int32_t) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.w, ones.data(), sizeof(double) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.r, ones.data(), sizeof(double) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.Hrowptr, h_rowptr, sizeof(int32_t) * (c.m + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && hnnz > 0) e = cudaMemcpy(ws.Hcol, h_col, sizeof(int32_t) * hnnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && hnnz > 0) e = cudaMemcpy(ws.Hw, h_w, sizeof(double) * hnnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.wa, wa.data(), sizeof(double) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.wb, wb.data(), sizeof(double) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.wcp, wcp.data(), sizeof(double) * c.m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.wmu, wmu.data(), sizeof(double) * nblk, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(ws.status, 0, sizeof(int32_t) * 4);
   if (e == cudaSuccess && ws.HA16) e = cudaMemset(ws.HA16, 0, enkf::mixed_image_bytes(h));
   if (e == cudaSuccess) e = cudaMemset(ws.bar, 0, sizeof(unsigned) * 4);
@@ -237,6 +288,20 @@ enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const i
   }
   *out = h;
   return ENKF_OK;
+}
+
+enkf_status enkf_create(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                        const double* h_w, const double* r_diag, void* cuda_stream,
+                        enkf_handle* out) {
+  return create_impl(cfg, h_rowptr, h_col, h_w, r_diag, nullptr, cuda_stream, out);
+}
+
+enkf_status enkf_create_tridiag(const enkf_config* cfg, const int32_t* h_rowptr, const int32_t* h_col,
+                                const double* h_w, const double* r_diag, const double* r_off,
+                                void* cuda_stream, enkf_handle* out) {
+  if (cfg && cfg->m > 1 && !r_off)
+    return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_create_tridiag: NULL r_off");
+  return create_impl(cfg, h_rowptr, h_col, h_w, r_diag, r_off, cuda_stream, out);
 }
 
 static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d_y,
@@ -258,9 +323,21 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
   if (h->timing) e = cudaEventRecord(h->ev[0], h->stream);
   if (c.warm_start && !enkf::warm_ready(h))
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: warm_start = 1 but no model attached (enkf_set_warm_model)");
+  // tridiagonal R: the observation rows are whitened first and the analysis runs on the
+  // whitened problem (H' = I, r' = 1); the update below still uses the caller's X_f
+  const void* Xin = d_Xf;
+  const double* yin = d_y;
+  const double* Ein = d_E;
+  if (h->tri && e == cudaSuccess) {
+    e = enkf::launch_whiten(h, d_Xf, d_y, emode == 1 ? d_E : nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze: whitening launch");
+    Xin = h->ws.Xw;
+    yin = h->ws.yw;
+    Ein = emode == 1 ? h->ws.wV : nullptr;
+  }
   if (e == cudaSuccess)
-    e = gram ? enkf::launch_gram_stage(h, d_Xf, d_y, d_E, emode, seed, counter)
-             : enkf::launch_innovations(h, d_Xf, d_y, d_E, emode, seed, counter);
+    e = gram ? enkf::launch_gram_stage(h, Xin, yin, Ein, emode, seed, counter)
+             : enkf::launch_innovations(h, Xin, yin, Ein, emode, seed, counter);
   if (e != cudaSuccess) return cuda_fail(h, e, gram ? "analyze: Gram pass launch" : "analyze: innovations launch");
   if (c.warm_start) {
     e = enkf::warm_prepare(h);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "enkf.h"
 
@@ -148,6 +149,21 @@ struct Workspace {
   void* stage_Xf = nullptr;     // host-API staging [n][N]
   double* stage_y = nullptr;    // [m]
   unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
+  // tridiagonal R (kernels_whiten.cu): the caller's H, the whitening scan's coefficients and
+  // buffers; rowptr / col / w / r above then hold H' = I and r' = 1 of the whitened problem
+  int32_t* Hrowptr = nullptr;   // [m+1]
+  int32_t* Hcol = nullptr;      // [nnz]
+  double* Hw = nullptr;         // [nnz]
+  double* wa = nullptr;         // [m]   1 / L_ii
+  double* wb = nullptr;         // [m]   -L_{i,i-1} / L_ii
+  double* wcp = nullptr;        // [m]   product of wb over the scan block up to row i
+  double* wmu = nullptr;        // [blocks] product of wb over each scan block
+  double* wU = nullptr;         // [m][N+1] anomalies and y - zbar, whitened in place
+  double* wV = nullptr;         // [m][N]  explicit perturbations, whitened in place
+  double* wcarry = nullptr;     // [blocks][N+1]
+  double* wcarryV = nullptr;    // [blocks][N]
+  void* Xw = nullptr;           // [m][N]  whitened observed ensemble (FP64 or FP32)
+  double* yw = nullptr;         // [m]     whitened y - zbar
 };
 
 struct BatchState;   // kernels_batch.cu: plan, arena and graph of a batched handle
@@ -177,6 +193,7 @@ struct enkf_handle_s {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   enkf::BatchState* batch = nullptr;   // non-NULL for a handle made by enkf_batch_create
   enkf::WarmState* warm = nullptr;     // learned warm start (enkf_set_warm_model / enkf_warm_features)
+  bool tri = false;                    // tridiagonal R: analyses run on the whitened problem
 };
 
 namespace enkf {
@@ -246,4 +263,9 @@ cudaError_t mlp_standardize(const enkf_mlp_shape* s, float* P, const float* X, c
                             cudaStream_t st);
 cudaError_t launch_draw_perturbations(uint64_t seed, uint64_t counter, const double* r,
                                       int64_t m, int N, double* E, cudaStream_t s);
+// kernels_whiten.cu: tridiagonal R through the whitened problem
+bool whiten_coefficients(int64_t m, const double* r, const double* r_off, std::vector<double>& a,
+                         std::vector<double>& b, std::vector<double>& cp, std::vector<double>& mu);
+int64_t whiten_blocks(int64_t m);
+cudaError_t launch_whiten(enkf_handle_s* h, const void* Xf, const double* y, const double* E);
 }  // namespace enkf

@@ -102,3 +102,29 @@ def test_selftest_rejects_bad_arguments_without_a_gpu():
     lib = enkf.load()
     for which, ms in ((2, 50.0), (0, 0.0), (1, 2e4)):
         assert enkf.STATUS[lib.enkf_selftest_wait_timeout(which, ms, None)] == "invalid_arg"
+
+
+@pytest.mark.parametrize("case", ["null_off", "indefinite", "plain_cg", "nonfinite"])
+def test_create_tridiag_rejects_bad_arguments_before_touching_the_gpu(case):
+    n, m, N = 10, 4, 5
+    rowptr = np.arange(m + 1, dtype=np.int32)
+    col = np.arange(m, dtype=np.int32)
+    w = np.ones(m)
+    r = np.ones(m)
+    off = np.full(m - 1, 0.2)
+    cfg = enkf.default_config(n, m, N, precondition=1)
+    expect = 1
+    if case == "null_off":
+        off = None
+    elif case == "indefinite":
+        off[:] = 0.9          # eigenvalues 1 + 1.8 cos(k pi / 5): the smallest is negative
+    elif case == "plain_cg":
+        cfg.precondition = 0
+        expect = 8
+    elif case == "nonfinite":
+        off[1] = np.nan
+    h = ctypes.c_void_p()
+    lib = enkf.load()
+    st = lib.enkf_create_tridiag(ctypes.byref(cfg), rowptr.ctypes.data, col.ctypes.data, w.ctypes.data,
+                                 r.ctypes.data, None if off is None else off.ctypes.data, None, ctypes.byref(h))
+    assert st == expect and not h.value, (case, st, lib.enkf_last_error(None))
