@@ -21,6 +21,7 @@ timed region, every other configuration of the method as keys of the same line:
   c3_batch         256 uneven analyses in one persistent launch (tuned plan, CUDA graph)
   c4_warm_start    the learned CG warm start, trained here, on held-out problems
   c0_l96           200 Lorenz-96 forecast + analysis cycles
+  e2b_table5       Example 2b: L96, H = I, N = 100, tridiagonal R, p up to 1e6 (Table 5)
   cpu_baseline(_1core), cpu_plain_fp64_cg   the CPU oracle and the paper's CG on the host
 each with its error against the FP64 oracle and the roofline of its solve.
 `--impl reference` times the CPU oracle instead (host cores).
@@ -641,7 +642,7 @@ def run_ours(args):
     t_sec["c1"] = time.time() - t0
 
     for name, fn in (("c2_mixed", section_c2), ("c3_batch", section_c3), ("c4_warm_start", section_c4),
-                     ("c0_l96", section_c0)):
+                     ("c0_l96", section_c0), ("e2b_table5", section_e2b)):
         if name in args.skip:
             continue
         t0 = time.time()
@@ -921,6 +922,68 @@ def section_c0(args, enkf, dev, timer):
                     "are launch-bound at this size"}
 
 
+def section_e2b(args, enkf, dev, timer):
+    """Example 2b (Table 5): Lorenz-96 with H = I, N = 100, tridiagonal Toeplitz R (sigma = 0.3,
+    rho = 0.2), one analysis per p in FP64: EnKF-Reduced (the Reduced analysis run to
+    convergence), CGD-EnKF-Reduced with r = 1..5 CG steps and the sEnKF comparator, each timed
+    on the GPU and its error against EnKF-Reduced reported beside the paper's printed value."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    printed = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table5_cgd_enkf_reduced.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                pp, r, v = line.split()
+                printed[(int(pp), int(r))] = float(v)
+    out = {}
+    for p in args.e2b_sizes:
+        t0 = time.time()
+        P = synth.l96_tridiag_problem(p, 100, seed=args.seed)
+        gen_s = time.time() - t0
+        Xf = torch.from_numpy(P.Xf).to(dev)
+        y = torch.from_numpy(P.y).to(dev)
+        Xa = torch.empty_like(Xf)
+
+        def timed(an, reps=5):
+            an.analyze(Xf, y, out=Xa)
+            torch.cuda.synchronize()
+            ms = []
+            for k in range(reps):
+                timer.flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(timer.stream)
+                an.analyze(Xf, y, out=Xa)
+                e1.record(timer.stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return float(np.median(ms)), Xa.cpu().numpy()
+
+        def mk(**cfg):
+            return enkf.Analysis(p, p, 100, P.rowptr, P.col, P.w, P.r, r_off=P.r_off, precision="fp64",
+                                 perturb_obs=0, **cfg)
+
+        ms_ref, exact = timed(mk(variant="reduced", tol=1e-13))
+        row = {"enkf_reduced_ms": ms_ref, "generation_s": gen_s}
+        if p <= 100000:
+            row["enkf_reduced_vs_oracle"] = oracle.rel_frobenius(
+                exact, oracle.enkf_alg2(P.Xf, P.rowptr, P.col, P.w, P.r, P.y, None, r_off=P.r_off))
+        for r in range(1, 6):
+            ms, X = timed(mk(variant="reduced", fixed_iters=r))
+            row[f"cgd_reduced_r{r}"] = {"ms": ms, "rel_err_vs_enkf_reduced": oracle.rel_frobenius(X, exact),
+                                         "paper": printed.get((p, r))}
+        ms, X = timed(mk(variant="senkf"))
+        row["senkf"] = {"ms": ms, "rel_err_vs_enkf_reduced": oracle.rel_frobenius(X, exact),
+                        "paper": printed.get((p, 0))}
+        out[str(p)] = row
+        del Xf, Xa
+        torch.cuda.empty_cache()
+    out["note"] = ("FP64 on one GB300; the paper's times are on 50 CPU cores (MPI); errors against the converged "
+                   "Reduced analysis (EnKF-Reduced) next to the printed Table 5 values")
+    return out
+
+
 def run_batched(args):
     """The batched workload alone: 256 independent analyses of uneven size (n log-uniform in
     [4096, 262144], m = n/4, N in {16, 32, 64, 128}, GRF ensembles with correlation length
@@ -1009,7 +1072,9 @@ def main():
     ap.add_argument("--headline-only", action="store_true",
                     help="only the timed headline configuration and its end-to-end number")
     ap.add_argument("--skip", default="", help="comma-separated sections to leave out of the default run: "
-                                               "c2_mixed, c3_batch, c4_warm_start, c0_l96")
+                                               "c2_mixed, c3_batch, c4_warm_start, c0_l96, e2b_table5")
+    ap.add_argument("--e2b-sizes", type=lambda v: [int(x) for x in v.split(",")], default=[1000, 10000, 100000, 1000000],
+                    help="state sizes p of the Example 2b (Table 5) section")
     ap.add_argument("--warm-train-seeds", type=int, default=40,
                     help="ensembles (x 8 observation draws) the learned warm start trains on in the default run")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],

@@ -182,7 +182,7 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
   }
   const int64_t mN = c.m * c.N;
   const int G = h->launch.G, NT = h->launch.NT;
-  const int64_t NE = (int64_t)c.N * c.N + 2 * c.N;
+  const int64_t NE = (int64_t)c.N * c.N + 4 * c.N;   // partials: N x N Gram + four column-sum vectors
   const size_t vs = elem_size(c);
   Workspace& ws = h->ws;
   struct Alloc { void** p; size_t bytes; };

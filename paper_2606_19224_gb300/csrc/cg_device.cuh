@@ -49,8 +49,10 @@ template <typename VT, int NT> __host__ __device__ constexpr bool async_passF() 
 template <int NT> __host__ __device__ constexpr bool async_xreg() { return NT == 128; }
 template <int NT> __host__ __device__ constexpr int passF_async_bytes();
 template <int NT> struct DFTile;
+template <int NT> __host__ __device__ constexpr int passH_async_bytes();
 template <typename VT, int NT> __host__ __device__ constexpr int union_bytes() {
-  constexpr int f = async_passF<VT, NT>() ? passF_async_bytes<NT>() : passF_bytes<VT, NT>();
+  constexpr int f0 = async_passF<VT, NT>() ? passF_async_bytes<NT>() : passF_bytes<VT, NT>();
+  constexpr int f = sizeof(VT) == 4 && passH_async_bytes<NT>() > f0 ? passH_async_bytes<NT>() : f0;
   constexpr int d = sizeof(VT) == 4 ? DFTile<NT>::bytes : 0;   // pipelined double-float refresh
   constexpr int m1 = refresh_union_bytes<NT>() > f ? refresh_union_bytes<NT>() : f;
   return m1 > d ? m1 : d;
@@ -922,6 +924,241 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ one-reduction Hestenes-Stiefel step
+// The FP32 inner solves use the textbook (Hestenes-Stiefel) recurrences with the matvec
+// q = S p = HA T/(N-1) + R p formed from T = HA^T p in every step, arranged so that a step
+// needs one pass over the rows and one grid reduction. T is carried in N x N space: with
+// p_{k+1} = z_{k+1} + beta_k p_k, HA^T p_{k+1} = HA^T z_{k+1} + beta_k T_k, and
+//   sum_i r_i p_{k+1,i}^2 = sum r_i z^2 + 2 beta_k sum r_i z p_k + beta_k^2 sum r_i p_k^2,
+// so (p, S p) = ||T||^2/(N-1) + sum r_i p^2 comes from column sums of the pass. Pass k, with
+// T_k staged, alpha_k and beta_{k-1}, per row: z_k = M^{-1} r_k (M = R preconditioned, else I),
+// p_k = z_k + beta_{k-1} p_{k-1}, q_k = HA T_k/(N-1) + r_i p_k, x += alpha_k p_k,
+// r -= alpha_k q_k, z_{k+1} = M^{-1} r_{k+1}; out = [HA^T z_{k+1} | (r, z) | (r, r) |
+// sum r_i z^2 | sum r_i z p_k] (N^2 + 4N). In FP32 the Chronopoulos-Gear arrangement (one
+// reduction, with S p carried by its own recurrence) needed about 1.7x the steps of this form on
+// the 512^2 / N = 64 workload (67 against 40), and this form moves no S p vector.
+template <int NT> __host__ __device__ constexpr int passH_async_bytes() {
+  constexpr int LD = NT + 4, TR = FTile<float, NT>::TR, NS = async_xreg<NT>() ? 3 : 4;
+  return NT * LD * 4 + 2 * (NS * TR * LD + TR) * 4;
+}
+
+template <int NT, bool PC, bool ASYNC>
+__device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0, int64_t row1, int N,
+                                      float* X, float* Res, float* P, const float* __restrict__ rv,
+                                      const float* sT, const float* alpha, const float* beta, float vinv,
+                                      unsigned char* tiles, double* __restrict__ out) {
+  constexpr int LD = NT + 4;
+  constexpr int MR = FTile<float, NT>::MR, TR = FTile<float, NT>::TR, C4 = NT / 4;
+  constexpr int NJ = NT / 4, NI = kThreads / NJ;
+  static_assert(NI * MR == TR, "fused tile");
+  constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
+  constexpr bool XREG = async_xreg<NT>();
+  constexpr int NS = XREG ? 3 : 4;          // staged arrays: HA, r, p (, x)
+  constexpr int BUF = NS * TR * LD + TR;   // floats per buffer
+  float* const buf0 = reinterpret_cast<float*>(tiles);
+  const int t = threadIdx.x;
+  const int tj = t % NJ, ti = t / NJ, j0 = tj * 4, r0 = ti * MR;
+  const int g = t / TPG, u = t % TPG, gj = u % NG, gk = u / NG, k0 = gk * MA, ja = gj * MA;
+  const bool vec = (N & 3) == 0;
+  float accT[MA][MA];
+#pragma unroll
+  for (int x = 0; x < MA; ++x)
+#pragma unroll
+    for (int y = 0; y < MA; ++y) accT[x][y] = 0.f;
+  float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+  float s3[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
+  float al[4], be[4];
+#pragma unroll
+  for (int y = 0; y < 4; ++y) { al[y] = alpha[j0 + y]; be[y] = beta[j0 + y]; }
+
+  // copy the tile starting at row i0 into buffer b: 16-byte cp.async pieces (zero-filled past
+  // the CTA's rows and past N) when rows are 16-byte aligned, else plain loads
+  auto fill = [&](int64_t i0, int b) {
+    float* sb = buf0 + b * BUF;
+#pragma unroll
+    for (int c = t; c < TR * C4; c += kThreads) {
+      const int ii = c / C4, c0 = (c % C4) * 4;
+      const int64_t i = i0 + ii;
+      const bool ok = i < row1 && c0 < N;
+      if (ASYNC) {
+        const int64_t off = ok ? i * N + c0 : row0 * N;
+        cp_async16(sb + 0 * TR * LD + ii * LD + c0, HA + off, ok);
+        cp_async16(sb + 1 * TR * LD + ii * LD + c0, Res + off, ok);
+        cp_async16(sb + 2 * TR * LD + ii * LD + c0, P + off, ok);
+        if (!XREG) cp_async16(sb + 3 * TR * LD + ii * LD + c0, X + off, ok);
+      } else {
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, rr[4] = {0.f, 0.f, 0.f, 0.f}, pp[4] = {0.f, 0.f, 0.f, 0.f};
+        float xx[4] = {0.f, 0.f, 0.f, 0.f};
+        if (ok) {
+          ld4<float>(a, HA + i * N, c0, N, vec);
+          ld4<float>(rr, Res + i * N, c0, N, vec);
+          ld4<float>(pp, P + i * N, c0, N, vec);
+          if (!XREG) ld4<float>(xx, X + i * N, c0, N, vec);
+        }
+        store_vec4<float>(sb + 0 * TR * LD + ii * LD + c0, a);
+        store_vec4<float>(sb + 1 * TR * LD + ii * LD + c0, rr);
+        store_vec4<float>(sb + 2 * TR * LD + ii * LD + c0, pp);
+        if (!XREG) store_vec4<float>(sb + 3 * TR * LD + ii * LD + c0, xx);
+      }
+    }
+    if (t < TR) {
+      const int64_t i = i0 + t;
+      if (ASYNC) cp_async4(sb + NS * TR * LD + t, rv + (i < row1 ? i : row0), i < row1);
+      else sb[NS * TR * LD + t] = i < row1 ? rv[i] : 0.f;
+    }
+    if (ASYNC) cp_async_commit();
+  };
+
+  int b = 0;
+  if (ASYNC && row0 < row1) fill(row0, 0);
+  for (int64_t i0 = row0; i0 < row1; i0 += TR, b ^= ASYNC ? 1 : 0) {
+    if (ASYNC) {
+      if (i0 + TR < row1) {
+        fill(i0 + TR, b ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      fill(i0, 0);
+    }
+    __syncthreads();
+    const float* sH = buf0 + b * BUF;
+    float* sR = buf0 + b * BUF + TR * LD;
+    const float* sP = sR + TR * LD;
+    const float* sX = sP + TR * LD;                      // (NS == 4 only)
+    const float* sRv = sR + (NS - 1) * TR * LD;
+    // NT = 128: the thread's x fragment straight from global, in flight during the contraction
+    float xg[MR][4];
+    if (XREG) {
+#pragma unroll
+      for (int x = 0; x < MR; ++x) {
+        const int64_t i = i0 + r0 + x;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) xg[x][y] = 0.f;
+        if (i < row1 && j0 < N) ld4<float>(xg[x], X + i * N, j0, N, vec);
+      }
+    }
+    // u = HA T (the 1/(N-1) is applied below); four k per step from float4 rows of HA
+    float acc[MR][4];
+#pragma unroll
+    for (int x = 0; x < MR; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < NT; k += 4) {
+      float4 a4[MR];
+#pragma unroll
+      for (int x = 0; x < MR; ++x) a4[x] = *reinterpret_cast<const float4*>(sH + (r0 + x) * LD + k);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 b4 = *reinterpret_cast<const float4*>(sT + (k + kk) * LD + j0);
+#pragma unroll
+        for (int x = 0; x < MR; ++x) {
+          const float av = kk == 0 ? a4[x].x : kk == 1 ? a4[x].y : kk == 2 ? a4[x].z : a4[x].w;
+          acc[x][0] = fmaf(av, b4.x, acc[x][0]);
+          acc[x][1] = fmaf(av, b4.y, acc[x][1]);
+          acc[x][2] = fmaf(av, b4.z, acc[x][2]);
+          acc[x][3] = fmaf(av, b4.w, acc[x][3]);
+        }
+      }
+    }
+    // the step on the thread's MR x 4 fragment
+#pragma unroll
+    for (int x = 0; x < MR; ++x) {
+      const int row = r0 + x;
+      const int64_t i = i0 + row;
+      if (i < row1 && j0 < N) {
+        const float ri = sRv[row];
+        const float4 rv4 = *reinterpret_cast<const float4*>(sR + row * LD + j0);
+        const float4 pv4 = *reinterpret_cast<const float4*>(sP + row * LD + j0);
+        const float4 xv4 = XREG ? make_float4(xg[x][0], xg[x][1], xg[x][2], xg[x][3])
+                                : *reinterpret_cast<const float4*>(sX + row * LD + j0);
+        const float rvv[4] = {rv4.x, rv4.y, rv4.z, rv4.w}, pvv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+        const float xvv[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
+        const float rinv = PC ? 1.f / ri : 0.f;
+        float pn[4], xn[4], rn[4], zn[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const float zz = PC ? rvv[y] * rinv : rvv[y];
+          // beta == 0 (first step, frozen columns) selects p = z without reading the old p
+          pn[y] = be[y] == 0.f ? zz : fmaf(be[y], pvv[y], zz);
+          const float q = fmaf(acc[x][y], vinv, ri * pn[y]);
+          xn[y] = fmaf(al[y], pn[y], xvv[y]);
+          rn[y] = fmaf(-al[y], q, rvv[y]);
+          zn[y] = PC ? rn[y] * rinv : rn[y];
+          s1[y] = fmaf(rn[y], zn[y], s1[y]);
+          s2[y] = fmaf(rn[y], rn[y], s2[y]);
+          s3[y] = fmaf(ri * zn[y], zn[y], s3[y]);
+          s4[y] = fmaf(ri * zn[y], pn[y], s4[y]);
+        }
+        st4<float>(P + i * N, j0, N, vec, pn);
+        st4<float>(X + i * N, j0, N, vec, xn);
+        st4<float>(Res + i * N, j0, N, vec, rn);
+        store_vec4<float>(sR + row * LD + j0, zn);
+      }
+    }
+    __syncthreads();
+    // next step's partial Gram HA^T z_new on the same tile (rows past row1 are zero)
+    const int nrows = (int)imin64(TR, row1 - i0);
+    for (int ii = g; ii < nrows; ii += RG) {
+      float a[MA], v[MA];
+      load_vec<float>(a, sH + ii * LD + k0, MA);
+      load_vec<float>(v, sR + ii * LD + ja, MA);
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) accT[x][y] = fmaf(a[x], v[y], accT[x][y]);
+    }
+    __syncthreads();   // this buffer is refilled by the copy issued in the next iteration
+  }
+  double* red = reinterpret_cast<double*>(tiles);
+  if (RG > 1) {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) red[(g * NT + k0 + x) * NT + ja + y] = (double)accT[x][y];
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int x = 0; x < MA; ++x)
+#pragma unroll
+        for (int y = 0; y < MA; ++y) {
+          const int k = k0 + x, j = ja + y;
+          double sum = 0.0;
+          for (int gg = 0; gg < RG; ++gg) sum += red[(gg * NT + k) * NT + j];
+          if (k < N && j < N) out[k * N + j] = sum;
+        }
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < MA; ++x)
+#pragma unroll
+      for (int y = 0; y < MA; ++y) {
+        const int k = k0 + x, j = ja + y;
+        if (k < N && j < N) out[k * N + j] = (double)accT[x][y];
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    red[(0 * NI + ti) * NT + j0 + y] = (double)s1[y];
+    red[(1 * NI + ti) * NT + j0 + y] = (double)s2[y];
+    red[(2 * NI + ti) * NT + j0 + y] = (double)s3[y];
+    red[(3 * NI + ti) * NT + j0 + y] = (double)s4[y];
+  }
+  __syncthreads();
+  if (t < N) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double sum = 0.0;
+      for (int q = 0; q < NI; ++q) sum += red[(c * NI + q) * NT + t];
+      out[N * N + c * N + t] = sum;
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ double-float refresh, pipelined
 // The two passes of the double-float refresh (FP32 mode, N % 4 == 0) with the row tiles
 // double-buffered through cp.async, as in passF_async. Same arithmetic and partial sums as
@@ -1190,6 +1427,40 @@ __device__ __forceinline__ void stage_T_norms(const double* __restrict__ Tred, i
     double s = 0.0;
     for (int q = 0; q < L; ++q) s += scratch[q * NT + t];
     tn2[t] = s;
+  }
+  __syncthreads();
+}
+
+// Stage T_{k+1} = Tz + beta_j T_k into shared memory in place (Tz: the reduced HA^T z_{k+1},
+// FP32 at the start of Tred; sT holds T_k, stride NT + 4, zero-padded; with beta_j = 0, T_k is
+// not read) and return the column norms ||T_{k+1,:j}||^2 (exact-product compensated FP32
+// sums, fixed order).
+template <int NT>
+__device__ __forceinline__ void stage_T_rec(const double* __restrict__ Tred, int N, const float* beta,
+                                            float* sT, double* tn2, double* scratch) {
+  constexpr int LD = NT + 4, L = kThreads / NT;
+  const int t = threadIdx.x, j = t % NT, k0 = t / NT;
+  const float* T32 = reinterpret_cast<const float*>(Tred);
+  const float bj = j < N ? beta[j] : 0.f;
+  SqAcc acc;
+  for (int k = k0; k < NT; k += L) {
+    float v = 0.f;
+    // beta == 0 (a new inner solve, frozen columns) takes Tz without reading the old T: the
+    // region may hold other passes' bytes, and 0 * NaN would not be 0
+    if (k < N && j < N) {
+      const float tz = __ldcg(T32 + k * N + j);
+      v = bj == 0.f ? tz : fmaf(bj, sT[k * LD + j], tz);
+    }
+    sT[k * LD + j] = v;
+    acc.add(v);
+  }
+  for (int k = t; k < NT * (LD - NT); k += kThreads) sT[(k / (LD - NT)) * LD + NT + k % (LD - NT)] = 0.f;
+  scratch[t] = acc.value();
+  __syncthreads();
+  if (t < NT) {
+    double sum = 0.0;
+    for (int q = 0; q < L; ++q) sum += scratch[q * NT + t];
+    tn2[t] = sum;
   }
   __syncthreads();
 }

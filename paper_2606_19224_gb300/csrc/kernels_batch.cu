@@ -462,7 +462,7 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
     nmax = std::max(nmax, (int)cfgs[i].N);
   }
   B.ntmax = nt_of(nmax);
-  B.ne_max = nmax * nmax + 2 * nmax;
+  B.ne_max = nmax * nmax + 4 * nmax;
   B.smem = B.ntmax == 32 ? batch_smem_nt<32>() : B.ntmax == 64 ? batch_smem_nt<64>() : batch_smem_nt<128>();
   void* fn = batch_fn(B.ntmax);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem);

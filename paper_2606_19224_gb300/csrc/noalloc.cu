@@ -97,7 +97,7 @@ enkf_status enkf_analyze_noalloc(const enkf_config* cfg, const int32_t* d_rowptr
 
   // carve the workspace out of the fixed array
   const size_t mN = size_t(c.m) * c.N;
-  const size_t NE = size_t(c.N) * c.N + 2 * size_t(c.N);
+  const size_t NE = size_t(c.N) * c.N + 4 * size_t(c.N);
   const bool fp64 = c.precision == ENKF_FP64;
   const size_t vs = fp64 ? 8 : 4;
   struct Part { void** p; size_t bytes; };

@@ -86,7 +86,7 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   const int64_t rows_per = (p.m + G - 1) / G;
   const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
   const int64_t row1 = imin64(p.m, row0 + rows_per);
-  const int NE = N * N + 2 * N;
+  const int NE = N * N + 4 * N;   // [N x N Gram | four N-vectors of column sums]
   const double inv_nm1 = 1.0 / (double)(N - 1);
   const bool refine = (p.mode == 1);
   const bool fixed = p.fixed_iters > 0;
@@ -110,6 +110,11 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   };
   int par = 0;
   bool ok = true;
+  // the last two column-sum vectors of the partials are written only by the FP32 step
+  if (t < N) {
+    Tp[N * N + 2 * N + t] = 0.0;
+    Tp[N * N + 3 * N + t] = 0.0;
+  }
 
   // a warm start keeps the given Zdf; B holds its residual (written by the decoder)
   const bool warm = refine && p.warm != 0;
@@ -182,7 +187,104 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   const int t_f32 = sizeof(VT) == 4 ? N * N : 0;
   int outer = 0, total_iter = 0, refinements = 0;
   while (ok) {
-   {
+   if constexpr (sizeof(VT) == 4) {
+    // ---- FP32 inner solve of S X = B from X = 0 in the one-reduction Hestenes-Stiefel form
+    // (passH): the first reduction gives [HA^T z_0 | sum r_i z_0^2 | (r_0, r_0)], T_0 = HA^T z_0
+    {
+      ProSetup<VT, PC> pro{B, X, Res, rv, N};
+      passA<VT, NT, ProSetup<VT, PC>, PC>(HA, row0, row1, N, rv, true, pro, uni, Tp);
+    }
+    if (t < N) {
+      Tp[N * N + 2 * N + t] = 0.0;
+      Tp[N * N + 3 * N + t] = 0.0;
+    }
+    if (!(ok = bar.sync())) break;
+    reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
+    if (!(ok = bar.sync())) break;
+    float* sTf = reinterpret_cast<float*>(sT);
+    float* bvf = reinterpret_cast<float*>(s_beta_v);
+    float* avf = reinterpret_cast<float*>(s_alpha_v);
+    if (t < NT) bvf[t] = 0.f;
+    __syncthreads();
+    stage_T_rec<NT>(p.Tred, N, bvf, sTf, s_tn2, scratch);
+    // slots: s_sig = gamma = (r, z); s_den = sum r_i p^2; s_gam = (r, r), the stopping rule's norm
+    if (t < NT) {
+      const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;       // sum r_i z_0^2
+      const double gm = t < N ? __ldcg(p.Tred + N * N + N + t) : 0.0;   // (r_0, r_0)
+      s_sig[t] = PC ? sg : gm;
+      s_den[t] = sg;
+      s_gam[t] = gm;
+      s_bn2[t] = gm;
+      s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    tick(PH_SETUP);
+    const int limit = fixed ? p.fixed_iters : (p.max_iter - total_iter);
+    int it = 0;
+    for (;;) {
+      // alpha_k = gamma_k / (p_k, S p_k), (p, S p) = ||T_k||^2/(N-1) + sum r_i p^2 (identical in
+      // every CTA: same sums in the same order)
+      int my_active = 0;
+      if (t < N) {
+        int a = s_active[t];
+        const double gm = s_gam[t];
+        if (a && it > 0) {
+          const double itm = s_itol[t] * (1.0 - 4.0 * 2.220446049250313e-16);
+          if (!isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
+          else if (fixed ? gm == 0.0 : gm <= itm * itm * s_bn2[t]) a = 0;
+        }
+        double al = 0.0;
+        if (a) {
+          const double pq = s_tn2[t] * inv_nm1 + s_den[t];
+          if (!isfinite(pq)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
+          else if (pq <= 0.0) { atomicOr(p.status, DS_BREAKDOWN); a = 0; }
+          else al = s_sig[t] / pq;
+        }
+        s_active[t] = a;
+        avf[t] = (float)al;
+        my_active = a;
+      }
+      if (!(__syncthreads_or(my_active) && it < limit)) break;
+      tick(PH_SCAL);
+      if ((N & 3) == 0)
+        passH<NT, PC, true>(reinterpret_cast<const float*>(HA), row0, row1, N, reinterpret_cast<float*>(X),
+                            reinterpret_cast<float*>(Res), reinterpret_cast<float*>(P),
+                            reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, Tp);
+      else
+        passH<NT, PC, false>(reinterpret_cast<const float*>(HA), row0, row1, N, reinterpret_cast<float*>(X),
+                             reinterpret_cast<float*>(Res), reinterpret_cast<float*>(P),
+                             reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, Tp);
+      tick(PH_PASS);
+      if (!(ok = bar.sync())) break;
+      tick(PH_BAR1);
+      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
+      tick(PH_RED);
+      if (!(ok = bar.sync())) break;
+      tick(PH_BAR2);
+      // beta_k = gamma_{k+1} / gamma_k; sum r_i p_{k+1}^2 from the expanded sums; frozen
+      // columns keep beta = 0 (their next p is never used: alpha = 0)
+      if (t < NT) {
+        float bf = 0.f;
+        if (t < N && s_active[t]) {
+          const double g1 = __ldcg(p.Tred + N * N + t), g2 = __ldcg(p.Tred + N * N + N + t);
+          const double g3 = __ldcg(p.Tred + N * N + 2 * N + t), g4 = __ldcg(p.Tred + N * N + 3 * N + t);
+          const double be = g1 / s_sig[t];
+          s_den[t] = g3 + 2.0 * be * g4 + be * be * s_den[t];
+          s_sig[t] = g1;
+          s_gam[t] = g2;
+          s_iters[t] += 1;
+          bf = (float)be;
+        }
+        bvf[t] = bf;
+      }
+      __syncthreads();
+      stage_T_rec<NT>(p.Tred, N, bvf, sTf, s_tn2, scratch);
+      tick(PH_SCAL);
+      ++it;
+    }
+    if (!ok) break;
+    total_iter += it;
+   } else {
     // ---- inner solve of S X = B from X = 0: first reduction of [HA^T r | sum r_i r^2 | (r, r)]
     {
       ProSetup<VT, PC> pro{B, X, Res, rv, N};
