@@ -1099,9 +1099,11 @@ __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0
       }
     }
     __syncthreads();
-    // next step's partial Gram HA^T z_new on the same tile (rows past row1 are zero)
-    const int nrows = (int)imin64(TR, row1 - i0);
-    for (int ii = g; ii < nrows; ii += RG) {
+    // next step's partial Gram HA^T z_new on the same tile; rows past row1 hold zeros in both
+    // operands, so the loop runs over the whole tile (a fixed trip count the compiler unrolls
+    // and pipelines)
+#pragma unroll 8
+    for (int ii = g; ii < TR; ii += RG) {
       float a[MA], v[MA];
       load_vec<float>(a, sH + ii * LD + k0, MA);
       load_vec<float>(v, sR + ii * LD + ja, MA);
@@ -1434,33 +1436,65 @@ __device__ __forceinline__ void stage_T_norms(const double* __restrict__ Tred, i
 // Stage T_{k+1} = Tz + beta_j T_k into shared memory in place (Tz: the reduced HA^T z_{k+1},
 // FP32 at the start of Tred; sT holds T_k, stride NT + 4, zero-padded; with beta_j = 0, T_k is
 // not read) and return the column norms ||T_{k+1,:j}||^2 (exact-product compensated FP32
-// sums, fixed order).
+// sums, fixed order). With `step` set, beta_j = gamma_{k+1}/gamma_k is formed here for the
+// active columns from the reduced column sums [(r, z) | (r, r) | sum r_i z^2 | sum r_i z p]
+// behind Tz, by every thread that stages a piece of column j (so the sums and Tz are read in
+// one round), and the column's scalars are advanced: s_den = sum r_i p^2, s_sig = gamma,
+// s_gam = (r, r), iteration count; beta (FP32) lands in beta[] for the next pass. Without
+// `step`, beta[] is read as given.
 template <int NT>
-__device__ __forceinline__ void stage_T_rec(const double* __restrict__ Tred, int N, const float* beta,
-                                            float* sT, double* tn2, double* scratch) {
+__device__ __forceinline__ void stage_T_rec(const double* __restrict__ Tred, int N, float* beta,
+                                            float* sT, double* tn2, double* scratch, bool step = false,
+                                            const int* s_active = nullptr, double* s_sig = nullptr,
+                                            double* s_den = nullptr, double* s_gam = nullptr,
+                                            int* s_iters = nullptr) {
   constexpr int LD = NT + 4, L = kThreads / NT;
   const int t = threadIdx.x, j = t % NT, k0 = t / NT;
   const float* T32 = reinterpret_cast<const float*>(Tred);
-  const float bj = j < N ? beta[j] : 0.f;
+  float tz[NT / L];
+#pragma unroll
+  for (int q = 0; q < NT / L; ++q) {
+    const int k = k0 + q * L;
+    tz[q] = (k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f;
+  }
+  float bj = 0.f;
+  double g1 = 0.0;
+  const bool act = step && j < N && s_active[j];
+  if (act) {
+    g1 = __ldcg(Tred + N * N + j);
+    bj = (float)(g1 / s_sig[j]);
+  } else if (!step && j < N) {
+    bj = beta[j];
+  }
   SqAcc acc;
-  for (int k = k0; k < NT; k += L) {
-    float v = 0.f;
+#pragma unroll
+  for (int q = 0; q < NT / L; ++q) {
+    const int k = k0 + q * L;
     // beta == 0 (a new inner solve, frozen columns) takes Tz without reading the old T: the
     // region may hold other passes' bytes, and 0 * NaN would not be 0
-    if (k < N && j < N) {
-      const float tz = __ldcg(T32 + k * N + j);
-      v = bj == 0.f ? tz : fmaf(bj, sT[k * LD + j], tz);
-    }
+    const float v = (bj == 0.f) ? tz[q] : fmaf(bj, sT[k * LD + j], tz[q]);
     sT[k * LD + j] = v;
     acc.add(v);
   }
   for (int k = t; k < NT * (LD - NT); k += kThreads) sT[(k / (LD - NT)) * LD + NT + k % (LD - NT)] = 0.f;
   scratch[t] = acc.value();
-  __syncthreads();
+  __syncthreads();   // every read of s_sig above precedes the updates below
   if (t < NT) {
     double sum = 0.0;
     for (int q = 0; q < L; ++q) sum += scratch[q * NT + t];
     tn2[t] = sum;
+    if (step) {
+      if (act) {
+        const double g2 = __ldcg(Tred + N * N + N + t);
+        const double g3 = __ldcg(Tred + N * N + 2 * N + t), g4 = __ldcg(Tred + N * N + 3 * N + t);
+        const double be = g1 / s_sig[t];
+        s_den[t] = g3 + 2.0 * be * g4 + be * be * s_den[t];
+        s_sig[t] = g1;
+        s_gam[t] = g2;
+        s_iters[t] += 1;
+      }
+      beta[t] = bj;
+    }
   }
   __syncthreads();
 }

@@ -261,24 +261,10 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       tick(PH_RED);
       if (!(ok = bar.sync())) break;
       tick(PH_BAR2);
-      // beta_k = gamma_{k+1} / gamma_k; sum r_i p_{k+1}^2 from the expanded sums; frozen
-      // columns keep beta = 0 (their next p is never used: alpha = 0)
-      if (t < NT) {
-        float bf = 0.f;
-        if (t < N && s_active[t]) {
-          const double g1 = __ldcg(p.Tred + N * N + t), g2 = __ldcg(p.Tred + N * N + N + t);
-          const double g3 = __ldcg(p.Tred + N * N + 2 * N + t), g4 = __ldcg(p.Tred + N * N + 3 * N + t);
-          const double be = g1 / s_sig[t];
-          s_den[t] = g3 + 2.0 * be * g4 + be * be * s_den[t];
-          s_sig[t] = g1;
-          s_gam[t] = g2;
-          s_iters[t] += 1;
-          bf = (float)be;
-        }
-        bvf[t] = bf;
-      }
-      __syncthreads();
-      stage_T_rec<NT>(p.Tred, N, bvf, sTf, s_tn2, scratch);
+      // beta_k = gamma_{k+1} / gamma_k, T_{k+1} = HA^T z_{k+1} + beta_k T_k, sum r_i p_{k+1}^2
+      // from the expanded sums; frozen columns keep beta = 0 (their next p is never used:
+      // alpha = 0)
+      stage_T_rec<NT>(p.Tred, N, bvf, sTf, s_tn2, scratch, true, s_active, s_sig, s_den, s_gam, s_iters);
       tick(PH_SCAL);
       ++it;
     }
