@@ -25,11 +25,12 @@ from .problems import (
     L96Cycle,
     WORKLOADS,
     l96_tridiag_problem,
+    ex1b_problem,
 )
 
 __all__ = [
     "grf_fields", "periodic_sqexp_eigenvalues", "l96_tendency", "l96_rk4", "Problem",
     "subsample_operator", "identity_operator", "every_kth_operator", "obs_variances",
     "grf_problem", "workload", "batched_problem_specs", "batched_problems", "L96Cycle",
-    "WORKLOADS", "l96_tridiag_problem",
+    "WORKLOADS", "l96_tridiag_problem", "ex1b_problem",
 ]

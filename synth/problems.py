@@ -151,6 +151,19 @@ def l96_tridiag_problem(p: int, N: int, seed: int, sigma: float = 0.3, rho: floa
                    dict(sigma=sigma, rho=rho, dt=dt, spinup=spinup, model_noise=model_noise), r_off)
 
 
+def ex1b_problem(m: int, N: int = 50, seed: int = 1, q: float = 0.1) -> Problem:
+    """The random-vector workload used for the CG error bounds: state and observations of size
+    m (H = I), truth ~ N(0, I), initial ensemble ~ N(0, I), one forecast step with the identity
+    model plus model noise N(0, q I), R = I, y = truth + N(0, I)."""
+    truth = _rng(seed, STREAM_TRUTH).standard_normal(m)
+    Xa0 = _rng(seed, STREAM_ENSEMBLE).standard_normal((m, N))
+    Xf = Xa0 + math.sqrt(q) * _rng(seed, STREAM_ENSEMBLE, 1).standard_normal((m, N))
+    rowptr, col, w = identity_operator(m)
+    r = np.ones(m)
+    y = truth + _rng(seed, STREAM_OBSNOISE).standard_normal(m)
+    return Problem(np.ascontiguousarray(Xf), rowptr, col, w, r, y, truth, dict(q=q))
+
+
 def batched_problem_specs(count: int, seed: int, n_lo: int = 4096, n_hi: int = 262144,
                           members=(16, 32, 64, 128)):
     """Shapes of a batch of uneven problems: n log-uniform in [n_lo, n_hi] rounded to a
