@@ -32,7 +32,7 @@ void free_workspace(Workspace& ws) {
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y,
                   ws.Hrowptr, ws.Hcol, ws.Hw, ws.wa, ws.wb, ws.wcp, ws.wmu, ws.wU, ws.wV, ws.wcarry,
-                  ws.wcarryV, ws.Xw, ws.yw};
+                  ws.wcarryV, ws.Xw, ws.yw, ws.Tk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace{};
@@ -228,7 +228,10 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
     allocs.push_back({(void**)&ws.Ddf, 8 * (size_t)mN});
     allocs.push_back({(void**)&ws.Zdf, 8 * (size_t)mN});
   }
-  if (mixed) allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
+  if (mixed) {
+    allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
+    allocs.push_back({(void**)&ws.Tk, sizeof(float) * 2 * c.N * c.N});
+  }
   const int64_t hnnz = h_rowptr[c.m];
   const int64_t nblk = enkf::whiten_blocks(c.m);
   if (tri) {

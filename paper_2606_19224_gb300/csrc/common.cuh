@@ -149,6 +149,7 @@ struct Workspace {
   void* stage_Xf = nullptr;     // host-API staging [n][N]
   double* stage_y = nullptr;    // [m]
   unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
+  float* Tk = nullptr;          // [2][N][N] T of the tensor-core step, carried between steps
   // tridiagonal R (kernels_whiten.cu): the caller's H, the whitening scan's coefficients and
   // buffers; rowptr / col / w / r above then hold H' = I and r' = 1 of the whitened problem
   int32_t* Hrowptr = nullptr;   // [m+1]

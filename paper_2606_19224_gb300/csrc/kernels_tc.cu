@@ -97,6 +97,7 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.Tred = ws.Tred;
   p.rrpart = ws.rrpart;
   p.W = ws.W;
+  p.Tk = ws.Tk;
   p.tol = c.tol;
   p.inner_tol = c.inner_tol;
   // accuracy an inner solve on the BF16 / FP16 operator can be asked for

@@ -165,7 +165,7 @@ __device__ __forceinline__ void tc_copy(unsigned char* sdst, const unsigned char
 
 template <typename T16, int NT, bool PC, int TERMS>
 __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, int64_t row1, int N,
-                          float* X, float* Res, float* P, float* Sv, const float* __restrict__ rv,
+                          float* X, float* Res, float* P, const float* __restrict__ rv,
                           const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
                           uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g, int* status,
                           bool& ok, double* __restrict__ out) {
@@ -195,12 +195,9 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
                                   (((j & 7) * 8 + (i & 7)) * 2));
   };
   (void)qmax;
-  for (int e = t; e < 8 * 2 * NT; e += kThreads) sacc[e] = 0.f;
-  float gA[DB ? CH : 1][16], gB[DB ? CH : 1][16];
-#pragma unroll
-  for (int c = 0; c < (DB ? CH : 1); ++c)
-#pragma unroll
-    for (int y = 0; y < 16; ++y) { gA[c][y] = 0.f; gB[c][y] = 0.f; }
+  // column sums [(r, z) | (r, r) | sum r_i z^2 | sum r_i z p] of the pass, one slot per warp
+  // quarter (a column is handled by the four warps of one half): sacc[(c * 4 + qd) * NT + j]
+  for (int e = t; e < 4 * 4 * NT; e += kThreads) sacc[e] = 0.f;
   if (Qb > 0) {
     tc_copy(reinterpret_cast<unsigned char*>(sAu), au_src(0), L::AUB);
     tc_cp_commit();
@@ -229,24 +226,21 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     const float ri = valid ? rv[i] : 1.f;
     const float rinv = 1.f / ri;
     // operands of the first chunk are loaded while the MMA runs
-    float rr[16], pp[16], ss[16], xx[16];
+    float rr[16], pp[16], xx[16];
     auto load_chunk = [&](int j0) {
 #pragma unroll
       for (int y4 = 0; y4 < 4; ++y4) {
         const int jj = j0 + 4 * y4;
-        float a[4] = {0.f, 0.f, 0.f, 0.f}, bq[4] = {0.f, 0.f, 0.f, 0.f};
-        float cq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, bq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid && jj < N) {
           ld4<float>(a, Res + i * N, jj, N, vec);
           ld4<float>(bq, P + i * N, jj, N, vec);
-          ld4<float>(cq, Sv + i * N, jj, N, vec);
           ld4<float>(dq, X + i * N, jj, N, vec);
         }
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           rr[4 * y4 + y] = a[y];
           pp[4 * y4 + y] = bq[y];
-          ss[4 * y4 + y] = cq[y];
           xx[4 * y4 + y] = dq[y];
         }
       }
@@ -255,31 +249,31 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
     ph_u ^= 1u;
     tc_fence_after();
-    float tA[16], tB[16];   // NT = 128: this chunk's column terms, reduced over the warp per chunk
+    float tS[4][16];   // this chunk's column terms, reduced over the warp per chunk
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int j0 = half * HALF + 16 * c;
       if (c > 0) load_chunk(j0);
       float u[16];
       tmem_ld16(d_u + ((uint32_t)(32 * qd) << 16) + j0, u);
-      float pn[16], sn[16], xn[16], rn[16];
+      float pn[16], xn[16], rn[16];
 #pragma unroll
       for (int y = 0; y < 16; ++y) {
         const int j = j0 + y;
+        // the step of passH: p = z + beta p, q = HA T/(N-1) + r_i p, x += alpha p, r -= alpha q
         const float uu = u[y] * ts[NT + j];
         const float zz = PC ? rr[y] * rinv : rr[y];
-        const float ww = PC ? uu + rr[y] : fmaf(ri, rr[y], uu);
         const float be = beta[j], al = alpha[j];
         pn[y] = be == 0.f ? zz : fmaf(be, pp[y], zz);
-        sn[y] = be == 0.f ? ww : fmaf(be, ss[y], ww);
+        const float qq = fmaf(ri, pn[y], uu);
         xn[y] = fmaf(al, pn[y], xx[y]);
-        rn[y] = fmaf(-al, sn[y], rr[y]);
+        rn[y] = fmaf(-al, qq, rr[y]);
         const float zn = PC ? rn[y] * rinv : rn[y];
         const bool live = valid && j < N;
-        const float a = live ? (PC ? rn[y] * zn : ri * rn[y] * rn[y]) : 0.f;
-        const float bb = live ? rn[y] * rn[y] : 0.f;
-        if (DB) { gA[DB ? c : 0][y] += a; gB[DB ? c : 0][y] += bb; }
-        else { tA[y] = a; tB[y] = bb; }
+        tS[0][y] = live ? rn[y] * zn : 0.f;
+        tS[1][y] = live ? rn[y] * rn[y] : 0.f;
+        tS[2][y] = live ? ri * zn * zn : 0.f;
+        tS[3][y] = live ? ri * zn * pn[y] : 0.f;
         const float zsc = live ? zn * zs[j] : 0.f;
         const T16 zh = H16<T16>::from(zsc);
         *bg_ptr(0, j, rt) = zh;
@@ -291,32 +285,24 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
           const int jj = j0 + 4 * y4;
           if (jj < N) {
             const float o1[4] = {pn[4 * y4], pn[4 * y4 + 1], pn[4 * y4 + 2], pn[4 * y4 + 3]};
-            const float o2[4] = {sn[4 * y4], sn[4 * y4 + 1], sn[4 * y4 + 2], sn[4 * y4 + 3]};
             const float o3[4] = {xn[4 * y4], xn[4 * y4 + 1], xn[4 * y4 + 2], xn[4 * y4 + 3]};
             const float o4[4] = {rn[4 * y4], rn[4 * y4 + 1], rn[4 * y4 + 2], rn[4 * y4 + 3]};
             st4<float>(P + i * N, jj, N, vec, o1);
-            st4<float>(Sv + i * N, jj, N, vec, o2);
             st4<float>(X + i * N, jj, N, vec, o3);
             st4<float>(Res + i * N, jj, N, vec, o4);
           }
         }
       }
-      if constexpr (!DB) {
-        // this chunk's per-column sums over the warp's 32 rows, into the warp's shared slot
+      // this chunk's per-column sums over the warp's 32 rows, into the warp quarter's slot
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
         for (int y = 0; y < 16; ++y) {
-          float a = tA[y], bb = tB[y];
+          float a = tS[cc][y];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            bb += __shfl_xor_sync(0xffffffffu, bb, o);
-          }
-          if (lane == 0) {
-            sacc[(warp * 2 + 0) * NT + j0 + y] += a;
-            sacc[(warp * 2 + 1) * NT + j0 + y] += bb;
-          }
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane == 0) sacc[(cc * 4 + qd) * NT + j0 + y] += a;
         }
-      }
     }
     tc_fence_before();
     fence_async_smem();
@@ -351,25 +337,6 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
     }
   }
   tc_cp_wait_all();
-  if constexpr (DB) {
-    // column sums of the pass: one warp reduction per column, this warp's shared slot
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int y = 0; y < 16; ++y) {
-        float a = gA[DB ? c : 0][y], bb = gB[DB ? c : 0][y];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          bb += __shfl_xor_sync(0xffffffffu, bb, o);
-        }
-        if (lane == 0) {
-          const int j = half * HALF + 16 * c + y;
-          sacc[(warp * 2 + 0) * NT + j] = a;
-          sacc[(warp * 2 + 1) * NT + j] = bb;
-        }
-      }
-  }
   // partial Gram from TMEM: D_g lane j, column k -> out[k*N + j] / zs_j (the condition is
   // uniform within a warp: tcgen05.ld is warp-collective)
   if (Qb > 0 && 32 * qd < N) {
@@ -391,14 +358,12 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
   tc_fence_before();
   __syncthreads();
   if (t < N) {
-    const int h = t / HALF;
-    double a = 0.0, bb = 0.0;
-    for (int w = 4 * h; w < 4 * h + 4; ++w) {
-      a += (double)sacc[(w * 2 + 0) * NT + t];
-      bb += (double)sacc[(w * 2 + 1) * NT + t];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double a = 0.0;
+      for (int w = 0; w < 4; ++w) a += (double)sacc[(cc * 4 + w) * NT + t];
+      out[N * N + cc * N + t] = a;
     }
-    out[N * N + t] = a;
-    out[N * N + N + t] = bb;
   }
   __syncthreads();
 }
@@ -411,7 +376,7 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
 // (r, r) sums of its four columns in registers for the whole pass.
 template <typename T16, int NT, bool PC, int TERMS>
 __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t row1, int N, float* X,
-                            float* Res, float* P, float* Sv, const float* __restrict__ rv,
+                            float* Res, float* P, const float* __restrict__ rv,
                             const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
                             uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g,
                             int* status, bool& ok, double* __restrict__ out) {
@@ -457,24 +422,24 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     const int part = e / ((kTR - NT) * kTR), rem = e % ((kTR - NT) * kTR);
     *bg_ptr(part, NT + rem / kTR, rem % kTR) = H16<T16>::from(0.f);
   }
-  float sg[4] = {0.f, 0.f, 0.f, 0.f}, sr[4] = {0.f, 0.f, 0.f, 0.f};
+  float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+  float s3[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
   if (Qb > 0) {
     tc_copy(sAu(0), au_src(0), L::AUB);
     tc_cp_commit();
   }
   const bool vec = (N & 3) == 0;
-  // the operands of one row sweep of the update: r, p, S p, x of the thread's four columns
-  // and r_i; loaded one sweep ahead so that their latency overlaps the previous sweep
-  struct Ops { float rr[4], pp[4], ss[4], xx[4], ri; };
+  // the operands of one row sweep of the update: r, p, x of the thread's four columns and
+  // r_i; loaded one sweep ahead so that their latency overlaps the previous sweep
+  struct Ops { float rr[4], pp[4], xx[4], ri; };
   auto load_ops = [&](int64_t i0, int r, Ops& o) {
     const int64_t i = i0 + r;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) { o.rr[y] = 0.f; o.pp[y] = 0.f; o.ss[y] = 0.f; o.xx[y] = 0.f; }
+    for (int y = 0; y < 4; ++y) { o.rr[y] = 0.f; o.pp[y] = 0.f; o.xx[y] = 0.f; }
     o.ri = 1.f;
     if (i < row1 && j0 < N) {
       ld4<float>(o.rr, Res + i * N, j0, N, vec);
       ld4<float>(o.pp, P + i * N, j0, N, vec);
-      ld4<float>(o.ss, Sv + i * N, j0, N, vec);
       ld4<float>(o.xx, X + i * N, j0, N, vec);
       o.ri = rv[i];
     }
@@ -533,21 +498,23 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       const float ri = cur.ri;
       const float rinv = 1.f / ri;
       const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
-      float pn[4], sn[4], xn[4], rn[4];
+      float pn[4], xn[4], rn[4];
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
+        // the step of passH: p = z + beta p, q = HA T/(N-1) + r_i p, x += alpha p, r -= alpha q
         const float uu = uv[y] * tsi[y];
         const float zz = PC ? cur.rr[y] * rinv : cur.rr[y];
-        const float ww = PC ? uu + cur.rr[y] : fmaf(ri, cur.rr[y], uu);
         pn[y] = be[y] == 0.f ? zz : fmaf(be[y], cur.pp[y], zz);
-        sn[y] = be[y] == 0.f ? ww : fmaf(be[y], cur.ss[y], ww);
+        const float qq = fmaf(ri, pn[y], uu);
         xn[y] = fmaf(al[y], pn[y], cur.xx[y]);
-        rn[y] = fmaf(-al[y], sn[y], cur.rr[y]);
+        rn[y] = fmaf(-al[y], qq, cur.rr[y]);
         const float zn = PC ? rn[y] * rinv : rn[y];
         const bool live = valid && j0 + y < N;
         if (live) {
-          sg[y] = PC ? fmaf(rn[y], zn, sg[y]) : fmaf(ri * rn[y], rn[y], sg[y]);
-          sr[y] = fmaf(rn[y], rn[y], sr[y]);
+          s1[y] = fmaf(rn[y], zn, s1[y]);
+          s2[y] = fmaf(rn[y], rn[y], s2[y]);
+          s3[y] = fmaf(ri * zn, zn, s3[y]);
+          s4[y] = fmaf(ri * zn, pn[y], s4[y]);
         }
         const float zv = live ? zn * zsc[y] : 0.f;
         const T16 zh = H16<T16>::from(zv);
@@ -556,7 +523,6 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       }
       if (valid) {
         st4<float>(P + i * N, j0, N, vec, pn);
-        st4<float>(Sv + i * N, j0, N, vec, sn);
         st4<float>(X + i * N, j0, N, vec, xn);
         st4<float>(Res + i * N, j0, N, vec, rn);
       }
@@ -608,22 +574,24 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   }
   tc_fence_before();
   __syncthreads();
-  // column sums: the RI row sweeps of each column, in a fixed order (the z region is free)
+  // column sums [(r, z) | (r, r) | sum r_i z^2 | sum r_i z p]: the RI row sweeps of each
+  // column, in a fixed order (the z region is free)
   double* red = reinterpret_cast<double*>(sBg);
 #pragma unroll
   for (int y = 0; y < 4; ++y) {
-    red[ti * NT + j0 + y] = (double)sg[y];
-    red[RI * NT + ti * NT + j0 + y] = (double)sr[y];
+    red[(0 * RI + ti) * NT + j0 + y] = (double)s1[y];
+    red[(1 * RI + ti) * NT + j0 + y] = (double)s2[y];
+    red[(2 * RI + ti) * NT + j0 + y] = (double)s3[y];
+    red[(3 * RI + ti) * NT + j0 + y] = (double)s4[y];
   }
   __syncthreads();
   if (t < N) {
-    double a = 0.0, bb = 0.0;
-    for (int qq = 0; qq < RI; ++qq) {
-      a += red[qq * NT + t];
-      bb += red[RI * NT + qq * NT + t];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double a = 0.0;
+      for (int qq = 0; qq < RI; ++qq) a += red[(cc * RI + qq) * NT + t];
+      out[N * N + cc * N + t] = a;
     }
-    out[N * N + t] = a;
-    out[N * N + N + t] = bb;
   }
   __syncthreads();
 }
@@ -687,6 +655,80 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
   __syncthreads();
 }
 
+// The recursive form of stage_Tt16 for the one-reduction Hestenes-Stiefel step (see passH in
+// cg_device.cuh): T_{k+1} = Tz + beta_j T_k with Tz the reduced HA^T z_{k+1} (FP32 at the
+// start of Tred) and T_k read from the global copy Tprev (not read where beta_j = 0); CTA 0
+// writes T_{k+1} to Tnext for the next step (a ping-pong pair; every CTA computes the same
+// values in the same order). With `step`, beta_j = gamma_{k+1}/gamma_k is formed from the
+// reduced column sums and the column's scalars are advanced as in stage_T_rec. Then the
+// column norms (tn2, FP64 from compensated FP32 sums), the per-column scale ts and the split
+// B operand of the u MMA, as in stage_Tt16.
+template <typename T16, int NT, int TERMS>
+__device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int N, double inv, const float* Tprev,
+                               float* Tnext, bool write_next, float* beta, bool step, const int* s_active,
+                               double* s_sig, double* s_den, double* s_gam, int* s_iters, T16* sBu,
+                               float* ts, double* tn2, double* scratch) {
+  constexpr int L = kThreads / NT, KQ = NT / L;
+  const int t = threadIdx.x, j = t % NT, k0 = t / NT;
+  const float* T32 = reinterpret_cast<const float*>(Tred);
+  float v[KQ];
+#pragma unroll
+  for (int q = 0; q < KQ; ++q) {
+    const int k = k0 + q * L;
+    v[q] = (k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f;
+  }
+  float bj = 0.f;
+  double g1 = 0.0;
+  const bool act = step && j < N && s_active[j];
+  if (act) {
+    g1 = __ldcg(Tred + N * N + j);
+    bj = (float)(g1 / s_sig[j]);
+  }
+  SqAcc acc;
+#pragma unroll
+  for (int q = 0; q < KQ; ++q) {
+    const int k = k0 + q * L;
+    if (bj != 0.f && k < N) v[q] = fmaf(bj, __ldcg(Tprev + k * N + j), v[q]);
+    if (write_next && k < N && j < N) Tnext[k * N + j] = v[q];
+    acc.add(v[q]);
+  }
+  scratch[t] = acc.value();
+  __syncthreads();   // every read of s_sig above precedes the updates below
+  if (t < NT) {
+    double sum = 0.0;
+    for (int q = 0; q < L; ++q) sum += scratch[q * NT + t];
+    tn2[t] = sum;
+    const double rms = sqrt(sum / (double)(N > 0 ? N : 1)) * inv;
+    ts[t] = (t < N && rms > 0.0) ? (float)(1.0 / rms) : 1.f;
+    ts[NT + t] = (t < N && rms > 0.0) ? (float)rms : 1.f;   // 1/ts: undoes the scale on u
+    if (step) {
+      if (act) {
+        const double g2 = __ldcg(Tred + N * N + N + t);
+        const double g3 = __ldcg(Tred + N * N + 2 * N + t), g4 = __ldcg(Tred + N * N + 3 * N + t);
+        const double be = g1 / s_sig[t];
+        s_den[t] = g3 + 2.0 * be * g4 + be * be * s_den[t];
+        s_sig[t] = g1;
+        s_gam[t] = g2;
+        s_iters[t] += 1;
+      }
+      beta[t] = bj;
+    }
+  }
+  __syncthreads();
+  const float inv_f = (float)inv;
+  const float tsj = ts[j];
+#pragma unroll
+  for (int q = 0; q < KQ; ++q) {
+    const int k = k0 + q * L;
+    const float x = v[q] * inv_f * tsj;
+    const T16 hi = H16<T16>::from(x);
+    sBu[core_idx(j, k, NT)] = hi;
+    if (TERMS == 3) sBu[NT * NT + core_idx(j, k, NT)] = H16<T16>::from(x - H16<T16>::to(hi));
+  }
+  fence_async_smem();
+  __syncthreads();
+}
+
 struct MixedParams {
   int64_t m;
   int N;
@@ -708,6 +750,7 @@ struct MixedParams {
   double* Tred;
   double* rrpart;
   double* W;
+  float* Tk;        // [2][N][N] the recursively updated T of the step (written by CTA 0)
   double tol, inner_tol, itol_floor;
   int max_iter, refresh_every;
   int* col_iters;
@@ -753,7 +796,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   const int64_t rows_per = (p.m + G - 1) / G;
   const int64_t row0 = imin64(p.m, (int64_t)b * rows_per);
   const int64_t row1 = imin64(p.m, row0 + rows_per);
-  const int NE = N * N + 2 * N;
+  const int NE = N * N + 4 * N;   // [N x N Gram | four N-vectors of column sums]
   GridBarrier bar{p.bar, reinterpret_cast<int*>(p.bar + 1), p.status, (unsigned)G, 0u};
   const double inv_nm1 = 1.0 / (double)(N - 1);
   double* Tp = p.Tpart + (int64_t)b * NE;
@@ -799,24 +842,31 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   }
   int total = 0, cycles = 0;
   while (ok) {
-    // ---- inner solve of S X = B from X = 0: first reduction of [HA^T z | slot A | slot B]
+    // ---- inner solve of S X = B from X = 0 in the one-reduction Hestenes-Stiefel form: the
+    // first reduction gives [HA^T z_0 | sum r_i z_0^2 | (r_0, r_0)], T_0 = HA^T z_0
     {
       ProSetup<float, PC> pro{p.B, p.X, p.Res, p.r32, N};
       passA<float, NT, ProSetup<float, PC>, PC>(p.HA32, row0, row1, N, p.r32, true, pro, uni, Tp);
     }
+    if (t < N) {
+      Tp[N * N + 2 * N + t] = 0.0;
+      Tp[N * N + 3 * N + t] = 0.0;
+    }
     if (!(ok = bar.sync())) break;
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
     if (!(ok = bar.sync())) break;
-    stage_Tt16<T16, NT, TERMS>(p.Tred, N, inv_nm1, sBu, s_ts, s_tn2, scratch);
+    int tbuf = 0;   // the global copy of T_k the next staging reads
+    stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, p.Tk, p.Tk, b == 0, s_beta_v, false, s_active, s_sig,
+                                   s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
     if (t < NT) {
-      const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;
-      const double gm = t < N ? __ldcg(p.Tred + N * N + N + t) : 0.0;
-      s_sig[t] = sg;
+      const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;       // sum r_i z_0^2
+      const double gm = t < N ? __ldcg(p.Tred + N * N + N + t) : 0.0;   // (r_0, r_0)
+      s_sig[t] = PC ? sg : gm;   // gamma = (r, z)
+      s_den[t] = sg;             // sum r_i p^2
+      s_beta_v[t] = 0.f;         // the first step takes p = z
       s_gam[t] = gm;
       s_bn2[t] = gm;   // residual norm^2 at the start of this inner solve
       s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
-      s_alpha[t] = 0.0;
-      s_den[t] = 0.0;
     }
     __syncthreads();
     int it = 0;
@@ -825,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       if (t < NT) {
         int a = s_active[t];
         const double gm = s_gam[t];
-        double al = 0.0, be = 0.0;
+        double al = 0.0;
         if (a && !isfinite(gm)) { atomicOr(p.status, DS_NONFINITE); a = 0; }
         // the inner solve of this column ends once its residual fell by the factor s_itol
         // (compared in squares: FP64 square roots are costly on this part's FP64 pipe)
@@ -834,47 +884,36 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
           if (gm <= itf * itf * s_bn2[t]) a = 0;
         }
         if (a) {
-          // beta gamma / alpha_old = beta^2 den_old (alpha_old = gamma_old / den_old)
-          const double cg = PC ? s_sig[t] : gm;
-          const double delta = s_tn2[t] * inv_nm1 + s_sig[t];
-          double den = delta;
-          if (it > 0) {
-            be = cg / s_gold[t];
-            den = delta - be * be * s_den[t];
-          }
-          // p^T S p = delta - beta gamma/alpha_old cancels; with BF16/FP16 contractions a
-          // small or non-positive value means the low-precision recurrences have drifted:
-          // this column's inner solve ends here and the refresh restarts it
-          if (!isfinite(den) || !(den > 0.05 * delta)) { a = 0; be = 0.0; }
-          else al = cg / den;
-          s_den[t] = den;
+          // alpha = gamma / (p, S p), (p, S p) = ||T||^2/(N-1) + sum r_i p^2; a non-positive or
+          // non-finite value means the low-precision recurrences have drifted: this column's
+          // inner solve ends here and the refresh restarts it
+          const double pq = s_tn2[t] * inv_nm1 + s_den[t];
+          if (!isfinite(pq) || !(pq > 0.0)) a = 0;
+          else al = s_sig[t] / pq;
         }
         s_active[t] = a;
         s_alpha[t] = al;
         s_alpha_v[t] = (float)al;
-        s_beta_v[t] = (float)be;
         s_zs[t] = (t < N && gm > 0.0) ? (float)(1.0 / sqrt(gm)) : 1.f;
         my_active = a;
       }
       const int any = __syncthreads_or(my_active);
       if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
       if constexpr (NT <= 64)
-        passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+        passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                         s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       else
-        passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.Sv, p.r32, s_alpha_v,
+        passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                       s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       if (!(ok = bar.sync() && ok)) break;
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
       if (!(ok = bar.sync())) break;
-      stage_Tt16<T16, NT, TERMS>(p.Tred, N, inv_nm1, sBu, s_ts, s_tn2, scratch);
-      if (t < N && s_active[t]) {
-        s_iters[t] += 1;
-        s_gold[t] = PC ? s_sig[t] : s_gam[t];
-        s_gam[t] = __ldcg(p.Tred + N * N + N + t);
-        s_sig[t] = __ldcg(p.Tred + N * N + t);
-      }
-      __syncthreads();
+      // beta, T_{k+1} = HA^T z_{k+1} + beta T_k (from the global copy of T_k), the scalars
+      const float* Tprev = p.Tk + (size_t)tbuf * N * N;
+      float* Tnext = p.Tk + (size_t)(tbuf ^ 1) * N * N;
+      stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, Tprev, Tnext, b == 0, s_beta_v, true, s_active,
+                                     s_sig, s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
+      tbuf ^= 1;
       ++it;
     }
     if (!ok) break;
