@@ -32,7 +32,7 @@ cudaError_t plan_solve_mixed(enkf_handle_s* h) {
   if (err != cudaSuccess) return err;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   // tensor memory: at most 512 columns per SM
-  const int tmem_cap = 512 / (NT == 32 ? 64 : 2 * NT);
+  const int tmem_cap = 512 / (NT == 32 ? tc_tmem_cols<32>() : (NT == 64 ? tc_tmem_cols<64>() : tc_tmem_cols<128>()));
   occ = std::min(occ, tmem_cap);
   const int max_coresident = occ * h->sms;
   int G = (int)std::min<int64_t>(max_coresident, std::max<int64_t>(1, (h->cfg.m + kTR - 1) / kTR));

@@ -105,7 +105,9 @@ __device__ __forceinline__ int core_idx(int r, int k, int Kd) {
 
 constexpr int kTR = 128;  // rows per tile = M of the u MMA = K of the Gram MMA
 
-template <int NT> __host__ __device__ constexpr int tc_tmem_cols() { return (2 * NT) < 32 ? 32 : 2 * NT; }
+// TMEM columns (a power of two >= 32): NT <= 64 keeps two u slots and the Gram (3 NT), NT = 128
+// one u and the Gram (2 NT)
+template <int NT> __host__ __device__ constexpr int tc_tmem_cols() { return NT <= 32 ? 128 : (NT <= 64 ? 256 : 2 * NT); }
 
 // ------------------------------------------------------------------ fused tensor-core CG step
 // Same recurrences as passF (Chronopoulos-Gear arrangement, optionally preconditioned by R);
@@ -133,8 +135,12 @@ template <int NT, int TERMS> struct TcLayout {
   static constexpr int AU = kTR * NT, BU = NT * NT;                  // elements per part
   static constexpr int TILE = TM * AU;                               // elements per tile image
   static constexpr int AUB = TILE * 2;                               // bytes per tile image
-  static constexpr uint32_t LBOG = DB ? 144 : 128;                   // z operand: K core stride
-  static constexpr uint32_t SBOG = 16 * LBOG;                        // 16 cores along K = 128
+  // z operand strides. NT <= 64: each warp writes one row i across 64 columns j, so the
+  // j-direction core stride is 16 B off a multiple of 128 B (2-way bank conflicts at most,
+  // against 8-way with a 128-B multiple); NT = 128: each warp writes 32 rows i of one column,
+  // K-direction core stride 128 B (smem is too tight for padding there).
+  static constexpr uint32_t LBOG = 128;                              // z operand: K core stride
+  static constexpr uint32_t SBOG = DB ? 16 * LBOG + 16 : 16 * LBOG;  // M core stride
   static constexpr int BGP = (int)(16 * SBOG);                       // bytes per z part (M = 128)
   static constexpr int n_au = DB ? 2 : 1;
   static constexpr int off_au = 0;
@@ -378,7 +384,7 @@ template <typename T16, int NT, bool PC, int TERMS>
 __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t row1, int N, float* X,
                             float* Res, float* P, const float* __restrict__ rv,
                             const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
-                            uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g,
+                            uint64_t* mbar_u2, uint64_t* mbar_g, uint32_t* ph_u2, uint32_t& ph_g,
                             int* status, bool& ok, double* __restrict__ out) {
   using L = TcLayout<NT, TERMS>;
   static_assert(L::DB, "NT <= 64 only");
@@ -389,6 +395,8 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   constexpr int HALF = NT / 2, CH = HALF / 16;    // TMEM read-out: columns per warp half
   constexpr int NG = NT / 4, GM = NG - 1;         // 4-float column groups, swizzle mask
   constexpr int NJ = NG, RI = kThreads / NJ;      // update: threads per row, rows per sweep
+  constexpr int SWEEPS = kTR / RI, SMID = SWEEPS / 2;
+  constexpr uint32_t sbo_u = (NT / 8) * 128;
   unsigned char* sAu0 = tcs + L::off_au;
   const T16* sBu = reinterpret_cast<const T16*>(tcs + L::off_bu);
   unsigned char* sBg = tcs + L::off_bg;
@@ -399,7 +407,8 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   const int qd = warp & 3, half = warp >> 2;
   const int rt = 32 * qd + lane;
   const int tj = t % NJ, ti = t / NJ, j0 = 4 * tj;
-  const uint32_t d_u = tmem, d_g = tmem + NT;
+  // TMEM: u of tile q in slot q % 2 (columns [slot NT, slot NT + NT)), the Gram at 2 NT
+  const uint32_t d_g = tmem + 2 * NT;
   const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
   const unsigned char* gimg = reinterpret_cast<const unsigned char*>(img);
   auto au_src = [&](int q) { return gimg + (size_t)q * L::AUB; };
@@ -407,6 +416,21 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   auto bg_ptr = [&](int part, int j, int i) {
     return reinterpret_cast<T16*>(sBg + part * L::BGP + (j >> 3) * L::SBOG + (i >> 3) * L::LBOG +
                                   (((j & 7) * 8 + (i & 7)) * 2));
+  };
+  // u = HA T of tile q (image in buffer q % 2) into TMEM slot q % 2, completion on mbar_u2[q % 2]
+  auto issue_u = [&](int q) {
+    tc_fence_after();
+    const uint32_t au = smem_addr(sAu(q)), bu = smem_addr(sBu);
+    const uint32_t d_u = tmem + (uint32_t)((q & 1) * NT);
+#pragma unroll
+    for (int kb = 0; kb < NT / 16; ++kb) {
+      umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
+      if (SPLIT) {
+        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
+        umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
+      }
+    }
+    umma_commit(&mbar_u2[q & 1]);
   };
   // per-column constants of the thread's four columns
   float al[4], be[4], tsi[4], zsc[4];
@@ -424,10 +448,6 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   }
   float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
   float s3[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
-  if (Qb > 0) {
-    tc_copy(sAu(0), au_src(0), L::AUB);
-    tc_cp_commit();
-  }
   const bool vec = (N & 3) == 0;
   // the operands of one row sweep of the update: r, p, x of the thread's four columns and
   // r_i; loaded one sweep ahead so that their latency overlaps the previous sweep
@@ -444,36 +464,27 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       o.ri = rv[i];
     }
   };
-  for (int q = 0; q < Qb && ok; ++q) {
-    const int64_t i0 = row0 + (int64_t)q * kTR;
+  // Pipeline over the CTA's tiles: u of tile q + 1 is issued half-way through the update of
+  // tile q (its image is copied at the start of tile q, once the Gram of tile q - 1, the last
+  // reader of that buffer, has completed); the Gram of tile q runs behind the read-out of
+  // tile q + 1 and is waited for only before the z operand is rewritten.
+  if (Qb > 0) {
+    tc_copy(sAu(0), au_src(0), L::AUB);
+    tc_cp_commit();
     tc_cp_wait_all();
     fence_async_smem();
     __syncthreads();
+    if (t == 0) issue_u(0);
+  }
+  for (int q = 0; q < Qb && ok; ++q) {
+    const int64_t i0 = row0 + (int64_t)q * kTR;
     Ops cur;
-    load_ops(i0, ti, cur);   // the first sweep's operands, in flight during the u MMA
-    if (q + 1 < Qb) {   // next tile's image into the other buffer, behind this whole tile
-      tc_copy(sAu(q + 1), au_src(q + 1), L::AUB);
-      tc_cp_commit();
-    }
-    const uint32_t au = smem_addr(sAu(q));
-    constexpr uint32_t sbo_u = (NT / 8) * 128;
-    if (t == 0) {
-      tc_fence_after();
-      const uint32_t bu = smem_addr(sBu);
-#pragma unroll
-      for (int kb = 0; kb < NT / 16; ++kb) {
-        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
-        if (SPLIT) {
-          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
-          umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
-        }
-      }
-      umma_commit(mbar_u);
-    }
-    if (!mbar_wait(mbar_u, ph_u, status)) ok = false;
-    ph_u ^= 1u;
+    load_ops(i0, ti, cur);   // the first sweep's operands, in flight during the wait
+    if (!mbar_wait(&mbar_u2[q & 1], ph_u2[q & 1], status)) ok = false;
+    ph_u2[q & 1] ^= 1u;
     tc_fence_after();
     // u out of TMEM, one row per thread, into the swizzled staging tile
+    const uint32_t d_u = tmem + (uint32_t)((q & 1) * NT);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int jc = half * HALF + 16 * c;
@@ -488,8 +499,27 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     }
     tc_fence_before();
     __syncthreads();
+    // the Gram of tile q - 1 reads the z operand and the image buffer of tile q + 1
+    if (q > 0) {
+      if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
+      ph_g ^= 1u;
+      tc_fence_after();
+    }
+    const bool more = q + 1 < Qb;
+    if (more) {
+      tc_copy(sAu(q + 1), au_src(q + 1), L::AUB);
+      tc_cp_commit();
+    }
     // the CG update, NT/4 threads per row
-    for (int r = ti; r < kTR; r += RI) {
+    int sw = 0;
+    for (int r = ti; r < kTR; r += RI, ++sw) {
+      if (sw == SMID && more) {
+        // the next tile's image has had half a tile to land: start its u MMA
+        tc_cp_wait_all();
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) issue_u(q + 1);
+      }
       const int64_t i = i0 + r;
       const bool valid = i < row1 && j0 < N;
       Ops nxt;
@@ -535,7 +565,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       tc_fence_after();
       // B = the same tile image read MN-major: K = rows (row-group stride sbo_u, two per K
       // block of 16), N = NT (core stride 128 B)
-      const uint32_t bg = smem_addr(sBg);
+      const uint32_t au = smem_addr(sAu(q)), bg = smem_addr(sBg);
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
@@ -550,6 +580,9 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       }
       umma_commit(mbar_g);
     }
+  }
+  // the last tile's Gram completes the partial in TMEM
+  if (Qb > 0) {
     if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
     ph_g ^= 1u;
     tc_fence_after();
@@ -763,7 +796,7 @@ struct MixedParams {
 template <typename T16, int NT, bool PC, int TERMS>
 __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[4];   // u (NT = 128), Gram, u slots 0 and 1 (NT <= 64)
   __shared__ uint32_t tmem_base;
   double* s_gam = reinterpret_cast<double*>(smem);
   double* s_gold = s_gam + NT;
@@ -804,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   const T16* img = static_cast<const T16*>(p.HA16) + (size_t)b * p.qmax * TL::TILE;
   constexpr int TMC = tc_tmem_cols<NT>();
 
-  if (t == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); }
+  if (t == 0) { mbar_init(&mbar[0]); mbar_init(&mbar[1]); mbar_init(&mbar[2]); mbar_init(&mbar[3]); }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)), "r"(TMC));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -814,6 +847,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   uint32_t ph_u = 0, ph_g = 0;
+  uint32_t ph_u2[2] = {0u, 0u};
   int par = 0;
   bool ok = true;
 
@@ -901,7 +935,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
       if constexpr (NT <= 64)
         passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
-                                        s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+                                        s_beta_v, uni, tmem, &mbar[2], &mbar[1], ph_u2, ph_g, p.status, ok, Tp);
       else
         passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                       s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
