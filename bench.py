@@ -122,9 +122,10 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
             "cg_iterations": iters, "refreshes": refreshes, "hbm_frac": t_b / t}
 
 # DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
-# captures summarised under profiles/, with the hash of the kernel sources each capture
-# measured; reported as null once those sources have changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 4.646017e9, "src_sha": "f359344179649ea3"},
+# captures summarised under profiles/ (FP32: solve_kernel_fp32_hs_grf512_N64_m65536.md), with
+# the hash of the kernel sources each capture measured; reported as null once those sources
+# have changed.
+NCU_TRAFFIC = {"fp32": {"bytes": 1.491656e9, "src_sha": "6e873226f765b161"},
                "fp16": {"bytes": 6.431757e9, "src_sha": "18d941411bdfab5b"}}
 # DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
 # profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
