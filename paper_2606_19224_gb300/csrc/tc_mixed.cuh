@@ -449,8 +449,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
   float s3[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
   const bool vec = (N & 3) == 0;
-  // the operands of one row sweep of the update: r, p, x of the thread's four columns and
-  // r_i; loaded one sweep ahead so that their latency overlaps the previous sweep
+  // the operands of one row sweep of the update: r, p, x of the thread's four columns and r_i
   struct Ops { float rr[4], pp[4], xx[4], ri; };
   auto load_ops = [&](int64_t i0, int r, Ops& o) {
     const int64_t i = i0 + r;
@@ -478,8 +477,11 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   }
   for (int q = 0; q < Qb && ok; ++q) {
     const int64_t i0 = row0 + (int64_t)q * kTR;
-    Ops cur;
-    load_ops(i0, ti, cur);   // the first sweep's operands, in flight during the wait
+    // every sweep's operands of this tile, in flight during the wait and the read-out (one
+    // L2 round trip per tile instead of one per sweep)
+    Ops ops[SWEEPS];
+#pragma unroll
+    for (int sw = 0; sw < SWEEPS; ++sw) load_ops(i0, ti + sw * RI, ops[sw]);
     if (!mbar_wait(&mbar_u2[q & 1], ph_u2[q & 1], status)) ok = false;
     ph_u2[q & 1] ^= 1u;
     tc_fence_after();
@@ -511,8 +513,9 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       tc_cp_commit();
     }
     // the CG update, NT/4 threads per row
-    int sw = 0;
-    for (int r = ti; r < kTR; r += RI, ++sw) {
+#pragma unroll
+    for (int sw = 0; sw < SWEEPS; ++sw) {
+      const int r = ti + sw * RI;
       if (sw == SMID && more) {
         // the next tile's image has had half a tile to land: start its u MMA
         tc_cp_wait_all();
@@ -522,8 +525,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       }
       const int64_t i = i0 + r;
       const bool valid = i < row1 && j0 < N;
-      Ops nxt;
-      if (r + RI < kTR) load_ops(i0, r + RI, nxt);
+      const Ops& cur = ops[sw];
       const float4 u4 = *reinterpret_cast<const float4*>(sU + r * NT + ((tj ^ (r & GM)) * 4));
       const float ri = cur.ri;
       const float rinv = 1.f / ri;
@@ -556,7 +558,6 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
         st4<float>(X + i * N, j0, N, vec, xn);
         st4<float>(Res + i * N, j0, N, vec, rn);
       }
-      if (r + RI < kTR) cur = nxt;
     }
     tc_fence_before();
     fence_async_smem();
