@@ -209,6 +209,8 @@ cudaError_t plan_solve_mixed(enkf_handle_s* h);
 cudaError_t launch_solve_mixed(enkf_handle_s* h);
 size_t mixed_image_bytes(const enkf_handle_s* h);   // tile images of HA (zeroed at create)
 cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa);
+// kernels_update_tc.cu: X_a = X_f + A W on the tensor cores (FP32 ensembles)
+cudaError_t launch_update_tc(enkf_handle_s* h, const void* Xf, void* Xa);
 cudaError_t launch_update_product(enkf_handle_s* h, const void* Xf, void* Xa);
 // kernels_reduced.cu: Gram pass + N x N CG of CGD-EnKF-Reduced; V lands in ws.W,
 // G in ws.Tred, M in ws.Wacc; the CTA partials use ws.Tpart ([reduced_grid][2 N N]).

@@ -219,6 +219,8 @@ static cudaError_t launch_update_mode(enkf_handle_s* h, const void* Xf, void* Xa
 }
 
 cudaError_t launch_update(enkf_handle_s* h, const void* Xf, void* Xa) {
+  // FP32 ensembles: the A W product on the tensor cores (kernels_update_tc.cu); FP64 on CUDA cores
+  if (h->cfg.precision != ENKF_FP64) return launch_update_tc(h, Xf, Xa);
   return launch_update_mode<0>(h, Xf, Xa);
 }
 
