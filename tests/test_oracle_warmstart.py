@@ -215,3 +215,29 @@ def test_forward_two_hidden_layers_evaluated_by_hand():
     g2 = [_gelu_by_hand(0.3 * g1[0] - 0.2 * g1[1]), _gelu_by_hand(0.1 * g1[0] + 0.4 * g1[1] - 1.0)]
     swapped = -3.0 + 0.5 * (0.75 * g2[0] - 1.25 * g2[1] - 0.05)
     assert abs(Y[0, 0] - swapped) > 1e-3
+
+
+def test_start_residual_amplifies_coefficient_error():
+    """The decoded start's residual is linear in the coefficient error, HA A (C - W) with
+    A = I + HA^T R^-1 HA/(N-1) (closed form from S = HA HA^T/(N-1) + R), so its size relative
+    to ||d_j|| (the zero start's residual) is the coefficient error amplified by A's spectrum,
+    which grows with m. On the 512^2 GRF workload shrunk 4x per side (m = 4,096, N = 64) a 5 %
+    error in c_j already gives a start residual above ||d_j||: the true-residual judge of the
+    learned start then prefers the zero start."""
+    from synth.problems import workload
+    P = workload("grf512_N64_m65536", seed=3, scale=4)
+    N = P.N
+    E = np.random.default_rng(1).standard_normal((P.m, N)) * np.sqrt(P.r)[:, None]
+    _, info = oracle.cgd_enkf(P.Xf, P.rowptr, P.col, P.w, P.r, P.y, E, tol=1e-12)
+    HA, D, Z = info["Zhat"], info["D"], info["Z"]
+    W = HA.T @ Z / (N - 1)
+    dn = np.linalg.norm(D, axis=0)
+    # exact coefficients: the start is the solution, its residual is the CG tolerance's
+    assert np.max(np.linalg.norm(ws.start_residual(HA, D, P.r, W), axis=0) / dn) < 1e-9
+    Dl = np.random.default_rng(2).standard_normal(W.shape)
+    Dl *= 0.05 * np.linalg.norm(W, axis=0) / np.linalg.norm(Dl, axis=0)
+    res = ws.start_residual(HA, D, P.r, W + Dl)
+    A = np.eye(N) + HA.T @ (HA / P.r[:, None]) / (N - 1)
+    assert np.max(np.abs(res - HA @ (A @ Dl))) < 1e-8 * np.max(np.abs(res))
+    rel = np.linalg.norm(res, axis=0) / dn
+    assert np.median(rel) > 1.0
