@@ -11,6 +11,9 @@ namespace enkf {
 // NT = padded column count (N <= NT). Pass A (T = HA^T V): MA x MA register tile per
 // thread over (k, j), TRA rows of HA and V staged in shared memory per step, RG row groups.
 // Pass B (Q = HA T): 4 x 4 register tile per thread over (i, j), TRB rows per tile.
+// Phase timer slots of the persistent solves (CTA 0, thread 0): accumulated ns per phase.
+enum : int { PH_SETUP = 0, PH_PASS, PH_BAR1, PH_RED, PH_BAR2, PH_SCAL, PH_REFRESH, PH_COUNT = 8 };
+
 template <int NT> struct Tile;
 template <> struct Tile<32> { static constexpr int MA = 4, TRA = 32, TRB = 128; };
 template <> struct Tile<64> { static constexpr int MA = 4, TRA = 32, TRB = 64; };

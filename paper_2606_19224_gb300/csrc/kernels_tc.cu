@@ -109,6 +109,7 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.col_true = ws.col_true;
   p.status = ws.status;
   p.bar = ws.bar;
+  p.prof = h->prof_enabled ? ws.prof : nullptr;
   cudaError_t err = cudaMemsetAsync(ws.bar, 0, 4 * sizeof(unsigned), h->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);
   if (err != cudaSuccess) return err;

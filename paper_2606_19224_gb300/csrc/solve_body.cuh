@@ -44,8 +44,6 @@ struct SolveParams {
   double* col_warm;          // [N] relative residual ||B_j|| / ||d_j|| of that start
 };
 
-// Phase timer slots (CTA 0, thread 0): accumulated ns per phase of the solve.
-enum : int { PH_SETUP = 0, PH_PASS, PH_BAR1, PH_RED, PH_BAR2, PH_SCAL, PH_REFRESH, PH_COUNT = 8 };
 
 // The persistent solve of one problem by G co-resident CTAs (this one is number b), with the
 // grid barrier `bar` over exactly those CTAs: the whole grid for one analysis, a team of the

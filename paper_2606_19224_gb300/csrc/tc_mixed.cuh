@@ -105,6 +105,11 @@ __device__ __forceinline__ int core_idx(int r, int k, int Kd) {
 
 constexpr int kTR = 128;  // rows per tile = M of the u MMA = K of the Gram MMA
 
+// two 16-bit values as one 32-bit word, `a` at the lower address
+template <typename T16> __device__ __forceinline__ uint32_t pack16(T16 a, T16 b) {
+  return (uint32_t)reinterpret_cast<const uint16_t&>(a) | ((uint32_t)reinterpret_cast<const uint16_t&>(b) << 16);
+}
+
 // TMEM columns (a power of two >= 32): NT <= 64 keeps two u slots and the Gram (3 NT), NT = 128
 // one u and the Gram (2 NT)
 template <int NT> __host__ __device__ constexpr int tc_tmem_cols() { return NT <= 32 ? 128 : (NT <= 64 ? 256 : 2 * NT); }
@@ -153,7 +158,9 @@ template <int NT, int TERMS> struct TcLayout {
   // NT <= 64: the tile's u = HA T read out of TMEM, staged as FP32 [128][NT] (swizzled 4-float
   // groups) for the coalesced epilogue
   static constexpr int off_u = off_ts + 8 * NT;
-  static constexpr int bytes = DB ? off_u + kTR * NT * 4 : off_ts + 8 * NT;
+  // NT <= 64: T_k of the Hestenes-Stiefel recurrence, FP32 [NT][NT] (stage_Tt16_rec)
+  static constexpr int off_tk = off_u + kTR * NT * 4;
+  static constexpr int bytes = DB ? off_tk + NT * NT * 4 : off_ts + 8 * NT;
   static_assert(off_bu % 1024 == 0 && off_bg % 1024 == 0 && off_u % 16 == 0, "operand alignment");
 };
 
@@ -217,14 +224,19 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
       tc_fence_after();
       constexpr uint32_t sbo_u = (NT / 8) * 128;
       const uint32_t au = smem_addr(sAu), bu = smem_addr(sBu);
+      // split operands: the small cross terms hi*lo + lo*hi first, then hi*hi, so that each
+      // addition into the FP32 accumulator rounds against the smaller partial sum first
+      if (SPLIT) {
 #pragma unroll
-      for (int kb = 0; kb < NT / 16; ++kb) {
-        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
-        if (SPLIT) {
-          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
+        for (int kb = 0; kb < NT / 16; ++kb) {
+          umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
           umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
         }
       }
+#pragma unroll
+      for (int kb = 0; kb < NT / 16; ++kb)
+        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc,
+                 (kb > 0 || SPLIT) ? 1u : 0u);
       umma_commit(mbar_u);
     }
     const int64_t i = i0 + rt;
@@ -319,17 +331,23 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
       // K block of 16), N = NT (core stride 128 B)
       const uint32_t au = smem_addr(sAu), bg = smem_addr(sBg);
       constexpr uint32_t kst = (NT / 8) * 128;
+      // split operands: the cross terms of the tile first, then hi*hi
+      if (SPLIT) {
+#pragma unroll
+        for (int kb = 0; kb < kTR / 16; ++kb) {
+          const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B0 = umma_desc(au + kb * 2 * kst, kst, 128);
+          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * kst, kst, 128);
+          umma_f16(d_g, A0, B1, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
+          umma_f16(d_g, A1, B0, idesc_g, 1u);
+        }
+      }
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
         const uint64_t B0 = umma_desc(au + kb * 2 * kst, kst, 128);
-        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
-        if (SPLIT) {
-          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * kst, kst, 128);
-          umma_f16(d_g, A0, B1, idesc_g, 1u);
-          umma_f16(d_g, A1, B0, idesc_g, 1u);
-        }
+        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0 && !SPLIT) ? 0u : 1u);
       }
       umma_commit(mbar_g);
     }
@@ -422,14 +440,18 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     tc_fence_after();
     const uint32_t au = smem_addr(sAu(q)), bu = smem_addr(sBu);
     const uint32_t d_u = tmem + (uint32_t)((q & 1) * NT);
+    // split operands: the small cross terms first, then hi*hi (as in passF_tc2)
+    if (SPLIT) {
 #pragma unroll
-    for (int kb = 0; kb < NT / 16; ++kb) {
-      umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
-      if (SPLIT) {
-        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, 1u);
+      for (int kb = 0; kb < NT / 16; ++kb) {
+        umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + 2 * L::BU + kb * 256, 128, sbo_u), idesc, kb > 0 ? 1u : 0u);
         umma_f16(d_u, umma_desc(au + 2 * L::AU + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc, 1u);
       }
     }
+#pragma unroll
+    for (int kb = 0; kb < NT / 16; ++kb)
+      umma_f16(d_u, umma_desc(au + kb * 256, 128, sbo_u), umma_desc(bu + kb * 256, 128, sbo_u), idesc,
+               (kb > 0 || SPLIT) ? 1u : 0u);
     umma_commit(&mbar_u2[q & 1]);
   };
   // per-column constants of the thread's four columns
@@ -567,17 +589,23 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       // B = the same tile image read MN-major: K = rows (row-group stride sbo_u, two per K
       // block of 16), N = NT (core stride 128 B)
       const uint32_t au = smem_addr(sAu(q)), bg = smem_addr(sBg);
+      // split operands: the cross terms of the tile first, then hi*hi
+      if (SPLIT) {
+#pragma unroll
+        for (int kb = 0; kb < kTR / 16; ++kb) {
+          const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B0 = umma_desc(au + kb * 2 * sbo_u, sbo_u, 128);
+          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
+          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * sbo_u, sbo_u, 128);
+          umma_f16(d_g, A0, B1, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
+          umma_f16(d_g, A1, B0, idesc_g, 1u);
+        }
+      }
 #pragma unroll
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
         const uint64_t B0 = umma_desc(au + kb * 2 * sbo_u, sbo_u, 128);
-        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
-        if (SPLIT) {
-          const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
-          const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * sbo_u, sbo_u, 128);
-          umma_f16(d_g, A0, B1, idesc_g, 1u);
-          umma_f16(d_g, A1, B0, idesc_g, 1u);
-        }
+        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0 && !SPLIT) ? 0u : 1u);
       }
       umma_commit(mbar_g);
     }
@@ -691,26 +719,33 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
 
 // The recursive form of stage_Tt16 for the one-reduction Hestenes-Stiefel step (see passH in
 // cg_device.cuh): T_{k+1} = Tz + beta_j T_k with Tz the reduced HA^T z_{k+1} (FP32 at the
-// start of Tred) and T_k read from the global copy Tprev (not read where beta_j = 0); CTA 0
-// writes T_{k+1} to Tnext for the next step (a ping-pong pair; every CTA computes the same
-// values in the same order). With `step`, beta_j = gamma_{k+1}/gamma_k is formed from the
-// reduced column sums and the column's scalars are advanced as in stage_T_rec. Then the
-// column norms (tn2, FP64 from compensated FP32 sums), the per-column scale ts and the split
-// B operand of the u MMA, as in stage_Tt16.
+// start of Tred); T_k is not read where beta_j = 0. For NT <= 64 every CTA keeps T_k in its
+// own shared memory (sTk, FP32 [NT][NT]; each entry is read and written by the same thread);
+// NT = 128 has no room for it, and T_k is read from the global copy Tprev while CTA 0 writes
+// T_{k+1} to Tnext (a ping-pong pair; every CTA computes the same values in the same order).
+// With `step`, beta_j = gamma_{k+1}/gamma_k is formed from the reduced column sums and the
+// column's scalars are advanced as in stage_T_rec. Then the column norms (tn2, FP64 from
+// compensated FP32 sums), the per-column scale ts = 2^-e (a power of two, so that the scaling
+// and its undoing on u are exact; e from the column's RMS, computed in FP32) and the split B
+// operand of the u MMA. Each thread owns pairs of consecutive k of one column j, so the two
+// 16-bit values of a pair go to shared memory in one 32-bit store (they are adjacent in the
+// core-matrix layout).
 template <typename T16, int NT, int TERMS>
 __device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int N, double inv, const float* Tprev,
-                               float* Tnext, bool write_next, float* beta, bool step, const int* s_active,
-                               double* s_sig, double* s_den, double* s_gam, int* s_iters, T16* sBu,
-                               float* ts, double* tn2, double* scratch) {
-  constexpr int L = kThreads / NT, KQ = NT / L;
-  const int t = threadIdx.x, j = t % NT, k0 = t / NT;
+                               float* Tnext, bool write_next, float* sTk, float* beta, bool step,
+                               const int* s_active, double* s_sig, double* s_den, double* s_gam, int* s_iters,
+                               T16* sBu, float* ts, double* tn2, double* scratch) {
+  constexpr int L = kThreads / NT, KP = NT / (2 * L);   // pairs of k per thread
+  const int t = threadIdx.x, j = t % NT, kp = t / NT;
   const float* T32 = reinterpret_cast<const float*>(Tred);
-  float v[KQ];
+  float v[KP][2];
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) {
-    const int k = k0 + q * L;
-    v[q] = (k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f;
-  }
+  for (int q = 0; q < KP; ++q)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * (kp + q * L) + h;
+      v[q][h] = (k < N && j < N) ? __ldcg(T32 + k * N + j) : 0.f;
+    }
   float bj = 0.f;
   double g1 = 0.0;
   const bool act = step && j < N && s_active[j];
@@ -720,21 +755,28 @@ __device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int
   }
   SqAcc acc;
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) {
-    const int k = k0 + q * L;
-    if (bj != 0.f && k < N) v[q] = fmaf(bj, __ldcg(Tprev + k * N + j), v[q]);
-    if (write_next && k < N && j < N) Tnext[k * N + j] = v[q];
-    acc.add(v[q]);
-  }
+  for (int q = 0; q < KP; ++q)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * (kp + q * L) + h;
+      if (bj != 0.f && k < N) v[q][h] = fmaf(bj, sTk ? sTk[k * NT + j] : __ldcg(Tprev + k * N + j), v[q][h]);
+      if (sTk) sTk[k * NT + j] = v[q][h];
+      else if (write_next && k < N && j < N) Tnext[k * N + j] = v[q][h];
+      acc.add(v[q][h]);
+    }
   scratch[t] = acc.value();
   __syncthreads();   // every read of s_sig above precedes the updates below
   if (t < NT) {
     double sum = 0.0;
     for (int q = 0; q < L; ++q) sum += scratch[q * NT + t];
     tn2[t] = sum;
-    const double rms = sqrt(sum / (double)(N > 0 ? N : 1)) * inv;
-    ts[t] = (t < N && rms > 0.0) ? (float)(1.0 / rms) : 1.f;
-    ts[NT + t] = (t < N && rms > 0.0) ? (float)rms : 1.f;   // 1/ts: undoes the scale on u
+    // ts = 2^(1 - e) with rms = f 2^e, f in [1/2, 1): the scaled column has RMS in [1, 2)
+    const float rms = sqrtf((float)sum * (1.f / (float)(N > 0 ? N : 1))) * (float)inv;
+    int e = 0;
+    const bool live = t < N && rms > 0.f && isfinite(rms);
+    if (live) frexpf(rms, &e);
+    ts[t] = live ? ldexpf(1.f, 1 - e) : 1.f;
+    ts[NT + t] = live ? ldexpf(1.f, e - 1) : 1.f;   // 1/ts: undoes the scale on u
     if (step) {
       if (act) {
         const double g2 = __ldcg(Tred + N * N + N + t);
@@ -752,12 +794,14 @@ __device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int
   const float inv_f = (float)inv;
   const float tsj = ts[j];
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) {
-    const int k = k0 + q * L;
-    const float x = v[q] * inv_f * tsj;
-    const T16 hi = H16<T16>::from(x);
-    sBu[core_idx(j, k, NT)] = hi;
-    if (TERMS == 3) sBu[NT * NT + core_idx(j, k, NT)] = H16<T16>::from(x - H16<T16>::to(hi));
+  for (int q = 0; q < KP; ++q) {
+    const int k = 2 * (kp + q * L);
+    const float x0 = v[q][0] * inv_f * tsj, x1 = v[q][1] * inv_f * tsj;
+    const T16 h0 = H16<T16>::from(x0), h1 = H16<T16>::from(x1);
+    *reinterpret_cast<uint32_t*>(sBu + core_idx(j, k, NT)) = pack16(h0, h1);
+    if (TERMS == 3)
+      *reinterpret_cast<uint32_t*>(sBu + NT * NT + core_idx(j, k, NT)) =
+          pack16(H16<T16>::from(x0 - H16<T16>::to(h0)), H16<T16>::from(x1 - H16<T16>::to(h1)));
   }
   fence_async_smem();
   __syncthreads();
@@ -792,6 +836,7 @@ struct MixedParams {
   double* col_true;
   int* status;
   unsigned* bar;
+  unsigned long long* prof;   // optional phase timers of CTA 0 (ns), nullptr when off
 };
 
 template <typename T16, int NT, bool PC, int TERMS>
@@ -825,6 +870,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   T16* sBu = reinterpret_cast<T16*>(uni + TL::off_bu);
   float* s_zs = reinterpret_cast<float*>(uni + TL::off_zs);
   float* s_ts = reinterpret_cast<float*>(uni + TL::off_ts);
+  float* sTk = TL::DB ? reinterpret_cast<float*>(uni + TL::off_tk) : nullptr;
 
   const int N = p.N, G = gridDim.x, b = blockIdx.x, t = threadIdx.x, warp = t >> 5;
   const int64_t rows_per = (p.m + G - 1) / G;
@@ -851,6 +897,16 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   uint32_t ph_u2[2] = {0u, 0u};
   int par = 0;
   bool ok = true;
+  const bool prof = p.prof != nullptr && b == 0 && t == 0;
+  unsigned long long ph[PH_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long tp = prof ? global_ns() : 0ull;
+  auto tick = [&](int slot) {
+    if (prof) {
+      const unsigned long long now = global_ns();
+      ph[slot] += now - tp;
+      tp = now;
+    }
+  };
 
   // ---- ||d_j||^2 (FP64) and Z = 0 (double-float solution accumulator)
   rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
@@ -891,7 +947,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
     if (!(ok = bar.sync())) break;
     int tbuf = 0;   // the global copy of T_k the next staging reads
-    stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, p.Tk, p.Tk, b == 0, s_beta_v, false, s_active, s_sig,
+    stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, p.Tk, p.Tk, b == 0, sTk, s_beta_v, false, s_active, s_sig,
                                    s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
     if (t < NT) {
       const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;       // sum r_i z_0^2
@@ -904,6 +960,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       s_active[t] = (t < N && !s_done[t] && gm > 0.0) ? 1 : 0;
     }
     __syncthreads();
+    tick(PH_SETUP);
     int it = 0;
     for (;;) {
       int my_active = 0;
@@ -934,22 +991,28 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       }
       const int any = __syncthreads_or(my_active);
       if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
+      tick(PH_SCAL);
       if constexpr (NT <= 64)
         passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                         s_beta_v, uni, tmem, &mbar[2], &mbar[1], ph_u2, ph_g, p.status, ok, Tp);
       else
         passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                       s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+      tick(PH_PASS);
       if (!(ok = bar.sync() && ok)) break;
+      tick(PH_BAR1);
       reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
+      tick(PH_RED);
       if (!(ok = bar.sync())) break;
+      tick(PH_BAR2);
       // beta, T_{k+1} = HA^T z_{k+1} + beta T_k (from the global copy of T_k), the scalars
       const float* Tprev = p.Tk + (size_t)tbuf * N * N;
       float* Tnext = p.Tk + (size_t)(tbuf ^ 1) * N * N;
-      stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, Tprev, Tnext, b == 0, s_beta_v, true, s_active,
+      stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, Tprev, Tnext, b == 0, sTk, s_beta_v, true, s_active,
                                      s_sig, s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
       tbuf ^= 1;
       ++it;
+      tick(PH_SCAL);
     }
     if (!ok) break;
     total += it;
@@ -1003,9 +1066,12 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       s_itol[t] = (float)fmin(it_next, 0.5);
     }
     const int all_done = __syncthreads_and(t >= N || s_done[t]);
+    tick(PH_REFRESH);
     if (all_done || total >= p.max_iter) break;
   }
 
+  if (prof)
+    for (int q = 0; q < PH_COUNT; ++q) p.prof[q] = ph[q];
   if (b == 0 && t < N) {
     p.col_iters[t] = s_iters[t];
     p.col_relres[t] = s_rel[t];
