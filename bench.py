@@ -122,10 +122,10 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
             "cg_iterations": iters, "refreshes": refreshes, "hbm_frac": t_b / t}
 
 # DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
-# captures summarised under profiles/ (FP32: solve_kernel_fp32_hs_grf512_N64_m65536.md), with
+# captures summarised under profiles/ (FP32: launches_grf512_N64_m65536.md), with
 # the hash of the kernel sources each capture measured; reported as null once those sources
 # have changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 1.491656e9, "src_sha": "6e873226f765b161"},
+NCU_TRAFFIC = {"fp32": {"bytes": 1.442546e9, "src_sha": "998371542af81f75"},
                "fp16": {"bytes": 6.431757e9, "src_sha": "18d941411bdfab5b"}}
 # DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
 # profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
@@ -534,7 +534,11 @@ def run_ours(args):
     e2e_s = _max_over_ranks(time.perf_counter() - t0, dev, ws)
     e2e = {"value": _job_rate(e2e_steps, e2e_s, ws), "unit": UNIT,
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
-           "d2h_bytes_per_step": int(Xo.numel() * 4)}
+           "d2h_bytes_per_step": int(Xo.numel() * 4),
+           "host_reads_bytes_per_step": int(len(p.col) * N * 4),
+           "note": "enkf_analyze_host with pinned buffers: the innovations read the observed rows of X_f "
+                   "from host memory (host_reads_bytes_per_step, over the CPU-GPU link, besides the "
+                   "copies), X_f is uploaded on a second stream while the solve runs, X_a is copied back"}
 
     # ---- roofline of the dominant kernel (the persistent CG solve), live CUDA-event time
     it_avg, ref_avg = float(np.mean(iters)), float(np.mean(refines))

@@ -188,10 +188,17 @@ enkf_status enkf_analyze(enkf_handle h, const void* d_Xf, const double* d_y, uin
 enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d_y,
                                 const double* d_E, void* d_Xa);
 
-/* End-to-end form with HOST buffers: copies h_Xf [n][N] and h_y [m] to device staging
-   buffers owned by the handle, runs enkf_analyze, copies X_a back into h_Xa [n][N] and
-   synchronises the stream before returning. Pinned host memory gives asynchronous
-   copies; pageable memory works but is slower. */
+/* End-to-end form with HOST buffers: h_Xf [n][N], h_y [m], h_Xa [n][N] (h_Xa == h_Xf is
+   allowed); the result is in h_Xa when the call returns (it synchronises the stream).
+   Pageable buffers: X_f and y are copied to device staging buffers owned by the handle, the
+   analysis runs there and X_a is copied back. Pinned (page-locked, device-mapped) buffers
+   with ENKF_CGD: the innovations read the observed rows of X_f directly from host memory
+   while the whole X_f is uploaded on a second stream that the handle creates on first use
+   (the upload overlaps the innovations and the solve; only the final update waits for it),
+   and X_a comes back by one copy. Either way every X_f byte crosses to the device and every
+   X_a byte back within the call. The
+   buffers must hold n N elements of the handle's dtype; the result is the same as
+   enkf_analyze's on device copies of the inputs. */
 enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y,
                               uint64_t seed, uint64_t counter, void* h_Xa);
 

@@ -307,15 +307,26 @@ enkf_status enkf_create_tridiag(const enkf_config* cfg, const int32_t* h_rowptr,
   return create_impl(cfg, h_rowptr, h_col, h_w, r_diag, r_off, cuda_stream, out);
 }
 
+// An upload of X_f that runs on the handle's copy stream once the innovations are done (their
+// reads of host memory then have the CPU-GPU link to themselves) and that the update waits for.
+struct XfUpload {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
+// d_Xf feeds the innovations (the observed rows of X_f); the update reads d_Xf_upd (nullptr:
+// d_Xf), after the upload `up` (if given) has completed.
 static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d_y,
                                 const double* d_E, int emode, uint64_t seed, uint64_t counter,
-                                void* d_Xa) {
+                                void* d_Xa, const void* d_Xf_upd = nullptr, const XfUpload* up = nullptr) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze: NULL handle");
   if (h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "analyze: batched handle (use the enkf_batch_* calls)");
   if (!d_Xf || !d_y || !d_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze: NULL X_f, y or X_a");
   const auto& c = h->cfg;
   const size_t xb = elem_size(c) * c.n * c.N;
-  const char* a = static_cast<const char*>(d_Xf);
+  if (!d_Xf_upd) d_Xf_upd = d_Xf;
+  const char* a = static_cast<const char*>(d_Xf_upd);
   const char* b = static_cast<const char*>(d_Xa);
   if (a != b && a < b + xb && b < a + xb)
     return fail(h, ENKF_ERR_INVALID_ARG, "analyze: X_a partially overlaps X_f");
@@ -342,6 +353,13 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
     e = gram ? enkf::launch_gram_stage(h, Xin, yin, Ein, emode, seed, counter)
              : enkf::launch_innovations(h, Xin, yin, Ein, emode, seed, counter);
   if (e != cudaSuccess) return cuda_fail(h, e, gram ? "analyze: Gram pass launch" : "analyze: innovations launch");
+  if (up) {
+    e = cudaEventRecord(h->host_ev[0], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->host_ev[0], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(up->dst, up->src, up->bytes, cudaMemcpyHostToDevice, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->host_ev[1], h->copy_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze: upload of X_f");
+  }
   if (c.warm_start) {
     e = enkf::warm_prepare(h);
     if (e != cudaSuccess) return cuda_fail(h, e, "analyze: learned warm start");
@@ -352,8 +370,10 @@ static enkf_status analyze_impl(enkf_handle h, const void* d_Xf, const double* d
              : (h->cfg.precision >= ENKF_BF16_REFINE ? enkf::launch_solve_mixed(h) : enkf::launch_solve(h));
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: CG launch");
   if (h->timing) e = cudaEventRecord(h->ev[2], h->stream);
+  if (e == cudaSuccess && up) e = cudaStreamWaitEvent(h->stream, h->host_ev[1], 0);
   if (e == cudaSuccess)
-    e = c.variant == ENKF_CGD_REDUCED ? enkf::launch_update_product(h, d_Xf, d_Xa) : enkf::launch_update(h, d_Xf, d_Xa);
+    e = c.variant == ENKF_CGD_REDUCED ? enkf::launch_update_product(h, d_Xf_upd, d_Xa)
+                                      : enkf::launch_update(h, d_Xf_upd, d_Xa);
   if (e != cudaSuccess) return cuda_fail(h, e, "analyze: update launch");
   if (h->timing) {
     e = cudaEventRecord(h->ev[3], h->stream);
@@ -375,6 +395,17 @@ enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d
   return analyze_impl(h, d_Xf, d_y, d_E, d_E ? 1 : 0, 0, 0, d_Xa);
 }
 
+// The device address of pinned (page-locked, mapped) host memory, or nullptr for any other
+// pointer (pageable host memory, device memory).
+static void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y, uint64_t seed,
                               uint64_t counter, void* h_Xa) {
   if (!h) return fail(nullptr, ENKF_ERR_INVALID_ARG, "analyze_host: NULL handle");
@@ -382,6 +413,36 @@ enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y
   if (!h_Xf || !h_y || !h_Xa) return fail(h, ENKF_ERR_INVALID_ARG, "analyze_host: NULL buffer");
   const auto& c = h->cfg;
   const size_t xb = elem_size(c) * c.n * c.N;
+  const void* xf_dev = device_view(h_Xf);
+  if (xf_dev && c.variant == ENKF_CGD) {
+    // Pinned X_f: the innovations read the observed rows of X_f directly from host memory (over
+    // the CPU-GPU link); the whole X_f is then uploaded on the copy stream while the solve runs,
+    // and only the update waits for it. X_a goes back by one copy (writing it to pinned host
+    // memory from the update kernel itself measured about 20x slower than the copy; two copies
+    // on two streams were no faster than one).
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_stream) {
+      e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+      for (auto& ev : h->host_ev)
+        if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: copy stream");
+    }
+    // (the upload starts after the innovations: run concurrently with them, it slowed their
+    // reads of host memory from 0.14 to 0.25 ms at n = 262,144, N = 64)
+    e = cudaMemcpyAsync(h->ws.stage_y, h_y, sizeof(double) * c.m, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: upload");
+    const XfUpload up{h->ws.stage_Xf, h_Xf, xb};
+    enkf_status s = analyze_impl(h, xf_dev, h->ws.stage_y, nullptr, h->cfg.perturb_obs ? 2 : 0, seed, counter,
+                                 h->ws.stage_Xf, h->ws.stage_Xf, &up);
+    if (s != ENKF_OK) {
+      cudaStreamSynchronize(h->copy_stream);
+      return s;
+    }
+    e = cudaMemcpyAsync(h_Xa, h->ws.stage_Xf, xb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: download");
+    return ENKF_OK;
+  }
   cudaError_t e = cudaMemcpyAsync(h->ws.stage_Xf, h_Xf, xb, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws.stage_y, h_y, sizeof(double) * c.m, cudaMemcpyHostToDevice, h->stream);
@@ -778,6 +839,12 @@ enkf_status enkf_destroy(enkf_handle h) {
   enkf::batch_free(h);
   enkf::warm_free(h);
   for (auto& ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->copy_stream) {
+    cudaStreamSynchronize(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream);
+  }
+  for (auto& ev : h->host_ev)
     if (ev) cudaEventDestroy(ev);
   free_workspace(h->ws);
   delete h;

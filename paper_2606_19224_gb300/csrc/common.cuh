@@ -192,6 +192,10 @@ struct enkf_handle_s {
   bool timed = false;
   bool prof_enabled = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // enkf_analyze_host with a pinned X_f: the upload of X_f runs on its own stream (created on
+  // first use) while the innovations read the observed rows from host memory
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t host_ev[2] = {nullptr, nullptr};
   enkf::BatchState* batch = nullptr;   // non-NULL for a handle made by enkf_batch_create
   enkf::WarmState* warm = nullptr;     // learned warm start (enkf_set_warm_model / enkf_warm_features)
   bool tri = false;                    // tridiagonal R: analyses run on the whitened problem

@@ -157,6 +157,32 @@ def test_in_place_and_host_api_and_determinism(lib):
     assert torch.equal(a, X2)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16"])
+def test_host_api_pinned_and_pageable_buffers(lib, prec):
+    """enkf_analyze_host: pinned X_f (innovations read host memory while X_f uploads on a second
+    stream), pinned or pageable X_a, pageable inputs (staged copies), in place on a pinned
+    buffer, and twice in a row on one handle: every combination equals enkf_analyze bitwise."""
+    dt = np.float64 if prec == "fp64" else np.float32
+    p = synth.workload("grf512_N64_m65536", 16, scale=4, dtype=dt)
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec)
+    Xf = torch.from_numpy(p.Xf).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    ref = an.analyze(Xf, y, seed=3, counter=4).cpu()
+    yp = torch.from_numpy(p.y).pin_memory()
+    for pin_in in (True, False):
+        for pin_out in (True, False):
+            Xh = torch.from_numpy(p.Xf.copy())
+            Xh = Xh.pin_memory() if pin_in else Xh
+            out = torch.empty(tuple(Xh.shape), dtype=Xh.dtype, pin_memory=pin_out)
+            for _ in range(2):
+                c = an.analyze_host(Xh, yp if pin_in else torch.from_numpy(p.y), seed=3, counter=4, out=out)
+                assert torch.equal(c, ref), (pin_in, pin_out)
+            assert torch.equal(Xh, torch.from_numpy(p.Xf))   # the input is left as it was
+    Xh = torch.from_numpy(p.Xf.copy()).pin_memory()
+    an.analyze_host(Xh, yp, seed=3, counter=4, out=Xh)      # in place on a pinned buffer
+    assert torch.equal(Xh, ref)
+
+
 def test_zero_innovation_column_and_tiny_problem(lib):
     p = _csr_problem(40, 20, 20, 21)
     Z = oracle.apply_H(p.rowptr, p.col, p.w, p.Xf)
