@@ -73,9 +73,10 @@ def F_ITER(m, N):
 
 
 def B_FUSED(m, N):
-    """The same step as one fused FP32 pass reads and writes it (HA read once, x, r, p and
-    S p read and written, r_i read): 36 m N + 4 m bytes."""
-    return 36 * m * N + 4 * m
+    """The same step as one fused FP32 pass of the one-reduction Hestenes-Stiefel form reads and
+    writes it (HA read once, x, r and p read and written, r_i read; S p is formed in the pass
+    and never stored): 28 m N + 4 m bytes."""
+    return 28 * m * N + 4 * m
 
 
 # Measured on a GB300 with a register-resident FMA loop (152 SMs at 2.07 GHz): FP64 FMA
@@ -550,8 +551,8 @@ def run_ours(args):
                                  traffic)
     roofline["fused_pass_model"] = {
         "bytes_per_launch": it_avg * B_FUSED(m, N) + ref_avg * 56 * m * N,
-        "note": "HA read once per step (36 m N + 4 m) and a double-float refresh of 56 m N bytes: what the "
-                "fused implementation moves at minimum"}
+        "note": "HA read once per step, x, r, p read and written (28 m N + 4 m) and a double-float refresh "
+                "of 56 m N bytes: what the fused implementation moves at minimum"}
 
     prec_name = {"fp32": "fp32 CG + double-float residual refresh",
                  "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
