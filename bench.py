@@ -11,11 +11,15 @@ N = 64 members, m = 65,536 randomly placed observations, r ~ U[0.5, 1.5], CG tol
 
 Prints one JSON line (rank 0). `value` is analyses/s summed over ranks (each rank runs its
 own independent analyses: weak scaling, no collective on the data path). The timed headline
-is FP32 CG preconditioned by R with a double-float residual refresh (meets 1e-6 relative
-Frobenius error against the FP64 oracle). On one GPU the same run then measures, after the
-timed region, every other configuration of the method as keys of the same line:
+is CG preconditioned by R with both HA contractions of every step on the tensor cores
+(tcgen05, FP16 hi/lo operands, FP32 accumulation), FP32 vectors, FP64 scalars and a
+double-float residual refresh (meets 1e-6 relative Frobenius error against the FP64 oracle;
+`--precision fp32` times the FP32 CUDA-core solve instead). On one GPU the same run then
+measures, after the timed region, every other configuration of the method as keys of the
+same line:
   c1_variants      the 512x512 workload in plain FP64 CG (the comparison point), FP64 CG
-                   preconditioned by R, plain FP32 CG, FP16 and BF16 tensor-core solves
+                   preconditioned by R, plain FP32 CG, and the other preconditioned solves
+                   (FP32 on the CUDA cores, BF16 / FP16 on the tensor cores)
   reduced_variant, senkf_comparator   the two one-pass variants on the same ensemble
   c2_mixed         1024x1024 GRF, N = 128, m = 262,144: BF16 / FP16 / FP32 / FP64
   c3_batch         256 uneven analyses in one persistent launch (tuned plan, CUDA graph)
@@ -123,7 +127,7 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
             "cg_iterations": iters, "refreshes": refreshes, "hbm_frac": t_b / t}
 
 # DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
-# captures summarised under profiles/ (FP32: launches_grf512_N64_m65536.md), with
+# captures summarised under profiles/ (FP32: launches_fp32_grf512_N64_m65536.md; FP16: launches_fp16_grf512_N64_m65536.md), with
 # the hash of the kernel sources each capture measured; reported as null once those sources
 # have changed.
 NCU_TRAFFIC = {"fp32": {"bytes": 1.442546e9, "src_sha": "998371542af81f75"},
@@ -593,8 +597,9 @@ def run_ours(args):
     c1["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp32_plain_cg"] = _variant(enkf, p, "fp32", 0, timer, Xf, y, seed, args.fp64_steps, 1, ref)
-    for prec in ("fp16", "bf16"):
-        c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref)
+    for prec in ("fp32", "fp16", "bf16"):
+        if prec != args.precision:
+            c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref)
     base = c1["fp64_plain_cg"]["ms_per_step"]
     for k, v in c1.items():
         v["speedup_vs_fp64_plain_cg"] = base / v["ms_per_step"]
@@ -1083,7 +1088,7 @@ def main():
                     help="state sizes p of the Example 2b (Table 5) section")
     ap.add_argument("--warm-train-seeds", type=int, default=40,
                     help="ensembles (x 8 observation draws) the learned warm start trains on in the default run")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"],
                     help="inner-solve precision of the timed path (default workload)")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="problems of the batched workload (256 is the benchmark; fewer for profiling)")

@@ -100,8 +100,14 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.Tk = ws.Tk;
   p.tol = c.tol;
   p.inner_tol = c.inner_tol;
-  // accuracy an inner solve on the BF16 / FP16 operator can be asked for
-  p.itol_floor = mixed_split(c) ? 1e-3 : (c.precision == ENKF_BF16_REFINE ? 2e-2 : 4e-3);
+  // accuracy an inner solve on the BF16 / FP16 operator can be asked for: the split FP16
+  // operator with N <= 64 (each tile's Gram summed in FP32 outside the tensor cores) gains
+  // about as much per inner solve as FP32 (512^2 / N = 64: 39 steps + 2 refreshes at 3e-5
+  // against 47 + 3 at 1e-3); BF16 pairs carry 16 bits and N = 128 keeps the Gram in one TMEM
+  // accumulator over all of a CTA's tiles, so those stay at 1e-3 (3 refreshes)
+  const int nt_launch = h->launch.NT;
+  p.itol_floor = mixed_split(c) ? ((c.precision == ENKF_FP16_REFINE && nt_launch <= 64) ? 3e-5 : 1e-3)
+                                : (c.precision == ENKF_BF16_REFINE ? 2e-2 : 4e-3);
   p.max_iter = c.max_iter;
   p.refresh_every = c.refresh_every;
   p.col_iters = ws.col_iters;

@@ -160,7 +160,9 @@ template <int NT, int TERMS> struct TcLayout {
   static constexpr int off_u = off_ts + 8 * NT;
   // NT <= 64: T_k of the Hestenes-Stiefel recurrence, FP32 [NT][NT] (stage_Tt16_rec)
   static constexpr int off_tk = off_u + kTR * NT * 4;
-  static constexpr int bytes = DB ? off_tk + NT * NT * 4 : off_ts + 8 * NT;
+  // NT <= 64: the pass's Gram summed over its tiles in FP32, [NT][NT + 1] (row j, column k)
+  static constexpr int off_gacc = off_tk + NT * NT * 4;
+  static constexpr int bytes = DB ? off_gacc + NT * (NT + 1) * 4 : off_ts + 8 * NT;
   static_assert(off_bu % 1024 == 0 && off_bg % 1024 == 0 && off_u % 16 == 0, "operand alignment");
 };
 
@@ -421,10 +423,29 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   float* sU = reinterpret_cast<float*>(tcs + L::off_u);
   const float* zs = reinterpret_cast<const float*>(tcs + L::off_zs);
   const float* ts = reinterpret_cast<const float*>(tcs + L::off_ts);
+  float* sG = reinterpret_cast<float*>(tcs + L::off_gacc);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int qd = warp & 3, half = warp >> 2;
   const int rt = 32 * qd + lane;
   const int tj = t % NJ, ti = t / NJ, j0 = 4 * tj;
+  // The Gram of each tile leaves TMEM once it is complete and is added to sG in FP32 (round to
+  // nearest), so no tensor-core accumulation chain spans more than one tile: a chain over all
+  // of a CTA's tiles cost the split FP16 mode steps and a refresh (more with fewer, longer
+  // row blocks). Thread (qd, half, lane) owns row j = 32 qd + lane, columns [half NT/2, +NT/2).
+  const bool g_owner = 32 * qd < N;
+  auto gram_out = [&]() {
+    if (!g_owner) return;
+#pragma unroll
+    for (int c = 0; c < HALF / 16; ++c) {
+      const int k0 = half * HALF + 16 * c;
+      float v[16];
+      tmem_ld16(tmem + 2 * NT + ((uint32_t)(32 * qd) << 16) + k0, v);
+#pragma unroll
+      for (int y = 0; y < 16; ++y) sG[rt * (NT + 1) + k0 + y] += v[y];
+    }
+  };
+  if (g_owner)
+    for (int k = half * HALF; k < half * HALF + HALF; ++k) sG[rt * (NT + 1) + k] = 0.f;
   // TMEM: u of tile q in slot q % 2 (columns [slot NT, slot NT + NT)), the Gram at 2 NT
   const uint32_t d_g = tmem + 2 * NT;
   const int Qb = row1 > row0 ? (int)((row1 - row0 + kTR - 1) / kTR) : 0;
@@ -528,6 +549,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
       ph_g ^= 1u;
       tc_fence_after();
+      gram_out();
     }
     const bool more = q + 1 < Qb;
     if (more) {
@@ -597,7 +619,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
           const uint64_t B0 = umma_desc(au + kb * 2 * sbo_u, sbo_u, 128);
           const uint64_t A1 = umma_desc(bg + L::BGP + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
           const uint64_t B1 = umma_desc(au + L::AU * 2 + kb * 2 * sbo_u, sbo_u, 128);
-          umma_f16(d_g, A0, B1, idesc_g, (q == 0 && kb == 0) ? 0u : 1u);
+          umma_f16(d_g, A0, B1, idesc_g, kb == 0 ? 0u : 1u);
           umma_f16(d_g, A1, B0, idesc_g, 1u);
         }
       }
@@ -605,34 +627,24 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
       for (int kb = 0; kb < kTR / 16; ++kb) {
         const uint64_t A0 = umma_desc(bg + kb * 2 * L::LBOG, L::LBOG, L::SBOG);
         const uint64_t B0 = umma_desc(au + kb * 2 * sbo_u, sbo_u, 128);
-        umma_f16(d_g, A0, B0, idesc_g, (q == 0 && kb == 0 && !SPLIT) ? 0u : 1u);
+        umma_f16(d_g, A0, B0, idesc_g, (kb == 0 && !SPLIT) ? 0u : 1u);
       }
       umma_commit(mbar_g);
     }
   }
-  // the last tile's Gram completes the partial in TMEM
+  // the last tile's Gram
   if (Qb > 0) {
     if (!mbar_wait(mbar_g, ph_g, status)) ok = false;
     ph_g ^= 1u;
     tc_fence_after();
+    gram_out();
   }
   tc_cp_wait_all();
-  // partial Gram from TMEM: lane j, column k -> out[k*N + j] / zs_j (warp-uniform condition)
-  if (Qb > 0 && 32 * qd < N) {
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int k0 = half * HALF + 16 * c;
-      float v[16];
-      tmem_ld16(d_g + ((uint32_t)(32 * qd) << 16) + k0, v);
-      if (rt < N) {
-        const float inv = 1.f / zs[rt];
-#pragma unroll
-        for (int y = 0; y < 16; ++y)
-          if (k0 + y < N) out[(k0 + y) * N + rt] = (double)(v[y] * inv);
-      }
-    }
-  } else if (Qb == 0) {
-    for (int e = t; e < N * N; e += kThreads) out[e] = 0.0;
+  // the pass's partial Gram: row j, column k -> out[k*N + j] / zs_j (all zero when Qb == 0)
+  if (g_owner && rt < N) {
+    const float inv = 1.f / zs[rt];
+    for (int k = half * HALF; k < half * HALF + HALF; ++k)
+      if (k < N) out[k * N + rt] = (double)(sG[rt * (NT + 1) + k] * inv);
   }
   tc_fence_before();
   __syncthreads();
