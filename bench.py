@@ -878,7 +878,19 @@ def section_c4(args, enkf, dev, timer):
             "speedup": res["ms_zero"] / res["ms_learned"],
             "rel_diff_zero_vs_learned_max": max(r["rel_diff_zero_vs_learned"] for r in ev),
             "warm_fallbacks": sum(r["learned"]["warm_fallbacks"] for r in ev),
-            "status": [r["learned"]["status"] for r in ev], "held_out_seeds": len(ev)}
+            "status": [r["learned"]["status"] for r in ev], "held_out_seeds": len(ev),
+            "judge": "a start is kept only if its true residual is at most ||d_j|| (warm_accept = 0)",
+            "accept_all_finite": {
+                "iters_mean": res["iters_mean_learned_accept"], "ms": res["ms_learned_accept"],
+                "speedup": res["ms_zero"] / res["ms_learned_accept"],
+                "rel_diff_zero_vs_learned_max": max(r["rel_diff_zero_vs_learned_accept"] for r in ev),
+                "true_relres_max": max(r["learned_accept"]["true_relres_max"] for r in ev),
+                "start_relres_max": max(r["learned_accept"]["warm_relres_max"] for r in ev),
+                "refinements": [r["learned_accept"]["refinements"] for r in ev],
+                "refinements_zero_start": [r["zero"]["refinements"] for r in ev],
+                "status": [r["learned_accept"]["status"] for r in ev],
+                "note": "every finite start kept (warm_accept = 1); the result is certified by the same "
+                        "double-float true residual <= tol"}}
 
 
 def section_c0(args, enkf, dev, timer):

@@ -99,7 +99,9 @@ typedef struct enkf_config {
   double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
   int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between double-float residual
                              refreshes; 0 (default): each inner solve runs until its
-                             residual fell by inner_tol (at least 2e-2 BF16, 4e-3 FP16)  */
+                             residual fell by inner_tol, but not below what the operator
+                             allows: 3e-5 for split FP16 with N <= 64, 1e-3 for the other
+                             split forms, 2e-2 / 4e-3 for single BF16 / FP16 operands   */
   int32_t perturb_obs;    /* 1: E ~ N(0, R) drawn from (seed, counter); 0: E = 0         */
   int32_t warm_start;     /* 0: start CG from Z = 0; 1: learned warm start from the model
                              attached by enkf_set_warm_model (ENKF_CGD, ENKF_FP32 only) */
@@ -113,7 +115,13 @@ typedef struct enkf_config {
                              into hi + lo parts and forms hi*hi + hi*lo + lo*hi (about 16
                              significant bits); 1 uses single BF16/FP16 operands, whose
                              refinement diverges once 2 eps cond(S) > 1                  */
-  int32_t reserved[5];    /* must be zero                                                */
+  int32_t warm_accept;    /* learned warm start, how its start is judged by the start's
+                             true residual B_j = d_j - S z0_j: 0 (default) a column whose
+                             ||B_j|| exceeds ||d_j|| (the zero start's) starts from zero;
+                             1 every finite start is kept. Either way a non-finite start
+                             starts from zero and the result is certified by the same
+                             double-float true residual <= tol                          */
+  int32_t reserved[4];    /* must be zero                                                */
 } enkf_config;
 
 typedef struct enkf_stats {

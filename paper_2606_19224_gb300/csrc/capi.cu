@@ -72,7 +72,8 @@ enkf_status check_problem(const enkf_config& c, const int32_t* h_rowptr, const i
   if (c.warm_start != 0 && c.warm_start != 1) return bad(ENKF_ERR_INVALID_ARG, "warm_start must be 0 or 1");
   if (c.warm_start && (c.precision != ENKF_FP32 || c.variant != ENKF_CGD || c.fixed_iters > 0))
     return bad(ENKF_ERR_UNSUPPORTED, "the learned warm start runs in ENKF_CGD / ENKF_FP32 without fixed_iters");
-  for (int q = 0; q < 5; ++q)
+  if (c.warm_accept != 0 && c.warm_accept != 1) return bad(ENKF_ERR_INVALID_ARG, "warm_accept must be 0 or 1");
+  for (int q = 0; q < 4; ++q)
     if (c.reserved[q]) return bad(ENKF_ERR_INVALID_ARG, "reserved fields must be 0");
   // observation operator and R
   if (h_rowptr[0] != 0) return bad(ENKF_ERR_INVALID_ARG, "rowptr[0] != 0");

@@ -181,6 +181,7 @@ cudaError_t launch_solve(enkf_handle_s* h) {
   p.status = ws.status;
   p.bar = ws.bar;
   p.warm = (h->cfg.warm_start && h->cfg.precision == ENKF_FP32) ? 1 : 0;
+  p.warm_accept = h->cfg.warm_accept;
   p.col_warm = ws.col_warm;
   cudaError_t err = cudaMemsetAsync(ws.bar, 0, 4 * sizeof(unsigned), h->stream);
   if (err != cudaSuccess) return err;

@@ -41,6 +41,7 @@ struct SolveParams {
   unsigned* bar;
   unsigned long long* prof;  // optional phase timers of CTA 0 (ns), nullptr when off
   int warm;                  // FP32 mode: Zdf holds a starting solution (learned warm start)
+  int warm_accept;           // 1: keep every finite start; 0: only those with ||B_j|| <= ||d_j||
   double* col_warm;          // [N] relative residual ||B_j|| / ||d_j|| of that start
 };
 
@@ -141,8 +142,9 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     __syncthreads();
   }
   if (ok && warm) {
-    // the start's true residual judges it: a column whose start is non-finite or whose
-    // residual is larger than the zero start's (d_j) falls back to z_j = 0, B_j = d_j
+    // the start's true residual judges it: a column whose start is non-finite or (unless
+    // warm_accept) whose residual is larger than the zero start's (d_j) falls back to
+    // z_j = 0, B_j = d_j
     VT* Bv = static_cast<VT*>(p.B);
     rows_reduce<NT>(row0, row1, N, [&](int64_t i, int j, double& acc) {
       const double v = (double)Bv[i * N + j];
@@ -154,7 +156,8 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
       par ^= 1;
       if (t < NT) {
-        const bool bad = t < N && !s_done[t] && !(s_tmp[t] <= s_dn2[t]);
+        const bool bad = t < N && !s_done[t] &&
+                         (p.warm_accept ? !isfinite(s_tmp[t]) : !(s_tmp[t] <= s_dn2[t]));
         if (b == 0 && t < N) p.col_warm[t] = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
         s_active[t] = bad ? 1 : 0;   // s_active is free until the first inner solve
         if (t < N && !s_done[t] && !bad) {

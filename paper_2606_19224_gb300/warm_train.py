@@ -84,7 +84,9 @@ def train(shape, F, T, epochs, batch, lr, seed, log=None):
 
 def evaluate(cfg, shape, params, seeds, K, reps=5):
     """Per held-out problem: mean / max CG iterations over columns and analysis time (ms),
-    zero start vs learned start, plus the learned start's true residual."""
+    zero start vs learned start, plus the learned start's true residual. The learned start is
+    judged both ways: "learned" keeps a column's start only if its true residual is at most
+    ||d_j|| (warm_accept = 0), "learned_accept" keeps every finite start (warm_accept = 1)."""
     import torch
     out = []
     for s in seeds:
@@ -92,10 +94,11 @@ def evaluate(cfg, shape, params, seeds, K, reps=5):
         Xf = torch.from_numpy(p.Xf).cuda()
         y = torch.from_numpy(p.y).cuda()
         row = dict(seed=s)
-        for mode in ("zero", "learned"):
+        for mode in ("zero", "learned", "learned_accept"):
             an = Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", precondition=1,
-                          tol=cfg["tol"], warm_start=1 if mode == "learned" else 0)
-            if mode == "learned":
+                          tol=cfg["tol"], warm_start=0 if mode == "zero" else 1,
+                          warm_accept=1 if mode == "learned_accept" else 0)
+            if mode != "zero":
                 an.set_warm_model(shape, params)
             Xa = an.analyze(Xf, y, seed=77 + s, counter=0)
             torch.cuda.synchronize()
@@ -118,9 +121,10 @@ def evaluate(cfg, shape, params, seeds, K, reps=5):
                              status=st["status"])
             row[mode + "_Xa"] = Xa
             an.close()
-        d = (row["zero_Xa"].double() - row["learned_Xa"].double()).norm() / row["zero_Xa"].double().norm()
-        row["rel_diff_zero_vs_learned"] = float(d.item())
-        del row["zero_Xa"], row["learned_Xa"]
+        for mode in ("learned", "learned_accept"):
+            d = (row["zero_Xa"].double() - row[mode + "_Xa"].double()).norm() / row["zero_Xa"].double().norm()
+            row["rel_diff_zero_vs_" + mode] = float(d.item())
+        del row["zero_Xa"], row["learned_Xa"], row["learned_accept_Xa"]
         out.append(row)
     return out
 
@@ -143,11 +147,9 @@ def run(cfg, log=print):
     res = dict(config=cfg, pairs=int(F.shape[0]), params=mlp_param_count(shape),
                trained_params=mlp_trained_count(shape), loss_first=hist[0], loss_last=hist[-1],
                loss_history=hist, collect_s=t1 - t0, train_s=t2 - t1, eval=ev)
-    z = np.mean([r["zero"]["iters_mean"] for r in ev])
-    l = np.mean([r["learned"]["iters_mean"] for r in ev])
-    res["iters_mean_zero"], res["iters_mean_learned"] = float(z), float(l)
-    res["ms_zero"] = float(np.mean([r["zero"]["ms"] for r in ev]))
-    res["ms_learned"] = float(np.mean([r["learned"]["ms"] for r in ev]))
+    for mode in ("zero", "learned", "learned_accept"):
+        res["iters_mean_" + mode] = float(np.mean([r[mode]["iters_mean"] for r in ev]))
+        res["ms_" + mode] = float(np.mean([r[mode]["ms"] for r in ev]))
     return res, params
 
 

@@ -115,8 +115,8 @@ def test_features_and_targets_match_oracle(lib):
     assert np.max(np.abs(T.cpu().numpy() - Tr)) <= 1e-5 * np.max(np.abs(Tr))
 
 
-@pytest.mark.parametrize("scale,expect_fallback", [(1.0, False), (1e8, True)])
-def test_warm_started_analysis_matches_exact(lib, scale, expect_fallback):
+@pytest.mark.parametrize("scale,expect_fallback,accept", [(1.0, False, 0), (1e8, True, 0), (1.0, False, 1)])
+def test_warm_started_analysis_matches_exact(lib, scale, expect_fallback, accept):
     p = _grf_small(9)
     K = 64
     shape = (K + p.N, 64, 2, p.N, 0)[:4]
@@ -124,7 +124,8 @@ def test_warm_started_analysis_matches_exact(lib, scale, expect_fallback):
     nw = lib.mlp_trained_count(shape)
     params[:nw] *= scale ** (1.0 / 3.0)   # scale ** 1 over the three layers: a wild model
     pt = torch.from_numpy(params).cuda()
-    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", precondition=1, warm_start=1)
+    an = lib.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision="fp32", precondition=1, warm_start=1,
+                      warm_accept=accept)
     an.set_warm_model(shape, pt)
     Xa = an.analyze(torch.from_numpy(p.Xf).cuda(), torch.from_numpy(p.y).cuda(), seed=5, counter=0)
     st = an.stats()
@@ -132,6 +133,8 @@ def test_warm_started_analysis_matches_exact(lib, scale, expect_fallback):
     assert st["warm_relres_max"] >= 0.0
     if expect_fallback:
         assert st["warm_fallbacks"] == p.N
+    if accept:
+        assert st["warm_fallbacks"] == 0   # every finite start is kept
     E = oracle.obs_perturbations(5, 0, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
     assert oracle.rel_frobenius(Xa.double().cpu().numpy(), ref) <= 1e-6
@@ -153,9 +156,12 @@ def test_trained_model_gain(lib):
     from paper_2606_19224_gb300 import warm_train as wt
     res, _ = wt.run(dict(wt.SMALL), log=lambda *_: None)
     print("learned warm start:", {k: res[k] for k in ("pairs", "loss_first", "loss_last", "iters_mean_zero",
-                                                       "iters_mean_learned", "ms_zero", "ms_learned")})
+                                                       "iters_mean_learned", "iters_mean_learned_accept",
+                                                       "ms_zero", "ms_learned", "ms_learned_accept")})
     assert res["loss_last"] < 0.5 * res["loss_first"]
     for r in res["eval"]:
-        assert r["zero"]["status"] == "ok" and r["learned"]["status"] == "ok"
+        for mode in ("zero", "learned", "learned_accept"):
+            assert r[mode]["status"] == "ok"
         assert r["rel_diff_zero_vs_learned"] <= 2e-6
+        assert r["rel_diff_zero_vs_learned_accept"] <= 2e-6
     assert res["iters_mean_learned"] <= res["iters_mean_zero"]
