@@ -322,10 +322,15 @@ enkf_status enkf_batch_analyze(enkf_handle h, const void* const* d_Xf, const dou
    four times re-plans from measured costs (each problem's duration in the last plan, as
    reported by enkf_batch_get_times and averaged over that plan's three timed analyses, times
    k^alpha for a team of k CTAs, averaged with the previous round's estimate) and times that
-   plan. It keeps the fastest plan and appends it (alpha, and the measured costs when a
-   measured plan won) to the ENKF_TUNE_CACHE file if that variable is set. Runs 28 to 44
-   analyses (X_a holds the last one's result); synchronises the stream. *best_ms (HOST, may
-   be NULL) receives the best mean time. */
+   plan. Last it searches the row-block floor of each ensemble-size class (N <= 16, <= 32,
+   <= 64, <= 128; the fewest rows a team's CTA may get, 64 by default, which caps a problem's
+   team at ceil(m / floor) CTAs): classes with at least 5 % of the cost, the largest first,
+   each floor in {128, 256, 512} planned from the best plan's costs and, where the plan
+   changes, timed, keeping a floor that is at least 1 % faster. It keeps the fastest plan
+   and appends it (alpha, the floors, and the measured costs when a measured plan won) to the
+   ENKF_TUNE_CACHE file if that variable is set. Runs 28 to 92 analyses (X_a holds the last
+   one's result); synchronises the stream. *best_ms (HOST, may be NULL) receives the best
+   mean time. */
 enkf_status enkf_batch_tune(enkf_handle h, const void* const* d_Xf, const double* const* d_y,
                             const uint64_t* seeds, const uint64_t* counters, void* const* d_Xa,
                             double* best_ms);
@@ -342,6 +347,10 @@ enkf_status enkf_batch_get_stats(enkf_handle h, int32_t* status, int32_t* iters_
    (0; checked at the first analysis) (HOST outputs, any may be NULL). */
 enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, double* alpha,
                                 int32_t* graphed);
+
+/* The row-block floors of the handle's current plan, per ensemble-size class N <= 16, <= 32,
+   <= 64, <= 128 (HOST array of 4; see enkf_batch_tune). */
+enkf_status enkf_batch_get_row_floors(enkf_handle h, int32_t* row_floors);
 
 /* Per-problem phase timers in later batched analyses (enable != 0) or not (0, the default):
    the first CTA of each team reads the global nanosecond timer around the phases of the CG
@@ -372,7 +381,9 @@ enkf_status enkf_selftest_wait_timeout(int32_t which, double timeout_ms, void* c
 
 /* The planner alone, on the host (no GPU needed). A problem costs c = m N^2 (N + 8) + 2 n N^2;
    a team of k CTAs is estimated to take c / k^alpha (0 < alpha <= 1). For a target makespan
-   T every problem with c > T gets the smallest team (2 <= k <= ceil(m / 64)) that meets T;
+   T every problem with c > T gets the smallest team (2 <= k <= ceil(m / floor)) that meets T,
+   floor = row_floors[class of N] (classes N <= 16, <= 32, <= 64, <= 128; HOST array of 4, or
+   NULL for 64 rows in every class);
    the others form a shared queue, longest first, from which the launch hands the next
    problem to whichever CTA is free (the CTAs outside teams from the start, a team's CTAs
    once its problem is done), each solving it alone; T must hold for that schedule too. The
@@ -384,10 +395,12 @@ enkf_status enkf_selftest_wait_timeout(int32_t which, double timeout_ms, void* c
    order[count] (every problem exactly once: the teams' problems, then from
    order[team_first[teams]] on the queue). Arrays of max_grid, max_grid, max_grid,
    max_grid + 1 and count entries are always large enough; any may be NULL. *grid and *teams
-   receive the sizes. ENKF_ERR_INVALID_ARG for alpha outside (0, 1] or bad shapes. */
+   receive the sizes. ENKF_ERR_INVALID_ARG for alpha outside (0, 1], a floor < 1 or bad
+   shapes. */
 enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
-                            int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
-                            int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams);
+                            const int32_t* row_floors, int32_t* cta_team, int32_t* cta_rank,
+                            int32_t* team_size, int32_t* team_first, int32_t* order, int32_t* grid,
+                            int32_t* teams);
 
 /* ---------------------------------------------------------------- learned warm start
    The paper's CG starts from zero. Every solution column of S Z = D has the form

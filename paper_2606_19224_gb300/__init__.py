@@ -25,7 +25,8 @@ EXPORTS = (
     "enkf_draw_perturbations", "enkf_destroy", "enkf_status_str", "enkf_last_error",
     "enkf_set_phase_timing", "enkf_get_phase_times", "enkf_analyze_noalloc", "enkf_create_tridiag",
     "enkf_get_solve_phases", "enkf_batch_create", "enkf_batch_analyze", "enkf_batch_tune",
-    "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_plan", "enkf_batch_set_phase_timing",
+    "enkf_batch_get_stats", "enkf_batch_get_plan", "enkf_batch_get_row_floors", "enkf_batch_plan",
+    "enkf_batch_set_phase_timing",
     "enkf_batch_get_times", "enkf_selftest_wait_timeout",
     "enkf_mlp_param_count", "enkf_mlp_work_bytes", "enkf_mlp_forward", "enkf_mlp_loss_grad",
     "enkf_mlp_adam", "enkf_mlp_train_epoch", "enkf_mlp_standardize", "enkf_warm_features",
@@ -106,6 +107,7 @@ def load(path: str = None):
         "enkf_batch_tune": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "enkf_batch_get_stats": (i32, [vp, vp, vp, vp, vp]),
         "enkf_batch_get_plan": (i32, [vp, vp, vp, vp, vp]),
+        "enkf_batch_get_row_floors": (i32, [vp, vp]),
         "enkf_batch_set_phase_timing": (i32, [vp, i32]),
         "enkf_batch_get_times": (i32, [vp, vp, vp, vp, vp]),
         "enkf_selftest_wait_timeout": (i32, [i32, ctypes.c_double, vp]),
@@ -121,7 +123,7 @@ def load(path: str = None):
         "enkf_warm_features": (i32, [vp, i32, vp, vp]),
         "enkf_set_warm_model": (i32, [vp, ctypes.POINTER(MlpShape), vp]),
         "enkf_batch_plan": (i32, [i32, ctypes.POINTER(Config), i32, ctypes.c_double, vp, vp, vp, vp, vp,
-                                  vp, vp]),
+                                  vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -348,10 +350,11 @@ def selftest_wait_timeout(which, timeout_ms=50.0, stream=None):
     return STATUS.get(st, st)
 
 
-def batch_plan(shapes, max_grid, alpha=1.0):
+def batch_plan(shapes, max_grid, alpha=1.0, row_floors=None):
     """The batched launch planner alone (host only): shapes is a list of (n, m, N), alpha the
-    team-scaling exponent in (0, 1]. Returns dict(grid, teams, cta_team, cta_rank, team_size,
-    team_first, order) as numpy arrays; order[team_first[teams]:] is the shared queue."""
+    team-scaling exponent in (0, 1], row_floors the fewest rows per CTA of a team for N <= 16,
+    <= 32, <= 64, <= 128 (None: 64 each). Returns dict(grid, teams, cta_team, cta_rank,
+    team_size, team_first, order) as numpy arrays; order[team_first[teams]:] is the queue."""
     import numpy as np
     cfgs = (Config * len(shapes))()
     for i, (n, m, N) in enumerate(shapes):
@@ -359,7 +362,9 @@ def batch_plan(shapes, max_grid, alpha=1.0):
     out = {k: np.zeros(max_grid + 1, dtype=np.int32) for k in ("cta_team", "cta_rank", "team_size", "team_first")}
     order = np.zeros(len(shapes), dtype=np.int32)
     grid, teams = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().enkf_batch_plan(len(shapes), cfgs, max_grid, alpha, out["cta_team"].ctypes.data,
+    fl = None if row_floors is None else np.ascontiguousarray(row_floors, dtype=np.int32)
+    _check(load().enkf_batch_plan(len(shapes), cfgs, max_grid, alpha, None if fl is None else fl.ctypes.data,
+                                  out["cta_team"].ctypes.data,
                                   out["cta_rank"].ctypes.data, out["team_size"].ctypes.data,
                                   out["team_first"].ctypes.data, order.ctypes.data, ctypes.byref(grid),
                                   ctypes.byref(teams)))
@@ -438,7 +443,9 @@ class BatchAnalysis:
         g, t, a, gr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
         _check(load().enkf_batch_get_plan(self.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(a),
                                           ctypes.byref(gr)), self.h)
-        return dict(grid=g.value, teams=t.value, alpha=a.value, graphed=gr.value)
+        fl = (ctypes.c_int32 * 4)()
+        _check(load().enkf_batch_get_row_floors(self.h, fl), self.h)
+        return dict(grid=g.value, teams=t.value, alpha=a.value, graphed=gr.value, row_floors=list(fl))
 
     def set_phase_timing(self, enable=True):
         _check(load().enkf_batch_set_phase_timing(self.h, 1 if enable else 0), self.h)

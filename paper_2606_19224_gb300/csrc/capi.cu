@@ -703,6 +703,14 @@ enkf_status enkf_batch_get_plan(enkf_handle h, int32_t* grid, int32_t* teams, do
   return ENKF_OK;
 }
 
+enkf_status enkf_batch_get_row_floors(enkf_handle h, int32_t* row_floors) {
+  if (!h || !h->batch) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_row_floors: not a batched handle");
+  if (!row_floors) return fail(h, ENKF_ERR_INVALID_ARG, "enkf_batch_get_row_floors: NULL output");
+  const enkf::BatchPlanOut p = enkf::batch_info(h);
+  for (int q = 0; q < 4; ++q) row_floors[q] = p.row_floors[q];
+  return ENKF_OK;
+}
+
 enkf_status enkf_selftest_wait_timeout(int32_t which, double timeout_ms, void* cuda_stream) {
   if ((which != 0 && which != 1) || !(timeout_ms > 0.0 && timeout_ms <= 10000.0))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_selftest_wait_timeout: which must be 0 or 1, timeout_ms in (0, 1e4]");
@@ -732,16 +740,20 @@ enkf_status enkf_batch_get_times(enkf_handle h, double* start_us, double* end_us
 }
 
 enkf_status enkf_batch_plan(int32_t count, const enkf_config* cfgs, int32_t max_grid, double alpha,
-                            int32_t* cta_team, int32_t* cta_rank, int32_t* team_size,
-                            int32_t* team_first, int32_t* order, int32_t* grid, int32_t* teams) {
+                            const int32_t* row_floors, int32_t* cta_team, int32_t* cta_rank,
+                            int32_t* team_size, int32_t* team_first, int32_t* order, int32_t* grid,
+                            int32_t* teams) {
   if (count < 1 || !cfgs || max_grid < 1 || !(alpha > 0.0 && alpha <= 1.0))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: bad argument");
+  if (row_floors)
+    for (int q = 0; q < 4; ++q)
+      if (row_floors[q] < 1) return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: row floor < 1");
   for (int32_t i = 0; i < count; ++i)
     if (cfgs[i].m < 1 || cfgs[i].n < 1 || cfgs[i].N < 2 || cfgs[i].N > 128)
       return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: bad problem shape");
   enkf::BatchPlanOut p;
-  if (!enkf::batch_plan_host(count, cfgs, max_grid, alpha, cta_team, cta_rank, team_size, team_first,
-                             order, &p))
+  if (!enkf::batch_plan_host(count, cfgs, max_grid, alpha, row_floors, cta_team, cta_rank, team_size,
+                             team_first, order, &p))
     return fail(nullptr, ENKF_ERR_INVALID_ARG, "enkf_batch_plan: planning failed");
   if (grid) *grid = p.grid;
   if (teams) *teams = p.teams;

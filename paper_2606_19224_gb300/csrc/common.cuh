@@ -226,8 +226,9 @@ struct BatchPlanOut {
   int grid = 0, teams = 0;
   double alpha = 0.0;
   int graphed = 0;
+  int row_floors[4] = {0, 0, 0, 0};   // per N class (<= 16, 32, 64, 128): rows per CTA at least
 };
-bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha,
+bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha, const int* row_floors,
                      int* cta_team, int* cta_rank, int* team_size, int* team_first, int* order,
                      BatchPlanOut* out);
 cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,

@@ -15,6 +15,7 @@
 // re-plans from the measured per-problem durations, and keeps the fastest plan; the choice
 // can be cached in the text file named by the ENKF_TUNE_CACHE variable.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -145,8 +146,17 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(
 }
 
 // ------------------------------------------------------------------ host side
+// Row-block floor per ensemble-size class (N <= 16, <= 32, <= 64, <= 128): a team of k CTAs
+// for a problem of m rows needs m / k >= floor rows per CTA, which caps the team at
+// ceil(m / floor) CTAs. The tuner searches it per class (64 .. 512 rows).
+constexpr int kNClasses = 4;
+using RowFloors = std::array<int, kNClasses>;
+constexpr RowFloors kDefaultFloors{64, 64, 64, 64};
+static int n_class(int N) { return N <= 16 ? 0 : (N <= 32 ? 1 : (N <= 64 ? 2 : 3)); }
+
 struct BatchPlan {
   double alpha = 1.0;
+  RowFloors floors = kDefaultFloors;
   std::vector<double> cost;   // per-problem one-CTA cost the plan was made from
   bool measured = false;      // cost holds measured times (ns) instead of the model's
   int grid = 0;
@@ -191,8 +201,8 @@ static double problem_cost(const enkf_config& c) {
 
 // Makespan planning. A team of k CTAs is assumed to finish a problem of cost c in c / k^alpha
 // (alpha <= 1 charges large teams for their barriers and reductions). For a target time T,
-// every problem with c > T gets the smallest team that meets T (at most ceil(m/64) CTAs, so
-// each CTA keeps >= 64 rows); the others form the shared queue, longest first. The queue is
+// every problem with c > T gets the smallest team that meets T (at most ceil(m / floor) CTAs,
+// floor the row-block floor of its N class); the others form the shared queue, longest first. The queue is
 // simulated as the kernel serves it: the next problem goes to the CTA that is free first
 // (the CTAs outside teams at time 0, each team's CTAs when its problem is done), and every
 // problem must end by T. The plan is the one for the smallest feasible T (bisection); CTAs
@@ -243,14 +253,17 @@ static bool try_plan(const std::vector<double>& cost, const std::vector<int>& ca
 
 // cost[i]: the estimated time of problem i on one CTA (problem_cost, or a measurement).
 static BatchPlan make_plan(const std::vector<enkf_config>& cfg, const std::vector<double>& cost, int G,
-                           double alpha) {
+                           double alpha, const RowFloors& floors = kDefaultFloors) {
   BatchPlan P;
   P.alpha = alpha;
+  P.floors = floors;
   P.cost = cost;
   const int count = (int)cfg.size();
   std::vector<int> cap(count);
-  for (int i = 0; i < count; ++i)
-    cap[i] = (int)std::max<int64_t>(1, std::min<int64_t>(G, (cfg[i].m + 63) / 64));   // >= 64 rows per CTA
+  for (int i = 0; i < count; ++i) {
+    const int64_t fl = floors[n_class(cfg[i].N)];
+    cap[i] = (int)std::max<int64_t>(1, std::min<int64_t>(G, (cfg[i].m + fl - 1) / fl));
+  }
   std::vector<int> idx(count);
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
@@ -318,19 +331,22 @@ static std::vector<double> model_costs(const std::vector<enkf_config>& cfg) {
   return cost;
 }
 
-bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha,
+bool batch_plan_host(int count, const enkf_config* cfgs, int max_grid, double alpha, const int* row_floors,
                      int* cta_team, int* cta_rank, int* team_size, int* team_first, int* order,
                      BatchPlanOut* out) {
   if (count < 1 || !cfgs || max_grid < 1) return false;
   const std::vector<enkf_config> cfg(cfgs, cfgs + count);
-  const BatchPlan P = make_plan(cfg, model_costs(cfg), max_grid, alpha);
+  RowFloors fl = kDefaultFloors;
+  if (row_floors)
+    for (int c = 0; c < kNClasses; ++c) fl[c] = row_floors[c];
+  const BatchPlan P = make_plan(cfg, model_costs(cfg), max_grid, alpha, fl);
   auto put = [](const std::vector<int>& v, int* dst) { if (dst) std::copy(v.begin(), v.end(), dst); };
   put(P.cta_team, cta_team);
   put(P.cta_rank, cta_rank);
   put(P.team_size, team_size);
   put(P.team_first, team_first);
   put(P.order, order);
-  if (out) *out = BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha};
+  if (out) *out = BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha, 0, {P.floors[0], P.floors[1], P.floors[2], P.floors[3]}};
   return true;
 }
 
@@ -557,8 +573,10 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
     B.probs.push_back(bp);
   }
   if (e != cudaSuccess) { err = "enkf_batch_create: upload of the observation operators"; return e; }
-  // a tuning result for this batch: "key alpha [cost_0 .. cost_{count-1}]"; the last one wins
+  // a tuning result for this batch: "key alpha [rows f_0 .. f_3] [cost_0 .. cost_{count-1}]"
+  // (row-block floors per N class, measured one-CTA costs); the last one wins
   double alpha = 1.0;
+  RowFloors floors = kDefaultFloors;
   std::vector<double> cost = model_costs(B.cfg);
   bool measured = false;
   if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
@@ -570,18 +588,30 @@ cudaError_t batch_build(enkf_handle_s* h, int count, const enkf_config* cfgs,
       std::string k;
       double a = 0.0;
       if (!(ls >> k >> a) || k != key || !(a > 0.0 && a <= 1.0)) continue;
+      RowFloors fl = kDefaultFloors;
       std::vector<double> c;
-      double v;
-      while (ls >> v) c.push_back(v);
+      std::string tok;
+      bool ok_f = true;
+      while (ls >> tok) {
+        if (tok == "rows" && c.empty()) {
+          for (int q = 0; q < kNClasses && ok_f; ++q) ok_f = static_cast<bool>(ls >> fl[q]) && fl[q] >= 1;
+        } else {
+          char* end = nullptr;
+          const double v = std::strtod(tok.c_str(), &end);
+          if (end == tok.c_str() || *end != '\0') { ok_f = false; break; }
+          c.push_back(v);
+        }
+      }
       const bool ok_c = (int)c.size() == count &&
                         std::all_of(c.begin(), c.end(), [](double x) { return x > 0.0 && std::isfinite(x); });
-      if (!c.empty() && !ok_c) continue;
+      if (!ok_f || (!c.empty() && !ok_c)) continue;
       alpha = a;
+      floors = fl;
       measured = !c.empty();
       cost = measured ? c : model_costs(B.cfg);
     }
   }
-  BatchPlan P = make_plan(B.cfg, cost, B.max_grid, alpha);
+  BatchPlan P = make_plan(B.cfg, cost, B.max_grid, alpha, floors);
   P.measured = measured;
   e = apply_plan(B, P, h->stream);
   if (e != cudaSuccess) err = "enkf_batch_create: plan upload";
@@ -627,7 +657,8 @@ static std::vector<int> problem_team(const BatchPlan& P, int count) {
 // that is another: each problem's one-CTA cost is estimated from its duration in the start
 // plan (the mean over its three timed analyses, times k^alpha for a team of k), the batch is
 // re-planned from those costs and timed, and the estimate is averaged with the new plan's
-// durations for the next of four rounds. The fastest plan of all is kept.
+// durations for the next of four rounds. Stage 3 searches the row-block floor of each N
+// class (below). The fastest plan of all is kept.
 cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* const* y,
                        const uint64_t* seeds, const uint64_t* counters, void* const* Xa,
                        double* best_alpha, double* best_ms) {
@@ -703,6 +734,36 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
       for (int i = 0; i < B.count; ++i) est[i] = 0.5 * (est[i] + now[i]);
     }
   }
+  // Stage 3: the row-block floor of each N class (the smallest row block a team's CTA may
+  // get, which caps the team size), by coordinate descent from the best plan with its costs
+  // and alpha: classes in order of their share of the cost (those under 5 % left at 64 rows),
+  // each floor in {128, 256, 512} planned and, where the plan changes, timed; a floor is kept
+  // when the batch is at least 1 % faster.
+  if (e == cudaSuccess) {
+    std::array<double, kNClasses> share{};
+    double total = 0.0;
+    for (int i = 0; i < B.count; ++i) {
+      share[n_class(B.cfg[i].N)] += best_plan.cost[i];
+      total += best_plan.cost[i];
+    }
+    std::array<int, kNClasses> cls{0, 1, 2, 3};
+    std::sort(cls.begin(), cls.end(), [&](int a, int b) { return share[a] > share[b]; });
+    for (int c : cls) {
+      if (e != cudaSuccess || !(share[c] >= 0.05 * total)) continue;
+      for (int fl : {128, 256, 512}) {
+        RowFloors f = best_plan.floors;
+        f[c] = fl;
+        BatchPlan P = make_plan(B.cfg, best_plan.cost, B.max_grid, best_plan.alpha, f);
+        P.measured = best_plan.measured;
+        if (P.team_size == best_plan.team_size && P.order == best_plan.order) continue;   // same plan
+        double ms = 0.0;
+        std::vector<double> ns;
+        e = time_plan(P, ms, ns);
+        if (e != cudaSuccess) break;
+        if (ms < 0.99 * best) { best = ms; best_plan = P; }
+      }
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
@@ -711,7 +772,8 @@ cudaError_t batch_tune(enkf_handle_s* h, const void* const* Xf, const double* co
   if (best_ms) *best_ms = best;
   if (const char* path = std::getenv("ENKF_TUNE_CACHE")) {
     std::ofstream f(path, std::ios::app);
-    f << cache_key(B) << " " << best_plan.alpha;
+    f << cache_key(B) << " " << best_plan.alpha << " rows";
+    for (int q = 0; q < kNClasses; ++q) f << " " << best_plan.floors[q];
     if (best_plan.measured) {
       char buf[32];
       for (double c : best_plan.cost) {
@@ -796,7 +858,8 @@ cudaError_t batch_times(enkf_handle_s* h, double* start_us, double* end_us, doub
 BatchPlanOut batch_info(const enkf_handle_s* h) {
   if (!h->batch) return BatchPlanOut{};
   const BatchPlan& P = h->batch->plan;
-  return BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha, h->batch->graph_ok ? 1 : 0};
+  return BatchPlanOut{P.grid, (int)P.team_size.size(), P.alpha, h->batch->graph_ok ? 1 : 0,
+                      {P.floors[0], P.floors[1], P.floors[2], P.floors[3]}};
 }
 
 int batch_count(const enkf_handle_s* h) { return h->batch ? h->batch->count : 0; }

@@ -125,3 +125,24 @@ def test_plan_rejects_bad_args(ext):
         ext.batch_plan([(100, 25, 16)], 8, 0.0)
     with pytest.raises(ext.EnKFError):
         ext.batch_plan([(100, 25, 16)], 8, 1.5)
+
+
+def test_row_floors_cap_the_teams(ext):
+    """A row floor f for an N class caps that class's teams at ceil(m / f) CTAs; the other
+    classes keep the default of 64 rows; every plan still covers each problem once."""
+    specs = batched_problem_specs(64, seed=3)
+    shapes = [(s["n"], s["m"], s["N"]) for s in specs]
+    cls = lambda N: 0 if N <= 16 else (1 if N <= 32 else (2 if N <= 64 else 3))
+    for floors in ([64, 64, 64, 512], [256, 128, 512, 64], [1000, 1000, 1000, 1000]):
+        plan = ext.batch_plan(shapes, 152, 1.0, row_floors=floors)
+        check_plan(shapes, 152, 1.0, dict(plan))
+        ts, tf, order = plan["team_size"], plan["team_first"], plan["order"]
+        for t in range(plan["teams"]):
+            for p in order[tf[t]:tf[t + 1]]:
+                n, m, N = shapes[p]
+                assert ts[t] <= max(1, -(-m // floors[cls(N)]))
+    # a floor that forbids every team sends every problem to the queue
+    big = ext.batch_plan(shapes, 152, 1.0, row_floors=[10 ** 9] * 4)
+    assert all(big["team_size"] == 1)
+    with pytest.raises(ext.EnKFError):
+        ext.batch_plan(shapes, 152, 1.0, row_floors=[64, 0, 64, 64])

@@ -122,8 +122,10 @@ def test_batch_tune_and_cache(lib, batch10, tmp_path, monkeypatch):
     assert plan["alpha"] in (1.0, 0.9, 0.8)
     line = cache.read_text().splitlines()[-1].split()
     assert float(line[1]) == plan["alpha"]
-    assert len(line) in (2, 2 + len(probs))        # alpha alone, or with the measured costs
-    assert all(float(c) > 0.0 for c in line[2:])
+    assert line[2] == "rows" and [int(v) for v in line[3:7]] == plan["row_floors"]
+    assert all(f in (64, 128, 256, 512) for f in plan["row_floors"])
+    assert len(line) in (7, 7 + len(probs))        # alpha and floors, or with the measured costs
+    assert all(float(c) > 0.0 for c in line[7:])
     Xa = ba.analyze(Xf, y, [4] * 8, None)
     for i, p in enumerate(probs):
         assert oracle.rel_frobenius(Xa[i].double().cpu().numpy(), _oracle(p, 4, 0)) <= TOL
@@ -131,7 +133,7 @@ def test_batch_tune_and_cache(lib, batch10, tmp_path, monkeypatch):
     # a new handle for the same batch rebuilds the cached plan
     ba2 = lib.BatchAnalysis(_dicts(probs))
     plan2 = ba2.plan()
-    assert all(plan2[k] == plan[k] for k in ("grid", "teams", "alpha"))
+    assert all(plan2[k] == plan[k] for k in ("grid", "teams", "alpha", "row_floors"))
     Xa = ba2.analyze(Xf, y, [4] * 8, None)
     for i, p in enumerate(probs):
         assert oracle.rel_frobenius(Xa[i].double().cpu().numpy(), _oracle(p, 4, 0)) <= TOL
