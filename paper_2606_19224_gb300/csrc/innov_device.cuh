@@ -36,22 +36,52 @@ __device__ __forceinline__ void perturbation_pair(int64_t i, int j, uint64_t see
 // pi 2 u2. Each normal is within about 1e-7 (relative to its size) of the FP64 form, and the
 // FP64 log and sincos, which dominate the innovations on a GPU whose FP64 rate is a small
 // fraction of its FP32 rate, are avoided.
+// Conversions that stay off the FP64 pipe (two operations per clock per SM on this part; the
+// 64-bit conversion instructions run there too).
+// The float nearest to the 53-bit integer a 2^21 + b (a < 2^32, b < 2^21), as a 64-bit to
+// float conversion rounds it, from 32-bit conversions: for a >= 2^25 the rounding drops at
+// least two bits of a, so ORing "b != 0" into its lowest bit supplies the sticky bit without
+// touching the round bit; otherwise a >> 1 and ((a & 1) << 21) | b are exact floats and one
+// FP32 fused multiply-add rounds their exact sum once.
+__device__ __forceinline__ float u53_to_float(uint32_t a, uint32_t b) {
+  if (a >= (1u << 25)) return __uint2float_rn(a | (b != 0u ? 1u : 0u)) * 0x1p21f;
+  return fmaf(__uint2float_rn(a >> 1), 0x1p22f, __uint2float_rn(((a & 1u) << 21) | b));
+}
+// (double)x by exponent rebias and mantissa shift for normal x and zero; subnormals,
+// infinities and NaN take the conversion instruction.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((uint64_t)u << 32));
+  if (e == 0u || e == 0xFFu) return (double)x;
+  return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                                          ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+// hi + lo rounded to FP64, as (double)hi + (double)lo: one FP64 addition
+__device__ __forceinline__ double df_to_double(const df32& v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
+// df32(x) for a double x: hi = x rounded to float, lo = (x - hi) rounded to float, with the
+// widening of hi done by f2d_bits (three FP64-pipe operations instead of four)
+__device__ __forceinline__ df32 df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return df32(hi, __double2float_rn(x - f2d_bits(hi)));
+}
+
 __device__ __forceinline__ void perturbation_pair_f32(int64_t i, int j, uint64_t seed, uint64_t counter,
                                                       float& n_even, float& n_odd) {
   uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(j >> 1), c2 = (uint32_t)counter, c3 = (uint32_t)(counter >> 32);
   philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
   const uint64_t x1 = ((uint64_t)c0 << 21) | (c1 >> 11);
-  const uint64_t x2 = ((uint64_t)c2 << 21) | (c3 >> 11);
   float lg;
   if (x1 < (1ull << 52)) {
-    lg = logf(fmaf(__ull2float_rn(x1), 0x1p-53f, 0x1p-54f));
+    lg = logf(fmaf(u53_to_float(c0, c1 >> 11), 0x1p-53f, 0x1p-54f));
   } else {
-    const float w = fmaf(__ull2float_rn((1ull << 53) - x1), 0x1p-53f, -0x1p-54f);   // 1 - u1
+    const uint64_t y1 = (1ull << 53) - x1;   // 1 - u1 = (y1 - 1/2) 2^-53, y1 <= 2^52
+    const float w = fmaf(u53_to_float((uint32_t)(y1 >> 21), (uint32_t)(y1 & 0x1FFFFFu)), 0x1p-53f, -0x1p-54f);
     lg = log1pf(-w);
   }
   const float rho = sqrtf(-2.f * lg);
   float sn, cs;
-  sincospif(__ull2float_rn(x2) * 0x1p-52f, &sn, &cs);
+  sincospif(u53_to_float(c2, c3 >> 11) * 0x1p-52f, &sn, &cs);
   n_even = rho * cs;
   n_odd = rho * sn;
 }
@@ -188,78 +218,92 @@ __device__ __forceinline__ void innov_rows_df(
   const int lane = threadIdx.x & 31;
   const df32 inv_n(1.0 / (double)N);
   const bool wide = N > 64;   // members 64..127 present (warp-uniform)
-  for (int64_t i = i_begin + warp; i < i_end; i += nwarps) {
-    df32 z[4];
-    const int k0 = rowptr[i], k1 = rowptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const df32 wk(w[k]);
-      const VT* xr = Xf + (int64_t)col[k] * N;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 2 * lane + (q & 1) + 64 * (q >> 1);
-        if (j < N) z[q] = fma(wk, df32((float)xr[j], 0.f), z[q]);
-      }
+  // The warp's rows are i0 + q nwarps, q = 0, 1, ...; the per-row values that come from FP64
+  // inputs (y_i and sqrt(r_i) as double-float pairs) are formed for 32 rows at a time, lane q
+  // for row i0 + q nwarps, and handed to the other lanes by shuffles: one FP64 evaluation per
+  // row instead of one per lane.
+  for (int64_t i0 = i_begin + warp; i0 < i_end; i0 += 32 * nwarps) {
+    const int64_t il = i0 + (int64_t)lane * nwarps;
+    df32 y_l, s_l;
+    if (il < i_end) {
+      y_l = df_from_double(y[il]);
+      if (emode == 2) s_l = df_from_double(sqrt(r[il]));
     }
-    df32 s = z[0] + z[1];
-    if (wide) s = s + (z[2] + z[3]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      s = s + df32(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
-    const df32 zbar = s * inv_n;
-    const df32 yd(y[i]);
-    const df32 sr = emode == 2 ? df32(sqrt(r[i])) : df32();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int jp = 2 * lane + 64 * h;   // even member of the pair
-      if (jp >= N) continue;
-      float nrm[2] = {0.f, 0.f};
-      if (emode == 2) perturbation_pair_f32(i, jp, seed, counter, nrm[0], nrm[1]);
-      const int64_t e0 = i * N + jp;
-      df32 hv[2], dv[2];
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        df32 pert;
-        if (jp + b < N) {
-          if (emode == 1) pert = df32(E[e0 + b]);
-          else if (emode == 2) pert = sr * df32(nrm[b], 0.f);
+    for (int q32 = 0; q32 < 32; ++q32) {
+      const int64_t i = i0 + (int64_t)q32 * nwarps;
+      if (i >= i_end) break;   // warp-uniform
+      const df32 yd(__shfl_sync(0xffffffffu, y_l.hi, q32), __shfl_sync(0xffffffffu, y_l.lo, q32));
+      const df32 sr(__shfl_sync(0xffffffffu, s_l.hi, q32), __shfl_sync(0xffffffffu, s_l.lo, q32));
+      df32 z[4];
+      const int k0 = rowptr[i], k1 = rowptr[i + 1];
+      for (int k = k0; k < k1; ++k) {
+        const df32 wk = df_from_double(w[k]);
+        const VT* xr = Xf + (int64_t)col[k] * N;
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 2 * lane + (q & 1) + 64 * (q >> 1);
+          if (j < N) z[q] = fma(wk, df32((float)xr[j], 0.f), z[q]);
         }
-        hv[b] = z[2 * h + b] - zbar;
-        dv[b] = (yd - z[2 * h + b]) + pert;
       }
-      if ((N & 1) == 0) {
-        // both members present and e0 even: one 8- or 16-byte store per array per lane
-        *reinterpret_cast<double2*>(D + e0) = make_double2((double)dv[0], (double)dv[1]);
-        if (HA32) *reinterpret_cast<float2*>(HA32 + e0) = make_float2(hv[0].hi, hv[1].hi);
-        if (B32) *reinterpret_cast<float2*>(B32 + e0) = make_float2(dv[0].hi, dv[1].hi);
-        if (HAdf) *reinterpret_cast<float4*>(HAdf + e0) = make_float4(hv[0].hi, hv[0].lo, hv[1].hi, hv[1].lo);
-        if (Ddf) *reinterpret_cast<float4*>(Ddf + e0) = make_float4(dv[0].hi, dv[0].lo, dv[1].hi, dv[1].lo);
-      } else {
-#pragma unroll
+      df32 s = z[0] + z[1];
+      if (wide) s = s + (z[2] + z[3]);
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        s = s + df32(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
+      const df32 zbar = s * inv_n;
+  #pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jp = 2 * lane + 64 * h;   // even member of the pair
+        if (jp >= N) continue;
+        float nrm[2] = {0.f, 0.f};
+        if (emode == 2) perturbation_pair_f32(i, jp, seed, counter, nrm[0], nrm[1]);
+        const int64_t e0 = i * N + jp;
+        df32 hv[2], dv[2];
+  #pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          df32 pert;
+          if (jp + b < N) {
+            if (emode == 1) pert = df_from_double(E[e0 + b]);
+            else if (emode == 2) pert = sr * df32(nrm[b], 0.f);
+          }
+          hv[b] = z[2 * h + b] - zbar;
+          dv[b] = (yd - z[2 * h + b]) + pert;
+        }
+        if ((N & 1) == 0) {
+          // both members present and e0 even: one 8- or 16-byte store per array per lane
+          *reinterpret_cast<double2*>(D + e0) = make_double2(df_to_double(dv[0]), df_to_double(dv[1]));
+          if (HA32) *reinterpret_cast<float2*>(HA32 + e0) = make_float2(hv[0].hi, hv[1].hi);
+          if (B32) *reinterpret_cast<float2*>(B32 + e0) = make_float2(dv[0].hi, dv[1].hi);
+          if (HAdf) *reinterpret_cast<float4*>(HAdf + e0) = make_float4(hv[0].hi, hv[0].lo, hv[1].hi, hv[1].lo);
+          if (Ddf) *reinterpret_cast<float4*>(Ddf + e0) = make_float4(dv[0].hi, dv[0].lo, dv[1].hi, dv[1].lo);
+        } else {
+  #pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            if (jp + b >= N) continue;
+            const int64_t e = e0 + b;
+            D[e] = df_to_double(dv[b]);
+            if (HA32) HA32[e] = hv[b].hi;
+            if (B32) B32[e] = dv[b].hi;
+            if (HAdf) HAdf[e] = hv[b];
+            if (Ddf) Ddf[e] = dv[b];
+          }
+        }
+        // optional copies (not requested by the current callers): FP64 HA and 16-bit images
+  #pragma unroll
         for (int b = 0; b < 2; ++b) {
           if (jp + b >= N) continue;
           const int64_t e = e0 + b;
-          D[e] = (double)dv[b];
-          if (HA32) HA32[e] = hv[b].hi;
-          if (B32) B32[e] = dv[b].hi;
-          if (HAdf) HAdf[e] = hv[b];
-          if (Ddf) Ddf[e] = dv[b];
-        }
-      }
-      // optional copies (not requested by the current callers): FP64 HA and 16-bit images
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        if (jp + b >= N) continue;
-        const int64_t e = e0 + b;
-        if (HA64) HA64[e] = (double)hv[b];
-        if (HAb) {
-          const __nv_bfloat16 hi = __float2bfloat16(hv[b].hi);
-          HAb[e] = hi;
-          if (split_lo) HAb[m * N + e] = __float2bfloat16((hv[b] - df32(__bfloat162float(hi), 0.f)).hi);
-        }
-        if (HAh) {
-          const __half hi = __float2half(hv[b].hi);
-          HAh[e] = hi;
-          if (split_lo) HAh[m * N + e] = __float2half((hv[b] - df32(__half2float(hi), 0.f)).hi);
+          if (HA64) HA64[e] = (double)hv[b];
+          if (HAb) {
+            const __nv_bfloat16 hi = __float2bfloat16(hv[b].hi);
+            HAb[e] = hi;
+            if (split_lo) HAb[m * N + e] = __float2bfloat16((hv[b] - df32(__bfloat162float(hi), 0.f)).hi);
+          }
+          if (HAh) {
+            const __half hi = __float2half(hv[b].hi);
+            HAh[e] = hi;
+            if (split_lo) HAh[m * N + e] = __float2half((hv[b] - df32(__half2float(hi), 0.f)).hi);
+          }
         }
       }
     }
