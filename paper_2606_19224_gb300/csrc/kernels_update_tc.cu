@@ -2,15 +2,16 @@
 // on the 5th-generation tensor cores, for FP32 ensembles.
 //
 // Per 128-row tile of X_f: the rows are staged in shared memory (16-byte cp.async; for N <= 64
-// the next tile's copy is in flight behind the current one), each row's mean and largest anomaly are
+// the next two tiles' copies are in flight behind the current one), each row's mean and largest anomaly are
 // formed, and the anomalies scaled by an exact power of two per row (so FP16 neither overflows
 // nor flushes) are split into hi + lo FP16 parts in the canonical K-major core-matrix layout,
 // the lo part stored times 2^11 so that it stays in FP16's normal range. W is staged once per
 // CTA the same way (rows j, K-major over k, a power-of-two scale per column). D = A W runs as
 // three M = 128 x N = NT x K = NT MMAs per K block with FP32 accumulation in TMEM: hi*hi into
 // one accumulator, hi*lo' + lo'*hi into a second, so D = D1 + 2^-11 D2 carries about 22
-// significant bits per product; the epilogue reads both row by row, undoes the scales and
-// writes X_a = X_f + D. X_a may be
+// significant bits per product; the epilogue reads both row by row, undoes the scales, forms
+// X_a = X_f + D in place of the staged tile and then writes the tile out with coalesced
+// 16-byte stores (a row per thread would scatter every store over 32 rows). X_a may be
 // X_f itself: a tile is read into shared memory before any of its rows is written, and no CTA
 // reads another CTA's tiles.
 #include <algorithm>
@@ -25,7 +26,7 @@ template <int NT> struct UpdLayout {
   static constexpr int XT = kTR * LDX * 4;                 // bytes per staged tile
   static constexpr int AIMG = 2 * kTR * NT * 2;            // A image: hi and lo parts
   static constexpr int BIMG = 2 * NT * NT * 2;             // W image: hi and lo parts
-  static constexpr int NBUF = NT <= 64 ? 2 : 1;            // staged tiles (NT = 128: one, smem)
+  static constexpr int NBUF = NT <= 64 ? 3 : 1;            // staged tiles (NT = 128: one, smem)
   static constexpr int off_x = 0;
   static constexpr int off_a = ((NBUF * XT + 1023) / 1024) * 1024;
   static constexpr int off_b = off_a + AIMG;
@@ -111,19 +112,26 @@ __global__ void __launch_bounds__(kThreads, 1) update_tc_kernel(const float* Xf,
   };
   uint32_t ph = 0;
   bool ok = true;
-  int buf = 0;
-  if (L::NBUF == 2 && (int64_t)blockIdx.x < ntiles) stage(blockIdx.x, sX0);
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= (L::NBUF - 1)) {
-    float* sX = sX0 + buf * (L::XT / 4);
-    const int64_t nxt = tile + gridDim.x;
+  auto xbuf = [&](int64_t k) { return sX0 + (int)(k % L::NBUF) * (L::XT / 4); };
+  // NBUF - 1 tiles in flight ahead of the one being processed (one commit group per tile,
+  // empty past the end, so that "all but the newest NBUF - 1 groups" is always this tile)
+  if (L::NBUF > 1)
+    for (int q = 0; q < L::NBUF - 1; ++q) {
+      const int64_t tq = (int64_t)blockIdx.x + (int64_t)q * gridDim.x;
+      if (tq < ntiles) stage(tq, xbuf(q));
+      else cp_async_commit();
+    }
+  int64_t k = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
+    float* sX = xbuf(k);
     if (L::NBUF == 1) {
       stage(tile, sX);
       cp_async_wait<0>();
-    } else if (nxt < ntiles) {
-      stage(nxt, sX0 + (buf ^ 1) * (L::XT / 4));
-      cp_async_wait<1>();
     } else {
-      cp_async_wait<0>();
+      const int64_t nxt = tile + (int64_t)(L::NBUF - 1) * gridDim.x;
+      if (nxt < ntiles) stage(nxt, xbuf(k + L::NBUF - 1));   // the buffer of tile k - 1, consumed
+      else cp_async_commit();
+      cp_async_wait<(L::NBUF > 1 ? L::NBUF - 1 : 0)>();
     }
     __syncthreads();
     // row means and the largest anomaly of each row: two threads per row
@@ -189,16 +197,28 @@ __global__ void __launch_bounds__(kThreads, 1) update_tc_kernel(const float* Xf,
         for (int y4 = 0; y4 < 4; ++y4) {
           const int jj = j0 + 4 * y4;
           if (jj < N) {
-            float o[4];
-#pragma unroll
-            for (int y = 0; y < 4; ++y)
-              o[y] = fmaf(d[4 * y4 + y] * irs, s_ws[jj + y], sX[rt * L::LDX + jj + y]);
-            st4<float>(Xa + i * N, jj, N, vec, o);
+            float* xr = sX + rt * L::LDX + jj;
+            const float4 xf = *reinterpret_cast<const float4*>(xr);
+            *reinterpret_cast<float4*>(xr) = make_float4(fmaf(d[4 * y4] * irs, s_ws[jj], xf.x),
+                                                         fmaf(d[4 * y4 + 1] * irs, s_ws[jj + 1], xf.y),
+                                                         fmaf(d[4 * y4 + 2] * irs, s_ws[jj + 2], xf.z),
+                                                         fmaf(d[4 * y4 + 3] * irs, s_ws[jj + 3], xf.w));
           }
         }
       }
     }
     tc_fence_before();
+    __syncthreads();
+    // the finished tile out: consecutive threads on consecutive 16-byte pieces of a row
+    for (int c = t; c < kTR * C4; c += kThreads) {
+      const int r = c / C4, c0 = (c % C4) * 4;
+      const int64_t ig = tile * kTR + r;
+      if (ig < n && c0 < N) {
+        const float4 v = *reinterpret_cast<const float4*>(sX + r * L::LDX + c0);
+        const float o[4] = {v.x, v.y, v.z, v.w};
+        st4<float>(Xa + ig * N, c0, N, vec, o);
+      }
+    }
     __syncthreads();   // the staged tile, the A image and TMEM are rewritten by the next tile
   }
   cp_async_wait<0>();
