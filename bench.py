@@ -131,7 +131,7 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
 # the hash of the kernel sources each capture measured; reported as null once those sources
 # have changed.
 NCU_TRAFFIC = {"fp32": {"bytes": 1.442546e9, "src_sha": "998371542af81f75"},
-               "fp16": {"bytes": 1.154300e9, "src_sha": "f21d8c6a874a6c42"}}
+               "fp16": {"bytes": 1.079231e9, "src_sha": "407a4cb0b01d51b9"}}
 # DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
 # profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
 NCU_TRAFFIC_BATCH = {"bytes": 1.436453e12, "problems": 256, "seed": 1, "src_sha": "869cf69968486ece"}

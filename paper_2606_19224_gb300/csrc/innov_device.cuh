@@ -219,25 +219,28 @@ __device__ __forceinline__ void innov_rows_df(
   const df32 inv_n(1.0 / (double)N);
   const bool wide = N > 64;   // members 64..127 present (warp-uniform)
   // The warp's rows are i0 + q nwarps, q = 0, 1, ...; the per-row values that come from FP64
-  // inputs (y_i and sqrt(r_i) as double-float pairs) are formed for 32 rows at a time, lane q
-  // for row i0 + q nwarps, and handed to the other lanes by shuffles: one FP64 evaluation per
-  // row instead of one per lane.
+  // inputs (y_i, sqrt(r_i) and the weight of the row's first operator entry as double-float
+  // pairs) are formed for 32 rows at a time, lane q for row i0 + q nwarps, and handed to the
+  // other lanes by shuffles: one FP64 evaluation per row instead of one per lane.
   for (int64_t i0 = i_begin + warp; i0 < i_end; i0 += 32 * nwarps) {
     const int64_t il = i0 + (int64_t)lane * nwarps;
-    df32 y_l, s_l;
+    df32 y_l, s_l, w_l;
     if (il < i_end) {
       y_l = df_from_double(y[il]);
       if (emode == 2) s_l = df_from_double(sqrt(r[il]));
+      const int kf = rowptr[il];
+      if (kf < rowptr[il + 1]) w_l = df_from_double(w[kf]);
     }
     for (int q32 = 0; q32 < 32; ++q32) {
       const int64_t i = i0 + (int64_t)q32 * nwarps;
       if (i >= i_end) break;   // warp-uniform
       const df32 yd(__shfl_sync(0xffffffffu, y_l.hi, q32), __shfl_sync(0xffffffffu, y_l.lo, q32));
       const df32 sr(__shfl_sync(0xffffffffu, s_l.hi, q32), __shfl_sync(0xffffffffu, s_l.lo, q32));
+      const df32 w0(__shfl_sync(0xffffffffu, w_l.hi, q32), __shfl_sync(0xffffffffu, w_l.lo, q32));
       df32 z[4];
       const int k0 = rowptr[i], k1 = rowptr[i + 1];
       for (int k = k0; k < k1; ++k) {
-        const df32 wk = df_from_double(w[k]);
+        const df32 wk = k == k0 ? w0 : df_from_double(w[k]);
         const VT* xr = Xf + (int64_t)col[k] * N;
   #pragma unroll
         for (int q = 0; q < 4; ++q) {
