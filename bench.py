@@ -84,7 +84,7 @@ def B_FUSED(m, N):
 
 
 # Measured on a GB300 with a register-resident FMA loop (152 SMs at 2.07 GHz): FP64 FMA
-# 1.20 TFLOP/s, FP32 FMA 74.7 TFLOP/s. Tensor peaks (BF16 = FP16) from the driver's file.
+# 1.20 TFLOP/s, FP32 FMA 74.7 TFLOP/s. Tensor peaks (BF16 = FP16) from MEASURED_PEAKS.json.
 FP64_TFLOPS = 1.20
 FP32_TFLOPS = 74.7
 

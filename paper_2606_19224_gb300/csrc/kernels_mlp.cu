@@ -262,7 +262,7 @@ __global__ void standardize_rows_kernel(const float* __restrict__ X, const int32
   }
 }
 
-// ------------------------------------------------------------------ MLP driver (host)
+// ------------------------------------------------------------------ MLP, host side
 struct MlpWork {
   float* Xs;     // standardised (gathered) input [B][in]
   float* Z[8];   // pre-activations per hidden layer [B][H]
