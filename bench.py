@@ -12,9 +12,11 @@ N = 64 members, m = 65,536 randomly placed observations, r ~ U[0.5, 1.5], CG tol
 Prints one JSON line (rank 0). `value` is analyses/s summed over ranks (each rank runs its
 own independent analyses: weak scaling, no collective on the data path). The timed headline
 is CG preconditioned by R with both HA contractions of every step on the tensor cores
-(tcgen05, FP16 hi/lo operands, FP32 accumulation), FP32 vectors, FP64 scalars and a
-double-float residual refresh (meets 1e-6 relative Frobenius error against the FP64 oracle;
-`--precision fp32` times the FP32 CUDA-core solve instead). On one GPU the same run then
+(tcgen05, FP16 hi/lo operands, FP32 accumulation), FP32 vectors, FP64 scalars, each step's
+sums over the CTAs formed by atomic adds (`--reduce-order 0`: in a fixed order, bitwise
+repeatable) and a double-float residual refresh (meets 1e-6 relative Frobenius error against
+the FP64 oracle; `--precision fp32` times the FP32 CUDA-core solve instead). On one GPU the
+same run then
 measures, after the timed region, every other configuration of the method as keys of the
 same line:
   c1_variants      the 512x512 workload in plain FP64 CG (the comparison point), FP64 CG
@@ -439,15 +441,19 @@ def _err(out, ref):
             "max_abs_err_over_max_abs": float(np.max(np.abs(X - ref)) / np.max(np.abs(ref)))}
 
 
+# how each step's sums over the CTAs are formed (enkf_config.reduce_order)
+REDUCE_NAME = {0: "fixed order (bitwise repeatable)",
+               1: "atomic adds (tensor-core modes, N <= 64; last bits vary from run to run)"}
 KERNEL_NAME = {"fp64": "solve_kernel<double>", "fp32": "solve_kernel<float>",
                "fp16": "solve_mixed_kernel<half>", "bf16": "solve_mixed_kernel<bf16>"}
 
 
-def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref):
+def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref, reduce_order=0):
     """One precision / solver variant on problem p: timing, iterations, accuracy and the
     roofline of its solve launch."""
     import torch
-    an = enkf.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8, precondition=pc)
+    an = enkf.Analysis(p.n, p.m, p.N, p.rowptr, p.col, p.w, p.r, precision=prec, tol=1e-8, precondition=pc,
+                       reduce_order=reduce_order)
     out = torch.empty_like(Xd)
     res = timer.analyses(an, Xd, y, seed, steps, warmup, out)
     an.analyze(Xd, y, seed, 0, out=out)
@@ -457,6 +463,7 @@ def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref):
     res["value"] = 1e3 / res["ms_per_step"]
     res["unit"] = UNIT
     res["solver"] = "CG preconditioned by R" if pc else "plain CG"
+    res["reduce_order"] = REDUCE_NAME[reduce_order]
     res["roofline"] = analysis_roofline(p.m, p.N, prec, res["iters"], res["refinements"] if prec != "fp64" else 1,
                                         res["solve_ms"], KERNEL_NAME[prec])
     an.close()
@@ -481,7 +488,7 @@ def run_ours(args):
     p = synth.workload(WORKLOAD, seed, dtype=np.float32)
     n, m, N = p.n, p.m, p.N
     an = enkf.Analysis(n, m, N, p.rowptr, p.col, p.w, p.r, precision=args.precision, tol=1e-8,
-                       precondition=args.precondition)
+                       precondition=args.precondition, reduce_order=args.reduce_order)
     an.set_phase_timing(True)
     Xf = torch.from_numpy(p.Xf).to(dev)
     y = torch.from_numpy(p.y).to(dev)
@@ -568,6 +575,7 @@ def run_ours(args):
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8, "precision": prec_name,
                        "solver": "CG preconditioned by R" if args.precondition else "plain CG",
+                       "reduce_order": REDUCE_NAME[args.reduce_order if args.precision != "fp32" else 0],
                        "l2": "flushed between steps", "status": last_status["status"]},
             "roofline": roofline, "e2e": e2e,
             # innovations, (tile images of HA for the tensor-core path,) solve, update
@@ -597,6 +605,11 @@ def run_ours(args):
     c1["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp32_plain_cg"] = _variant(enkf, p, "fp32", 0, timer, Xf, y, seed, args.fp64_steps, 1, ref)
+    if args.precision != "fp32":
+        # the headline's precision with the other reduction order
+        other = 1 - args.reduce_order
+        c1[args.precision + "_pcg_" + ("atomic" if other else "fixed_order")] = _variant(
+            enkf, p, args.precision, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref, reduce_order=other)
     for prec in ("fp32", "fp16", "bf16"):
         if prec != args.precision:
             c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref)
@@ -1100,6 +1113,9 @@ def main():
                     help="state sizes p of the Example 2b (Table 5) section")
     ap.add_argument("--warm-train-seeds", type=int, default=40,
                     help="ensembles (x 8 observation draws) the learned warm start trains on in the default run")
+    ap.add_argument("--reduce-order", type=int, default=1, choices=[0, 1],
+                    help="tensor-core headline: 1 sums each step over the CTAs by atomic adds (one grid "
+                         "barrier per step), 0 in a fixed order (bitwise repeatable)")
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"],
                     help="inner-solve precision of the timed path (default workload)")
     ap.add_argument("--batch-count", type=int, default=256,

@@ -121,7 +121,15 @@ typedef struct enkf_config {
                              1 every finite start is kept. Either way a non-finite start
                              starts from zero and the result is certified by the same
                              double-float true residual <= tol                          */
-  int32_t reserved[4];    /* must be zero                                                */
+  int32_t reduce_order;   /* 0 (default): every step's column sums and Gram are summed over
+                             the CTAs in a fixed order (bitwise repeatable results, two
+                             grid barriers per step); 1: BF16/FP16 modes with N <= 64 add
+                             them into the total by atomic adds (one barrier per step, the
+                             last bits of the sums depend on the order in which the CTAs
+                             arrive, so results can differ from run to run in the last
+                             bits; the result is still certified by the double-float true
+                             residual <= tol); ignored by the other modes               */
+  int32_t reserved[3];    /* must be zero                                                */
 } enkf_config;
 
 typedef struct enkf_stats {

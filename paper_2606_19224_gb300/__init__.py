@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
         ("perturb_obs", ctypes.c_int32), ("warm_start", ctypes.c_int32),
         ("true_residual", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
         ("precondition", ctypes.c_int32), ("lowprec_terms", ctypes.c_int32),
-        ("warm_accept", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("warm_accept", ctypes.c_int32), ("reduce_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
 

@@ -32,7 +32,7 @@ void free_workspace(Workspace& ws) {
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y,
                   ws.Hrowptr, ws.Hcol, ws.Hw, ws.wa, ws.wb, ws.wcp, ws.wmu, ws.wU, ws.wV, ws.wcarry,
-                  ws.wcarryV, ws.Xw, ws.yw, ws.Tk};
+                  ws.wcarryV, ws.Xw, ws.yw, ws.Tk, ws.Tacc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace{};
@@ -73,7 +73,8 @@ enkf_status check_problem(const enkf_config& c, const int32_t* h_rowptr, const i
   if (c.warm_start && (c.precision != ENKF_FP32 || c.variant != ENKF_CGD || c.fixed_iters > 0))
     return bad(ENKF_ERR_UNSUPPORTED, "the learned warm start runs in ENKF_CGD / ENKF_FP32 without fixed_iters");
   if (c.warm_accept != 0 && c.warm_accept != 1) return bad(ENKF_ERR_INVALID_ARG, "warm_accept must be 0 or 1");
-  for (int q = 0; q < 4; ++q)
+  if (c.reduce_order != 0 && c.reduce_order != 1) return bad(ENKF_ERR_INVALID_ARG, "reduce_order must be 0 or 1");
+  for (int q = 0; q < 3; ++q)
     if (c.reserved[q]) return bad(ENKF_ERR_INVALID_ARG, "reserved fields must be 0");
   // observation operator and R
   if (h_rowptr[0] != 0) return bad(ENKF_ERR_INVALID_ARG, "rowptr[0] != 0");
@@ -232,6 +233,7 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
   if (mixed) {
     allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
     allocs.push_back({(void**)&ws.Tk, sizeof(float) * 2 * c.N * c.N});
+    allocs.push_back({(void**)&ws.Tacc, sizeof(double) * 3 * ((size_t)c.N * c.N + 4 * c.N)});
   }
   const int64_t hnnz = h_rowptr[c.m];
   const int64_t nblk = enkf::whiten_blocks(c.m);

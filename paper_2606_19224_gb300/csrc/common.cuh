@@ -150,6 +150,7 @@ struct Workspace {
   double* stage_y = nullptr;    // [m]
   unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
   float* Tk = nullptr;          // [2][N][N] T of the tensor-core step, carried between steps
+  double* Tacc = nullptr;       // [3][N N + 4 N] step sums of the tensor-core solve (atomic adds)
   // tridiagonal R (kernels_whiten.cu): the caller's H, the whitening scan's coefficients and
   // buffers; rowptr / col / w / r above then hold H' = I and r' = 1 of the whitened problem
   int32_t* Hrowptr = nullptr;   // [m+1]

@@ -98,6 +98,8 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.rrpart = ws.rrpart;
   p.W = ws.W;
   p.Tk = ws.Tk;
+  p.Tacc = ws.Tacc;
+  p.atomic_reduce = (c.reduce_order == 1 && h->launch.NT <= 64) ? 1 : 0;
   p.tol = c.tol;
   p.inner_tol = c.inner_tol;
   // accuracy an inner solve on the BF16 / FP16 operator can be asked for: the split FP16

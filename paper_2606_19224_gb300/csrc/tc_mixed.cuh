@@ -405,7 +405,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
                             float* Res, float* P, const float* __restrict__ rv,
                             const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
                             uint64_t* mbar_u2, uint64_t* mbar_g, uint32_t* ph_u2, uint32_t& ph_g,
-                            int* status, bool& ok, double* __restrict__ out) {
+                            int* status, bool& ok, double* __restrict__ out, bool atomic_out) {
   using L = TcLayout<NT, TERMS>;
   static_assert(L::DB, "NT <= 64 only");
   constexpr bool SPLIT = TERMS == 3;
@@ -640,11 +640,17 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     gram_out();
   }
   tc_cp_wait_all();
-  // the pass's partial Gram: row j, column k -> out[k*N + j] / zs_j (all zero when Qb == 0)
+  // the pass's partial Gram: row j, column k -> out[k*N + j] / zs_j (all zero when Qb == 0);
+  // with atomic_out it is added into the FP32 total at reinterpret_cast<float*>(out)[k*N + j]
+  // (the layout in which reduce_slice leaves the reduced Gram) instead
   if (g_owner && rt < N) {
     const float inv = 1.f / zs[rt];
     for (int k = half * HALF; k < half * HALF + HALF; ++k)
-      if (k < N) out[k * N + rt] = (double)(sG[rt * (NT + 1) + k] * inv);
+      if (k < N) {
+        const float v = sG[rt * (NT + 1) + k] * inv;
+        if (atomic_out) atomicAdd(reinterpret_cast<float*>(out) + k * N + rt, v);
+        else out[k * N + rt] = (double)v;
+      }
   }
   tc_fence_before();
   __syncthreads();
@@ -664,7 +670,8 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
     for (int cc = 0; cc < 4; ++cc) {
       double a = 0.0;
       for (int qq = 0; qq < RI; ++qq) a += red[(cc * RI + qq) * NT + t];
-      out[N * N + cc * N + t] = a;
+      if (atomic_out) atomicAdd(out + N * N + cc * N + t, a);
+      else out[N * N + cc * N + t] = a;
     }
   }
   __syncthreads();
@@ -841,6 +848,8 @@ struct MixedParams {
   double* rrpart;
   double* W;
   float* Tk;        // [2][N][N] the recursively updated T of the step (written by CTA 0)
+  double* Tacc;     // [3][N N + 4 N] step totals accumulated by atomic adds (atomic_reduce)
+  int atomic_reduce;   // N <= 64: a step's sums are added into Tacc (one barrier per step)
   double tol, inner_tol, itol_floor;
   int max_iter, refresh_every;
   int* col_iters;
@@ -909,6 +918,15 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   uint32_t ph_u2[2] = {0u, 0u};
   int par = 0;
   bool ok = true;
+  // atomic_reduce: CG steps so far (the same in every CTA) pick the step's accumulator; all
+  // three start at zero (ordered before their first use by the first grid barrier)
+  const bool atomic = NT <= 64 && p.atomic_reduce;
+  int gstep = 0;
+  if (atomic) {
+    const int chunk = (3 * NE + G - 1) / G;
+    const int e1 = min(3 * NE, (b + 1) * chunk);
+    for (int e = b * chunk + t; e < e1; e += kThreads) p.Tacc[e] = 0.0;
+  }
   const bool prof = p.prof != nullptr && b == 0 && t == 0;
   unsigned long long ph[PH_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long tp = prof ? global_ns() : 0ull;
@@ -1004,23 +1022,38 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       const int any = __syncthreads_or(my_active);
       if (!(any && (p.refresh_every <= 0 || it < p.refresh_every) && total + it < p.max_iter)) break;
       tick(PH_SCAL);
+      // the step's sums: into this CTA's partial (then a fixed-order reduction between two grid
+      // barriers), or added into the step's accumulator (atomic_reduce: one barrier; the
+      // accumulator two steps ahead is cleared behind it, every CTA having read it before)
+      double* acc = atomic ? p.Tacc + (size_t)(gstep % 3) * NE : Tp;
       if constexpr (NT <= 64)
         passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
-                                        s_beta_v, uni, tmem, &mbar[2], &mbar[1], ph_u2, ph_g, p.status, ok, Tp);
+                                        s_beta_v, uni, tmem, &mbar[2], &mbar[1], ph_u2, ph_g, p.status, ok, acc,
+                                        atomic);
       else
         passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                       s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
       tick(PH_PASS);
       if (!(ok = bar.sync() && ok)) break;
       tick(PH_BAR1);
-      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
-      tick(PH_RED);
-      if (!(ok = bar.sync())) break;
-      tick(PH_BAR2);
+      const double* tsum = p.Tred;
+      if (atomic) {
+        double* z = p.Tacc + (size_t)((gstep + 2) % 3) * NE;
+        const int chunk = (NE + G - 1) / G;
+        const int e1 = min(NE, (b + 1) * chunk);
+        for (int e = b * chunk + t; e < e1; e += kThreads) z[e] = 0.0;
+        tsum = acc;
+        ++gstep;
+      } else {
+        reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
+        tick(PH_RED);
+        if (!(ok = bar.sync())) break;
+        tick(PH_BAR2);
+      }
       // beta, T_{k+1} = HA^T z_{k+1} + beta T_k (from the global copy of T_k), the scalars
       const float* Tprev = p.Tk + (size_t)tbuf * N * N;
       float* Tnext = p.Tk + (size_t)(tbuf ^ 1) * N * N;
-      stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, Tprev, Tnext, b == 0, sTk, s_beta_v, true, s_active,
+      stage_Tt16_rec<T16, NT, TERMS>(tsum, N, inv_nm1, Tprev, Tnext, b == 0, sTk, s_beta_v, true, s_active,
                                      s_sig, s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
       tbuf ^= 1;
       ++it;

@@ -52,7 +52,7 @@ def _create(cfg, rowptr, col, w, r):
 
 
 @pytest.mark.parametrize("case", ["N1", "bad_col", "neg_r", "rowptr", "N_big", "tol", "reserved",
-                                  "variant", "senkf_bf16", "senkf_warm", "warm_accept"])
+                                  "variant", "senkf_bf16", "senkf_warm", "warm_accept", "reduce_order"])
 def test_create_rejects_bad_arguments_before_touching_the_gpu(case):
     n, m, N = 10, 4, 5
     rowptr = np.arange(m + 1, dtype=np.int32)
@@ -79,6 +79,8 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(case):
         cfg.reserved[1] = 1
     elif case == "warm_accept":
         cfg.warm_accept = 2
+    elif case == "reduce_order":
+        cfg.reduce_order = 2
     elif case == "variant":
         cfg.variant = 3
         expect = 8

@@ -78,10 +78,12 @@ MULTI = [(37, 8000, 8), (64, 12000, 12), (64, 1024, 4), (100, 6000, 4), (128, 16
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("pc", [0, 1])
 @pytest.mark.parametrize("N,m,G", MULTI)
-def test_split_mixed_several_tiles_per_cta(lib, prec, pc, N, m, G):
+@pytest.mark.parametrize("order", [0, 1])
+def test_split_mixed_several_tiles_per_cta(lib, prec, pc, N, m, G, order):
+    # order 1: the step sums by atomic adds (N <= 64; ignored for N > 64)
     side = max(64, int(np.ceil(np.sqrt(2 * m))))
     p = synth.grf_problem(side, 6.0, N, m, 0.25, 1.0, seed=13 * m + N + G, dtype=np.float32)
-    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=pc, grid_blocks=G)
+    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=pc, grid_blocks=G, reduce_order=order)
     assert st["grid_blocks"] == G and (m + G - 1) // G > 128, st
     E = oracle.obs_perturbations(7, 3, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
@@ -103,15 +105,18 @@ def test_single_term_mixed_several_tiles_per_cta(lib, prec, N, m, G):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_full_size_grf512_N64_m65536_tensor_cores(lib, prec):
+@pytest.mark.parametrize("order", [0, 1])
+def test_full_size_grf512_N64_m65536_tensor_cores(lib, prec, order):
     """The 512 x 512 workload (n = 262,144, m = 65,536, N = 64) at full size on the automatic
-    grid (several tiles per CTA), preconditioned as the benchmark runs it."""
+    grid (several tiles per CTA), preconditioned as the benchmark runs it, with fixed-order and
+    with atomic step sums. The analysis error stays at the FP32 path's level (the split
+    operator and the double-float refresh): within 1e-6, the FP32 bar."""
     p = synth.workload("grf512_N64_m65536", 1, dtype=np.float32)
-    an, Xa, st = _run(lib, p, prec, seed=1, counter=0, tol=1e-8, precondition=1)
+    an, Xa, st = _run(lib, p, prec, seed=1, counter=0, tol=1e-8, precondition=1, reduce_order=order)
     E = oracle.obs_perturbations(1, 0, p.r, p.N)
     ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
     assert st["status"] == "ok", st
-    _check_close(Xa, ref, 1e-4)
+    _check_close(Xa, ref, 1e-6, 1e-5)
     assert st["true_relres_max"] <= 1e-8, st
 
 
