@@ -443,7 +443,7 @@ def _err(out, ref):
 
 # how each step's sums over the CTAs are formed (enkf_config.reduce_order)
 REDUCE_NAME = {0: "fixed order (bitwise repeatable)",
-               1: "atomic adds (tensor-core modes, N <= 64; last bits vary from run to run)"}
+               1: "atomic adds (N <= 64; last bits vary from run to run)"}
 KERNEL_NAME = {"fp64": "solve_kernel<double>", "fp32": "solve_kernel<float>",
                "fp16": "solve_mixed_kernel<half>", "bf16": "solve_mixed_kernel<bf16>"}
 
@@ -575,7 +575,7 @@ def run_ours(args):
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8, "precision": prec_name,
                        "solver": "CG preconditioned by R" if args.precondition else "plain CG",
-                       "reduce_order": REDUCE_NAME[args.reduce_order if args.precision != "fp32" else 0],
+                       "reduce_order": REDUCE_NAME[args.reduce_order],
                        "l2": "flushed between steps", "status": last_status["status"]},
             "roofline": roofline, "e2e": e2e,
             # innovations, (tile images of HA for the tensor-core path,) solve, update
@@ -605,14 +605,15 @@ def run_ours(args):
     c1["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, args.fp64_steps, 1, ref)
     c1["fp32_plain_cg"] = _variant(enkf, p, "fp32", 0, timer, Xf, y, seed, args.fp64_steps, 1, ref)
-    if args.precision != "fp32":
-        # the headline's precision with the other reduction order
-        other = 1 - args.reduce_order
-        c1[args.precision + "_pcg_" + ("atomic" if other else "fixed_order")] = _variant(
-            enkf, p, args.precision, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref, reduce_order=other)
+    # the headline's precision with the other reduction order, then the other precisions with
+    # the headline's order
+    other = 1 - args.reduce_order
+    c1[args.precision + "_pcg_" + ("atomic" if other else "fixed_order")] = _variant(
+        enkf, p, args.precision, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref, reduce_order=other)
     for prec in ("fp32", "fp16", "bf16"):
         if prec != args.precision:
-            c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref)
+            c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref,
+                                         reduce_order=args.reduce_order)
     base = c1["fp64_plain_cg"]["ms_per_step"]
     for k, v in c1.items():
         v["speedup_vs_fp64_plain_cg"] = base / v["ms_per_step"]
@@ -1114,8 +1115,8 @@ def main():
     ap.add_argument("--warm-train-seeds", type=int, default=40,
                     help="ensembles (x 8 observation draws) the learned warm start trains on in the default run")
     ap.add_argument("--reduce-order", type=int, default=1, choices=[0, 1],
-                    help="tensor-core headline: 1 sums each step over the CTAs by atomic adds (one grid "
-                         "barrier per step), 0 in a fixed order (bitwise repeatable)")
+                    help="1 sums each CG step over the CTAs by atomic adds (one grid barrier per step; "
+                         "N <= 64), 0 in a fixed order (bitwise repeatable)")
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"],
                     help="inner-solve precision of the timed path (default workload)")
     ap.add_argument("--batch-count", type=int, default=256,

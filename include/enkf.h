@@ -123,8 +123,9 @@ typedef struct enkf_config {
                              double-float true residual <= tol                          */
   int32_t reduce_order;   /* 0 (default): every step's column sums and Gram are summed over
                              the CTAs in a fixed order (bitwise repeatable results, two
-                             grid barriers per step); 1: BF16/FP16 modes with N <= 64 add
-                             them into the total by atomic adds (one barrier per step, the
+                             grid barriers per step); 1: ENKF_CGD in the FP32, BF16 and
+                             FP16 modes with N <= 64 adds them into the total by
+                             atomic adds (one barrier per step, the
                              last bits of the sums depend on the order in which the CTAs
                              arrive, so results can differ from run to run in the last
                              bits; the result is still certified by the double-float true

@@ -233,8 +233,9 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
   if (mixed) {
     allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
     allocs.push_back({(void**)&ws.Tk, sizeof(float) * 2 * c.N * c.N});
-    allocs.push_back({(void**)&ws.Tacc, sizeof(double) * 3 * ((size_t)c.N * c.N + 4 * c.N)});
   }
+  if (c.precision != ENKF_FP64 && c.variant == ENKF_CGD)
+    allocs.push_back({(void**)&ws.Tacc, sizeof(double) * 3 * ((size_t)c.N * c.N + 4 * c.N)});
   const int64_t hnnz = h_rowptr[c.m];
   const int64_t nblk = enkf::whiten_blocks(c.m);
   if (tri) {

@@ -937,7 +937,9 @@ __device__ __forceinline__ void passF_async(const float* __restrict__ HA, int64_
 // T_k staged, alpha_k and beta_{k-1}, per row: z_k = M^{-1} r_k (M = R preconditioned, else I),
 // p_k = z_k + beta_{k-1} p_{k-1}, q_k = HA T_k/(N-1) + r_i p_k, x += alpha_k p_k,
 // r -= alpha_k q_k, z_{k+1} = M^{-1} r_{k+1}; out = [HA^T z_{k+1} | (r, z) | (r, r) |
-// sum r_i z^2 | sum r_i z p_k] (N^2 + 4N). In FP32 the Chronopoulos-Gear arrangement (one
+// sum r_i z^2 | sum r_i z p_k] (N^2 + 4N); with atomic_out the Gram is added into the FP32
+// total at reinterpret_cast<float*>(out)[k*N + j] and the column sums into the FP64 totals
+// (the layout reduce_slice leaves). In FP32 the Chronopoulos-Gear arrangement (one
 // reduction, with S p carried by its own recurrence) needed about 1.7x the steps of this form on
 // the 512^2 / N = 64 workload (67 against 40), and this form moves no S p vector.
 template <int NT> __host__ __device__ constexpr int passH_async_bytes() {
@@ -949,7 +951,7 @@ template <int NT, bool PC, bool ASYNC>
 __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0, int64_t row1, int N,
                                       float* X, float* Res, float* P, const float* __restrict__ rv,
                                       const float* sT, const float* alpha, const float* beta, float vinv,
-                                      unsigned char* tiles, double* __restrict__ out) {
+                                      unsigned char* tiles, double* __restrict__ out, bool atomic_out = false) {
   constexpr int LD = NT + 4;
   constexpr int MR = FTile<float, NT>::MR, TR = FTile<float, NT>::TR, C4 = NT / 4;
   constexpr int NJ = NT / 4, NI = kThreads / NJ;
@@ -1132,7 +1134,10 @@ __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0
           const int k = k0 + x, j = ja + y;
           double sum = 0.0;
           for (int gg = 0; gg < RG; ++gg) sum += red[(gg * NT + k) * NT + j];
-          if (k < N && j < N) out[k * N + j] = sum;
+          if (k < N && j < N) {
+            if (atomic_out) atomicAdd(reinterpret_cast<float*>(out) + k * N + j, (float)sum);
+            else out[k * N + j] = sum;
+          }
         }
     }
   } else {
@@ -1141,7 +1146,10 @@ __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0
 #pragma unroll
       for (int y = 0; y < MA; ++y) {
         const int k = k0 + x, j = ja + y;
-        if (k < N && j < N) out[k * N + j] = (double)accT[x][y];
+        if (k < N && j < N) {
+          if (atomic_out) atomicAdd(reinterpret_cast<float*>(out) + k * N + j, accT[x][y]);
+          else out[k * N + j] = (double)accT[x][y];
+        }
       }
   }
   __syncthreads();
@@ -1158,7 +1166,8 @@ __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0
     for (int c = 0; c < 4; ++c) {
       double sum = 0.0;
       for (int q = 0; q < NI; ++q) sum += red[(c * NI + q) * NT + t];
-      out[N * N + c * N + t] = sum;
+      if (atomic_out) atomicAdd(out + N * N + c * N + t, sum);
+      else out[N * N + c * N + t] = sum;
     }
   }
   __syncthreads();

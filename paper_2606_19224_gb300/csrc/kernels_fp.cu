@@ -183,6 +183,10 @@ cudaError_t launch_solve(enkf_handle_s* h) {
   p.warm = (h->cfg.warm_start && h->cfg.precision == ENKF_FP32) ? 1 : 0;
   p.warm_accept = h->cfg.warm_accept;
   p.col_warm = ws.col_warm;
+  p.Tacc = ws.Tacc;
+  // atomic step sums pay for N <= 64; at N = 128 the 16,384 atomic adds per CTA and step cost
+  // more than the reduction they replace (1024^2 / N = 128: 37.5 -> 41.3 ms)
+  p.atomic_reduce = (c.reduce_order == 1 && !fp64 && h->launch.NT <= 64) ? 1 : 0;
   cudaError_t err = cudaMemsetAsync(ws.bar, 0, 4 * sizeof(unsigned), h->stream);
   if (err != cudaSuccess) return err;
   err = cudaMemsetAsync(ws.status, 0, 4 * sizeof(int32_t), h->stream);

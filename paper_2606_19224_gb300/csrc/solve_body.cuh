@@ -42,6 +42,8 @@ struct SolveParams {
   unsigned long long* prof;  // optional phase timers of CTA 0 (ns), nullptr when off
   int warm;                  // FP32 mode: Zdf holds a starting solution (learned warm start)
   int warm_accept;           // 1: keep every finite start; 0: only those with ||B_j|| <= ||d_j||
+  double* Tacc = nullptr;    // FP32 mode, atomic_reduce: [3][N N + 4 N] rotating step totals
+  int atomic_reduce = 0;     // FP32 mode: a step's sums are added into Tacc (one barrier per step)
   double* col_warm;          // [N] relative residual ||B_j|| / ||d_j|| of that start
 };
 
@@ -109,6 +111,15 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
   };
   int par = 0;
   bool ok = true;
+  // atomic_reduce (FP32 mode): CG steps so far (the same in every CTA) pick the step's
+  // accumulator; all three start at zero (ordered before their first use by the first barrier)
+  const bool atomic = sizeof(VT) == 4 && p.atomic_reduce && p.Tacc != nullptr;
+  int gstep = 0;
+  if (atomic) {
+    const int chunk = (3 * NE + G - 1) / G;
+    const int e1 = min(3 * NE, (b + 1) * chunk);
+    for (int e = b * chunk + t; e < e1; e += kThreads) p.Tacc[e] = 0.0;
+  }
   // the last two column-sum vectors of the partials are written only by the FP32 step
   if (t < N) {
     Tp[N * N + 2 * N + t] = 0.0;
@@ -247,25 +258,41 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       }
       if (!(__syncthreads_or(my_active) && it < limit)) break;
       tick(PH_SCAL);
+      // the step's sums: into this CTA's partial (then a fixed-order reduction between two grid
+      // barriers), or added into the step's accumulator (atomic_reduce: one barrier; the
+      // accumulator two steps ahead is cleared behind it, every CTA having read it before)
+      double* acc = atomic ? p.Tacc + (size_t)(gstep % 3) * NE : Tp;
       if ((N & 3) == 0)
         passH<NT, PC, true>(reinterpret_cast<const float*>(HA), row0, row1, N, reinterpret_cast<float*>(X),
                             reinterpret_cast<float*>(Res), reinterpret_cast<float*>(P),
-                            reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, Tp);
+                            reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, acc,
+                            atomic);
       else
         passH<NT, PC, false>(reinterpret_cast<const float*>(HA), row0, row1, N, reinterpret_cast<float*>(X),
                              reinterpret_cast<float*>(Res), reinterpret_cast<float*>(P),
-                             reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, Tp);
+                             reinterpret_cast<const float*>(rv), sTf, avf, bvf, (float)inv_nm1, tiles, acc,
+                             atomic);
       tick(PH_PASS);
       if (!(ok = bar.sync())) break;
       tick(PH_BAR1);
-      reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
-      tick(PH_RED);
-      if (!(ok = bar.sync())) break;
-      tick(PH_BAR2);
+      const double* tsum = p.Tred;
+      if (atomic) {
+        double* z = p.Tacc + (size_t)((gstep + 2) % 3) * NE;
+        const int chunk = (NE + G - 1) / G;
+        const int e1 = min(NE, (b + 1) * chunk);
+        for (int e = b * chunk + t; e < e1; e += kThreads) z[e] = 0.0;
+        tsum = acc;
+        ++gstep;
+      } else {
+        reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, t_f32);
+        tick(PH_RED);
+        if (!(ok = bar.sync())) break;
+        tick(PH_BAR2);
+      }
       // beta_k = gamma_{k+1} / gamma_k, T_{k+1} = HA^T z_{k+1} + beta_k T_k, sum r_i p_{k+1}^2
       // from the expanded sums; frozen columns keep beta = 0 (their next p is never used:
       // alpha = 0)
-      stage_T_rec<NT>(p.Tred, N, bvf, sTf, s_tn2, scratch, true, s_active, s_sig, s_den, s_gam, s_iters);
+      stage_T_rec<NT>(tsum, N, bvf, sTf, s_tn2, scratch, true, s_active, s_sig, s_den, s_gam, s_iters);
       tick(PH_SCAL);
       ++it;
     }

@@ -264,12 +264,28 @@ def test_preconditioned_cg_matches_exact_oracle(lib, prec, shape):
     assert st0["iters_max"] >= st["iters_max"]
 
 
-def test_preconditioned_full_size_grf512_N64_m65536_fp32(lib):
+@pytest.mark.parametrize("order", [0, 1])
+def test_preconditioned_full_size_grf512_N64_m65536_fp32(lib, order):
     p = synth.workload("grf512_N64_m65536", 1, dtype=np.float32)
-    an, Xa, st = _run(lib, p, "fp32", seed=1, counter=0, tol=1e-8, precondition=1)
+    an, Xa, st = _run(lib, p, "fp32", seed=1, counter=0, tol=1e-8, precondition=1, reduce_order=order)
     E = oracle.obs_perturbations(1, 0, p.r, p.N)
     err = oracle.rel_frobenius(Xa, _oracle_exact(p, E))
     assert st["status"] == "ok" and err <= 1e-6, (err, st)
+
+
+@pytest.mark.parametrize("N,m,G,pc", [(37, 3000, 6, 1), (64, 5000, 9, 0), (100, 4000, 7, 1), (128, 6000, 11, 1)])
+def test_fp32_atomic_step_sums_match_oracle(lib, N, m, G, pc):
+    """reduce_order = 1 in the FP32 mode: each step's Gram and column sums are added into
+    rotating accumulators by atomic adds (one grid barrier per step; N > 64 keeps the
+    fixed-order reduction); ragged N (N % 4 != 0), plain and preconditioned CG, several CTAs,
+    against the exact analysis."""
+    p = _csr_problem(2 * m, N, m, 100 + N, dtype=np.float32)
+    E = np.random.default_rng(N).standard_normal((m, N)) * np.sqrt(p.r)[:, None]
+    an, Xa, st = _run(lib, p, "fp32", E=E, tol=1e-8, precondition=pc, grid_blocks=G, reduce_order=1)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    err = oracle.rel_frobenius(Xa, ref)
+    assert st["status"] == "ok" and err <= 1e-6, (err, st)
+    assert st["grid_blocks"] == G
 
 
 def test_fp32_intermediates_are_the_double_float_arrays(lib):
