@@ -551,7 +551,8 @@ def run_ours(args):
            "host_reads_bytes_per_step": int(len(p.col) * N * 4),
            "note": "enkf_analyze_host with pinned buffers: the innovations read the observed rows of X_f "
                    "from host memory (host_reads_bytes_per_step, over the CPU-GPU link, besides the "
-                   "copies), X_f is uploaded on a second stream while the solve runs, X_a is copied back"}
+                   "copies), X_f is uploaded on a second stream while the solve runs, the update "
+                   "writes X_a straight into the pinned output buffer"}
 
     # ---- roofline of the dominant kernel (the persistent CG solve), live CUDA-event time
     it_avg, ref_avg = float(np.mean(iters)), float(np.mean(refines))

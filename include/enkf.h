@@ -212,8 +212,8 @@ enkf_status enkf_analyze_with_E(enkf_handle h, const void* d_Xf, const double* d
    with ENKF_CGD: the innovations read the observed rows of X_f directly from host memory
    while the whole X_f is uploaded on a second stream that the handle creates on first use
    (the upload overlaps the innovations and the solve; only the final update waits for it),
-   and X_a comes back by one copy. Either way every X_f byte crosses to the device and every
-   X_a byte back within the call. The
+   and the update writes a pinned h_Xa directly (else X_a comes back by one copy). Either way
+   every X_f byte crosses to the device and every X_a byte back within the call. The
    buffers must hold n N elements of the handle's dtype; the result is the same as
    enkf_analyze's on device copies of the inputs. */
 enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y,

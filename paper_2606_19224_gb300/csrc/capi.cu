@@ -418,12 +418,13 @@ enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y
   const auto& c = h->cfg;
   const size_t xb = elem_size(c) * c.n * c.N;
   const void* xf_dev = device_view(h_Xf);
+  void* xa_dev = device_view(h_Xa);
   if (xf_dev && c.variant == ENKF_CGD) {
     // Pinned X_f: the innovations read the observed rows of X_f directly from host memory (over
     // the CPU-GPU link); the whole X_f is then uploaded on the copy stream while the solve runs,
-    // and only the update waits for it. X_a goes back by one copy (writing it to pinned host
-    // memory from the update kernel itself measured about 20x slower than the copy; two copies
-    // on two streams were no faster than one).
+    // and only the update waits for it. A pinned X_a is written by the update kernel itself
+    // (its coalesced 16-byte stores reach host memory about as fast as a copy does, and the
+    // separate download disappears); otherwise X_a goes back by one copy.
     cudaError_t e = cudaSuccess;
     if (!h->copy_stream) {
       e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
@@ -437,12 +438,12 @@ enkf_status enkf_analyze_host(enkf_handle h, const void* h_Xf, const double* h_y
     if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: upload");
     const XfUpload up{h->ws.stage_Xf, h_Xf, xb};
     enkf_status s = analyze_impl(h, xf_dev, h->ws.stage_y, nullptr, h->cfg.perturb_obs ? 2 : 0, seed, counter,
-                                 h->ws.stage_Xf, h->ws.stage_Xf, &up);
+                                 xa_dev ? xa_dev : h->ws.stage_Xf, h->ws.stage_Xf, &up);
     if (s != ENKF_OK) {
       cudaStreamSynchronize(h->copy_stream);
       return s;
     }
-    e = cudaMemcpyAsync(h_Xa, h->ws.stage_Xf, xb, cudaMemcpyDeviceToHost, h->stream);
+    if (!xa_dev) e = cudaMemcpyAsync(h_Xa, h->ws.stage_Xf, xb, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "analyze_host: download");
     return ENKF_OK;
