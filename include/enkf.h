@@ -74,7 +74,13 @@ typedef enum {
   ENKF_BF16_REFINE = 2, /* BF16 HA contractions on tensor cores (tcgen05), FP32
                            accumulation, FP32 vectors, FP64 scalars; inner solves refined
                            by the same double-float residual refresh (see refresh_every) */
-  ENKF_FP16_REFINE = 3  /* as ENKF_BF16_REFINE with FP16 HA                              */
+  ENKF_FP16_REFINE = 3  /* as ENKF_BF16_REFINE with FP16 HA; the tensor-core images of HA
+                           are scaled by the power of two that brings the largest |HA| of
+                           the analysis into [2^13, 2^14) and the products are scaled back
+                           exactly; the Gram's z operand is normalised by ||r|| and, with
+                           precondition = 1, by the power of two nearest the geometric mean
+                           of r_diag: the mode works in any units of the state and of R
+                           without FP16 overflow or subnormal loss                        */
 } enkf_precision;
 
 typedef enum {

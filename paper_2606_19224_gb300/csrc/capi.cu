@@ -32,7 +32,7 @@ void free_workspace(Workspace& ws) {
                   ws.Res, ws.P, ws.Sv, ws.prof, ws.Tpart, ws.Tred, ws.rrpart, ws.Wacc, ws.W, ws.col_iters,
                   ws.col_relres, ws.col_true, ws.col_warm, ws.status, ws.bar, ws.stage_Xf, ws.stage_y,
                   ws.Hrowptr, ws.Hcol, ws.Hw, ws.wa, ws.wb, ws.wcp, ws.wmu, ws.wU, ws.wV, ws.wcarry,
-                  ws.wcarryV, ws.Xw, ws.yw, ws.Tk, ws.Tacc};
+                  ws.wcarryV, ws.Xw, ws.yw, ws.Tk, ws.Tacc, ws.hamax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace{};
@@ -174,6 +174,12 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->nnz = nnz;
   h->tri = tri;
+  if (!tri && c.m > 0) {
+    double sl = 0.0;
+    for (int64_t i = 0; i < c.m; ++i) sl += std::log2(r_diag[i]);
+    const long k = std::lround(sl / (double)c.m);
+    h->r_pow2 = std::ldexp(1.f, (int)std::max(-120L, std::min(120L, k)));
+  }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = mixed ? enkf::plan_solve_mixed(h) : enkf::plan_solve(h);
@@ -233,6 +239,7 @@ static enkf_status create_impl(const enkf_config* cfg, const int32_t* h_rowptr, 
   if (mixed) {
     allocs.push_back({(void**)&ws.HA16, enkf::mixed_image_bytes(h)});
     allocs.push_back({(void**)&ws.Tk, sizeof(float) * 2 * c.N * c.N});
+    allocs.push_back({(void**)&ws.hamax, sizeof(unsigned) * 4});
   }
   if (c.precision != ENKF_FP64 && c.variant == ENKF_CGD)
     allocs.push_back({(void**)&ws.Tacc, sizeof(double) * 3 * ((size_t)c.N * c.N + 4 * c.N)});

@@ -151,6 +151,7 @@ struct Workspace {
   unsigned long long* prof = nullptr;  // [8] in-kernel phase timers of the solve (ns)
   float* Tk = nullptr;          // [2][N][N] T of the tensor-core step, carried between steps
   double* Tacc = nullptr;       // [3][N N + 4 N] step sums of the tensor-core solve (atomic adds)
+  unsigned* hamax = nullptr;    // tensor-core modes: largest |HA| of the analysis (float bits)
   // tridiagonal R (kernels_whiten.cu): the caller's H, the whitening scan's coefficients and
   // buffers; rowptr / col / w / r above then hold H' = I and r' = 1 of the whitened problem
   int32_t* Hrowptr = nullptr;   // [m+1]
@@ -200,6 +201,8 @@ struct enkf_handle_s {
   enkf::BatchState* batch = nullptr;   // non-NULL for a handle made by enkf_batch_create
   enkf::WarmState* warm = nullptr;     // learned warm start (enkf_set_warm_model / enkf_warm_features)
   bool tri = false;                    // tridiagonal R: analyses run on the whitened problem
+  float r_pow2 = 1.f;                  // power of two nearest the geometric mean of R's diagonal
+                                       // (1 for the whitened problem)
 };
 
 namespace enkf {

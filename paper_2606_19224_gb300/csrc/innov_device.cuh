@@ -213,9 +213,10 @@ __device__ __forceinline__ void innov_rows_df(
     double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
     float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
     int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
-    int64_t warp, int64_t nwarps) {
+    int64_t warp, int64_t nwarps, unsigned* hamax = nullptr) {
   static_assert(sizeof(VT) == 4, "double-float innovations take an FP32 ensemble");
   const int lane = threadIdx.x & 31;
+  float hmax = 0.f;   // largest |HA| of the warp's rows (hamax: atomic maximum of the float bits)
   const df32 inv_n(1.0 / (double)N);
   const bool wide = N > 64;   // members 64..127 present (warp-uniform)
   // The warp's rows are i0 + q nwarps, q = 0, 1, ...; the per-row values that come from FP64
@@ -271,6 +272,7 @@ __device__ __forceinline__ void innov_rows_df(
           }
           hv[b] = z[2 * h + b] - zbar;
           dv[b] = (yd - z[2 * h + b]) + pert;
+          if (jp + b < N) hmax = fmaxf(hmax, fabsf(hv[b].hi));
         }
         if ((N & 1) == 0) {
           // both members present and e0 even: one 8- or 16-byte store per array per lane
@@ -311,6 +313,11 @@ __device__ __forceinline__ void innov_rows_df(
       }
     }
   }
+  if (hamax) {
+    // non-negative floats order as their bit patterns
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(hmax));
+    if (lane == 0 && mb > 0u) atomicMax(hamax, mb);
+  }
 }
 
 // Rows [i_begin, i_end) of the innovation step: FP64 arithmetic for FP64 ensembles,
@@ -323,10 +330,10 @@ __device__ __forceinline__ void innov_rows(
     double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
     float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
     int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, int64_t i_begin, int64_t i_end,
-    int64_t warp, int64_t nwarps) {
+    int64_t warp, int64_t nwarps, unsigned* hamax = nullptr) {
   if constexpr (sizeof(VT) == 4)
     innov_rows_df<VT>(Xf, rowptr, col, w, y, r, E, emode, seed, counter, m, N, HA64, HA32, D, B32,
-                      HAb, HAh, split_lo, HAdf, Ddf, i_begin, i_end, warp, nwarps);
+                      HAb, HAh, split_lo, HAdf, Ddf, i_begin, i_end, warp, nwarps, hamax);
   else
     innov_rows_f64<VT>(Xf, rowptr, col, w, y, r, E, emode, seed, counter, m, N, HA64, HA32, D, B32,
                        HAb, HAh, split_lo, HAdf, Ddf, i_begin, i_end, warp, nwarps);

@@ -42,11 +42,11 @@ __global__ void __launch_bounds__(kThreads) innov_kernel(
     const double* __restrict__ E, int emode, uint64_t seed, uint64_t counter, int64_t m, int N,
     double* __restrict__ HA64, float* __restrict__ HA32, double* __restrict__ D,
     float* __restrict__ B32, __nv_bfloat16* __restrict__ HAb, __half* __restrict__ HAh,
-    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf) {
+    int split_lo, df32* __restrict__ HAdf, df32* __restrict__ Ddf, unsigned* hamax) {
   const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   innov_rows<VT>(Xf, rowptr, col, w, y, r, E, emode, seed, counter, m, N, HA64, HA32, D, B32, HAb,
-                 HAh, split_lo, HAdf, Ddf, 0, m, warp, nwarps);
+                 HAh, split_lo, HAdf, Ddf, 0, m, warp, nwarps, hamax);
 }
 
 __global__ void draw_perturbations_kernel(uint64_t seed, uint64_t counter,
@@ -123,15 +123,20 @@ cudaError_t launch_innovations(enkf_handle_s* h, const void* Xf, const double* y
   auto& ws = h->ws;
   const int blocks = (int)std::min<int64_t>((c.m + 7) / 8, (int64_t)h->sms * 16);
   const bool fp64 = c.precision == ENKF_FP64;
+  // the tensor-core modes scale the HA image by a power of two from the largest |HA|
+  if (ws.hamax) {
+    cudaError_t e = cudaMemsetAsync(ws.hamax, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess) return e;
+  }
   if (fp64)
     innov_kernel<double><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const double*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
-        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr, nullptr, nullptr, 0, nullptr, nullptr);
+        c.m, c.N, ws.HA64, nullptr, ws.D, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr);
   else
     innov_kernel<float><<<blocks, kThreads, 0, h->stream>>>(
         static_cast<const float*>(Xf), ws.rowptr, ws.col, ws.w, y, ws.r, E, emode, seed, counter,
         c.m, c.N, ws.HA64, ws.HA32, ws.D, static_cast<float*>(ws.B),
-        nullptr, nullptr, 0, static_cast<df32*>(ws.HAdf), static_cast<df32*>(ws.Ddf));
+        nullptr, nullptr, 0, static_cast<df32*>(ws.HAdf), static_cast<df32*>(ws.Ddf), ws.hamax);
   return cudaGetLastError();
 }
 

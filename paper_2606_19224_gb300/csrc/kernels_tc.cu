@@ -61,12 +61,12 @@ static cudaError_t launch_tc_images(enkf_handle_s* h) {
   const bool split = mixed_split(c);
   if (c.precision == ENKF_BF16_REFINE) {
     auto* img = static_cast<__nv_bfloat16*>(h->ws.HA16);
-    if (split) tc_images_kernel<__nv_bfloat16, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
-    else tc_images_kernel<__nv_bfloat16, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+    if (split) tc_images_kernel<__nv_bfloat16, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img, h->ws.hamax);
+    else tc_images_kernel<__nv_bfloat16, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img, h->ws.hamax);
   } else {
     auto* img = static_cast<__half*>(h->ws.HA16);
-    if (split) tc_images_kernel<__half, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
-    else tc_images_kernel<__half, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img);
+    if (split) tc_images_kernel<__half, 3><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img, h->ws.hamax);
+    else tc_images_kernel<__half, 1><<<blocks, 256, 0, h->stream>>>(HAdf, c.m, c.N, NT, rp, qm, img, h->ws.hamax);
   }
   return cudaGetLastError();
 }
@@ -99,6 +99,8 @@ cudaError_t launch_solve_mixed(enkf_handle_s* h) {
   p.W = ws.W;
   p.Tk = ws.Tk;
   p.Tacc = ws.Tacc;
+  p.hamax = ws.hamax;
+  p.zr = h->r_pow2;
   p.atomic_reduce = (c.reduce_order == 1 && h->launch.NT <= 64) ? 1 : 0;
   p.tol = c.tol;
   p.inner_tol = c.inner_tol;

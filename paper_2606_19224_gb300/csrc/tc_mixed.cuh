@@ -183,7 +183,7 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
                           float* X, float* Res, float* P, const float* __restrict__ rv,
                           const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
                           uint64_t* mbar_u, uint64_t* mbar_g, uint32_t& ph_u, uint32_t& ph_g, int* status,
-                          bool& ok, double* __restrict__ out) {
+                          bool& ok, double* __restrict__ out, float gsi) {
   using L = TcLayout<NT, TERMS>;
   constexpr bool SPLIT = TERMS == 3, DB = L::DB;
   static_assert(!DB, "NT = 128 only");
@@ -372,7 +372,7 @@ __device__ void passF_tc2(const T16* __restrict__ img, int qmax, int64_t row0, i
       float v[16];
       tmem_ld16(d_g + ((uint32_t)(32 * qd) << 16) + k0, v);
       if (rt < N) {
-        const float inv = 1.f / zs[rt];
+        const float inv = gsi / zs[rt];
 #pragma unroll
         for (int y = 0; y < 16; ++y)
           if (k0 + y < N) out[(k0 + y) * N + rt] = (double)(v[y] * inv);
@@ -405,7 +405,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
                             float* Res, float* P, const float* __restrict__ rv,
                             const float* alpha, const float* beta, unsigned char* tcs, uint32_t tmem,
                             uint64_t* mbar_u2, uint64_t* mbar_g, uint32_t* ph_u2, uint32_t& ph_g,
-                            int* status, bool& ok, double* __restrict__ out, bool atomic_out) {
+                            int* status, bool& ok, double* __restrict__ out, bool atomic_out, float gsi) {
   using L = TcLayout<NT, TERMS>;
   static_assert(L::DB, "NT <= 64 only");
   constexpr bool SPLIT = TERMS == 3;
@@ -644,7 +644,7 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   // with atomic_out it is added into the FP32 total at reinterpret_cast<float*>(out)[k*N + j]
   // (the layout in which reduce_slice leaves the reduced Gram) instead
   if (g_owner && rt < N) {
-    const float inv = 1.f / zs[rt];
+    const float inv = gsi / zs[rt];
     for (int k = half * HALF; k < half * HALF + HALF; ++k)
       if (k < N) {
         const float v = sG[rt * (NT + 1) + k] * inv;
@@ -677,6 +677,19 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
   __syncthreads();
 }
 
+// The power of two that scales the largest |HA| (hamax: its float bits) into [2^13, 2^14), so
+// that the FP16 image neither overflows (65,504) nor loses its small entries to the subnormal
+// range whatever the units of the state; 1 when there is no maximum. The passes undo it
+// exactly (image_scale_inv).
+__device__ __forceinline__ float image_scale(const unsigned* hamax) {
+  const float mx = hamax ? __uint_as_float(*hamax) : 0.f;
+  if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+  int e;
+  frexpf(mx, &e);   // mx = f 2^e, f in [1/2, 1)
+  return ldexpf(1.f, 14 - e);
+}
+__device__ __forceinline__ float image_scale_inv(const unsigned* hamax) { return 1.f / image_scale(hamax); }
+
 // The tile images of the tensor-core pass, from the double-float HA: for CTA b (rows
 // [b rows_per, ...)) and its tile q (128 rows), at (b qmax + q) TM 128 NT elements: [hi | lo],
 // element (r, k) of each part at core_idx(r, k, NT); hi = round(HA), lo = round(HA - hi) in
@@ -684,9 +697,10 @@ __device__ void passF_tc_db(const T16* __restrict__ img, int64_t row0, int64_t r
 // handle is created).
 template <typename T16, int TERMS>
 __global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N, int NT, int64_t rows_per,
-                                 int qmax, T16* __restrict__ img) {
+                                 int qmax, T16* __restrict__ img, const unsigned* __restrict__ hamax) {
   constexpr int TM = TERMS == 3 ? 2 : 1;
   const int64_t tile = (int64_t)TM * kTR * NT;
+  const float sc = image_scale(hamax);   // exact power of two
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * N; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / N;
     const int k = (int)(e % N);
@@ -694,9 +708,10 @@ __global__ void tc_images_kernel(const df32* __restrict__ HAdf, int64_t m, int N
     const int q = (int)(l / kTR), r = (int)(l % kTR);
     T16* base = img + (b * qmax + q) * tile;
     const df32 h = HAdf[e];
-    const T16 hi = H16<T16>::from(h.hi);
+    const float hs = h.hi * sc;
+    const T16 hi = H16<T16>::from(hs);
     base[core_idx(r, k, NT)] = hi;
-    if (TM == 2) base[(int64_t)kTR * NT + core_idx(r, k, NT)] = H16<T16>::from((h.hi - (float)hi) + h.lo);
+    if (TM == 2) base[(int64_t)kTR * NT + core_idx(r, k, NT)] = H16<T16>::from((hs - (float)hi) + h.lo * sc);
   }
 }
 
@@ -750,7 +765,7 @@ __device__ __forceinline__ void stage_Tt16(const double* __restrict__ Tred, int 
 // 16-bit values of a pair go to shared memory in one 32-bit store (they are adjacent in the
 // core-matrix layout).
 template <typename T16, int NT, int TERMS>
-__device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int N, double inv, const float* Tprev,
+__device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int N, double inv, float usi, const float* Tprev,
                                float* Tnext, bool write_next, float* sTk, float* beta, bool step,
                                const int* s_active, double* s_sig, double* s_den, double* s_gam, int* s_iters,
                                T16* sBu, float* ts, double* tn2, double* scratch) {
@@ -795,7 +810,7 @@ __device__ __noinline__ void stage_Tt16_rec(const double* __restrict__ Tred, int
     const bool live = t < N && rms > 0.f && isfinite(rms);
     if (live) frexpf(rms, &e);
     ts[t] = live ? ldexpf(1.f, 1 - e) : 1.f;
-    ts[NT + t] = live ? ldexpf(1.f, e - 1) : 1.f;   // 1/ts: undoes the scale on u
+    ts[NT + t] = (live ? ldexpf(1.f, e - 1) : 1.f) * usi;   // undoes ts and the image scale on u
     if (step) {
       if (act) {
         const double g2 = __ldcg(Tred + N * N + N + t);
@@ -848,6 +863,8 @@ struct MixedParams {
   double* rrpart;
   double* W;
   float* Tk;        // [2][N][N] the recursively updated T of the step (written by CTA 0)
+  const unsigned* hamax;   // largest |HA| (float bits): the images' power-of-two scale
+  float zr;   // PC: power of two nearest the typical r_i (z = R^-1 r is about r / zr)
   double* Tacc;     // [3][N N + 4 N] step totals accumulated by atomic adds (atomic_reduce)
   int atomic_reduce;   // N <= 64: a step's sums are added into Tacc (one barrier per step)
   double tol, inner_tol, itol_floor;
@@ -921,6 +938,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
   // atomic_reduce: CG steps so far (the same in every CTA) pick the step's accumulator; all
   // three start at zero (ordered before their first use by the first grid barrier)
   const bool atomic = NT <= 64 && p.atomic_reduce;
+  const float img_si = image_scale_inv(p.hamax);   // undoes the images' scale (exact)
   int gstep = 0;
   if (atomic) {
     const int chunk = (3 * NE + G - 1) / G;
@@ -977,7 +995,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     reduce_slice(p.Tpart, G, NE, p.Tred, scratch, b, N * N);
     if (!(ok = bar.sync())) break;
     int tbuf = 0;   // the global copy of T_k the next staging reads
-    stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, p.Tk, p.Tk, b == 0, sTk, s_beta_v, false, s_active, s_sig,
+    stage_Tt16_rec<T16, NT, TERMS>(p.Tred, N, inv_nm1, img_si, p.Tk, p.Tk, b == 0, sTk, s_beta_v, false, s_active, s_sig,
                                    s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
     if (t < NT) {
       const double sg = t < N ? __ldcg(p.Tred + N * N + t) : 0.0;       // sum r_i z_0^2
@@ -1016,7 +1034,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
         s_active[t] = a;
         s_alpha[t] = al;
         s_alpha_v[t] = (float)al;
-        s_zs[t] = (t < N && gm > 0.0) ? (float)(1.0 / sqrt(gm)) : 1.f;
+        // the Gram's z operand scaled to unit norm: z = r (or R^-1 r, about r / zr) over ||r||,
+        // whatever the units of the problem
+        s_zs[t] = (t < N && gm > 0.0) ? (float)(1.0 / sqrt(gm)) * (PC ? p.zr : 1.f) : 1.f;
         my_active = a;
       }
       const int any = __syncthreads_or(my_active);
@@ -1029,10 +1049,10 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       if constexpr (NT <= 64)
         passF_tc_db<T16, NT, PC, TERMS>(img, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
                                         s_beta_v, uni, tmem, &mbar[2], &mbar[1], ph_u2, ph_g, p.status, ok, acc,
-                                        atomic);
+                                        atomic, img_si);
       else
         passF_tc2<T16, NT, PC, TERMS>(img, p.qmax, row0, row1, N, p.X, p.Res, p.P, p.r32, s_alpha_v,
-                                      s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp);
+                                      s_beta_v, uni, tmem, &mbar[0], &mbar[1], ph_u, ph_g, p.status, ok, Tp, img_si);
       tick(PH_PASS);
       if (!(ok = bar.sync() && ok)) break;
       tick(PH_BAR1);
@@ -1053,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
       // beta, T_{k+1} = HA^T z_{k+1} + beta T_k (from the global copy of T_k), the scalars
       const float* Tprev = p.Tk + (size_t)tbuf * N * N;
       float* Tnext = p.Tk + (size_t)(tbuf ^ 1) * N * N;
-      stage_Tt16_rec<T16, NT, TERMS>(tsum, N, inv_nm1, Tprev, Tnext, b == 0, sTk, s_beta_v, true, s_active,
+      stage_Tt16_rec<T16, NT, TERMS>(tsum, N, inv_nm1, img_si, Tprev, Tnext, b == 0, sTk, s_beta_v, true, s_active,
                                      s_sig, s_den, s_gam, s_iters, sBu, s_ts, s_tn2, scratch);
       tbuf ^= 1;
       ++it;

@@ -138,3 +138,26 @@ def test_full_size_grf1024_N128_m262144(lib, grf1024, prec, bar, elem_bar):
     _check_close(Xa, ref, bar, elem_bar)
     assert st["true_relres_max"] <= 1e-8, st
     an.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("scale", [1e6, 1e-6])
+@pytest.mark.parametrize("N,m,G", [(64, 1024, None), (64, 12000, 12)])
+def test_split_mixed_in_any_units(lib, prec, scale, N, m, G):
+    """The same problem in other units (X_f and y times s, R times s^2; the analysis scales
+    by s): |HA| near 1e6 would overflow FP16 and near 1e-6 would fall into its subnormal
+    range, so the tile images are scaled by a power of two chosen from the largest |HA|, and
+    the Gram's z operand (R^-1 r, which scales as 1/s) by the power of two nearest the typical
+    r_i. FP32 runs on the CUDA cores and needs neither."""
+    side = max(64, int(np.ceil(np.sqrt(2 * m))))
+    p = synth.grf_problem(side, 6.0, N, m, 0.25, 1.0, seed=29 * m + N, dtype=np.float32)
+    p.Xf = (p.Xf.astype(np.float64) * scale).astype(np.float32)
+    p.y = p.y * scale
+    p.r = p.r * scale * scale
+    extra = {} if G is None else {"grid_blocks": G}
+    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=1, reduce_order=1, **extra)
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert st["status"] == "ok", st
+    _check_close(Xa, ref, 1e-4)
+    assert 0 < st["true_relres_max"] <= 1e-8, st
