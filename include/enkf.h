@@ -100,8 +100,11 @@ typedef struct enkf_config {
   double tol;             /* stop column j when ||r_j||_2 <= tol * ||d_j||_2             */
   int32_t fixed_iters;    /* > 0: run exactly this many CG steps (the paper's Tables 4-5
                              mode); tol is then ignored                                  */
-  int32_t max_refine;     /* FP32 and tensor-core modes: maximum double-float residual
-                             refreshes (default 4)                                       */
+  int32_t max_refine;     /* ENKF_FP32: maximum double-float residual refreshes (default
+                             4). The tensor-core modes refresh until every column has
+                             converged, stalled (no halving over a cycle) or turned
+                             non-finite; each refresh follows at least one CG step, so
+                             max_iter bounds them                                         */
   double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
   int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between double-float residual
                              refreshes; 0 (default): each inner solve runs until its

@@ -451,8 +451,13 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
     par ^= 1;
     ++refinements;
     if (t < N) {
-      const double tr = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+      // a non-finite residual or ||d_j|| (NaN or Inf in the inputs) ends the column with the
+      // non-finite status
+      const bool fin = isfinite(s_dn2[t]) && isfinite(s_tmp[t]);
+      if (!fin) atomicOr(p.status, DS_NONFINITE);
+      const double tr = !fin ? (double)NAN : (s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0);
       s_true[t] = tr;
+      if (!fin) s_done[t] = 1;
       if (refine) {
         if (tr <= p.tol) s_done[t] = 1;
         // next inner solve only has to gain the remaining factor tol/tr (with margin 0.1)

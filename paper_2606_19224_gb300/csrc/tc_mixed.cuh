@@ -1116,12 +1116,16 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     reduce_all<NT>(p.rrpart + (int64_t)par * G * NT, G, N, s_tmp, scratch);
     par ^= 1;
     if (t < N) {
-      const double rel = s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0;
+      // a non-finite residual or ||d_j|| (NaN or Inf in the inputs) ends the column with the
+      // non-finite status
+      const bool fin = isfinite(s_dn2[t]) && isfinite(s_tmp[t]);
+      if (!fin) atomicOr(p.status, DS_NONFINITE);
+      const double rel = !fin ? (double)NAN : (s_dn2[t] > 0.0 ? sqrt(s_tmp[t] / s_dn2[t]) : 0.0);
       s_rel[t] = rel;
       s_true[t] = rel;
       if (!s_done[t]) {
-        // converged, or stalled (no halving over a cycle)
-        if (rel <= p.tol || (cycles >= 2 && rel > 0.5 * s_prev[t])) s_done[t] = 1;
+        // converged, stalled (no halving over a cycle) or non-finite
+        if (!fin || rel <= p.tol || (cycles >= 2 && rel > 0.5 * s_prev[t])) s_done[t] = 1;
       }
       s_prev[t] = rel;
       // the next inner solve only has to gain the remaining factor tol/rel (margin 0.1),
@@ -1132,7 +1136,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     }
     const int all_done = __syncthreads_and(t >= N || s_done[t]);
     tick(PH_REFRESH);
-    if (all_done || total >= p.max_iter) break;
+    // every cycle either takes a step (total grows to at most max_iter) or ends the solve:
+    // without an active column (it == 0) the next cycle would repeat this one
+    if (all_done || total >= p.max_iter || it == 0) break;
   }
 
   if (prof)

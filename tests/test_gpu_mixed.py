@@ -161,3 +161,29 @@ def test_split_mixed_in_any_units(lib, prec, scale, N, m, G):
     assert st["status"] == "ok", st
     _check_close(Xa, ref, 1e-4)
     assert 0 < st["true_relres_max"] <= 1e-8, st
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_nonfinite_input_ends_with_the_nonfinite_status(lib, prec):
+    """A NaN in one member's state makes the ensemble mean of that element, and so a row of
+    HA in every column, NaN: the refinement ends every column at its first residual refresh
+    with the non-finite status (no step can make progress, so the solve stops there)."""
+    q = synth.workload("grf512_N64_m65536", 15, scale=8, dtype=np.float32)
+    q.Xf[q.col[3], 4] = np.nan
+    an, Xa, st = _run(lib, q, prec, tol=1e-8, precondition=1)
+    assert st["status"] == "nonfinite", st
+    assert st["iters_max"] < 1000, st
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_identical_members(lib, prec):
+    """No ensemble spread: HA = 0 and A = 0, so S = R and X_a = X_f (the images' scale is 1
+    when the largest |HA| is zero)."""
+    p = synth.grf_problem(64, 6.0, 16, 1024, 0.25, 1.0, seed=3, dtype=np.float32)
+    p.Xf = np.repeat(p.Xf[:, :1], p.N, axis=1).copy()
+    an, Xa, st = _run(lib, p, prec, tol=1e-8, precondition=1)
+    assert st["status"] == "ok", st
+    E = oracle.obs_perturbations(7, 3, p.r, p.N)
+    ref = oracle.enkf_exact(p.Xf.astype(np.float64), p.rowptr, p.col, p.w, p.r, p.y, E)
+    assert np.allclose(ref, p.Xf.astype(np.float64), rtol=0, atol=1e-12 * np.abs(ref).max())
+    _check_close(Xa, ref, 1e-6)
