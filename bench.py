@@ -129,12 +129,12 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
             "cg_iterations": iters, "refreshes": refreshes, "hbm_frac": t_b / t}
 
 # DRAM bytes (read + write) of one solve launch on this workload per precision, from the ncu
-# captures summarised under profiles/ (FP32: launches_fp32_grf512_N64_m65536.md, fixed-order
-# step sums; FP16: launches_fp16_grf512_N64_m65536.md, atomic step sums), with
+# captures summarised under profiles/ (FP32: solve_kernel_fp32_hs_grf512_N64_m65536.md; FP16:
+# solve_mixed_kernel_fp16_grf512_N64_m65536.md; both with atomic step sums, the default), with
 # the hash of the kernel sources each capture measured; reported as null once those sources
 # have changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 1.442546e9, "src_sha": "998371542af81f75"},
-               "fp16": {"bytes": 0.890024e9, "src_sha": "4e1c6173400e9783"}}
+NCU_TRAFFIC = {"fp32": {"bytes": 1.013768e9, "src_sha": "410d54652e382c04"},
+               "fp16": {"bytes": 0.935388e9, "src_sha": "5de9af6c3f41f90a"}}
 # DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
 # profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
 NCU_TRAFFIC_BATCH = {"bytes": 1.436453e12, "problems": 256, "seed": 1, "src_sha": "869cf69968486ece"}
