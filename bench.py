@@ -146,6 +146,15 @@ _KERNEL_SOURCES = {
 }
 
 
+def _recorded_traffic(precision, precondition, reduce_order):
+    """The captured DRAM bytes of one solve launch on the 512^2 workload, if the capture's
+    configuration (CG preconditioned by R, atomic step sums) and kernel sources are these."""
+    tr = NCU_TRAFFIC.get(precision)
+    if tr is None or precondition != 1 or reduce_order != 1 or tr["src_sha"] != _src_hash(precision):
+        return None
+    return tr["bytes"]
+
+
 def _src_hash(precision="fp32"):
     h = hashlib.sha256()
     for f in _KERNEL_SOURCES[precision]:
@@ -449,7 +458,7 @@ KERNEL_NAME = {"fp64": "solve_kernel<double>", "fp32": "solve_kernel<float>",
                "fp16": "solve_mixed_kernel<half>", "bf16": "solve_mixed_kernel<bf16>"}
 
 
-def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref, reduce_order=0):
+def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref, reduce_order=0, traffic=None):
     """One precision / solver variant on problem p: timing, iterations, accuracy and the
     roofline of its solve launch."""
     import torch
@@ -466,7 +475,7 @@ def _variant(enkf, p, prec, pc, timer, Xd, y, seed, steps, warmup, ref, reduce_o
     res["solver"] = "CG preconditioned by R" if pc else "plain CG"
     res["reduce_order"] = REDUCE_NAME[reduce_order]
     res["roofline"] = analysis_roofline(p.m, p.N, prec, res["iters"], res["refinements"] if prec != "fp64" else 1,
-                                        res["solve_ms"], KERNEL_NAME[prec])
+                                        res["solve_ms"], KERNEL_NAME[prec], traffic)
     an.close()
     return res
 
@@ -557,8 +566,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (the persistent CG solve), live CUDA-event time
     it_avg, ref_avg = float(np.mean(iters)), float(np.mean(refines))
     solve_avg_ms = float(np.mean(solve_ms))
-    tr = NCU_TRAFFIC.get(args.precision, {})
-    traffic = tr.get("bytes") if tr.get("src_sha") == _src_hash(args.precision) else None
+    traffic = _recorded_traffic(args.precision, args.precondition, args.reduce_order)
     roofline = analysis_roofline(m, N, args.precision, it_avg, ref_avg, solve_avg_ms,
                                  KERNEL_NAME[args.precision] + ("<64, preconditioned>" if args.precondition else "<64>"),
                                  traffic)
@@ -615,7 +623,8 @@ def run_ours(args):
     for prec in ("fp32", "fp16", "bf16"):
         if prec != args.precision:
             c1[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, max(3, args.steps // 4), 2, ref,
-                                         reduce_order=args.reduce_order)
+                                         reduce_order=args.reduce_order,
+                                         traffic=_recorded_traffic(prec, 1, args.reduce_order))
     base = c1["fp64_plain_cg"]["ms_per_step"]
     for k, v in c1.items():
         v["speedup_vs_fp64_plain_cg"] = base / v["ms_per_step"]
