@@ -105,7 +105,9 @@ typedef struct enkf_config {
                              converged, stalled (no halving over a cycle) or turned
                              non-finite; each refresh follows at least one CG step, so
                              max_iter bounds them                                         */
-  double inner_tol;       /* ENKF_FP32: relative tolerance of each FP32 inner solve      */
+  double inner_tol;       /* FP32, BF16 and FP16 modes: relative tolerance of each inner
+                             solve (default 1e-5); the tensor-core modes raise it to the
+                             floor their operator allows (see refresh_every)              */
   int32_t refresh_every;  /* BF16/FP16 modes: cap on CG steps between double-float residual
                              refreshes; 0 (default): each inner solve runs until its
                              residual fell by inner_tol, but not below what the operator
