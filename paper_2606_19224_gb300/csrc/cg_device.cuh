@@ -3,6 +3,8 @@
 // contraction passes of the matvec (Eq. matvec_decomp) and the fused CG step.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace enkf {
@@ -437,6 +439,32 @@ __device__ __forceinline__ void passB(const CT* __restrict__ HA, int64_t row0, i
     }
     __syncthreads();
     CT acc[4][4];
+    if constexpr (std::is_same<CT, df32>::value) {
+      // double-float: the products enter unnormalised (sum, error) pairs, renormalised every
+      // 4 terms (DFAcc), as in refreshB_async
+      DFAcc dacc[4][4];
+#pragma unroll 4
+      for (int k = 0; k < N; ++k) {
+        df32 a[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) a[x] = sH[(r0 + x) * LD + k];
+        load_vec<df32>(bv, sT + k * LD + j0, 4);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) dacc[x][y].add(a[x], bv[y]);
+        if ((k & 3) == 3) {
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) dacc[x][y].renorm();
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = dacc[x][y].value();
+    } else {
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -465,6 +493,7 @@ __device__ __forceinline__ void passB(const CT* __restrict__ HA, int64_t row0, i
 #pragma unroll
           for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bv[y], acc[x][y]);
       }
+    }
     }
 #pragma unroll
     for (int x = 0; x < 4; ++x) {

@@ -406,8 +406,8 @@ __device__ void solve_body(const SolveParams& p, const int G, const int b, GridB
       ProRefresh<VT> pro{p.Z, X, N, refine};
       passA<double, NT>(p.HA64, row0, row1, N, p.r, false, pro, uni, Tp);
     } else {
-      if (DFTile<NT>::B_ASYNC && (N & 3) == 0) {
-        refreshA_async<(NT <= 64 ? NT : 64)>(p.HAdf, p.Zdf, reinterpret_cast<const float*>(X), row0, row1, N, uni, Tp);
+      if ((N & 3) == 0) {
+        refreshA_async<NT>(p.HAdf, p.Zdf, reinterpret_cast<const float*>(X), row0, row1, N, uni, Tp);
       } else {
         ProRefreshDF<VT> pro{p.Zdf, X, N, true};
         passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);

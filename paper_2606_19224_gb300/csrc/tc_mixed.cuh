@@ -1083,8 +1083,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_mixed_kernel(MixedParams p)
     total += it;
     ++cycles;
     // ---- double-float refresh: Z += X; T = HA^T Z; W; true residual D - S Z -> next B
-    if (DFTile<NT>::B_ASYNC && (N & 3) == 0) {
-      refreshA_async<(NT <= 64 ? NT : 64)>(p.HAdf, p.Zdf, p.X, row0, row1, N, uni, Tp);
+    if ((N & 3) == 0) {
+      refreshA_async<NT>(p.HAdf, p.Zdf, p.X, row0, row1, N, uni, Tp);
     } else {
       ProRefreshDF<float> pro{p.Zdf, p.X, N, true};
       passA<df32, NT>(p.HAdf, row0, row1, N, static_cast<const df32*>(nullptr), false, pro, uni, Tp);
