@@ -54,3 +54,15 @@ def test_single_rank_helpers():
     assert bench._rank_seed(3, 0) == 3
     assert bench._max_over_ranks(4.25, None, 1) == 4.25
     assert bench._job_rate(256, 0.5, 1) == 512.0
+
+
+def test_recorded_traffic_only_for_the_captured_configuration():
+    """The DRAM bytes of a capture are reported only for the configuration it measured (CG
+    preconditioned by R, atomic step sums) and while the kernel sources keep its hash."""
+    for prec, rec in bench.NCU_TRAFFIC.items():
+        got = bench._recorded_traffic(prec, 1, 1)
+        assert got == (rec["bytes"] if rec["src_sha"] == bench._src_hash(prec) else None)
+        assert bench._recorded_traffic(prec, 0, 1) is None
+        assert bench._recorded_traffic(prec, 1, 0) is None
+    assert bench._recorded_traffic("fp64", 1, 1) is None
+    assert bench._recorded_traffic("bf16", 1, 1) is None
