@@ -133,8 +133,8 @@ def analysis_roofline(m, N, prec, iters, refreshes, solve_ms, kernel, traffic=No
 # solve_mixed_kernel_fp16_grf512_N64_m65536.md; both with atomic step sums, the default), with
 # the hash of the kernel sources each capture measured; reported as null once those sources
 # have changed.
-NCU_TRAFFIC = {"fp32": {"bytes": 0.765940e9, "src_sha": "0e40699082285af6"},
-               "fp16": {"bytes": 0.800592e9, "src_sha": "c4ca9790047bdbd8"}}
+NCU_TRAFFIC = {"fp32": {"bytes": 0.765940e9, "src_sha": "e360a9e69a4aec5f"},
+               "fp16": {"bytes": 0.800592e9, "src_sha": "ceff5266981415e8"}}
 # DRAM bytes of one batch_kernel launch on the 256-problem batch (seed 1), recorded in
 # profiles/batch_kernel_batched256_grf_dram.md for the sources with this hash.
 NCU_TRAFFIC_BATCH = {"bytes": 1.436453e12, "problems": 256, "seed": 1, "src_sha": "869cf69968486ece"}

@@ -1203,9 +1203,10 @@ __device__ __forceinline__ void passH(const float* __restrict__ HA, int64_t row0
 }
 
 // ------------------------------------------------------------------ double-float refresh, pipelined
-// The two passes of the double-float refresh (FP32 mode, N % 4 == 0) with the row tiles
-// double-buffered through cp.async, as in passF_async. Same arithmetic and partial sums as
-// passA / passB with ProRefreshDF / EpiRefreshDF.
+// The two passes of the double-float refresh (N % 4 == 0) with the row tiles double-buffered
+// through cp.async, as in passF_async: pass A at every NT, pass B for NT <= 64 (at NT = 128
+// its staged T and two tiles do not fit, and passB runs synchronously with the same
+// compensated pairs). Same partial sums as passA / passB with ProRefreshDF / EpiRefreshDF.
 template <int NT> struct DFTile {
   static constexpr int MA = Tile<NT>::MA, NG = NT / MA, TPG = NG * NG, RG = kThreads / TPG;
   static constexpr int TRA = NT == 128 ? 16 : 32;                  // pass A rows per tile
@@ -1213,7 +1214,7 @@ template <int NT> struct DFTile {
   static constexpr int NJ = NT / 4, NI = kThreads / NJ, MR = 2, TRB = NI * MR;   // pass B
   static constexpr int LDT = NT + 2;                                // df32 row stride of T
   static constexpr int BUFB = TRB * NT * 24;                        // HA, Z, D (8 B each)
-  static constexpr bool B_ASYNC = NT <= 64;                         // NT = 128 keeps passA/passB
+  static constexpr bool B_ASYNC = NT <= 64;                         // NT = 128: synchronous passB
   static constexpr int RED = RG > 1 ? RG * NT * NT * 8 : 0;        // cross-group reduction
   static constexpr int bytes_a = 2 * BUFA > RED ? 2 * BUFA : RED;
   static constexpr int bytes_b = NT * LDT * 8 + 2 * BUFB;
