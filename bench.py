@@ -452,6 +452,10 @@ def _err(out, ref):
 
 
 # how each step's sums over the CTAs are formed (enkf_config.reduce_order)
+DTYPE = {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}
+PRECISION_NAME = {"fp32": "fp32 CG + double-float residual refresh",
+                  "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
+                  "bf16": "BF16 hi/lo tensor-core contractions (tcgen05) + double-float refresh"}
 REDUCE_NAME = {0: "fixed order (bitwise repeatable)",
                1: "atomic adds (N <= 64; last bits vary from run to run)"}
 KERNEL_NAME = {"fp64": "solve_kernel<double>", "fp32": "solve_kernel<float>",
@@ -575,13 +579,11 @@ def run_ours(args):
         "note": "HA read once per step, x, r, p read and written (28 m N + 4 m) and a double-float refresh "
                 "of 56 m N bytes: what the fused implementation moves at minimum"}
 
-    prec_name = {"fp32": "fp32 CG + double-float residual refresh",
-                 "fp16": "FP16 hi/lo tensor-core contractions (tcgen05) + double-float refresh",
-                 "bf16": "BF16 hi/lo tensor-core contractions (tcgen05) + double-float refresh"}[args.precision]
+    prec_name = PRECISION_NAME[args.precision]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
+            "dtype": DTYPE[args.precision],
             "data": "synthetic (seeded 512x512 GRF ensemble, random point observations)",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "N": N, "tol": 1e-8, "precision": prec_name,
                        "solver": "CG preconditioned by R" if args.precondition else "plain CG",
@@ -758,9 +760,15 @@ def section_c2(args, enkf, dev, timer):
     y = torch.from_numpy(p.y).to(dev)
     res = {"workload": MIXED_WORKLOAD, "n": p.n, "m": p.m, "N": p.N}
     steps = max(3, min(args.steps, 6))
+    X64 = Xf.double()
+    if getattr(args, "headline_only", False) and getattr(args, "workload", None) == MIXED_WORKLOAD:
+        # the workload alone in one precision (a short run for profiling that one solve)
+        prec = args.precision
+        res[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, X64 if prec == "fp64" else Xf, y, seed, steps, 2,
+                                      ref)
+        return res
     for prec in ("bf16", "fp16", "fp32"):
         res[prec + "_pcg"] = _variant(enkf, p, prec, 1, timer, Xf, y, seed, steps, 2, ref)
-    X64 = Xf.double()
     res["fp64_pcg"] = _variant(enkf, p, "fp64", 1, timer, X64, y, seed, 2, 1, ref)
     res["fp64_plain_cg"] = _variant(enkf, p, "fp64", 0, timer, X64, y, seed, 1, 1, ref)
     base = res["fp64_plain_cg"]["ms_per_step"]
@@ -1078,7 +1086,8 @@ def run_batched(args):
 
 def run_mixed(args):
     """The mixed-precision workload alone (see section_c2): `value` is the BF16 tensor-core
-    path."""
+    path; with --headline-only, only the --precision solve is run and reported (a short run,
+    e.g. for profiling that one solve)."""
     import torch
     ws, rank, local = _dist()
     if ws > 1:
@@ -1093,17 +1102,17 @@ def run_mixed(args):
     clocks.start()
     res = section_c2(args, enkf, dev, timer)
     clk = clocks.stop()
-    ms = _max_over_ranks(res["bf16_pcg"]["ms_per_step"], dev, ws)
+    key = args.precision + "_pcg" if args.headline_only else "bf16_pcg"
+    ms = _max_over_ranks(res[key]["ms_per_step"], dev, ws)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": _job_rate(1, ms / 1e3, ws), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16",
+            "vs_baseline": None, "dtype": DTYPE[key[:4]],
             "data": "synthetic (seeded 1024x1024 GRF ensemble, random point observations)",
             "config": {"workload": MIXED_WORKLOAD, "n": res["n"], "m": res["m"], "N": res["N"], "tol": 1e-8,
-                       "precision": "BF16 hi/lo split operands on tcgen05, FP32 accumulation, double-float refresh",
-                       "l2": "flushed between steps"},
-            "roofline": res["bf16_pcg"]["roofline"], "variants": res, "gpu_launches": 4 * args.steps,
+                       "precision": PRECISION_NAME[key[:4]], "l2": "flushed between steps"},
+            "roofline": res[key]["roofline"], "variants": res, "gpu_launches": 4 * args.steps,
             "clocks": clk}
     print(json.dumps(line), flush=True)
 
