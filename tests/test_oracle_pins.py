@@ -210,6 +210,42 @@ def test_analysis_mean_unaffected_by_member_order():
     assert np.max(np.abs(a[:, perm] - b)) < 1e-12
 
 
+def _analyses():
+    """Every exact or converged analysis form of the oracle, as functions of
+    (Xf, rowptr, col, w, r, y, E)."""
+    return {
+        "alg1": oracle.enkf_alg1,
+        "alg2": oracle.enkf_alg2,
+        "cgd": lambda *a: oracle.cgd_enkf(*a, tol=1e-14, max_iter=500)[0],
+        "reduced": lambda *a: oracle.cgd_enkf_reduced(*a, tol=1e-14, max_iter=500)[0],
+    }
+
+
+@pytest.mark.parametrize("s", [1e-6, 1e6])
+def test_analysis_scales_with_the_units_of_state_and_observations(s):
+    """The same problem in other units (X_f, y and E times s, R times s^2) has S, D and the
+    anomalies scaled by s^2, s and s, so the analysis scales by s. Using sqrt(r) for r, or
+    an unscaled perturbation, would break it."""
+    Xf, rowptr, col, w, r, y, E = _tiny_problem(40, 8, 20, 11)
+    for name, fn in _analyses().items():
+        a = fn(Xf, rowptr, col, w, r, y, E)
+        b = fn(s * Xf, rowptr, col, w, s * s * r, s * y, s * E)
+        assert oracle.rel_frobenius(b / s, a) < 1e-10, name
+
+
+def test_analysis_follows_a_shift_of_the_state():
+    """Adding one state c to every member and H c to y leaves the anomalies and the
+    innovations as they were, so every member's analysis moves by c. Forming the gain from
+    the uncentred observed ensemble instead of HA would break it."""
+    Xf, rowptr, col, w, r, y, E = _tiny_problem(40, 8, 20, 12)
+    c = 3.0 + np.random.default_rng(5).standard_normal(40)
+    Hc = oracle.apply_H(rowptr, col, w, c[:, None])[:, 0]
+    for name, fn in _analyses().items():
+        a = fn(Xf, rowptr, col, w, r, y, E)
+        b = fn(Xf + c[:, None], rowptr, col, w, r, y + Hc, E)
+        assert np.max(np.abs(b - (a + c[:, None]))) < 1e-9 * np.max(np.abs(b)), name
+
+
 # ---------------------------------------------------------------- CG pins
 def _krylov_galerkin_iterate(S, d, k):
     """The k-th CG iterate from 0 is the Galerkin solution on the Krylov space
